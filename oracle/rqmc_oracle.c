@@ -1,0 +1,466 @@
+/*
+ * CPU FP64 ORACLE for randomized rank-1 lattice QMC over sector-decomposed,
+ * eps-expanded Feynman-parameter integrands.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library. It shares no code with
+ * the CUDA path: it is a plain, slow, literal restatement of the method.
+ *
+ * What it computes (citations are to arXiv:2305.19768):
+ *  - the randomly shifted rank-1 lattice rule of the Disteval integrator
+ *    (Section "The new Quasi-Monte-Carlo evaluator Disteval"; median rules,
+ *    Eq. (median) and the set U_n): points x_k = frac(k z / n + Delta),
+ *    k = 0..n-1, one estimate Q_s = (1/n) sum_k f(x_k) per random shift s;
+ *  - the korobov3 periodizing transform named in the timings section;
+ *  - contour deformation z = t - i lambda t (1 - t) dF/dt with its Jacobian
+ *    determinant (the paper only names the presampling that tunes lambda);
+ *  - the eps-expanded sector integrand with plus-distribution subtraction of
+ *    the logarithmic endpoint singularities t_j^{-1 + b_j eps}.
+ * The paper is silent on the lattice-point rounding, the transform formula,
+ * the deformation formula and the subtraction; the readings used here are:
+ *  x = (double)r / (double)n + Delta; if (x >= 1) x -= 1, with r = k z mod n
+ *  exact in 64-bit integers; t = u^4 (35 - 84 u + 70 u^2 - 20 u^3),
+ *  1 - t = phi(1 - u), weight 140 u^3 (1 - u)^3; a point whose weight is 0 or
+ *  whose transformed coordinate underflows to 0 contributes 0.
+ *
+ * Parity pins (checked by the CPU test suite, not by this file): closed forms
+ * of the one-loop massive triangle, massless box and massive bubble,
+ * lattice-sum invariants, Korobov moments, 1-D and 2-D subtraction integrals
+ * with polynomial G, and tensor-product Gauss-Legendre quadrature.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_DMAX 8
+#define ORC_LMAX 16      /* series coefficients kept */
+#define ORC_SMAX 6       /* singular variables per sector */
+
+typedef double complex cplx;
+
+typedef struct {
+    int d;
+    int a[ORC_DMAX];
+    double b[ORC_DMAX];
+    double u0, u1, f0, f1;
+    int nU, nF;
+    const int *Ue;       /* [nU][d] exponents */
+    const double *Uc;    /* [nU] coefficient values at the kinematic point */
+    const int *Fe;       /* [nF][d] */
+    const double *Fc;    /* [nF] */
+    int deform;
+    double lambda[ORC_DMAX];
+} orc_sector;
+
+/* ---------------- splitmix64 (Steele, Lea & Flood 2014) ---------------- */
+static uint64_t sm64(uint64_t *state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Random shifts Delta[s][j] in [0,1): 53-bit uniforms, state seeded with
+ * seed ^ (golden gamma * (sector id + 1)), drawn shift-major. */
+void orc_shifts(uint64_t seed, uint64_t sector_id, int m, int d, double *out) {
+    uint64_t st = seed ^ (0x9E3779B97F4A7C15ULL * (sector_id + 1));
+    for (int s = 0; s < m; ++s)
+        for (int j = 0; j < d; ++j)
+            out[s * d + j] = (double)(sm64(&st) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ---------------- lattice ---------------- */
+/* r_j = (k z_j) mod n by 128-bit product, then x = r/n + Delta folded to [0,1). */
+void orc_lattice_points(uint64_t n, const uint32_t *z, int d, const double *delta,
+                        uint64_t k0, uint64_t count, double *x_out, uint64_t *r_out) {
+    for (uint64_t i = 0; i < count; ++i) {
+        uint64_t k = k0 + i;
+        for (int j = 0; j < d; ++j) {
+            uint64_t r = (uint64_t)(((unsigned __int128)k * z[j]) % n);
+            double x = (double)r / (double)n;
+            x = x + delta[j];
+            if (x >= 1.0) x -= 1.0;
+            if (x_out) x_out[i * d + j] = x;
+            if (r_out) r_out[i * d + j] = r;
+        }
+    }
+}
+
+/* ---------------- korobov3 ---------------- */
+static double korobov_phi(double u) {
+    return u * u * u * u * (35.0 - 84.0 * u + 70.0 * u * u - 20.0 * u * u * u);
+}
+static double korobov_w(double u) {
+    double v = 1.0 - u;
+    return 140.0 * u * u * u * v * v * v;
+}
+void orc_korobov3(double u, double *t, double *omt, double *w) {
+    *t = korobov_phi(u);
+    *omt = korobov_phi(1.0 - u);
+    *w = korobov_w(u);
+}
+
+/* ---------------- truncated Laurent series in eps ---------------- */
+typedef struct {
+    int lo;               /* order of c[0] */
+    int n;                /* number of coefficients */
+    cplx c[ORC_LMAX];
+} series;
+
+static series s_const(cplx v) {
+    series s;
+    memset(&s, 0, sizeof s);
+    s.lo = 0; s.n = 1; s.c[0] = v;
+    return s;
+}
+/* exp(eps * L) up to eps^hi */
+static series s_exp_eps(cplx L, int hi) {
+    series s;
+    memset(&s, 0, sizeof s);
+    s.lo = 0; s.n = hi + 1;
+    cplx term = 1.0;
+    for (int k = 0; k <= hi; ++k) {
+        s.c[k] = term;
+        term = term * L / (double)(k + 1);
+    }
+    return s;
+}
+static series s_mul(const series *a, const series *b, int hi) {
+    series r;
+    memset(&r, 0, sizeof r);
+    r.lo = a->lo + b->lo;
+    r.n = hi - r.lo + 1;
+    if (r.n < 0) r.n = 0;
+    if (r.n > ORC_LMAX) abort();
+    for (int i = 0; i < a->n; ++i)
+        for (int j = 0; j < b->n; ++j) {
+            int k = i + j;
+            if (k < r.n) r.c[k] += a->c[i] * b->c[j];
+        }
+    return r;
+}
+static series s_scale(const series *a, cplx v) {
+    series r = *a;
+    for (int i = 0; i < r.n; ++i) r.c[i] *= v;
+    return r;
+}
+/* a + b (any lo), keep up to eps^hi */
+static series s_add(const series *a, const series *b, int hi) {
+    series r;
+    memset(&r, 0, sizeof r);
+    r.lo = a->lo < b->lo ? a->lo : b->lo;
+    r.n = hi - r.lo + 1;
+    if (r.n > ORC_LMAX) abort();
+    for (int i = 0; i < a->n; ++i) {
+        int k = a->lo + i - r.lo;
+        if (k < r.n) r.c[k] += a->c[i];
+    }
+    for (int i = 0; i < b->n; ++i) {
+        int k = b->lo + i - r.lo;
+        if (k < r.n) r.c[k] += b->c[i];
+    }
+    return r;
+}
+static cplx s_coef(const series *a, int order) {
+    int k = order - a->lo;
+    if (k < 0 || k >= a->n) return 0.0;
+    return a->c[k];
+}
+
+/* ---------------- polynomials ---------------- */
+static cplx cipow(cplx x, int e) {
+    cplx r = 1.0;
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+/* Mixed partial derivative d^|D| P / prod dt_j^{D_j} at complex/real point x,
+ * from the monomial table: each monomial c prod x^e contributes
+ * c prod_j e_j (e_j - 1) ... (e_j - D_j + 1) x_j^(e_j - D_j). */
+static cplx poly_deriv(int nterms, int d, const int *ex, const double *co, const cplx *x,
+                       const int *D) {
+    cplx sum = 0.0;
+    for (int m = 0; m < nterms; ++m) {
+        cplx term = co[m];
+        for (int j = 0; j < d; ++j) {
+            int e = ex[m * d + j];
+            int dj = D ? D[j] : 0;
+            if (e < dj) { term = 0.0; break; }
+            for (int q = 0; q < dj; ++q) term *= (double)(e - q);
+            term *= cipow(x[j], e - dj);
+        }
+        sum += term;
+    }
+    return sum;
+}
+
+/* ---------------- determinant (Leibniz formula) ---------------- */
+static cplx det_leibniz(int d, const cplx *A) {
+    int perm[ORC_DMAX];
+    for (int i = 0; i < d; ++i) perm[i] = i;
+    cplx det = 0.0;
+    /* iterate permutations in lexicographic order, tracking the sign by
+     * counting inversions */
+    for (;;) {
+        int inv = 0;
+        for (int i = 0; i < d; ++i)
+            for (int j = i + 1; j < d; ++j)
+                if (perm[i] > perm[j]) ++inv;
+        cplx p = (inv % 2) ? -1.0 : 1.0;
+        for (int i = 0; i < d; ++i) p *= A[i * d + perm[i]];
+        det += p;
+        int i = d - 2;
+        while (i >= 0 && perm[i] > perm[i + 1]) --i;
+        if (i < 0) break;
+        int j = d - 1;
+        while (perm[j] < perm[i]) --j;
+        int tmp = perm[i]; perm[i] = perm[j]; perm[j] = tmp;
+        for (int l = i + 1, r = d - 1; l < r; ++l, --r) {
+            tmp = perm[l]; perm[l] = perm[r]; perm[r] = tmp;
+        }
+    }
+    return det;
+}
+
+static int is_singular(const orc_sector *S, int j) { return S->a[j] == -1; }
+
+/* G(t', eps): everything in the sector integrand except prod_{j in S}
+ * t_j^{-1 + b_j eps}, at the real point tp (omtp = 1 - tp), as a series up
+ * to eps^hi. With deformation, z_j = t_j - i lambda_j t_j (1 - t_j) dF/dt_j,
+ * rho_j = z_j / t_j, J = dz/dt, and
+ *   G = prod_{j not in S} z_j^{a_j + b_j eps} prod_{j in S} rho_j^{-1 + b_j eps}
+ *       U(z)^{u0 + u1 eps} F(z)^{f0 + f1 eps} det J.
+ * Counts Im F(z) > 0 (wrong side of the F - i0 cut) in *signfail. */
+static series G_series(const orc_sector *S, const double *tp, const double *omtp, int hi,
+                       int *signfail) {
+    int d = S->d;
+    cplx t[ORC_DMAX], z[ORC_DMAX], rho[ORC_DMAX], dF[ORC_DMAX];
+    cplx J[ORC_DMAX * ORC_DMAX];
+    cplx detJ = 1.0;
+    for (int j = 0; j < d; ++j) { t[j] = tp[j]; z[j] = tp[j]; rho[j] = 1.0; }
+    if (S->deform) {
+        int D[ORC_DMAX];
+        for (int j = 0; j < d; ++j) {
+            memset(D, 0, sizeof D);
+            D[j] = 1;
+            dF[j] = poly_deriv(S->nF, d, S->Fe, S->Fc, t, D);
+        }
+        for (int j = 0; j < d; ++j) {
+            double tj = tp[j], omt = omtp[j];
+            z[j] = tj - I * S->lambda[j] * tj * omt * dF[j];
+            rho[j] = 1.0 - I * S->lambda[j] * omt * dF[j];
+            for (int l = 0; l < d; ++l) {
+                memset(D, 0, sizeof D);
+                D[j] += 1;
+                D[l] += 1;
+                cplx d2 = poly_deriv(S->nF, d, S->Fe, S->Fc, t, D);
+                cplx v = -I * S->lambda[j] * (tj * omt * d2 + (j == l ? (omt - tj) * dF[j] : 0.0));
+                J[j * d + l] = (j == l ? 1.0 : 0.0) + v;
+            }
+        }
+        detJ = det_leibniz(d, J);
+    }
+    cplx U = poly_deriv(S->nU, d, S->Ue, S->Uc, z, NULL);
+    cplx F = poly_deriv(S->nF, d, S->Fe, S->Fc, z, NULL);
+    if (cimag(F) > 0.0) ++*signfail;
+    if (cimag(F) == 0.0) F = CMPLX(creal(F), -0.0); /* F - i0 */
+    if (cimag(U) == 0.0) U = CMPLX(creal(U), 0.0);
+
+    series G = s_const(detJ);
+    for (int j = 0; j < d; ++j) {
+        cplx base;
+        double a, b;
+        if (is_singular(S, j)) { base = rho[j]; a = -1.0; b = S->b[j]; }
+        else { base = z[j]; a = S->a[j]; b = S->b[j]; }
+        if (a == 0.0 && b == 0.0) continue;
+        cplx lg = clog(base);
+        series f = s_exp_eps(b * lg, hi);
+        f = s_scale(&f, cexp(a * lg));
+        G = s_mul(&G, &f, hi);
+    }
+    {
+        cplx lg = clog(U);
+        series f = s_exp_eps(S->u1 * lg, hi);
+        f = s_scale(&f, cexp(S->u0 * lg));
+        G = s_mul(&G, &f, hi);
+    }
+    {
+        cplx lg = clog(F);
+        series f = s_exp_eps(S->f1 * lg, hi);
+        f = s_scale(&f, cexp(S->f0 * lg));
+        G = s_mul(&G, &f, hi);
+    }
+    return G;
+}
+
+/* The eps-expanded integrand at the transformed point t (omt = 1 - t):
+ *   f = sum_{V subset of S} G(t with t_V = 0)
+ *         prod_{j in V} (1/(b_j eps) - t_j^{-1+b_j eps}) prod_{j in S\V} t_j^{-1+b_j eps},
+ * which integrates over [0,1]^d to the Laurent expansion of the sector
+ * integral (each j in S: int t^{-1+b eps} g = g(0)/(b eps) + int t^{-1+b eps}(g - g(0))).
+ * Returns coefficients of eps^lo .. eps^hi in out[(o - lo)]. */
+static void integrand_series(const orc_sector *S, const double *t, const double *omt, int lo,
+                             int hi, cplx *out, int *signfail) {
+    int d = S->d;
+    int sing[ORC_SMAX], ns = 0;
+    for (int j = 0; j < d; ++j)
+        if (is_singular(S, j)) {
+            if (ns == ORC_SMAX) abort();
+            sing[ns++] = j;
+        }
+    int H = hi + ns; /* every factor truncated here is exact up to eps^hi */
+    series total;
+    memset(&total, 0, sizeof total);
+    total.lo = lo; total.n = hi - lo + 1;
+    for (int V = 0; V < (1 << ns); ++V) {
+        double tp[ORC_DMAX], omtp[ORC_DMAX];
+        for (int j = 0; j < d; ++j) { tp[j] = t[j]; omtp[j] = omt[j]; }
+        for (int q = 0; q < ns; ++q)
+            if (V & (1 << q)) { tp[sing[q]] = 0.0; omtp[sing[q]] = 1.0; }
+        series term = G_series(S, tp, omtp, H, signfail);
+        for (int q = 0; q < ns; ++q) {
+            int j = sing[q];
+            double b = S->b[j];
+            series tpow = s_exp_eps(b * log(t[j]), H);
+            tpow = s_scale(&tpow, 1.0 / t[j]);          /* t^{-1 + b eps} */
+            series fac;
+            if (V & (1 << q)) {
+                series pole;
+                memset(&pole, 0, sizeof pole);
+                pole.lo = -1; pole.n = 1; pole.c[0] = 1.0 / b;
+                series neg = s_scale(&tpow, -1.0);
+                fac = s_add(&pole, &neg, H);
+            } else {
+                fac = tpow;
+            }
+            term = s_mul(&term, &fac, H);
+        }
+        total = s_add(&total, &term, hi);
+    }
+    for (int o = lo; o <= hi; ++o) out[o - lo] = s_coef(&total, o);
+}
+
+/* Integrand times the korobov3 weight at the raw lattice point u[d].
+ * out[(o - lo) * 2 + {0,1}] = Re, Im. Returns 0 if the point contributes 0. */
+int orc_point_value(const orc_sector *S, const double *u, int lo, int norders, double *out,
+                    int *signfail) {
+    int d = S->d;
+    double t[ORC_DMAX], omt[ORC_DMAX], W = 1.0;
+    for (int o = 0; o < 2 * norders; ++o) out[o] = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double w;
+        orc_korobov3(u[j], &t[j], &omt[j], &w);
+        W *= w;
+    }
+    if (W == 0.0) return 0;
+    for (int j = 0; j < d; ++j)
+        if (t[j] == 0.0) return 0;
+    cplx vals[ORC_LMAX];
+    integrand_series(S, t, omt, lo, lo + norders - 1, vals, signfail);
+    for (int o = 0; o < norders; ++o) {
+        out[2 * o] = W * creal(vals[o]);
+        out[2 * o + 1] = W * cimag(vals[o]);
+    }
+    return 1;
+}
+
+/* Integrand (no weight) at a transformed point t in (0,1]^d: used by the
+ * quadrature cross-checks. */
+void orc_integrand_at(const orc_sector *S, const double *t, int lo, int norders, double *out,
+                      int *signfail) {
+    double omt[ORC_DMAX];
+    cplx vals[ORC_LMAX];
+    for (int j = 0; j < S->d; ++j) omt[j] = 1.0 - t[j];
+    integrand_series(S, t, omt, lo, lo + norders - 1, vals, signfail);
+    for (int o = 0; o < norders; ++o) {
+        out[2 * o] = creal(vals[o]);
+        out[2 * o + 1] = cimag(vals[o]);
+    }
+}
+
+/* ---------------- per-shift sums ---------------- */
+typedef struct { double s, c; } neum;
+static void neum_add(neum *a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+#define ORC_CHUNK 4096
+
+/* Per-shift estimates Q_s = (1/n) sum_{k=k0}^{k1-1} f(x_k + Delta_s) for each
+ * eps order, out[(s * norders + o) * 2 + {re, im}]; absout[s * norders + o] =
+ * (1/n) sum |Re f| + |Im f| (the scale for relative comparisons).
+ * The k range is cut into fixed chunks of ORC_CHUNK points, each summed
+ * left to right with Neumaier compensation, and the chunk sums are combined
+ * in index order, so the result does not depend on the thread count.
+ * Returns the number of sign-check failures. */
+long orc_shift_sums(const orc_sector *S, uint64_t n, const uint32_t *z, int m,
+                    const double *delta, uint64_t k0, uint64_t k1, int lo, int norders,
+                    double *out, double *absout, int nthreads) {
+    int d = S->d;
+    uint64_t nk = k1 > k0 ? k1 - k0 : 0;
+    uint64_t nchunks = (nk + ORC_CHUNK - 1) / ORC_CHUNK;
+    size_t per = (size_t)norders * 2;
+    double *part = (double *)calloc((size_t)m * nchunks * per * 3 + 1, sizeof(double));
+    long fails = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : fails)
+    for (long long job = 0; job < (long long)(m * nchunks); ++job) {
+        int s = (int)(job / nchunks);
+        uint64_t c = job % nchunks;
+        uint64_t ka = k0 + c * ORC_CHUNK;
+        uint64_t kb = ka + ORC_CHUNK < k1 ? ka + ORC_CHUNK : k1;
+        neum acc[ORC_LMAX * 2];
+        double aacc[ORC_LMAX];
+        memset(acc, 0, sizeof acc);
+        memset(aacc, 0, sizeof aacc);
+        int sf = 0;
+        for (uint64_t k = ka; k < kb; ++k) {
+            double u[ORC_DMAX], v[ORC_LMAX * 2];
+            orc_lattice_points(n, z, d, delta + (size_t)s * d, k, 1, u, NULL);
+            if (!orc_point_value(S, u, lo, norders, v, &sf)) continue;
+            for (int q = 0; q < 2 * norders; ++q) neum_add(&acc[q], v[q]);
+            for (int o = 0; o < norders; ++o) aacc[o] += fabs(v[2 * o]) + fabs(v[2 * o + 1]);
+        }
+        double *dst = part + ((size_t)s * nchunks + c) * per * 3;
+        for (size_t q = 0; q < per; ++q) { dst[q] = acc[q].s; dst[per + q] = acc[q].c; }
+        for (int o = 0; o < norders; ++o) dst[2 * per + o] = aacc[o];
+        fails += sf;
+    }
+    for (int s = 0; s < m; ++s) {
+        for (size_t q = 0; q < per; ++q) {
+            neum a = {0.0, 0.0};
+            for (uint64_t c = 0; c < nchunks; ++c) {
+                const double *src = part + ((size_t)s * nchunks + c) * per * 3;
+                neum_add(&a, src[q]);
+                neum_add(&a, src[per + q]);
+            }
+            out[s * per + q] = (a.s + a.c) / (double)n;
+        }
+        if (absout)
+            for (int o = 0; o < norders; ++o) {
+                double a = 0.0;
+                for (uint64_t c = 0; c < nchunks; ++c)
+                    a += part[((size_t)s * nchunks + c) * per * 3 + 2 * per + o];
+                absout[s * norders + o] = a / (double)n;
+            }
+    }
+    free(part);
+    return fails;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

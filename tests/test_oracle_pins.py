@@ -1,0 +1,304 @@
+"""Pins of the CPU oracle against what the mathematics fixes (no GPU).
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped
+term, a wrong sign or index, a transposed operand) fails it: closed forms of
+one-loop integrals (tests/golden/closed_forms.txt), exact lattice-sum
+invariants, brute-force integer lattice points, Korobov moments, exact
+eps-expansions of subtracted integrals with polynomial G, tensor-product
+Gauss-Legendre quadrature, lambda-independence of contour deformation.
+"""
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial.legendre import leggauss
+
+import oracle
+from oracle import combine
+from paper_2305_19768_gb300.inputs import workloads as w
+from paper_2305_19768_gb300.inputs.feynman import prefactor_series
+from paper_2305_19768_gb300.inputs.integral import Integral
+from paper_2305_19768_gb300.inputs.lattice import cbc_fast, next_prime
+from paper_2305_19768_gb300.inputs.polynomial import LinPoly
+from paper_2305_19768_gb300.inputs.secdec import Sector
+from golden_values import closed_form
+
+
+def rqmc_integral(I, inv, n, m, lo, norders, lam=None, seed=1):
+    """Oracle estimate of the full integral: prefactor x sum of sectors.
+    Returns (mean [norders] complex at orders lo.., variance (re+im) per order)."""
+    d = I.dmax
+    z = cbc_fast(n, d)
+    slo = -I.max_poles
+    sno = lo + norders - 1 - I.prefactor_lo - slo + 1
+    acc = np.zeros((m, sno), dtype=complex)
+    for si in range(len(I.sectors)):
+        v = oracle.SectorView(I, si, inv, lam)
+        dl = oracle.shifts(seed, si, m, I.sectors[si].d)
+        out, _, _ = oracle.shift_sums(v, n, z[:I.sectors[si].d], dl, slo, sno)
+        acc += out[..., 0] + 1j * out[..., 1]
+    res = np.array([combine.laurent_product(I.prefactor_lo, np.array(I.prefactor), slo, acc[s], lo,
+                                            norders) for s in range(m)])
+    mean, var = combine.shift_stats(res)
+    return mean, var.real + var.imag
+
+
+def assert_within(mean, var, exact, rel=1e-12, nsig=3.0):
+    for o, (mv, vv, ex) in enumerate(zip(mean, var, exact)):
+        tol = nsig * math.sqrt(vv) + rel * abs(ex) + 1e-14
+        assert abs(mv - ex) <= tol, (o, mv, ex, abs(mv - ex), tol)
+
+
+# ---------------------------------------------------------------- lattice
+@pytest.mark.parametrize("n,d", [(101, 3), (1009, 4), (65537, 2)])
+def test_lattice_points_bruteforce_and_invariants(n, d):
+    z = cbc_fast(n, d)
+    delta = oracle.shifts(7, 0, 1, d)[0]
+    x, r = oracle.lattice_points(n, z, delta, 0, n)
+    for j in range(d):
+        rj = r[:, j].astype(object)
+        assert all(int(rj[k]) == (k * z[j]) % n for k in range(0, n, max(1, n // 997)))
+        assert sum(int(v) for v in rj) == n * (n - 1) // 2
+        assert sum(int(v) ** 2 for v in rj) == (n - 1) * n * (2 * n - 1) // 6
+    assert np.all(x >= 0.0) and np.all(x < 1.0)
+    # the shifted point is frac(r/n + delta) up to one rounding
+    frac = (r.astype(np.float64) / n + delta) % 1.0
+    assert np.max(np.abs(frac - x)) < 1e-15
+
+
+def test_lattice_large_index_128bit():
+    n = 4294967291  # largest prime below 2^32: k*z overflows 64 bits
+    z = np.array([4294967290, 3000000019], dtype=np.uint32)
+    k0 = n - 5
+    _, r = oracle.lattice_points(n, z, np.zeros(2), k0, 5)
+    for i in range(5):
+        for j in range(2):
+            assert int(r[i, j]) == ((k0 + i) * int(z[j])) % n
+
+
+def test_lattice_character_sums():
+    # the unshifted rank-1 rule integrates exp(2 pi i h.x) to 1 iff h.z = 0 mod n
+    n, d = 257, 2
+    z = cbc_fast(n, d)
+    x, _ = oracle.lattice_points(n, z, np.zeros(d), 0, n)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        h = rng.integers(-300, 300, size=d)
+        val = np.exp(2j * np.pi * (x @ h)).mean()
+        expect = 1.0 if (int(h @ np.array(z)) % n) == 0 else 0.0
+        assert abs(val - expect) < 1e-12
+    h = np.array([z[1], -z[0]])  # dual lattice vector
+    assert abs(np.exp(2j * np.pi * (x @ h)).mean() - 1.0) < 1e-12
+
+
+def test_shifts_splitmix64_reference_stream():
+    # published splitmix64 outputs from state 0: e220a8397b1dcdaf, 6e789e6aa1b965f4, ...
+    # the oracle's shifts for seed s, sector c use state s ^ (gamma * (c + 1));
+    # with seed = gamma the state for sector 0 is 0.
+    g = 0x9E3779B97F4A7C15
+    dl = oracle.shifts(g, 0, 1, 3)[0]
+    expect = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    for v, e in zip(dl, expect):
+        assert v == (e >> 11) * 2.0 ** -53
+
+
+# ---------------------------------------------------------------- korobov
+def test_korobov3_moments_and_symmetry():
+    xs, ws = leggauss(40)
+    u = 0.5 * (xs + 1.0)
+    wq = 0.5 * ws
+    vals = np.array([oracle.korobov3(float(v)) for v in u])
+    t, omt, wt = vals[:, 0], vals[:, 1], vals[:, 2]
+    assert abs(np.sum(wq * wt) - 1.0) < 1e-14
+    for p in range(6):
+        assert abs(np.sum(wq * wt * t ** p) - 1.0 / (p + 1)) < 1e-13
+    assert np.max(np.abs(t + omt - 1.0)) < 5e-14  # two independently rounded polynomials
+    assert oracle.korobov3(0.0) == (0.0, 1.0, 0.0)
+    assert oracle.korobov3(1.0)[0] == 1.0
+    h = 1e-6
+    for v in (0.1, 0.37, 0.8):
+        dphi = (oracle.korobov3(v + h)[0] - oracle.korobov3(v - h)[0]) / (2 * h)
+        assert abs(dphi - oracle.korobov3(v)[2]) < 1e-8
+
+
+# ---------------------------------------------------------------- subtraction
+def _toy_integral(d, a, b, Uterms, u0=1, u1=0, Fterms=None, f0=0, f1=0):
+    U = LinPoly(d, 1, {e: (c,) for e, c in Uterms.items()})
+    F = LinPoly(d, 1, Fterms and {e: (c,) for e, c in Fterms.items()} or {tuple([0] * d): (1,)})
+    from fractions import Fraction as Fr
+    s = Sector(d, list(a), [Fr(x) for x in b], U, F, Fr(u0), Fr(u1), Fr(f0), Fr(f1))
+    return Integral("toy", 1, d + 1, 4, [], 0, [1.0], [s])
+
+
+def _series_of_inverse_linear(k, beta, lo, norders):
+    """Laurent coefficients of 1/(k + beta eps)."""
+    out = np.zeros(norders, dtype=complex)
+    for o in range(lo, lo + norders):
+        if k == 0:
+            if o == -1:
+                out[o - lo] = 1.0 / beta
+        elif o >= 0:
+            out[o - lo] = (1.0 / k) * (-beta / k) ** o
+    return out
+
+
+def test_subtraction_1d_exact_series():
+    # int_0^1 t^{-1 + b eps} G(t) dt, G = 1 + 2 t + 3 t^2: sum_k c_k / (k + b eps)
+    b = -1.5
+    I = _toy_integral(1, [-1], [b], {(0,): 1, (1,): 2, (2,): 3})
+    lo, no = -1, 4
+    exact = sum(c * _series_of_inverse_linear(k, b, lo, no) for k, c in ((0, 1), (1, 2), (2, 3)))
+    mean, var = rqmc_integral(I, [], next_prime(4000), 8, lo, no)
+    assert_within(mean, var, exact, rel=1e-11)
+
+
+def test_subtraction_2d_nonseparable_exact_series():
+    # int t1^{-1+b1 eps} t2^{-1+b2 eps} sum c_ij t1^i t2^j = sum c_ij / ((i+b1 eps)(j+b2 eps))
+    b1, b2 = -1.0, 2.0
+    coefs = {(0, 0): 2.0, (1, 0): -1.0, (0, 1): 0.5, (1, 1): 3.0, (2, 1): -2.0}
+    I = _toy_integral(2, [-1, -1], [b1, b2], coefs)
+    lo, no = -2, 4
+    exact = np.zeros(no, dtype=complex)
+    for (i, j), c in coefs.items():
+        exact += c * combine.laurent_product(
+            -1 if i == 0 else 0, _series_of_inverse_linear(i, b1, -1 if i == 0 else 0, no + 2),
+            -1 if j == 0 else 0, _series_of_inverse_linear(j, b2, -1 if j == 0 else 0, no + 2), lo, no)
+    mean, var = rqmc_integral(I, [], next_prime(20000), 8, lo, no)
+    assert_within(mean, var, exact, rel=1e-10)
+
+
+def test_regular_eps_exponents_exact_series():
+    # a = 0 with b != 0 and U^{u1 eps}: int_0^1 t^{2 + b eps} (1 + t)^{c eps} dt
+    # checked against adaptive quadrature (QUADPACK) of the eps-Taylor coefficients
+    from scipy.integrate import quad
+    b, c = 0.5, -2.0
+    I = _toy_integral(1, [2], [b], {(0,): 1, (1,): 1}, u0=0, u1=c)
+    lo, no = 0, 3
+    exact = np.array([quad(lambda t: t ** 2 * (b * math.log(t) + c * math.log1p(t)) ** k
+                           / math.factorial(k), 0, 1, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+                      for k in range(no)])
+    assert abs(exact[1] - (-b / 9 + c * (2 * math.log(2) / 3 - 5 / 18))) < 1e-14
+    mean, var = rqmc_integral(I, [], next_prime(4000), 8, lo, no)
+    assert_within(mean, var, exact, rel=1e-11)
+
+
+# ---------------------------------------------------------------- closed forms
+def test_triangle_massive_closed_form():
+    I = w.triangle_massive()
+    exact = closed_form("triangle_m1_pm1")
+    mean, var = rqmc_integral(I, [], next_prime(10000), 8, 0, 1)
+    assert_within(mean, var, [exact[0]])
+    assert math.sqrt(var[0]) < 1e-10
+
+
+def test_triangle_tensor_quadrature():
+    # brute-force check: 48x48 Gauss-Legendre on each primary sector (no lattice)
+    I = w.triangle_massive()
+    xs, ws = leggauss(48)
+    t = 0.5 * (xs + 1)
+    wq = 0.5 * ws
+    total = 0.0
+    for si in range(3):
+        v = oracle.SectorView(I, si, [])
+        for i in range(48):
+            for j in range(48):
+                total += wq[i] * wq[j] * oracle.integrand_at(v, [t[i], t[j]], 0, 1)[0, 0]
+    total *= I.prefactor[0].real
+    assert abs(total - closed_form("triangle_m1_pm1")[0].real) < 1e-13
+
+
+@pytest.mark.parametrize("s,t", [(-3, -2), (-5, -1)])
+def test_massless_box_closed_form(s, t):
+    I = w.box_massless()
+    ex = closed_form("box1L_massless", f"s={s},t={t}")
+    mean, var = rqmc_integral(I, [float(s), float(t)], next_prime(20000), 8, -2, 3)
+    assert_within(mean, var, [ex[-2], ex[-1], ex[0]], rel=1e-9)
+
+
+def test_massless_box_sector_count_and_poles():
+    I = w.box_massless()
+    assert len(I.sectors) == 12
+    assert I.max_poles == 2
+    assert all(s.u0 == 0 and s.u1 == 2 and s.f0 == -2 and s.f1 == -1 for s in I.sectors)
+
+
+@pytest.mark.parametrize("s", [-3, 10])
+def test_bubbles_closed_form(s):
+    # massive bubble: Gamma(eps) pole times a sector integral needed to O(eps)
+    lam = None if s < 0 else 0.5
+    I = w.bubble(1, "s", deform=s > 0)
+    ex = closed_form("bubble_m1", f"s={s}")
+    mean, var = rqmc_integral(I, [float(s)], next_prime(4000), 8, -1, 2, lam=lam)
+    assert_within(mean, var, [ex[-1], ex[0]], rel=1e-12)
+    # massless bubble: F is a constant after factorisation; tests the F - i0 rule
+    I0 = w.bubble(0, "s", deform=s > 0)
+    ex0 = closed_form("bubble_m0", f"s={s}")
+    mean, var = rqmc_integral(I0, [float(s)], next_prime(4000), 8, -1, 2, lam=lam)
+    assert_within(mean, var, [ex0[-1], ex0[0]], rel=1e-12)
+
+
+@pytest.mark.parametrize("s", [-3, 10])
+def test_one_mass_triangle_closed_form(s):
+    lam = None if s < 0 else 0.3
+    I = w.triangle_one_offshell(0, "s", deform=s > 0)
+    ex = closed_form("triangle_m0", f"s={s}")
+    mean, var = rqmc_integral(I, [float(s)], next_prime(10000), 8, -2, 3, lam=lam)
+    assert_within(mean, var, [ex[-2], ex[-1], ex[0]], rel=1e-10)
+
+
+# ---------------------------------------------------------------- deformation
+def test_massive_box_lambda_independence_and_sign():
+    I = w.box_massive()
+    inv = [12.0, -3.0]
+    m1, v1 = rqmc_integral(I, inv, next_prime(20000), 8, 0, 1, lam=0.3)
+    m2, v2 = rqmc_integral(I, inv, next_prime(20000), 8, 0, 1, lam=0.15)
+    assert abs(m1[0] - m2[0]) <= 4 * math.sqrt(v1[0] + v2[0]) + 1e-12
+    assert abs(m1[0].imag) > 1e-3  # above threshold: non-zero imaginary part
+    # lambda of the wrong sign puts F(z) on the wrong side of the cut
+    v = oracle.SectorView(I, 0, inv, -0.3)
+    _, _, fails = oracle.shift_sums(v, 1009, cbc_fast(1009, 3), oracle.shifts(1, 0, 2, 3), 0, 1)
+    assert fails > 0
+    v = oracle.SectorView(I, 0, inv, 0.3)
+    _, _, fails = oracle.shift_sums(v, 1009, cbc_fast(1009, 3), oracle.shifts(1, 0, 2, 3), 0, 1)
+    assert fails == 0
+
+
+def test_massive_box_euclidean_deformation_on_off_and_quadrature():
+    I = w.box_massive()
+    inv = [-3.0, -2.0]
+    m_off, v_off = rqmc_integral(w.box_massive(deform=False), inv, next_prime(20000), 8, 0, 1)
+    m_on, v_on = rqmc_integral(I, inv, next_prime(20000), 8, 0, 1, lam=0.3)
+    assert abs(m_off[0] - m_on[0]) <= 4 * math.sqrt(v_off[0] + v_on[0]) + 1e-12
+    # 3-D tensor Gauss-Legendre on the undeformed sectors
+    xs, ws = leggauss(16)
+    t = 0.5 * (xs + 1)
+    wq = 0.5 * ws
+    total = 0.0
+    Ioff = w.box_massive(deform=False)
+    for si in range(4):
+        v = oracle.SectorView(Ioff, si, inv)
+        for i in range(16):
+            for j in range(16):
+                for k in range(16):
+                    total += wq[i] * wq[j] * wq[k] * oracle.integrand_at(v, [t[i], t[j], t[k]], 0, 1)[0, 0]
+    total *= Ioff.prefactor[0].real
+    assert abs(total - m_off[0].real) < 1e-9
+
+
+def test_error_decreases_faster_than_mc():
+    # log-log slope of the RQMC error against n on a smooth korobov3 integrand
+    I = w.triangle_massive()
+    ns = [next_prime(v) for v in (1000, 4000, 16000)]
+    errs = [math.sqrt(rqmc_integral(I, [], n, 16, 0, 1)[1][0]) for n in ns]
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert slope < -1.0, (errs, slope)
+
+
+# ---------------------------------------------------------------- prefactor
+def test_prefactor_series_matches_gamma():
+    for N, L, D0 in ((4, 1, 4), (2, 1, 4), (7, 2, 4), (3, 1, 4)):
+        lo, cs = prefactor_series(N, L, D0, 5)
+        for eps in (1e-3, -2e-3):
+            approx = sum(c * eps ** (lo + i) for i, c in enumerate(cs))
+            exact = (-1) ** N * math.gamma(N - L * D0 / 2 + L * eps)
+            assert abs(approx - exact) <= 1e-12 * abs(exact)
