@@ -1,0 +1,275 @@
+"""Benchmark: randomized rank-1 lattice QMC over the sector-decomposed one-loop
+massless box (s = -3, t = -2, D = 4 - 2 eps, orders eps^-2 .. eps^0; twelve
+sectors in three Feynman parameters), lattice n = 1000003 with a CBC vector,
+32 random shifts per sector: 3.84e8 integrand evaluations per step.
+
+A step is one full evaluation pass: every sector on its lattice with every
+shift (lattice point, shift, korobov3, eps-expanded integrand with
+subtraction, per-shift reduction), computed by the CUDA kernels behind the
+C-ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank evaluates its own
+independent batch (its own shift streams): weak scaling, no data-path
+collective. ``--impl reference`` times the CPU FP64 oracle on bounded samples
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n=1000003 CBC, m=32 shifts"
+METRIC = "integrand evals/s"
+UNIT = "evals/s"
+LO, NORD = -2, 3
+INV = [-3.0, -2.0]
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def clock_sampler_start(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+           "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        fh = open(path, "w")
+        return subprocess.Popen(cmd, stdout=fh, stderr=subprocess.DEVNULL), fh
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def clock_sampler_stop(proc, fh, path, device_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    fh.close()
+    sm, smax, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+    except OSError:
+        return None
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def oracle_sample(I, inv, n, m, seed, ks, sectors=None):
+    """Oracle per-shift sums of every sector over lattice indices [0, ks):
+    returns (evaluations, seconds, threads)."""
+    import oracle
+    from paper_2305_19768_gb300.inputs.lattice import lattice_for
+
+    sectors = range(len(I.sectors)) if sectors is None else sectors
+    t0 = time.perf_counter()
+    evals = 0
+    for s in sectors:
+        sec = I.sectors[s]
+        _, z = lattice_for(n, sec.d)
+        dl = oracle.shifts(seed, s, m, sec.d)
+        view = oracle.SectorView(I, s, inv)
+        oracle.shift_sums(view, n, z, dl, LO, NORD, k0=0, k1=ks)
+        evals += m * ks
+    return evals, time.perf_counter() - t0, oracle.max_threads()
+
+
+def run_reference(args):
+    """CPU FP64 oracle on bounded samples of the bench workload."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from paper_2305_19768_gb300.inputs import workloads as w
+
+    I = w.box_massless()
+    n, m = args.n, args.shifts
+    ks = 1500
+    for _ in range(args.warmup):
+        oracle_sample(I, INV, n, m, 1, ks)
+    tot_e, tot_t, thr = 0, 0.0, 1
+    for _ in range(args.steps):
+        e, t, thr = oracle_sample(I, INV, n, m, 1, ks)
+        tot_e += e
+        tot_t += t
+    val = tot_e / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"k in [0,{ks}) per sector and shift"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"all 12 sectors x {m} shifts x lattice indices [0,{ks}) of n={n}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1000003)
+    ap.add_argument("--shifts", type=int, default=32)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ppt", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2305_19768_gb300 import flops as flopmod
+    from paper_2305_19768_gb300 import qmc
+    from paper_2305_19768_gb300.inputs import workloads as w
+
+    I = w.box_massless()
+    opts = {}
+    if args.block:
+        opts["block"] = args.block
+    if args.ppt:
+        opts["ppt"] = args.ppt
+    ctx = qmc.qmc_create(local, **opts)
+    qmc.load_lattice_table(ctx)
+    iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+    kin = np.array([INV], dtype=np.float64)
+    qmc.qmc_set_kinematics(ctx, kin)
+    nsec = len(I.sectors)
+    seed = 1 + rank  # independent shift streams per rank
+    specs = qmc.jobs_for_integral(iid, nsec, 1, args.n, args.shifts, seed=seed)
+    jobs, nj = qmc.make_jobs(specs)
+    plan = qmc.qmc_plan_create(ctx, jobs, nj, LO, NORD)
+    out_n = qmc.qmc_plan_output_size(plan)
+    out_dev = torch.empty(out_n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    evals_per_step = nsec * args.shifts * args.n
+
+    for _ in range(max(3, args.warmup)):
+        qmc.qmc_plan_run(ctx, plan, out_dev.data_ptr(), sptr)
+    torch.cuda.synchronize()
+
+    peak_gflops = qmc.qmc_fp64_peak(ctx)
+    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/bench_clocks_r{rank}.csv"
+    proc, fh = clock_sampler_start(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    eval_ms = []
+    launches = 0
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                          # evict L2 between timed steps (untimed)
+        ev[i][0].record(stream)
+        qmc.qmc_plan_run(ctx, plan, out_dev.data_ptr(), sptr)
+        ev[i][1].record(stream)
+        _, ms_eval, nl = qmc.qmc_plan_last_time(ctx, plan)
+        eval_ms.append(ms_eval)
+        launches += nl
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clock_sampler_stop(proc, fh, clk_path, local)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = evals_per_step * args.steps * world / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers: kinematics and the
+    # job table in, per-shift sums out, every step
+    e2e_val = None
+    h2d = kin.nbytes + nj * 128
+    d2h = out_n * 8
+    host_out = np.zeros(out_n)
+    t_e2e = 0.0
+    for i in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        qmc.qmc_set_kinematics(ctx, kin)
+        host_out = qmc.qmc_eval_jobs(ctx, jobs, nj, LO, NORD, out_n)
+        t_e2e += time.perf_counter() - t0
+    e2e_val = evals_per_step * max(1, args.steps // 2) * world / t_e2e
+
+    # roofline of the evaluator kernel: algorithmic FP64 flops / event time
+    fl_per_eval = flopmod.workload_flops(I, LO, NORD)
+    avg_eval_ms = float(np.mean(eval_ms))
+    achieved = fl_per_eval * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s (fp64)",
+            "frac": achieved / peak_gflops, "traffic": None,
+            "flops_per_eval": fl_per_eval, "peak_source": "DFMA probe in this run"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ks = 1500
+        e, t, thr = oracle_sample(I, INV, args.n, args.shifts, 1, ks)
+        cpu = {"value": e / t, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"all {nsec} sectors x {args.shifts} shifts x lattice indices [0,{ks}) of n={args.n}"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "evals_per_step": evals_per_step,
+                       "l2": "flushed between timed steps (256 MB write)", "wall_s": wall},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    qmc.qmc_plan_destroy(plan)
+    qmc.qmc_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * qmc.h -- C-ABI of the GB300 randomized-lattice QMC integrator for
+ * sector-decomposed, eps-expanded Feynman-parameter integrals.
+ *
+ * What the library computes follows arXiv:2305.19768 (pySecDec 1.6,
+ * "Numerical scattering amplitudes with pySecDec"):
+ *   - the randomized rank-1 shifted lattice rule of the Disteval integrator
+ *     (section "The new Quasi-Monte-Carlo evaluator Disteval"): for each
+ *     sector and random shift Delta_s, Q_s = (1/n) sum_{k<n} f(frac(k z/n + Delta_s)),
+ *     value = mean over shifts, error = sqrt(var/m);
+ *   - the korobov3 transform (timings section), contour deformation with its
+ *     Jacobian determinant (number_of_presamples in the usage section), and the
+ *     eps-expansion of the sector integrands;
+ *   - weighted sums A_k = sum_i C_ki I_i with the variance-driven lattice
+ *     allocation of Eq. (adaptive-solution), alpha = 2, minimum lattice 10^4
+ *     (section "Adaptive weighted sum evaluation");
+ *   - the per-coefficient relative error sqrt(dR^2 + dI^2) / sqrt(R^2 + I^2)
+ *     (timings section).
+ *
+ * Conventions for every entry point:
+ *   - Return 0 on success, a negative QMC_E_* code on failure; the message of
+ *     the last failure on a context is available from qmc_last_error().
+ *   - Input buffers are borrowed for the duration of the call only (copied).
+ *     Output buffers are owned by the caller and must hold the stated size.
+ *   - Pointers documented as "host" are ordinary host memory (pinned or not);
+ *     "device" pointers are CUDA device memory of the context's device.
+ *   - A context is used by one host thread at a time. All GPU work of a
+ *     context is issued on its own CUDA stream unless a stream is passed.
+ *   - Nothing falls back to the CPU: without a usable CUDA device every call
+ *     that needs one returns QMC_E_CUDA.
+ */
+#ifndef QMC_H
+#define QMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QMC_OK 0
+#define QMC_E_INVAL (-1)          /* bad argument or unsupported sector shape */
+#define QMC_E_PARSE (-2)          /* malformed sector description */
+#define QMC_E_CUDA (-3)           /* CUDA runtime error (message has the detail) */
+#define QMC_E_TIMEOUT (-4)        /* qmc_integrate ran past timeout_s */
+#define QMC_E_NOT_CONVERGED (-5)  /* max_points reached before the requested accuracy */
+#define QMC_E_SIGN_CHECK (-6)     /* contour deformation put F on the wrong side of the cut */
+#define QMC_E_NONFINITE (-7)      /* a partial sum was NaN or Inf */
+#define QMC_E_NOMEM (-8)          /* allocation failed */
+
+typedef struct qmc_ctx qmc_ctx;
+typedef struct qmc_plan qmc_plan;
+
+typedef struct {
+    double re, im;
+} qmc_c64;
+
+/* Options of a context. Zero-initialise and set what you need; zero fields
+ * take the defaults in brackets, which mirror the paper's call arguments
+ * (points = 1e4, number_of_presamples, timeout, lattice_candidates). */
+typedef struct {
+    int shifts;            /* m random shifts per lattice [32] */
+    uint64_t seed;         /* seed of the shift streams [1] */
+    int block;             /* threads per block of the evaluator, 128 or 256 [autotuned] */
+    int ppt;               /* lattice points per thread [autotuned] */
+    uint64_t min_points;   /* smallest lattice (pilot pass) [10000] */
+    uint64_t max_points;   /* largest lattice qmc_integrate may use [largest tabulated] */
+    int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
+    int reserved[8];
+} qmc_options;
+
+/* One evaluation job: one sector of one loaded integral at one kinematic
+ * point, on one lattice, with `shifts` random shifts. */
+typedef struct {
+    int32_t integral_id;   /* from qmc_load_sectors_mem */
+    int32_t sector;        /* sector index within the integral */
+    int32_t point;         /* kinematic point index (qmc_set_kinematics) */
+    int32_t shifts;        /* m >= 1 */
+    uint64_t n;            /* lattice size; must be in the lattice table */
+    uint64_t seed;         /* shift seed */
+    uint64_t stream;       /* shift stream id: Delta[s][j] is output s*d+j of
+                              splitmix64 started at seed ^ (0x9E3779B97F4A7C15 * (stream + 1)),
+                              as (out >> 11) * 2^-53 */
+    double lambda[6];      /* deformation parameter per variable (deformed sectors) */
+} qmc_job;
+
+/* Create a context on CUDA device `device`. `opt` may be NULL (defaults).
+ * On success *out owns all device memory the context allocates; free with
+ * qmc_destroy. Errors: QMC_E_CUDA (no device), QMC_E_NOMEM. */
+int qmc_create(qmc_ctx **out, int device, const qmc_options *opt);
+
+/* Destroy a context and everything it owns (plans included). NULL is a no-op. */
+void qmc_destroy(qmc_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none). The string is
+ * owned by the context and valid until the next call on it. */
+const char *qmc_last_error(const qmc_ctx *ctx);
+
+/* Install the table of rank-1 lattices: count rows of (n[i], z[i][0..5]),
+ * host buffers. Generating vectors are an input: the paper uses
+ * pre-computed component-by-component vectors (section on median QMC
+ * rules). n must be < 2^32 and every z component coprime to n.
+ * Errors: QMC_E_INVAL. */
+int qmc_set_lattices(qmc_ctx *ctx, const uint64_t *n, const uint32_t *z, int count);
+
+/* Parse one integral's sector description (text, `len` bytes, host) and
+ * upload its monomial tables to the device. The format (one integral: name,
+ * loop and propagator counts, D0, invariant names, prefactor Laurent series,
+ * then per sector the dimension, deformation flag, monomial prefactor
+ * exponents a_j + b_j eps, and the monomial tables of U^{u0+u1 eps} and
+ * F^{f0+f1 eps}) is the one written by the Python input generators. Sector
+ * limits: d <= 6, at most 4 variables with a_j = -1 (a_j >= -1 otherwise),
+ * exponents <= 4 per variable, <= 3 invariants; deformed sectors d <= 3 with
+ * at most 2 singular variables. *integral_id receives the new id.
+ * Errors: QMC_E_PARSE, QMC_E_INVAL (limits), QMC_E_CUDA. */
+int qmc_load_sectors_mem(qmc_ctx *ctx, const char *text, size_t len, int *integral_id);
+
+/* Same as qmc_load_sectors_mem, reading the description from a file. */
+int qmc_load_sectors(qmc_ctx *ctx, const char *path, int *integral_id);
+
+/* Sector count, maximal number of singular variables and prefactor series
+ * (lowest order and up to `cap` complex coefficients) of a loaded integral.
+ * Any output pointer may be NULL. */
+int qmc_integral_info(qmc_ctx *ctx, int integral_id, int *nsectors, int *max_poles,
+                      int *prefactor_lo, qmc_c64 *prefactor, int cap, int *prefactor_len);
+
+/* Set the kinematic points: inv is a host array [npoints][ninv] of the
+ * invariants in the order of the sector description. Replaces earlier points.
+ * Errors: QMC_E_INVAL, QMC_E_CUDA. */
+int qmc_set_kinematics(qmc_ctx *ctx, const double *inv, int npoints, int ninv);
+
+/* Build an evaluation plan for `njobs` jobs (host array): uploads the job
+ * table, sizes the tile queue and partial-sum scratch, and picks the kernel
+ * class of every job. Each job yields per-shift estimates of the eps orders
+ * lo .. lo+norders-1 of its sector integral (orders below the sector's
+ * leading pole are 0). *out owns its device buffers; destroy with
+ * qmc_plan_destroy (or with the context). Errors: QMC_E_INVAL, QMC_E_CUDA. */
+int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
+                    qmc_plan **out);
+
+/* Number of doubles the plan writes: sum over jobs of shifts * norders * 2. */
+size_t qmc_plan_output_size(const qmc_plan *plan);
+
+/* Enqueue one evaluation of the plan on `stream` (a cudaStream_t; NULL =
+ * the context's stream) writing per-shift sums to `out_dev` (device, layout
+ * [job][shift][order][re, im], qmc_plan_output_size doubles; NULL = the
+ * plan's own buffer). Asynchronous: returns after the launches are queued.
+ * Errors: QMC_E_CUDA. */
+int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream);
+
+/* Wait for the plan's last run, then copy its per-shift sums to the host
+ * buffer `out` (same layout as qmc_plan_run), and check the device status:
+ * QMC_E_NONFINITE if a partial sum was NaN/Inf, QMC_E_SIGN_CHECK if a
+ * deformed point had Im F > 0 (the sums are still written).
+ * `sign_failures` (may be NULL) receives the count of such points. */
+int qmc_plan_results(qmc_plan *plan, double *out, uint64_t *sign_failures);
+
+/* Device time of the plan's last run measured with CUDA events on the stream
+ * it ran on: ms_total for the whole run, ms_eval for the evaluator kernels
+ * alone (without the finishing reduction), and the number of kernel launches
+ * it issued. Waits for the run to finish. Any output may be NULL. */
+int qmc_plan_last_time(qmc_plan *plan, float *ms_total, float *ms_eval, int *launches);
+
+/* Free a plan. NULL is a no-op. */
+void qmc_plan_destroy(qmc_plan *plan);
+
+/* One-shot evaluation through host buffers: plan, run, copy back, free.
+ * `out` is a host array of qmc_plan_output_size doubles. */
+int qmc_eval_jobs(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
+                  double *out);
+
+/* The shifted lattice points the evaluator uses (steps "lattice index" and
+ * "shifted point"): x[i][j] = frac((k0+i) z_j / n + delta_j) for
+ * i < count, as (double)r/(double)n + delta with r = (k z_j) mod n exact,
+ * folded once into [0,1). Host buffers: z[d], delta[d], x[count][d],
+ * r[count][d] (r may be NULL). Errors: QMC_E_INVAL, QMC_E_CUDA. */
+int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d,
+                       const double *delta, uint64_t k0, uint64_t count, double *x,
+                       uint64_t *r);
+
+/* Random shifts the evaluator draws for (seed, stream): Delta[s][j], host
+ * array [m][d] (see qmc_job.stream). Computed on the device. */
+int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta);
+
+/* Measure the FP64 fused-multiply-add throughput of the device (the
+ * roofline denominator of the evaluator): *gflops = 2 * DFMA / s over a
+ * dependent-chain-free loop timed with CUDA events. */
+int qmc_fp64_peak(qmc_ctx *ctx, double *gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMC_H */

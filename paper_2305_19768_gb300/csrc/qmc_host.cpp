@@ -1,0 +1,816 @@
+// Host side of the C-ABI (include/qmc.h): sector-description parser, packing
+// of monomial tables for the kernels, evaluation plans (job tables, tile
+// queue, partial-sum scratch), and the adaptive integration driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "qmc_internal.h"
+
+extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void *stream);
+extern "C" int qmc_k_occupancy(int cls, int block);
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+struct Term {
+    int e[QMC_DMAX];
+    double c[QMC_NCOEF];
+};
+
+struct HostSector {
+    int d = 0;
+    bool deform = false;
+    int a[QMC_DMAX] = {0};
+    double b[QMC_DMAX] = {0};
+    double u0 = 0, u1 = 0, f0 = 0, f1 = 0;
+    std::vector<Term> U, F;
+    int ns = 0;
+    int cls = 0;
+    int global_index = 0;  // index in the device sector table
+};
+
+struct HostIntegral {
+    std::string name;
+    int L = 0, N = 0, D0 = 0;
+    std::vector<std::string> invariants;
+    int pref_lo = 0;
+    std::vector<qmc_c64> pref;
+    std::vector<HostSector> sectors;
+    int max_poles = 0;
+};
+
+}  // namespace
+
+struct qmc_plan;
+
+struct qmc_ctx {
+    int device = 0;
+    qmc_options opt{};
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    std::map<uint64_t, std::vector<uint32_t>> lattices;
+    std::vector<HostIntegral> integrals;
+    // device tables (rebuilt when an integral is loaded)
+    QmcSectorDev *d_sectors = nullptr;
+    QmcMono *d_monos = nullptr;
+    int nsectors_dev = 0;
+    double *d_kin = nullptr;
+    int npoints = 0, ninv = 0;
+    std::vector<qmc_plan *> plans;
+};
+
+struct ClassLaunch {
+    int cls = 0;
+    QmcLaunch L{};
+    QmcJobDev *d_jobs = nullptr;
+    double *d_partials = nullptr;
+    unsigned long long *d_queue = nullptr;
+    int block = 128, ppt = 4, grid = 0;
+};
+
+struct qmc_plan {
+    qmc_ctx *ctx = nullptr;
+    int lo = 0, norders = 0, njobs = 0;
+    size_t out_size = 0;
+    double *d_out = nullptr;
+    unsigned long long *d_status = nullptr;
+    std::vector<ClassLaunch> launches;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> kev;   // [2 * class launch]: around each evaluator kernel
+    cudaStream_t last_stream = nullptr;
+    double *last_out = nullptr;
+    int last_launches = 0;
+};
+
+namespace {
+
+int fail(qmc_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                     \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail((ctx), QMC_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                        __FILE__, __LINE__);                                                    \
+    } while (0)
+
+// ------------------------------------------------------------------ parsing
+struct Tok {
+    std::istringstream is;
+    bool ok = true;
+    explicit Tok(const std::string &s) : is(s) {}
+    std::string word() {
+        std::string w;
+        if (!(is >> w)) ok = false;
+        return w;
+    }
+    bool expect(const char *w) { return word() == w && ok; }
+    long long integer() {
+        std::string w = word();
+        if (!ok) return 0;
+        char *end = nullptr;
+        long long v = strtoll(w.c_str(), &end, 10);
+        if (!end || *end) ok = false;
+        return v;
+    }
+    double real() {
+        std::string w = word();
+        if (!ok) return 0;
+        char *end = nullptr;
+        double v = strtod(w.c_str(), &end);
+        if (!end || *end) ok = false;
+        return v;
+    }
+};
+
+int parse_integral(qmc_ctx *ctx, const std::string &text, HostIntegral &I) {
+    Tok t(text);
+    if (!t.expect("qmc-sectors") || t.integer() != 1) return fail(ctx, QMC_E_PARSE, "bad header");
+    if (!t.expect("name")) return fail(ctx, QMC_E_PARSE, "expected 'name'");
+    I.name = t.word();
+    if (!t.expect("loops")) return fail(ctx, QMC_E_PARSE, "expected 'loops'");
+    I.L = (int)t.integer();
+    if (!t.expect("propagators")) return fail(ctx, QMC_E_PARSE, "expected 'propagators'");
+    I.N = (int)t.integer();
+    if (!t.expect("dim")) return fail(ctx, QMC_E_PARSE, "expected 'dim'");
+    I.D0 = (int)t.integer();
+    if (!t.expect("invariants")) return fail(ctx, QMC_E_PARSE, "expected 'invariants'");
+    long long k = t.integer();
+    if (!t.ok || k < 0 || k > QMC_NCOEF - 1)
+        return fail(ctx, QMC_E_INVAL, "invariant count %lld outside 0..%d", k, QMC_NCOEF - 1);
+    for (long long i = 0; i < k; ++i) I.invariants.push_back(t.word());
+    if (!t.expect("prefactor")) return fail(ctx, QMC_E_PARSE, "expected 'prefactor'");
+    I.pref_lo = (int)t.integer();
+    long long np = t.integer();
+    if (!t.ok || np < 1 || np > 64) return fail(ctx, QMC_E_PARSE, "bad prefactor length");
+    for (long long i = 0; i < np; ++i) {
+        qmc_c64 c;
+        c.re = t.real();
+        c.im = t.real();
+        I.pref.push_back(c);
+    }
+    if (!t.expect("nsectors")) return fail(ctx, QMC_E_PARSE, "expected 'nsectors'");
+    long long ns = t.integer();
+    if (!t.ok || ns < 1 || ns > 1000000) return fail(ctx, QMC_E_PARSE, "bad sector count");
+    for (long long si = 0; si < ns; ++si) {
+        HostSector S;
+        if (!t.expect("sector")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'sector'", si);
+        t.integer();
+        if (!t.expect("d")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'd'", si);
+        S.d = (int)t.integer();
+        if (S.d < 1 || S.d > QMC_DMAX)
+            return fail(ctx, QMC_E_INVAL, "sector %lld: d=%d outside 1..%d", si, S.d, QMC_DMAX);
+        if (!t.expect("deform")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'deform'", si);
+        S.deform = t.integer() != 0;
+        if (!t.expect("a")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'a'", si);
+        for (int j = 0; j < S.d; ++j) S.a[j] = (int)t.integer();
+        if (!t.expect("b")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'b'", si);
+        for (int j = 0; j < S.d; ++j) S.b[j] = t.real();
+        for (int which = 0; which < 2; ++which) {
+            if (!t.expect(which == 0 ? "U" : "F"))
+                return fail(ctx, QMC_E_PARSE, "sector %lld: expected '%s'", si, which ? "F" : "U");
+            double e0 = t.real(), e1 = t.real();
+            long long nt = t.integer();
+            if (!t.ok || nt < 1 || nt > QMC_MAXMONO)
+                return fail(ctx, QMC_E_INVAL, "sector %lld: term count out of range", si);
+            std::vector<Term> &P = which == 0 ? S.U : S.F;
+            for (long long m = 0; m < nt; ++m) {
+                Term T{};
+                for (int j = 0; j < S.d; ++j) T.e[j] = (int)t.integer();
+                for (long long i = 0; i <= k; ++i) T.c[i] = t.real();
+                P.push_back(T);
+            }
+            if (which == 0) {
+                S.u0 = e0;
+                S.u1 = e1;
+            } else {
+                S.f0 = e0;
+                S.f1 = e1;
+            }
+        }
+        if (!t.ok) return fail(ctx, QMC_E_PARSE, "sector %lld: truncated", si);
+        I.sectors.push_back(std::move(S));
+    }
+    if (!t.expect("end")) return fail(ctx, QMC_E_PARSE, "expected 'end'");
+    return QMC_OK;
+}
+
+// ------------------------------------------------------------------ packing
+uint32_t pack_exps(const int *e, int d) {
+    uint32_t v = 0;
+    for (int j = 0; j < d; ++j) v |= (uint32_t)e[j] << (4 * j);
+    return v;
+}
+
+int classify(qmc_ctx *ctx, HostSector &S, int si) {
+    S.ns = 0;
+    for (int j = 0; j < S.d; ++j) {
+        if (S.a[j] < -1) return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d < -1 needs higher-order subtraction", si, j, S.a[j]);
+        if (S.a[j] == -1) {
+            if (S.b[j] == 0.0) return fail(ctx, QMC_E_INVAL, "sector %d: unregulated 1/t_%d", si, j);
+            ++S.ns;
+        } else if (S.a[j] > QMC_EMAX) {
+            return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d above %d", si, j, S.a[j], QMC_EMAX);
+        }
+    }
+    if (S.ns > QMC_SMAX) return fail(ctx, QMC_E_INVAL, "sector %d: %d singular variables > %d", si, S.ns, QMC_SMAX);
+    if (S.deform) {
+        if (S.d > 3 || S.ns > 2)
+            return fail(ctx, QMC_E_INVAL, "sector %d: deformed sectors need d <= 3 and <= 2 singular variables", si);
+        S.cls = QMC_CLASS_CPLX3;
+    } else if (S.d <= 3 && S.ns <= 2) {
+        S.cls = QMC_CLASS_REAL3;
+    } else {
+        S.cls = QMC_CLASS_REAL6;
+    }
+    return QMC_OK;
+}
+
+// Pack one sector: header + monomials appended to `monos`.
+int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector<QmcMono> &monos,
+                QmcSectorDev &H) {
+    memset(&H, 0, sizeof H);
+    H.d = S.d;
+    H.ns = S.ns;
+    H.deform = S.deform ? 1 : 0;
+    H.ninv = ninv;
+    H.u0 = S.u0;
+    H.u1 = S.u1;
+    H.f0 = S.f0;
+    H.f1 = S.f1;
+    H.u0_int = (S.u0 == std::floor(S.u0) && std::fabs(S.u0) <= QMC_EMAX) ? 1 : 0;
+    H.f0_int = (S.f0 == std::floor(S.f0) && std::fabs(S.f0) <= QMC_EMAX) ? 1 : 0;
+    int q = 0;
+    for (int j = 0; j < S.d; ++j) {
+        H.a[j] = S.a[j];
+        H.b[j] = S.b[j];
+        if (S.a[j] == -1) H.sing[q++] = j;
+        else if (S.a[j] != 0 || S.b[j] != 0.0) H.regular_mask |= 1 << j;
+    }
+    int emax = 0;
+    auto mask_of = [&](const Term &T) {
+        int m = 0;
+        for (int qq = 0; qq < S.ns; ++qq)
+            if (T.e[H.sing[qq]] > 0) m |= 1 << qq;
+        return m;
+    };
+    std::vector<QmcMono> local;
+    auto push = [&](const Term &T) -> int {
+        QmcMono M{};
+        for (int j = 0; j < S.d; ++j) {
+            if (T.e[j] < 0 || T.e[j] > QMC_EMAX)
+                return fail(ctx, QMC_E_INVAL, "sector %d: exponent %d outside 0..%d", si, T.e[j], QMC_EMAX);
+            emax = std::max(emax, T.e[j]);
+        }
+        M.exps = pack_exps(T.e, S.d);
+        for (int i = 0; i < QMC_NCOEF; ++i) M.coef[i] = T.c[i];
+        local.push_back(M);
+        return QMC_OK;
+    };
+    // U and F sorted by singular mask, with group boundaries
+    for (int which = 0; which < 2; ++which) {
+        const std::vector<Term> &P = which == 0 ? S.U : S.F;
+        int32_t *g = which == 0 ? H.gU : H.gF;
+        int count = 0;
+        for (int grp = 0; grp < QMC_NGROUP; ++grp) {
+            g[grp] = count;
+            for (const Term &T : P)
+                if (mask_of(T) == grp) {
+                    int rc = push(T);
+                    if (rc) return rc;
+                    ++count;
+                }
+        }
+        g[QMC_NGROUP] = count;
+        if (which == 0) H.nU = count;
+        else H.nF = count;
+    }
+    if (S.deform) {
+        // dF/dt_j and d2F/dt_j dt_k (j <= k) as monomial tables, merged by exponent
+        auto deriv = [&](const std::vector<Term> &P, int j) {
+            std::vector<Term> out;
+            for (const Term &T : P) {
+                if (T.e[j] == 0) continue;
+                Term D = T;
+                for (int i = 0; i < QMC_NCOEF; ++i) D.c[i] *= T.e[j];
+                D.e[j] -= 1;
+                bool merged = false;
+                for (Term &O : out)
+                    if (memcmp(O.e, D.e, sizeof D.e) == 0) {
+                        for (int i = 0; i < QMC_NCOEF; ++i) O.c[i] += D.c[i];
+                        merged = true;
+                        break;
+                    }
+                if (!merged) out.push_back(D);
+            }
+            return out;
+        };
+        int base = (int)local.size();
+        for (int j = 0; j < S.d; ++j) {
+            std::vector<Term> dj = deriv(S.F, j);
+            H.dFoff[j] = (int)local.size() - base;
+            H.dFn[j] = (int)dj.size();
+            for (const Term &T : dj) {
+                int rc = push(T);
+                if (rc) return rc;
+            }
+        }
+        for (int j = 0; j < S.d; ++j) {
+            std::vector<Term> dj = deriv(S.F, j);
+            for (int k = j; k < S.d; ++k) {
+                std::vector<Term> hk = deriv(dj, k);
+                const int h = j * QMC_DMAX - j * (j - 1) / 2 + (k - j);
+                H.Hoff[h] = (int)local.size() - base;
+                H.Hn[h] = (int)hk.size();
+                for (const Term &T : hk) {
+                    int rc = push(T);
+                    if (rc) return rc;
+                }
+            }
+        }
+    }
+    if ((int)local.size() > QMC_MAXMONO)
+        return fail(ctx, QMC_E_INVAL, "sector %d: %zu monomials > %d", si, local.size(), QMC_MAXMONO);
+    H.pad0 = std::max(emax, 1);
+    for (int j = 0; j < S.d; ++j)
+        if (S.a[j] > 0) H.pad0 = std::max(H.pad0, S.a[j]);
+    H.monoU = (int)monos.size();
+    H.monoF = H.monoU + H.nU;
+    H.nmono = (int)local.size();
+    monos.insert(monos.end(), local.begin(), local.end());
+    return QMC_OK;
+}
+
+int upload_tables(qmc_ctx *ctx) {
+    std::vector<QmcSectorDev> secs;
+    std::vector<QmcMono> monos;
+    for (HostIntegral &I : ctx->integrals) {
+        for (size_t si = 0; si < I.sectors.size(); ++si) {
+            HostSector &S = I.sectors[si];
+            QmcSectorDev H;
+            int rc = pack_sector(ctx, S, (int)si, (int)I.invariants.size(), monos, H);
+            if (rc) return rc;
+            S.global_index = (int)secs.size();
+            secs.push_back(H);
+        }
+    }
+    cudaFree(ctx->d_sectors);
+    cudaFree(ctx->d_monos);
+    ctx->d_sectors = nullptr;
+    ctx->d_monos = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_sectors, std::max<size_t>(1, secs.size()) * sizeof(QmcSectorDev)));
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_monos, std::max<size_t>(1, monos.size()) * sizeof(QmcMono)));
+    CUDA_TRY(ctx, cudaMemcpy(ctx->d_sectors, secs.data(), secs.size() * sizeof(QmcSectorDev),
+                             cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpy(ctx->d_monos, monos.data(), monos.size() * sizeof(QmcMono),
+                             cudaMemcpyHostToDevice));
+    ctx->nsectors_dev = (int)secs.size();
+    return QMC_OK;
+}
+
+void free_plan_buffers(qmc_plan *p) {
+    for (ClassLaunch &c : p->launches) {
+        cudaFree(c.d_jobs);
+        cudaFree(c.d_partials);
+        cudaFree(c.d_queue);
+    }
+    p->launches.clear();
+    cudaFree(p->d_out);
+    cudaFree(p->d_status);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    for (cudaEvent_t e : p->kev) cudaEventDestroy(e);
+    p->kev.clear();
+    p->d_out = nullptr;
+    p->d_status = nullptr;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+extern "C" {
+
+int qmc_create(qmc_ctx **out, int device, const qmc_options *opt) {
+    if (!out) return QMC_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return QMC_E_CUDA;
+    if (device < 0 || device >= ndev) return QMC_E_INVAL;
+    qmc_ctx *ctx = new (std::nothrow) qmc_ctx();
+    if (!ctx) return QMC_E_NOMEM;
+    ctx->device = device;
+    if (opt) ctx->opt = *opt;
+    if (ctx->opt.shifts <= 0) ctx->opt.shifts = 32;
+    if (ctx->opt.seed == 0) ctx->opt.seed = 1;
+    if (ctx->opt.min_points == 0) ctx->opt.min_points = 10000;
+    if (ctx->opt.presamples <= 0) ctx->opt.presamples = 10000;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return QMC_E_CUDA;
+    }
+    ctx->sm_count = qmc_k_sm_count(device);
+    *out = ctx;
+    return QMC_OK;
+}
+
+void qmc_destroy(qmc_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (qmc_plan *p : ctx->plans) {
+        free_plan_buffers(p);
+        delete p;
+    }
+    ctx->plans.clear();
+    cudaFree(ctx->d_sectors);
+    cudaFree(ctx->d_monos);
+    cudaFree(ctx->d_kin);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int qmc_set_lattices(qmc_ctx *ctx, const uint64_t *n, const uint32_t *z, int count) {
+    if (!ctx || !n || !z || count <= 0) return fail(ctx, QMC_E_INVAL, "qmc_set_lattices: bad arguments");
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 2 || n[i] >= (1ULL << 32)) return fail(ctx, QMC_E_INVAL, "lattice n=%llu outside 2..2^32-1", (unsigned long long)n[i]);
+        std::vector<uint32_t> v(z + (size_t)i * 6, z + (size_t)i * 6 + 6);
+        for (uint32_t c : v) {
+            uint64_t a = c, b = n[i];
+            while (b) { uint64_t r = a % b; a = b; b = r; }
+            if (c == 0 || c >= n[i] || a != 1)
+                return fail(ctx, QMC_E_INVAL, "lattice n=%llu: component %u not in U_n", (unsigned long long)n[i], c);
+        }
+        ctx->lattices[n[i]] = v;
+    }
+    return QMC_OK;
+}
+
+int qmc_load_sectors_mem(qmc_ctx *ctx, const char *text, size_t len, int *integral_id) {
+    if (!ctx || !text) return fail(ctx, QMC_E_INVAL, "qmc_load_sectors_mem: null argument");
+    cudaSetDevice(ctx->device);
+    HostIntegral I;
+    int rc = parse_integral(ctx, std::string(text, len), I);
+    if (rc) return rc;
+    for (size_t si = 0; si < I.sectors.size(); ++si) {
+        rc = classify(ctx, I.sectors[si], (int)si);
+        if (rc) return rc;
+        I.max_poles = std::max(I.max_poles, I.sectors[si].ns);
+    }
+    ctx->integrals.push_back(std::move(I));
+    rc = upload_tables(ctx);
+    if (rc) {
+        ctx->integrals.pop_back();
+        return rc;
+    }
+    if (integral_id) *integral_id = (int)ctx->integrals.size() - 1;
+    return QMC_OK;
+}
+
+int qmc_load_sectors(qmc_ctx *ctx, const char *path, int *integral_id) {
+    if (!ctx || !path) return fail(ctx, QMC_E_INVAL, "qmc_load_sectors: null argument");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return fail(ctx, QMC_E_INVAL, "cannot open %s", path);
+    std::stringstream ss;
+    ss << f.rdbuf();
+    std::string s = ss.str();
+    return qmc_load_sectors_mem(ctx, s.data(), s.size(), integral_id);
+}
+
+int qmc_integral_info(qmc_ctx *ctx, int integral_id, int *nsectors, int *max_poles, int *prefactor_lo,
+                      qmc_c64 *prefactor, int cap, int *prefactor_len) {
+    if (!ctx || integral_id < 0 || integral_id >= (int)ctx->integrals.size())
+        return fail(ctx, QMC_E_INVAL, "bad integral id");
+    const HostIntegral &I = ctx->integrals[integral_id];
+    if (nsectors) *nsectors = (int)I.sectors.size();
+    if (max_poles) *max_poles = I.max_poles;
+    if (prefactor_lo) *prefactor_lo = I.pref_lo;
+    if (prefactor_len) *prefactor_len = (int)I.pref.size();
+    if (prefactor)
+        for (int i = 0; i < cap && i < (int)I.pref.size(); ++i) prefactor[i] = I.pref[i];
+    return QMC_OK;
+}
+
+int qmc_set_kinematics(qmc_ctx *ctx, const double *inv, int npoints, int ninv) {
+    if (!ctx || npoints < 0 || ninv < 0 || ninv > QMC_NCOEF - 1 || (npoints > 0 && ninv > 0 && !inv))
+        return fail(ctx, QMC_E_INVAL, "qmc_set_kinematics: bad arguments");
+    cudaSetDevice(ctx->device);
+    for (size_t i = 0; i < (size_t)npoints * ninv; ++i)
+        if (!std::isfinite(inv[i])) return fail(ctx, QMC_E_INVAL, "non-finite invariant at %zu", i);
+    cudaFree(ctx->d_kin);
+    ctx->d_kin = nullptr;
+    size_t bytes = std::max<size_t>(1, (size_t)npoints * ninv) * sizeof(double);
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_kin, bytes));
+    if (npoints * ninv > 0)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_kin, inv, (size_t)npoints * ninv * sizeof(double),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->npoints = npoints;
+    ctx->ninv = ninv;
+    return QMC_OK;
+}
+
+int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, qmc_plan **out) {
+    if (!ctx || !out || (njobs > 0 && !jobs) || njobs < 0 || norders < 1)
+        return fail(ctx, QMC_E_INVAL, "qmc_plan_create: bad arguments");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    const int hi = lo + norders - 1;
+    std::vector<std::vector<QmcJobDev>> per(QMC_NCLASS);
+    uint64_t out_off = 0;
+    for (int i = 0; i < njobs; ++i) {
+        const qmc_job &J = jobs[i];
+        if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size())
+            return fail(ctx, QMC_E_INVAL, "job %d: bad integral id %d", i, J.integral_id);
+        const HostIntegral &I = ctx->integrals[J.integral_id];
+        if (J.sector < 0 || J.sector >= (int)I.sectors.size())
+            return fail(ctx, QMC_E_INVAL, "job %d: bad sector %d", i, J.sector);
+        const HostSector &S = I.sectors[J.sector];
+        if ((int)I.invariants.size() != ctx->ninv && ctx->ninv * ctx->npoints > 0)
+            return fail(ctx, QMC_E_INVAL, "job %d: integral has %zu invariants, kinematics %d", i,
+                        I.invariants.size(), ctx->ninv);
+        if (J.point < 0 || (J.point >= ctx->npoints && !(I.invariants.empty() && J.point == 0)))
+            return fail(ctx, QMC_E_INVAL, "job %d: bad kinematic point %d", i, J.point);
+        if (J.shifts < 1) return fail(ctx, QMC_E_INVAL, "job %d: shifts < 1", i);
+        auto it = ctx->lattices.find(J.n);
+        if (it == ctx->lattices.end())
+            return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
+        if (norders > qmc_class_lmax(S.cls) || hi + S.ns + 1 > qmc_class_lmax(S.cls))
+            return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d with %d poles exceed the evaluator's series length %d",
+                        i, lo, hi, S.ns, qmc_class_lmax(S.cls));
+        if (S.cls == QMC_CLASS_REAL6)
+            return fail(ctx, QMC_E_INVAL, "job %d: sector needs the d<=6 evaluator, which this build lacks", i);
+        QmcJobDev D{};
+        D.sector = S.global_index;
+        D.point = I.invariants.empty() ? 0 : J.point;
+        D.shifts = J.shifts;
+        D.n = J.n;
+        D.seed_state = J.seed ^ (kGamma * (J.stream + 1));
+        D.out_off = out_off;
+        for (int j = 0; j < QMC_DMAX; ++j) {
+            D.z[j] = j < S.d ? it->second[j] : 0;
+            D.lambda[j] = (S.deform && j < S.d) ? J.lambda[j] : 0.0;
+        }
+        out_off += (uint64_t)J.shifts * norders * 2;
+        per[S.cls].push_back(D);
+    }
+    qmc_plan *p = new qmc_plan();
+    p->ctx = ctx;
+    p->lo = lo;
+    p->norders = norders;
+    p->njobs = njobs;
+    p->out_size = (size_t)out_off;
+    auto bail = [&](int rc) {
+        free_plan_buffers(p);
+        delete p;
+        return rc;
+    };
+#define PLAN_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return bail(fail(ctx, QMC_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)));        \
+    } while (0)
+    PLAN_TRY(cudaMalloc(&p->d_out, std::max<size_t>(1, p->out_size) * sizeof(double)));
+    PLAN_TRY(cudaMalloc(&p->d_status, 2 * sizeof(unsigned long long)));
+    PLAN_TRY(cudaMemset(p->d_status, 0, 2 * sizeof(unsigned long long)));
+    PLAN_TRY(cudaEventCreate(&p->ev0));
+    PLAN_TRY(cudaEventCreate(&p->ev1));
+    for (int cls = 0; cls < QMC_NCLASS; ++cls) {
+        std::vector<QmcJobDev> &v = per[cls];
+        if (v.empty()) continue;
+        ClassLaunch c;
+        c.cls = cls;
+        c.block = ctx->opt.block == 256 ? 256 : 128;
+        c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 4;
+        const uint64_t tile_k = (uint64_t)c.block * c.ppt;
+        uint64_t tiles = 0;
+        for (QmcJobDev &D : v) {
+            D.tiles_per_shift = (int32_t)((D.n + tile_k - 1) / tile_k);
+            D.tile_begin = tiles;
+            tiles += (uint64_t)D.tiles_per_shift * D.shifts;
+        }
+        PLAN_TRY(cudaMalloc(&c.d_jobs, v.size() * sizeof(QmcJobDev)));
+        PLAN_TRY(cudaMemcpy(c.d_jobs, v.data(), v.size() * sizeof(QmcJobDev), cudaMemcpyHostToDevice));
+        PLAN_TRY(cudaMalloc(&c.d_partials, std::max<uint64_t>(1, tiles) * 2 * norders * sizeof(double)));
+        PLAN_TRY(cudaMalloc(&c.d_queue, sizeof(unsigned long long)));
+        PLAN_TRY(cudaMemset(c.d_queue, 0, sizeof(unsigned long long)));
+        int occ = qmc_k_occupancy(cls, c.block);
+        if (occ < 1) occ = 1;
+        c.grid = (int)std::min<uint64_t>(tiles, (uint64_t)ctx->sm_count * occ);
+        if (c.grid < 1) c.grid = 1;
+        QmcLaunch &L = c.L;
+        L.sectors = ctx->d_sectors;
+        L.monos = ctx->d_monos;
+        L.kin = ctx->d_kin;
+        L.jobs = c.d_jobs;
+        L.njobs = (int)v.size();
+        L.ninv = ctx->ninv;
+        L.lo = lo;
+        L.norders = norders;
+        L.ntiles = tiles;
+        L.tile_k = (uint32_t)tile_k;
+        L.partials = c.d_partials;
+        L.queue = c.d_queue;
+        L.status = p->d_status;
+        L.out = p->d_out;
+        p->launches.push_back(c);
+    }
+    for (size_t i = 0; i < 2 * p->launches.size(); ++i) {
+        cudaEvent_t e;
+        PLAN_TRY(cudaEventCreate(&e));
+        p->kev.push_back(e);
+    }
+#undef PLAN_TRY
+    ctx->plans.push_back(p);
+    *out = p;
+    return QMC_OK;
+}
+
+size_t qmc_plan_output_size(const qmc_plan *plan) { return plan ? plan->out_size : 0; }
+
+int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
+    if (!plan) return QMC_E_INVAL;
+    qmc_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    double *out = out_dev ? out_dev : plan->d_out;
+    CUDA_TRY(ctx, cudaMemsetAsync(plan->d_status, 0, 2 * sizeof(unsigned long long), st));
+    CUDA_TRY(ctx, cudaEventRecord(plan->ev0, st));
+    int launches = 0;
+    for (size_t i = 0; i < plan->launches.size(); ++i) {
+        ClassLaunch &c = plan->launches[i];
+        c.L.out = out;
+        c.L.kin = ctx->d_kin;
+        CUDA_TRY(ctx, cudaEventRecord(plan->kev[2 * i], st));
+        if (c.L.ntiles > 0) {
+            if (qmc_k_launch_eval(c.cls, &c.L, c.block, c.ppt, c.grid, st))
+                return fail(ctx, QMC_E_CUDA, "evaluator launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            ++launches;
+        }
+        CUDA_TRY(ctx, cudaEventRecord(plan->kev[2 * i + 1], st));
+        if (qmc_k_launch_finish(&c.L, st))
+            return fail(ctx, QMC_E_CUDA, "finish launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        ++launches;
+    }
+    CUDA_TRY(ctx, cudaEventRecord(plan->ev1, st));
+    plan->last_stream = st;
+    plan->last_out = out;
+    plan->last_launches = launches;
+    return QMC_OK;
+}
+
+int qmc_plan_results(qmc_plan *plan, double *out, uint64_t *sign_failures) {
+    if (!plan) return QMC_E_INVAL;
+    qmc_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = plan->last_stream ? plan->last_stream : ctx->stream;
+    unsigned long long status[2] = {0, 0};
+    if (out && plan->out_size)
+        CUDA_TRY(ctx, cudaMemcpyAsync(out, plan->last_out ? plan->last_out : plan->d_out,
+                                      plan->out_size * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(status, plan->d_status, sizeof status, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (sign_failures) *sign_failures = status[0];
+    if (status[1]) return fail(ctx, QMC_E_NONFINITE, "%llu tile partial sums were not finite", status[1]);
+    if (status[0]) return fail(ctx, QMC_E_SIGN_CHECK, "%llu deformed points had Im F > 0", status[0]);
+    return QMC_OK;
+}
+
+int qmc_plan_last_time(qmc_plan *plan, float *ms_total, float *ms_eval, int *launches) {
+    if (!plan) return QMC_E_INVAL;
+    qmc_ctx *ctx = plan->ctx;
+    CUDA_TRY(ctx, cudaEventSynchronize(plan->ev1));
+    float t = 0.f, te = 0.f;
+    CUDA_TRY(ctx, cudaEventElapsedTime(&t, plan->ev0, plan->ev1));
+    for (size_t i = 0; i < plan->launches.size(); ++i) {
+        float x = 0.f;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&x, plan->kev[2 * i], plan->kev[2 * i + 1]));
+        te += x;
+    }
+    if (ms_total) *ms_total = t;
+    if (ms_eval) *ms_eval = te;
+    if (launches) *launches = plan->last_launches;
+    return QMC_OK;
+}
+
+void qmc_plan_destroy(qmc_plan *plan) {
+    if (!plan) return;
+    qmc_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(plan->last_stream ? plan->last_stream : ctx->stream);
+    free_plan_buffers(plan);
+    ctx->plans.erase(std::remove(ctx->plans.begin(), ctx->plans.end(), plan), ctx->plans.end());
+    delete plan;
+}
+
+int qmc_eval_jobs(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, double *out) {
+    qmc_plan *p = nullptr;
+    int rc = qmc_plan_create(ctx, jobs, njobs, lo, norders, &p);
+    if (rc) return rc;
+    rc = qmc_plan_run(p, nullptr, nullptr);
+    if (!rc) rc = qmc_plan_results(p, out, nullptr);
+    qmc_plan_destroy(p);
+    return rc;
+}
+
+int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d, const double *delta,
+                       uint64_t k0, uint64_t count, double *x, uint64_t *r) {
+    if (!ctx || !z || !delta || !x || d < 1 || d > QMC_DMAX || n < 2 || n >= (1ULL << 32))
+        return fail(ctx, QMC_E_INVAL, "qmc_lattice_points: bad arguments");
+    cudaSetDevice(ctx->device);
+    uint32_t *dz = nullptr;
+    double *dd = nullptr, *dx = nullptr;
+    uint64_t *dr = nullptr;
+    int rc = QMC_OK;
+    do {
+        if (cudaMalloc(&dz, d * sizeof(uint32_t)) || cudaMalloc(&dd, d * sizeof(double)) ||
+            cudaMalloc(&dx, std::max<uint64_t>(1, count) * d * sizeof(double)) ||
+            (r && cudaMalloc(&dr, std::max<uint64_t>(1, count) * d * sizeof(uint64_t)))) {
+            rc = fail(ctx, QMC_E_CUDA, "qmc_lattice_points: allocation failed");
+            break;
+        }
+        cudaMemcpyAsync(dz, z, d * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(dd, delta, d * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (qmc_k_lattice_points(n, dz, d, dd, k0, count, dx, dr, ctx->stream)) {
+            rc = fail(ctx, QMC_E_CUDA, "lattice kernel launch failed");
+            break;
+        }
+        cudaMemcpyAsync(x, dx, count * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (r) cudaMemcpyAsync(r, dr, count * d * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = fail(ctx, QMC_E_CUDA, "qmc_lattice_points: %s", cudaGetErrorString(e));
+    } while (0);
+    cudaFree(dz);
+    cudaFree(dd);
+    cudaFree(dx);
+    cudaFree(dr);
+    return rc;
+}
+
+int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta) {
+    if (!ctx || !delta || m < 1 || d < 1) return fail(ctx, QMC_E_INVAL, "qmc_shifts: bad arguments");
+    cudaSetDevice(ctx->device);
+    double *dd = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&dd, (size_t)m * d * sizeof(double)));
+    int rc = qmc_k_shifts(seed ^ (kGamma * (stream + 1)), m, d, dd, ctx->stream);
+    if (!rc) {
+        cudaMemcpyAsync(delta, dd, (size_t)m * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = QMC_E_CUDA;
+    } else {
+        rc = QMC_E_CUDA;
+    }
+    cudaFree(dd);
+    return rc ? fail(ctx, rc, "qmc_shifts failed") : QMC_OK;
+}
+
+int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {
+    if (!ctx || !gflops) return QMC_E_INVAL;
+    cudaSetDevice(ctx->device);
+    double *d = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&d, 2 * sizeof(double)));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int block = 256, grid = ctx->sm_count * 8, iters = 4096;
+    qmc_k_fp64_probe(d, 64, grid, block, ctx->stream);  // warm-up
+    cudaEventRecord(a, ctx->stream);
+    qmc_k_fp64_probe(d, iters, grid, block, ctx->stream);
+    cudaEventRecord(b, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ctx, QMC_E_CUDA, "fp64 probe: %s", cudaGetErrorString(e));
+    const double flops = 2.0 * 8.0 * iters * (double)grid * block;
+    *gflops = flops / (ms * 1e-3) / 1e9;
+    return QMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Internal layouts shared by the host library (qmc_host.cpp) and the kernels
+// (qmc_kernels.cu). Not part of the public C-ABI.
+#pragma once
+#include <cstdint>
+
+#define QMC_DMAX 6          // integration variables per sector
+#define QMC_SMAX 4          // logarithmically singular variables per sector
+#define QMC_NCOEF 4         // 1 + up to 3 kinematic invariants per coefficient
+#define QMC_EMAX 4          // largest exponent of one variable in one monomial
+#define QMC_MAXMONO 160     // monomials per sector (U, F and, if deformed, dF, d2F)
+#define QMC_NGROUP (1 << QMC_SMAX)
+#define QMC_NHESS (QMC_DMAX * (QMC_DMAX + 1) / 2)
+
+// One monomial c(inv) * prod_j t_j^{e_j}; exponents packed 4 bits per variable.
+struct QmcMono {
+    uint32_t exps;
+    uint32_t pad;
+    double coef[QMC_NCOEF];   // c_0 + c_1 inv_1 + ...
+};
+
+// Per-sector description as the kernels read it. Monomials of U and F are
+// sorted by their mask of singular variables (bit q set if the monomial
+// contains t_{sing[q]}); group g of U is monomials [gU[g], gU[g+1]) counted
+// from monoU. Deformed sectors also carry dF/dt_j and d2F/dt_j dt_k tables.
+struct QmcSectorDev {
+    int32_t d, ns, nU, nF;
+    int32_t deform, u0_int, f0_int, ninv;   // u0_int/f0_int: 1 if the exponent is an integer
+    int32_t monoU, monoF, nmono, pad0;      // offsets into the global monomial array
+    int32_t a[QMC_DMAX];
+    int32_t sing[QMC_SMAX];                 // variable index of singular slot q
+    int32_t regular_mask;                   // bit j: j not singular and (a_j != 0 or b_j != 0)
+    int32_t pad1;
+    int32_t gU[QMC_NGROUP + 1];
+    int32_t gF[QMC_NGROUP + 1];
+    int32_t dFoff[QMC_DMAX], dFn[QMC_DMAX];   // relative to monoF + nF
+    int32_t Hoff[QMC_NHESS], Hn[QMC_NHESS];   // j <= k packed row-major
+    double b[QMC_DMAX];
+    double u0, u1, f0, f1;
+};
+
+// One evaluation job: (sector, kinematic point) with its lattice and shifts.
+struct QmcJobDev {
+    int32_t sector;        // index into the sector table
+    int32_t point;         // kinematic point
+    int32_t shifts;        // m
+    int32_t tiles_per_shift;
+    uint64_t n;            // lattice size
+    uint64_t tile_begin;   // first global tile of this job
+    uint64_t seed_state;   // splitmix64 state for this job's shifts
+    uint64_t out_off;      // offset (in doubles) of [shifts][norders][2] in the output
+    uint32_t z[QMC_DMAX];  // generating vector
+    int32_t pad;
+    double lambda[QMC_DMAX];
+};
+
+struct QmcLaunch {
+    const QmcSectorDev *sectors;
+    const QmcMono *monos;
+    const double *kin;     // [npoints][ninv]
+    const QmcJobDev *jobs;
+    int32_t njobs;
+    int32_t ninv;
+    int32_t lo;            // lowest eps order written
+    int32_t norders;
+    uint64_t ntiles;
+    uint32_t tile_k;       // points per tile = block * ppt
+    uint32_t pad;
+    double *partials;      // [ntiles][norders][2]
+    unsigned long long *queue;   // tile counter (reset by the finish kernel)
+    unsigned long long *status;  // [0]: sign-check failures, [1]: non-finite partials
+    double *out;           // per-shift sums
+};
+
+// Kernel classes (compile-time sizes of the evaluator).
+enum QmcClass {
+    QMC_CLASS_REAL3 = 0,   // real integrand, d <= 3, <= 2 singular variables
+    QMC_CLASS_CPLX3 = 1,   // contour-deformed, d <= 3, <= 2 singular variables
+    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6, <= 4 singular variables
+    QMC_NCLASS = 3
+};
+
+// Series length (orders) each class supports: K + ns + 1 <= class_lmax.
+static inline int qmc_class_lmax(int cls) { return cls == QMC_CLASS_REAL6 ? 6 : 4; }
+static inline int qmc_class_dmax(int cls) { return cls == QMC_CLASS_REAL6 ? 6 : 3; }
+static inline int qmc_class_smax(int cls) { return cls == QMC_CLASS_REAL6 ? 4 : 2; }
+
+extern "C" {
+// Launch helpers implemented in qmc_kernels.cu (all asynchronous on `stream`).
+int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt, int grid, void *stream);
+int qmc_k_launch_finish(const QmcLaunch *L, void *stream);
+int qmc_k_lattice_points(uint64_t n, const uint32_t *z_dev, int d, const double *delta_dev,
+                         uint64_t k0, uint64_t count, double *x_dev, uint64_t *r_dev, void *stream);
+int qmc_k_fp64_probe(double *out_dev, int iters, int grid, int block, void *stream);
+int qmc_k_sm_count(int device);
+}

@@ -1,0 +1,274 @@
+"""Python binding of the C-ABI in include/qmc.h (argument marshalling only).
+
+Every function keeps the C name. Arrays go in as numpy arrays (host) or as
+raw device pointers (ints, e.g. ``torch_tensor.data_ptr()``); streams as raw
+``cudaStream_t`` values (``torch.cuda.current_stream().cuda_stream``).
+All computation happens in libqmc.so; there is no Python or CPU fallback:
+if the library is missing or no GPU is usable, calls raise ``QmcError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+P = ctypes.POINTER
+_lock = threading.Lock()
+_lib = None
+
+QMC_OK = 0
+ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIMEOUT",
+          -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
+
+
+class QmcError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qmc_options(ctypes.Structure):
+    _fields_ = [("shifts", ctypes.c_int), ("seed", ctypes.c_uint64), ("block", ctypes.c_int),
+                ("ppt", ctypes.c_int), ("min_points", ctypes.c_uint64),
+                ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class qmc_job(ctypes.Structure):
+    _fields_ = [("integral_id", ctypes.c_int32), ("sector", ctypes.c_int32),
+                ("point", ctypes.c_int32), ("shifts", ctypes.c_int32), ("n", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint64),
+                ("lambda_", ctypes.c_double * 6)]
+
+
+class qmc_c64(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libqmc.so (building it first if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise QmcError(-3, f"libqmc.so missing at {path}")
+            L = ctypes.CDLL(path)
+            vp, i32, u64, dbl, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t
+            sig = {
+                "qmc_create": ([P(vp), i32, P(qmc_options)], i32),
+                "qmc_destroy": ([vp], None),
+                "qmc_last_error": ([vp], ctypes.c_char_p),
+                "qmc_set_lattices": ([vp, P(u64), P(ctypes.c_uint32), i32], i32),
+                "qmc_load_sectors_mem": ([vp, ctypes.c_char_p, sz, P(i32)], i32),
+                "qmc_load_sectors": ([vp, ctypes.c_char_p, P(i32)], i32),
+                "qmc_integral_info": ([vp, i32, P(i32), P(i32), P(i32), P(qmc_c64), i32, P(i32)], i32),
+                "qmc_set_kinematics": ([vp, P(dbl), i32, i32], i32),
+                "qmc_plan_create": ([vp, P(qmc_job), i32, i32, i32, P(vp)], i32),
+                "qmc_plan_output_size": ([vp], sz),
+                "qmc_plan_run": ([vp, vp, vp], i32),
+                "qmc_plan_results": ([vp, P(dbl), P(u64)], i32),
+                "qmc_plan_last_time": ([vp, P(ctypes.c_float), P(ctypes.c_float), P(i32)], i32),
+                "qmc_plan_destroy": ([vp], None),
+                "qmc_eval_jobs": ([vp, P(qmc_job), i32, i32, i32, P(dbl)], i32),
+                "qmc_lattice_points": ([vp, u64, P(ctypes.c_uint32), i32, P(dbl), u64, u64, P(dbl),
+                                        P(u64)], i32),
+                "qmc_shifts": ([vp, u64, u64, i32, i32, P(dbl)], i32),
+                "qmc_fp64_peak": ([vp, P(dbl)], i32),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding expects libqmc.so to export."""
+    return ["qmc_create", "qmc_destroy", "qmc_last_error", "qmc_set_lattices",
+            "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
+            "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
+            "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
+            "qmc_shifts", "qmc_fp64_peak"]
+
+
+def _dp(a):
+    return a.ctypes.data_as(P(ctypes.c_double))
+
+
+def _check(ctx, rc):
+    if rc != QMC_OK:
+        msg = lib().qmc_last_error(ctx).decode() if ctx else ""
+        raise QmcError(rc, msg)
+
+
+# ------------------------------------------------------------------ C names
+def qmc_create(device: int = 0, **opts):
+    o = qmc_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    rc = lib().qmc_create(ctypes.byref(h), device, ctypes.byref(o))
+    if rc != QMC_OK:
+        raise QmcError(rc, "qmc_create failed (no usable CUDA device?)")
+    return h
+
+
+def qmc_destroy(ctx):
+    lib().qmc_destroy(ctx)
+
+
+def qmc_last_error(ctx) -> str:
+    return lib().qmc_last_error(ctx).decode()
+
+
+def qmc_set_lattices(ctx, n, z):
+    n = np.ascontiguousarray(n, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint32).reshape(len(n), 6)
+    _check(ctx, lib().qmc_set_lattices(ctx, n.ctypes.data_as(P(ctypes.c_uint64)),
+                                       z.ctypes.data_as(P(ctypes.c_uint32)), len(n)))
+
+
+def qmc_load_sectors_mem(ctx, text: str) -> int:
+    b = text.encode()
+    iid = ctypes.c_int()
+    _check(ctx, lib().qmc_load_sectors_mem(ctx, b, len(b), ctypes.byref(iid)))
+    return iid.value
+
+
+def qmc_load_sectors(ctx, path: str) -> int:
+    iid = ctypes.c_int()
+    _check(ctx, lib().qmc_load_sectors(ctx, path.encode(), ctypes.byref(iid)))
+    return iid.value
+
+
+def qmc_integral_info(ctx, integral_id: int):
+    ns, mp, lo, ln = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    buf = (qmc_c64 * 64)()
+    _check(ctx, lib().qmc_integral_info(ctx, integral_id, ctypes.byref(ns), ctypes.byref(mp),
+                                        ctypes.byref(lo), buf, 64, ctypes.byref(ln)))
+    return ns.value, mp.value, lo.value, [complex(buf[i].re, buf[i].im) for i in range(ln.value)]
+
+
+def qmc_set_kinematics(ctx, inv):
+    inv = np.ascontiguousarray(inv, dtype=np.float64)
+    if inv.ndim == 1:
+        inv = inv.reshape(-1, 1) if inv.size else inv.reshape(0, 0)
+    npts, ninv = inv.shape
+    _check(ctx, lib().qmc_set_kinematics(ctx, _dp(inv), npts, ninv))
+
+
+def make_jobs(specs):
+    """specs: iterable of dicts with integral_id, sector, point, shifts, n, seed, stream, lambda."""
+    specs = list(specs)
+    arr = (qmc_job * max(1, len(specs)))()
+    for i, s in enumerate(specs):
+        arr[i].integral_id = s["integral_id"]
+        arr[i].sector = s["sector"]
+        arr[i].point = s.get("point", 0)
+        arr[i].shifts = s["shifts"]
+        arr[i].n = s["n"]
+        arr[i].seed = s.get("seed", 1)
+        arr[i].stream = s.get("stream", 0)
+        lam = np.broadcast_to(np.asarray(s.get("lambda", 0.0), dtype=np.float64), (6,))
+        for j in range(6):
+            arr[i].lambda_[j] = float(lam[j])
+    return arr, len(specs)
+
+
+def qmc_plan_create(ctx, jobs, njobs: int, lo: int, norders: int):
+    h = ctypes.c_void_p()
+    _check(ctx, lib().qmc_plan_create(ctx, jobs, njobs, lo, norders, ctypes.byref(h)))
+    return h
+
+
+def qmc_plan_output_size(plan) -> int:
+    return lib().qmc_plan_output_size(plan)
+
+
+def qmc_plan_run(ctx, plan, out_dev_ptr=None, stream_ptr=None):
+    _check(ctx, lib().qmc_plan_run(plan, ctypes.c_void_p(out_dev_ptr or 0) if out_dev_ptr else None,
+                                   ctypes.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def qmc_plan_results(ctx, plan, out=None, check=True):
+    size = qmc_plan_output_size(plan)
+    if out is None:
+        out = np.zeros(size, dtype=np.float64)
+    fails = ctypes.c_uint64()
+    rc = lib().qmc_plan_results(plan, _dp(out) if size else None, ctypes.byref(fails))
+    if check:
+        _check(ctx, rc)
+    return out, fails.value, rc
+
+
+def qmc_plan_last_time(ctx, plan):
+    ms, mse, nl = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+    _check(ctx, lib().qmc_plan_last_time(plan, ctypes.byref(ms), ctypes.byref(mse), ctypes.byref(nl)))
+    return ms.value, mse.value, nl.value
+
+
+def qmc_plan_destroy(plan):
+    lib().qmc_plan_destroy(plan)
+
+
+def qmc_eval_jobs(ctx, jobs, njobs: int, lo: int, norders: int, size: int):
+    out = np.zeros(size, dtype=np.float64)
+    _check(ctx, lib().qmc_eval_jobs(ctx, jobs, njobs, lo, norders, _dp(out)))
+    return out
+
+
+def qmc_lattice_points(ctx, n: int, z, delta, k0: int, count: int):
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    d = len(z)
+    delta = np.ascontiguousarray(delta, dtype=np.float64).reshape(d)
+    x = np.zeros((count, d), dtype=np.float64)
+    r = np.zeros((count, d), dtype=np.uint64)
+    _check(ctx, lib().qmc_lattice_points(ctx, n, z.ctypes.data_as(P(ctypes.c_uint32)), d, _dp(delta),
+                                         k0, count, _dp(x), r.ctypes.data_as(P(ctypes.c_uint64))))
+    return x, r
+
+
+def qmc_shifts(ctx, seed: int, stream: int, m: int, d: int):
+    out = np.zeros((m, d), dtype=np.float64)
+    _check(ctx, lib().qmc_shifts(ctx, seed, stream, m, d, _dp(out)))
+    return out
+
+
+def qmc_fp64_peak(ctx) -> float:
+    g = ctypes.c_double()
+    _check(ctx, lib().qmc_fp64_peak(ctx, ctypes.byref(g)))
+    return g.value
+
+
+# ------------------------------------------------------------------ helpers
+def load_lattice_table(ctx):
+    """Install the committed CBC table (inputs/cbc_table.txt) into a context."""
+    from .inputs.lattice import load_table
+
+    rows = load_table()
+    n = np.array([r[0] for r in rows], dtype=np.uint64)
+    z = np.array([list(r[1]) + [1] * (6 - len(r[1])) for r in rows], dtype=np.uint32)
+    qmc_set_lattices(ctx, n, z)
+    return rows
+
+
+def jobs_for_integral(integral_id: int, nsectors: int, npoints: int, n: int, shifts: int, seed=1,
+                      lam=0.0, stream_base: int = 0):
+    """One job per (point, sector); shift stream id = stream_base + point * nsectors + sector."""
+    specs = []
+    for p in range(npoints):
+        for s in range(nsectors):
+            L = lam[p][s] if hasattr(lam, "__len__") else lam
+            specs.append(dict(integral_id=integral_id, sector=s, point=p, shifts=shifts, n=n,
+                              seed=seed, stream=stream_base + p * nsectors + s, **{"lambda": L}))
+    return specs

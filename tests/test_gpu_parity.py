@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Bit-exact: lattice indices r, shifted points x, random shifts. FP64 per-shift
+sums: within RTOL = 1e-12 of the oracle (see tests/parity.py for the
+derivation). Sizes span several tiles and a ragged tail (every n is prime,
+so no tile size divides it); the full-size case is the bench workload.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_19768_gb300 import qmc
+from paper_2305_19768_gb300.inputs import workloads as w
+from paper_2305_19768_gb300.inputs.lattice import lattice_for, lattice_sizes
+
+from parity import Gpu, assert_close, oracle_sums
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    g = Gpu()
+    yield g
+    g.close()
+
+
+def _specs(iid, sectors, points, n, m, seed=1, lam=0.0, nsec_total=None):
+    nsec_total = nsec_total or len(sectors)
+    out = []
+    for p in points:
+        for s in sectors:
+            out.append(dict(integral_id=iid, sector=s, point=p, shifts=m, n=n, seed=seed,
+                            stream=p * nsec_total + s, **{"lambda": lam}))
+    return out
+
+
+# ---------------------------------------------------------------- bit-exact
+@pytest.mark.parametrize("n,d", [(1009, 3), (1000003, 3), (100000007, 6), (4294967291, 2)])
+def test_lattice_points_bit_exact(gpu, n, d):
+    if n in lattice_sizes():
+        z = np.array(lattice_for(n, d)[1], dtype=np.uint32)
+    else:
+        z = np.array([4294967290, 3000000019][:d], dtype=np.uint32)
+    delta = oracle.shifts(5, 3, 1, d)[0]
+    for k0 in (0, n // 3, n - 777):
+        cnt = min(777, n - k0)
+        xg, rg = qmc.qmc_lattice_points(gpu.ctx, n, z, delta, k0, cnt)
+        xo, ro = oracle.lattice_points(n, z, delta, k0, cnt)
+        assert np.array_equal(rg, ro)
+        assert np.array_equal(xg.view(np.uint64), xo.view(np.uint64))
+
+
+def test_shifts_bit_exact(gpu):
+    for seed, stream, m, d in ((1, 0, 32, 3), (12345, 77, 7, 6), (2**63 + 5, 2**40, 3, 2)):
+        g = qmc.qmc_shifts(gpu.ctx, seed, stream, m, d)
+        o = oracle.shifts(seed, stream, m, d)
+        assert np.array_equal(g.view(np.uint64), o.view(np.uint64))
+
+
+# ---------------------------------------------------------------- FP64 sums
+def _compare_integral(gpu, I, inv_points, n, m, lo, norders, lam=None, sectors=None, seed=1):
+    iid = gpu.load(I)
+    inv_arr = np.array(inv_points, dtype=np.float64).reshape(len(inv_points), -1)
+    qmc.qmc_set_kinematics(gpu.ctx, inv_arr if inv_arr.shape[1] else np.zeros((0, 0)))
+    sectors = list(range(len(I.sectors))) if sectors is None else sectors
+    pts = list(range(len(inv_points)))
+    specs = _specs(iid, sectors, pts, n, m, seed=seed, lam=lam if lam is not None else 0.0,
+                   nsec_total=len(I.sectors))
+    out, fails, rc = gpu.eval(iid, specs, lo, norders)
+    assert rc == 0, qmc.qmc_last_error(gpu.ctx)
+    out = out.reshape(len(specs), m, norders, 2)
+    worst = 0.0
+    for i, sp in enumerate(specs):
+        o, a, _ = oracle_sums(I, sp["sector"], list(inv_points[sp["point"]]), n, m, seed,
+                              sp["stream"], lo, norders, lam)
+        worst = max(worst, assert_close(out[i], o, a, what=f"sector {sp['sector']} point {sp['point']}"))
+    return worst
+
+
+def test_triangle_massive_sums(gpu):
+    I = w.triangle_massive()
+    _compare_integral(gpu, I, [[]], 10007, 8, 0, 1)
+
+
+def test_massless_box_sums(gpu):
+    I = w.box_massless()
+    _compare_integral(gpu, I, [[-3.0, -2.0]], 20011, 4, -2, 3)
+
+
+def test_massless_box_two_points_more_orders(gpu):
+    I = w.box_massless()
+    _compare_integral(gpu, I, [[-3.0, -2.0], [-5.0, -1.0]], 4001, 3, -2, 4, sectors=[0, 5, 11])
+
+
+def test_deformed_massive_box_sums(gpu):
+    I = w.box_massive()
+    pts = [[12.0, -3.0], [7.5, -1.5], [19.0, -7.0]]
+    _compare_integral(gpu, I, pts, 10007, 4, 0, 1, lam=0.3)
+
+
+def test_deformed_bubbles_and_triangle(gpu):
+    _compare_integral(gpu, w.bubble(1, "s"), [[10.0]], 4001, 4, 0, 2, lam=0.5)
+    _compare_integral(gpu, w.bubble(0, "s"), [[10.0]], 4001, 4, 0, 2, lam=0.5)
+    _compare_integral(gpu, w.triangle_one_offshell(0, "s"), [[10.0]], 4001, 4, -2, 3, lam=0.3)
+
+
+def test_tiny_lattices_below_one_tile(gpu):
+    # n smaller than one tile and than one thread's PPT span; custom lattices
+    I = w.box_massless()
+    iid = gpu.load(I)
+    qmc.qmc_set_kinematics(gpu.ctx, np.array([[-3.0, -2.0]]))
+    for n, z in ((2, [1, 1, 1]), (3, [1, 2, 1]), (7, [1, 3, 2]), (131, [1, 37, 55])):
+        qmc.qmc_set_lattices(gpu.ctx, np.array([n], dtype=np.uint64),
+                             np.array([z + [1, 1, 1]], dtype=np.uint32))
+        specs = _specs(iid, [0, 4], [0], n, 2, nsec_total=12)
+        out, _, rc = gpu.eval(iid, specs, -2, 3)
+        assert rc == 0
+        out = out.reshape(2, 2, 3, 2)
+        for i, sp in enumerate(specs):
+            view = oracle.SectorView(I, sp["sector"], [-3.0, -2.0])
+            dl = oracle.shifts(1, sp["stream"], 2, 3)
+            o, a, _ = oracle.shift_sums(view, n, z, dl, -2, 3)
+            assert_close(out[i], o, a, what=f"n={n}")
+
+
+def test_full_size_sampled_outputs():
+    """Bench workload (massless box, n = 1000003, m = 32, all 12 sectors, same
+    launch configuration as bench.py); the oracle recomputes sampled
+    (sector, shift) outputs one by one at full n."""
+    g = Gpu()
+    try:
+        I = w.box_massless()
+        iid = g.load(I)
+        qmc.qmc_set_kinematics(g.ctx, np.array([[-3.0, -2.0]]))
+        n, m = 1000003, 32
+        specs = _specs(iid, list(range(12)), [0], n, m)
+        out, _, rc = g.eval(iid, specs, -2, 3)
+        assert rc == 0
+        out = out.reshape(12, m, 3, 2)
+        for sector, shift in ((0, 0), (5, 17), (11, 31)):
+            o, a, _ = oracle_sums(I, sector, [-3.0, -2.0], n, m, 1, sector, -2, 3, shift_rows=[shift])
+            assert_close(out[sector, shift][None], o, a, what=f"full-size sector {sector} shift {shift}")
+        # property at any size: the mean over shifts reproduces the closed form
+        from golden_values import closed_form
+        ex = closed_form("box1L_massless", "s=-3,t=-2")
+        sec = out[..., 0] + 1j * out[..., 1]       # [12][m][3]
+        tot = sec.sum(axis=0)                       # [m][3] sector sum per shift
+        pref = np.array(I.prefactor)
+        res = np.array([[sum(pref[p] * tot[s, o - p] for p in range(o + 1)) for o in range(3)]
+                        for s in range(m)])
+        mean = res.mean(0)
+        err = res.real.std(0, ddof=1) / np.sqrt(m)
+        for o, order in enumerate((-2, -1, 0)):
+            assert abs(mean[o] - ex[order]) <= 4 * err[o] + 1e-12
+    finally:
+        g.close()
+
+
+# ---------------------------------------------------------------- status / errors
+def test_sign_check_reported(gpu):
+    I = w.box_massive()
+    iid = gpu.load(I)
+    qmc.qmc_set_kinematics(gpu.ctx, np.array([[12.0, -3.0]]))
+    specs = _specs(iid, [0], [0], 1009, 2, lam=-0.3, nsec_total=4)
+    out, fails, rc = gpu.eval(iid, specs, 0, 1)
+    assert rc == -6 and fails > 0
+    specs = _specs(iid, [0], [0], 1009, 2, lam=0.3, nsec_total=4)
+    out, fails, rc = gpu.eval(iid, specs, 0, 1)
+    assert rc == 0 and fails == 0
+
+
+def test_invalid_inputs_rejected(gpu):
+    I = w.box_massless()
+    iid = gpu.load(I)
+    qmc.qmc_set_kinematics(gpu.ctx, np.array([[-3.0, -2.0]]))
+    with pytest.raises(qmc.QmcError) as e:
+        jobs, nj = qmc.make_jobs(_specs(iid, [0], [0], 1000, 2, nsec_total=12))  # 1000 not tabulated
+        qmc.qmc_plan_create(gpu.ctx, jobs, nj, -2, 3)
+    assert e.value.code == -1
+    with pytest.raises(qmc.QmcError) as e:
+        qmc.qmc_load_sectors_mem(gpu.ctx, "qmc-sectors 1 name broken")
+    assert e.value.code == -2
+    bad = I.to_text().replace("a -1 -1 0", "a -2 -1 0", 1)
+    with pytest.raises(qmc.QmcError) as e:
+        qmc.qmc_load_sectors_mem(gpu.ctx, bad)
+    assert e.value.code == -1
+    with pytest.raises(qmc.QmcError) as e:
+        qmc.qmc_set_lattices(gpu.ctx, np.array([10], dtype=np.uint64), np.array([[2, 1, 1, 1, 1, 1]]))
+    assert e.value.code == -1
