@@ -416,7 +416,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
             for (int k = j; k < DMAX; ++k) {
                 H[j][k] = 0.0;
                 if (j < d && k < d) {
-                    const int h = j * DMAX - j * (j - 1) / 2 + (k - j);
+                    const int h = j * QMC_DMAX - j * (j - 1) / 2 + (k - j);  // host packing order
                     H[j][k] = poly_sum<DMAX, double>(S.exps, S.cval, dbase + sec.Hoff[h],
                                                      dbase + sec.Hoff[h] + sec.Hn[h], tp);
                 }
