@@ -183,7 +183,8 @@ def main():
     plan = qmc.qmc_plan_create(ctx, jobs, nj, LO, NORD)
     out_n = qmc.qmc_plan_output_size(plan)
     out_dev = torch.empty(out_n, dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()           # a real stream handle: the plan runs on it
+    torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     evals_per_step = nsec * args.shifts * args.n

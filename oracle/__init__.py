@@ -154,19 +154,23 @@ def integrand_at(view: SectorView, t, lo: int, norders: int):
 
 
 def shift_sums(view: SectorView, n: int, z, delta, lo: int, norders: int, k0: int = 0,
-               k1: int | None = None, nthreads: int = 0):
-    """Per-shift estimates [m][norders][2], absolute scale [m][norders], sign failures."""
+               k1: int | None = None, nthreads: int = 0, with_cond: bool = False):
+    """Per-shift estimates [m][norders][2], absolute mass (1/n) sum |f| [m][norders],
+    sign failures; with ``with_cond`` also the corner-term mass [m][norders]
+    (the size of what cancels inside the subtraction)."""
     z = np.ascontiguousarray(z, dtype=np.uint32)
     delta = np.ascontiguousarray(delta, dtype=np.float64)
     m = delta.shape[0]
     out = np.zeros((m, norders, 2))
-    absout = np.zeros((m, norders))
+    absout = np.zeros((2 * m, norders))
     if k1 is None:
         k1 = n
     fails = lib().orc_shift_sums(ctypes.byref(view.st), n, z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                  m, _dptr(delta), k0, k1, lo, norders, _dptr(out), _dptr(absout),
                                  nthreads)
-    return out, absout, fails
+    if with_cond:
+        return out, absout[:m], fails, absout[m:]
+    return out, absout[:m], fails
 
 
 def max_threads() -> int:

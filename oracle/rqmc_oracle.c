@@ -304,7 +304,7 @@ static series G_series(const orc_sector *S, const double *tp, const double *omtp
  * integral (each j in S: int t^{-1+b eps} g = g(0)/(b eps) + int t^{-1+b eps}(g - g(0))).
  * Returns coefficients of eps^lo .. eps^hi in out[(o - lo)]. */
 static void integrand_series(const orc_sector *S, const double *t, const double *omt, int lo,
-                             int hi, cplx *out, int *signfail) {
+                             int hi, cplx *out, double *cond, int *signfail) {
     int d = S->d;
     int sing[ORC_SMAX], ns = 0;
     for (int j = 0; j < d; ++j)
@@ -340,14 +340,21 @@ static void integrand_series(const orc_sector *S, const double *t, const double 
             term = s_mul(&term, &fac, H);
         }
         total = s_add(&total, &term, hi);
+        if (cond)
+            for (int o = lo; o <= hi; ++o) {
+                cplx c = s_coef(&term, o);
+                cond[o - lo] += fabs(creal(c)) + fabs(cimag(c));
+            }
     }
     for (int o = lo; o <= hi; ++o) out[o - lo] = s_coef(&total, o);
 }
 
 /* Integrand times the korobov3 weight at the raw lattice point u[d].
- * out[(o - lo) * 2 + {0,1}] = Re, Im. Returns 0 if the point contributes 0. */
-int orc_point_value(const orc_sector *S, const double *u, int lo, int norders, double *out,
-                    int *signfail) {
+ * out[(o - lo) * 2 + {0,1}] = Re, Im; cond[o - lo] (may be NULL) = W times
+ * the sum over subtraction corners of |Re| + |Im| of each corner's term (the
+ * size of what cancels). Returns 0 if the point contributes 0. */
+static int point_value_cond(const orc_sector *S, const double *u, int lo, int norders,
+                            double *out, double *cond, int *signfail) {
     int d = S->d;
     double t[ORC_DMAX], omt[ORC_DMAX], W = 1.0;
     for (int o = 0; o < 2 * norders; ++o) out[o] = 0.0;
@@ -360,12 +367,19 @@ int orc_point_value(const orc_sector *S, const double *u, int lo, int norders, d
     for (int j = 0; j < d; ++j)
         if (t[j] == 0.0) return 0;
     cplx vals[ORC_LMAX];
-    integrand_series(S, t, omt, lo, lo + norders - 1, vals, signfail);
+    double cnd[ORC_LMAX] = {0};
+    integrand_series(S, t, omt, lo, lo + norders - 1, vals, cnd, signfail);
     for (int o = 0; o < norders; ++o) {
         out[2 * o] = W * creal(vals[o]);
         out[2 * o + 1] = W * cimag(vals[o]);
+        if (cond) cond[o] = W * cnd[o];
     }
     return 1;
+}
+
+int orc_point_value(const orc_sector *S, const double *u, int lo, int norders, double *out,
+                    int *signfail) {
+    return point_value_cond(S, u, lo, norders, out, NULL, signfail);
 }
 
 /* Integrand (no weight) at a transformed point t in (0,1]^d: used by the
@@ -375,7 +389,7 @@ void orc_integrand_at(const orc_sector *S, const double *t, int lo, int norders,
     double omt[ORC_DMAX];
     cplx vals[ORC_LMAX];
     for (int j = 0; j < S->d; ++j) omt[j] = 1.0 - t[j];
-    integrand_series(S, t, omt, lo, lo + norders - 1, vals, signfail);
+    integrand_series(S, t, omt, lo, lo + norders - 1, vals, NULL, signfail);
     for (int o = 0; o < norders; ++o) {
         out[2 * o] = creal(vals[o]);
         out[2 * o + 1] = cimag(vals[o]);
@@ -395,7 +409,9 @@ static void neum_add(neum *a, double x) {
 
 /* Per-shift estimates Q_s = (1/n) sum_{k=k0}^{k1-1} f(x_k + Delta_s) for each
  * eps order, out[(s * norders + o) * 2 + {re, im}]; absout[s * norders + o] =
- * (1/n) sum |Re f| + |Im f| (the scale for relative comparisons).
+ * (1/n) sum |Re f| + |Im f| (the scale for relative comparisons) and
+ * absout[(m + s) * norders + o] = (1/n) sum of the corner-term masses
+ * (the size of the cancellation inside the subtraction).
  * The k range is cut into fixed chunks of ORC_CHUNK points, each summed
  * left to right with Neumaier compensation, and the chunk sums are combined
  * in index order, so the result does not depend on the thread count.
@@ -407,7 +423,8 @@ long orc_shift_sums(const orc_sector *S, uint64_t n, const uint32_t *z, int m,
     uint64_t nk = k1 > k0 ? k1 - k0 : 0;
     uint64_t nchunks = (nk + ORC_CHUNK - 1) / ORC_CHUNK;
     size_t per = (size_t)norders * 2;
-    double *part = (double *)calloc((size_t)m * nchunks * per * 3 + 1, sizeof(double));
+    const size_t stride = per * 3 + (size_t)norders;
+    double *part = (double *)calloc((size_t)m * nchunks * stride + 1, sizeof(double));
     long fails = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -419,27 +436,31 @@ long orc_shift_sums(const orc_sector *S, uint64_t n, const uint32_t *z, int m,
         uint64_t ka = k0 + c * ORC_CHUNK;
         uint64_t kb = ka + ORC_CHUNK < k1 ? ka + ORC_CHUNK : k1;
         neum acc[ORC_LMAX * 2];
-        double aacc[ORC_LMAX];
+        double aacc[ORC_LMAX], cacc[ORC_LMAX];
         memset(acc, 0, sizeof acc);
         memset(aacc, 0, sizeof aacc);
+        memset(cacc, 0, sizeof cacc);
         int sf = 0;
         for (uint64_t k = ka; k < kb; ++k) {
-            double u[ORC_DMAX], v[ORC_LMAX * 2];
+            double u[ORC_DMAX], v[ORC_LMAX * 2], cv[ORC_LMAX];
             orc_lattice_points(n, z, d, delta + (size_t)s * d, k, 1, u, NULL);
-            if (!orc_point_value(S, u, lo, norders, v, &sf)) continue;
+            if (!point_value_cond(S, u, lo, norders, v, cv, &sf)) continue;
             for (int q = 0; q < 2 * norders; ++q) neum_add(&acc[q], v[q]);
-            for (int o = 0; o < norders; ++o) aacc[o] += fabs(v[2 * o]) + fabs(v[2 * o + 1]);
+            for (int o = 0; o < norders; ++o) {
+                aacc[o] += fabs(v[2 * o]) + fabs(v[2 * o + 1]);
+                cacc[o] += cv[o];
+            }
         }
-        double *dst = part + ((size_t)s * nchunks + c) * per * 3;
+        double *dst = part + ((size_t)s * nchunks + c) * stride;
         for (size_t q = 0; q < per; ++q) { dst[q] = acc[q].s; dst[per + q] = acc[q].c; }
-        for (int o = 0; o < norders; ++o) dst[2 * per + o] = aacc[o];
+        for (int o = 0; o < norders; ++o) { dst[2 * per + o] = aacc[o]; dst[3 * per + o] = cacc[o]; }
         fails += sf;
     }
     for (int s = 0; s < m; ++s) {
         for (size_t q = 0; q < per; ++q) {
             neum a = {0.0, 0.0};
             for (uint64_t c = 0; c < nchunks; ++c) {
-                const double *src = part + ((size_t)s * nchunks + c) * per * 3;
+                const double *src = part + ((size_t)s * nchunks + c) * stride;
                 neum_add(&a, src[q]);
                 neum_add(&a, src[per + q]);
             }
@@ -447,10 +468,13 @@ long orc_shift_sums(const orc_sector *S, uint64_t n, const uint32_t *z, int m,
         }
         if (absout)
             for (int o = 0; o < norders; ++o) {
-                double a = 0.0;
-                for (uint64_t c = 0; c < nchunks; ++c)
-                    a += part[((size_t)s * nchunks + c) * per * 3 + 2 * per + o];
+                double a = 0.0, cm = 0.0;
+                for (uint64_t c = 0; c < nchunks; ++c) {
+                    a += part[((size_t)s * nchunks + c) * stride + 2 * per + o];
+                    cm += part[((size_t)s * nchunks + c) * stride + 3 * per + o];
+                }
                 absout[s * norders + o] = a / (double)n;
+                absout[((size_t)m + s) * norders + o] = cm / (double)n;
             }
     }
     free(part);

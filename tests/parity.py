@@ -1,14 +1,21 @@
 """Shared helpers of the GPU parity tests: run the CUDA path through the C-ABI
 and the CPU oracle on the same seeded inputs, and compare.
 
-Tolerance (FP64 per-shift sums): |gpu - oracle| <= RTOL * max(|oracle|, A)
-with A = (1/n) sum_k |Re f_k| + |Im f_k| the absolute mass of the sum (the
-oracle reports it). Both sides evaluate every point in FP64 with library
-transcendentals (<= 1 ulp apart); the GPU sums in a different order (PPT
-points per thread, a 5-level warp tree, warps in order, Neumaier over tiles),
-whose worst-case relative error is ~ (PPT + 12) u A / |Q| << 1e-12, and the
-subtraction terms' cancellation near t = 0 is damped by the korobov3 weight
-(W / t ~ 4 / u), adding ~ u ln(n) per singular variable. RTOL = 1e-12.
+Tolerance (FP64 per-shift sums):
+    |gpu - oracle| <= RTOL * max(|oracle|, A) + CTOL * C
+with A = (1/n) sum_k |Re f_k| + |Im f_k| the absolute mass of the sum and
+C = (1/n) sum_k W_k sum_V |term_V| the mass of the subtraction-corner terms
+before they cancel (the oracle reports both). Derivation: both sides
+evaluate every point in FP64 with library transcendentals (<= 1 ulp apart);
+the GPU sums in a different order (PPT points per thread, a 5-level warp
+tree, warps in order, Neumaier over tiles), worst-case relative error
+~ (PPT + 12) u A / |Q|, covered by RTOL = 1e-12; each corner term carries a
+few roundings on each side (products, logs, series powers), so the two
+evaluations of a cancelling sum differ by at most ~ 9 u C: CTOL = 1e-15.
+C / A stays below ~4e3 up to eps^0 of the box workloads, so there the bound
+is within a few 1e-12 of A; it grows at higher eps orders (1.4e5 at eps^1),
+where the subtraction with (ln t)^k terms is intrinsically worse
+conditioned in FP64.
 """
 from __future__ import annotations
 
@@ -19,6 +26,7 @@ from paper_2305_19768_gb300 import qmc
 from paper_2305_19768_gb300.inputs.lattice import lattice_for
 
 RTOL = 1e-12
+CTOL = 1e-15
 
 
 class Gpu:
@@ -45,22 +53,27 @@ class Gpu:
 
 def oracle_sums(integral, sector, inv, n, m, seed, stream, lo, norders, lam=None, shift_rows=None,
                 nthreads=0):
-    """Oracle per-shift sums [m][norders][2] and absolute masses [m][norders]."""
+    """Oracle per-shift sums [m][norders][2], absolute masses [m][norders] and
+    corner-term masses [m][norders]."""
     s = integral.sectors[sector]
     _, z = lattice_for(n, s.d)
     dl = oracle.shifts(seed, stream, m, s.d)
     if shift_rows is not None:
         dl = dl[list(shift_rows)]
     view = oracle.SectorView(integral, sector, inv, lam)
-    out, absm, fails = oracle.shift_sums(view, n, z, dl, lo, norders, nthreads=nthreads)
-    return out, absm, fails
+    out, absm, fails, cond = oracle.shift_sums(view, n, z, dl, lo, norders, nthreads=nthreads,
+                                               with_cond=True)
+    return out, absm, cond
 
 
-def assert_close(gpu, orc, absm, rtol=RTOL, what=""):
+def assert_close(gpu, orc, absm, cond=None, rtol=RTOL, what=""):
     gpu = np.asarray(gpu).reshape(orc.shape)
     scale = np.maximum(np.abs(orc), absm[..., None])
     err = np.abs(gpu - orc)
-    bad = err > rtol * scale + 1e-300
+    allow = rtol * scale + 1e-300
+    if cond is not None:
+        allow = allow + CTOL * cond[..., None]
+    bad = err > allow
     if bad.any():
         idx = np.argwhere(bad)[:5]
         rel = (err / np.maximum(scale, 1e-300)).max()

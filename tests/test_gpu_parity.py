@@ -36,12 +36,17 @@ def _specs(iid, sectors, points, n, m, seed=1, lam=0.0, nsec_total=None):
 
 
 # ---------------------------------------------------------------- bit-exact
+# large primes with explicit generating vectors (every component < n is in U_n)
+EXPLICIT_Z = {100000007: [1, 39435, 7612354, 23817, 99999, 12345678],
+              4294967291: [4294967290, 3000000019]}
+
+
 @pytest.mark.parametrize("n,d", [(1009, 3), (1000003, 3), (100000007, 6), (4294967291, 2)])
 def test_lattice_points_bit_exact(gpu, n, d):
-    if n in lattice_sizes():
-        z = np.array(lattice_for(n, d)[1], dtype=np.uint32)
+    if n in EXPLICIT_Z:
+        z = np.array(EXPLICIT_Z[n][:d], dtype=np.uint32)
     else:
-        z = np.array([4294967290, 3000000019][:d], dtype=np.uint32)
+        z = np.array(lattice_for(n, d)[1], dtype=np.uint32)
     delta = oracle.shifts(5, 3, 1, d)[0]
     for k0 in (0, n // 3, n - 777):
         cnt = min(777, n - k0)
@@ -72,9 +77,9 @@ def _compare_integral(gpu, I, inv_points, n, m, lo, norders, lam=None, sectors=N
     out = out.reshape(len(specs), m, norders, 2)
     worst = 0.0
     for i, sp in enumerate(specs):
-        o, a, _ = oracle_sums(I, sp["sector"], list(inv_points[sp["point"]]), n, m, seed,
+        o, a, c = oracle_sums(I, sp["sector"], list(inv_points[sp["point"]]), n, m, seed,
                               sp["stream"], lo, norders, lam)
-        worst = max(worst, assert_close(out[i], o, a, what=f"sector {sp['sector']} point {sp['point']}"))
+        worst = max(worst, assert_close(out[i], o, a, c, what=f"sector {sp['sector']} point {sp['point']}"))
     return worst
 
 
@@ -120,8 +125,8 @@ def test_tiny_lattices_below_one_tile(gpu):
         for i, sp in enumerate(specs):
             view = oracle.SectorView(I, sp["sector"], [-3.0, -2.0])
             dl = oracle.shifts(1, sp["stream"], 2, 3)
-            o, a, _ = oracle.shift_sums(view, n, z, dl, -2, 3)
-            assert_close(out[i], o, a, what=f"n={n}")
+            o, a, _, c = oracle.shift_sums(view, n, z, dl, -2, 3, with_cond=True)
+            assert_close(out[i], o, a, c, what=f"n={n}")
 
 
 def test_full_size_sampled_outputs():
@@ -139,8 +144,8 @@ def test_full_size_sampled_outputs():
         assert rc == 0
         out = out.reshape(12, m, 3, 2)
         for sector, shift in ((0, 0), (5, 17), (11, 31)):
-            o, a, _ = oracle_sums(I, sector, [-3.0, -2.0], n, m, 1, sector, -2, 3, shift_rows=[shift])
-            assert_close(out[sector, shift][None], o, a, what=f"full-size sector {sector} shift {shift}")
+            o, a, c = oracle_sums(I, sector, [-3.0, -2.0], n, m, 1, sector, -2, 3, shift_rows=[shift])
+            assert_close(out[sector, shift][None], o, a, c, what=f"full-size sector {sector} shift {shift}")
         # property at any size: the mean over shifts reproduces the closed form
         from golden_values import closed_form
         ex = closed_form("box1L_massless", "s=-3,t=-2")
