@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n=1000003 CBC, m=32 shifts"
+WORKLOAD = "box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n={n} CBC, m={m} shifts"
 METRIC = "integrand evals/s"
 UNIT = "evals/s"
 LO, NORD = -2, 3
@@ -129,7 +129,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"k in [0,{ks}) per sector and shift"},
+            "data": "synthetic", "config": {"workload": WORKLOAD.format(n=n, m=m), "sample": f"k in [0,{ks}) per sector and shift"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": f"all 12 sectors x {m} shifts x lattice indices [0,{ks}) of n={n}"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -259,7 +259,7 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "evals_per_step": evals_per_step,
+            "config": {"workload": WORKLOAD.format(n=args.n, m=args.shifts), "evals_per_step": evals_per_step,
                        "l2": "flushed between timed steps (256 MB write)", "wall_s": wall},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
