@@ -183,6 +183,35 @@ int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d,
  * array [m][d] (see qmc_job.stream). Computed on the device. */
 int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta);
 
+/* Evaluation that allocates nothing. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * time they evaluate -- code running while a CUDA stream is being captured
+ * into a graph, hard real-time loops that must not hit cudaMalloc's implicit
+ * device synchronisation, or hosts whose device memory is owned by another
+ * allocator with a fixed budget. It computes what qmc_eval_jobs computes for
+ * the same jobs (per-shift sums, layout [job][shift][order][re, im]) but
+ * writes them to the caller's device buffer `out_dev`
+ * (qmc_plan_output_size doubles for the same jobs) and keeps its job table,
+ * tile counter, status words and tile partial sums in one fixed 4 MiB array
+ * in device memory that every GPU loading this library holds until the
+ * process exits. Limits: at most 256 jobs per call, all of one evaluator
+ * class (all deformed or all undeformed, d <= 3), and at most 520160
+ * doubles of tile partials ((4 MiB - 33024 bytes) / 8), counted as the sum
+ * over jobs of shifts * ceil(n / (block * ppt)) * 2 * norders; larger
+ * requests are rejected with QMC_E_INVAL and a message, before any GPU work.
+ * It never calls cudaMalloc, cudaFree or any allocating library routine.
+ * The context (qmc_create, qmc_set_lattices, qmc_load_sectors_mem,
+ * qmc_set_kinematics) must be set up beforehand; that set-up does allocate.
+ * The first call on a device looks up the array's device address (a
+ * one-time set-up with that device current), so make that first call
+ * before any stream capture. Every call reuses the same array and clears
+ * the counter and status words it needs at zero; calls that overlap on the
+ * GPU (other threads, other streams) race on it and give wrong results.
+ * Runs on `stream` (NULL = the context's stream) and returns after the work
+ * has finished, with QMC_E_NONFINITE / QMC_E_SIGN_CHECK as qmc_plan_results. */
+int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
+                          double *out_dev, void *stream);
+
 /* Measure the FP64 fused-multiply-add throughput of the device (the
  * roofline denominator of the evaluator): *gflops = 2 * DFMA / s over a
  * dependent-chain-free loop timed with CUDA events. */

@@ -814,3 +814,83 @@ int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation entry point
+extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
+                                     double *out_dev, void *stream) {
+    if (!ctx || !jobs || !out_dev || njobs < 1 || norders < 1)
+        return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: bad arguments");
+    if (njobs > QMC_NOALLOC_MAX_JOBS)
+        return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: %d jobs exceed the fixed limit of %d", njobs,
+                    QMC_NOALLOC_MAX_JOBS);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, QMC_E_CUDA, "cudaSetDevice failed");
+    QmcJobDev recs[QMC_NOALLOC_MAX_JOBS];
+    const int block = ctx->opt.block == 256 ? 256 : 128;
+    const int ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 4;
+    const uint64_t tile_k = (uint64_t)block * ppt;
+    const int hi = lo + norders - 1;
+    int cls = -1;
+    uint64_t tiles = 0, out_off = 0;
+    for (int i = 0; i < njobs; ++i) {
+        const qmc_job &J = jobs[i];
+        if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size())
+            return fail(ctx, QMC_E_INVAL, "job %d: bad integral id %d", i, J.integral_id);
+        const HostIntegral &I = ctx->integrals[J.integral_id];
+        if (J.sector < 0 || J.sector >= (int)I.sectors.size())
+            return fail(ctx, QMC_E_INVAL, "job %d: bad sector %d", i, J.sector);
+        const HostSector &S = I.sectors[J.sector];
+        if (J.point < 0 || (J.point >= ctx->npoints && !(I.invariants.empty() && J.point == 0)))
+            return fail(ctx, QMC_E_INVAL, "job %d: bad kinematic point %d", i, J.point);
+        if (J.shifts < 1) return fail(ctx, QMC_E_INVAL, "job %d: shifts < 1", i);
+        auto it = ctx->lattices.find(J.n);
+        if (it == ctx->lattices.end())
+            return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
+        if (cls < 0) cls = S.cls;
+        if (S.cls != cls)
+            return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: all jobs must use one evaluator class");
+        if (cls == QMC_CLASS_REAL6 || norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
+            return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d not supported by the evaluator", i, lo, hi);
+        QmcJobDev &D = recs[i];
+        memset(&D, 0, sizeof D);
+        D.sector = S.global_index;
+        D.point = I.invariants.empty() ? 0 : J.point;
+        D.shifts = J.shifts;
+        D.n = J.n;
+        D.seed_state = J.seed ^ (kGamma * (J.stream + 1));
+        D.out_off = out_off;
+        for (int j = 0; j < QMC_DMAX; ++j) {
+            D.z[j] = j < S.d ? it->second[j] : 0;
+            D.lambda[j] = (S.deform && j < S.d) ? J.lambda[j] : 0.0;
+        }
+        D.tiles_per_shift = (int32_t)((D.n + tile_k - 1) / tile_k);
+        D.tile_begin = tiles;
+        tiles += (uint64_t)D.tiles_per_shift * D.shifts;
+        out_off += (uint64_t)J.shifts * norders * 2;
+    }
+    const uint64_t need = tiles * (uint64_t)(2 * norders);
+    const uint64_t cap = qmc_k_noalloc_partial_capacity();
+    if (need > cap)
+        return fail(ctx, QMC_E_INVAL,
+                    "qmc_eval_jobs_noalloc: %llu tile partials exceed the fixed scratch of %llu doubles "
+                    "(%u bytes); use fewer points or shifts per call, or qmc_eval_jobs",
+                    (unsigned long long)need, (unsigned long long)cap, (unsigned)QMC_NOALLOC_BYTES);
+    QmcLaunch L{};
+    L.sectors = ctx->d_sectors;
+    L.monos = ctx->d_monos;
+    L.kin = ctx->d_kin;
+    L.ninv = ctx->ninv;
+    L.lo = lo;
+    L.norders = norders;
+    L.ntiles = tiles;
+    L.tile_k = (uint32_t)tile_k;
+    L.out = out_dev;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    unsigned long long status[2] = {0, 0};
+    int rc = qmc_k_noalloc_eval(ctx->device, cls, recs, njobs, &L, block, ppt, ctx->sm_count, status, st);
+    if (rc == -2) return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: size beyond the fixed scratch");
+    if (rc) return fail(ctx, QMC_E_CUDA, "qmc_eval_jobs_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (status[1]) return fail(ctx, QMC_E_NONFINITE, "%llu tile partial sums were not finite", status[1]);
+    if (status[0]) return fail(ctx, QMC_E_SIGN_CHECK, "%llu deformed points had Im F > 0", status[0]);
+    return QMC_OK;
+}

@@ -1,6 +1,7 @@
 // Internal layouts shared by the host library (qmc_host.cpp) and the kernels
 // (qmc_kernels.cu). Not part of the public C-ABI.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 #define QMC_DMAX 6          // integration variables per sector
@@ -71,6 +72,10 @@ struct QmcLaunch {
     double *out;           // per-shift sums
 };
 
+// Fixed scratch of the no-allocation entry point (qmc_eval_jobs_noalloc).
+#define QMC_NOALLOC_BYTES (4u << 20)   // 4 MiB per device
+#define QMC_NOALLOC_MAX_JOBS 256
+
 // Kernel classes (compile-time sizes of the evaluator).
 enum QmcClass {
     QMC_CLASS_REAL3 = 0,   // real integrand, d <= 3, <= 2 singular variables
@@ -92,4 +97,9 @@ int qmc_k_lattice_points(uint64_t n, const uint32_t *z_dev, int d, const double 
                          uint64_t k0, uint64_t count, double *x_dev, uint64_t *r_dev, void *stream);
 int qmc_k_fp64_probe(double *out_dev, int iters, int grid, int block, void *stream);
 int qmc_k_sm_count(int device);
+int qmc_k_occupancy(int cls, int block);
+size_t qmc_k_noalloc_partial_capacity(void);
+int qmc_k_noalloc_setup(int device, void **ptr);
+int qmc_k_noalloc_eval(int device, int cls, const QmcJobDev *jobs_host, int njobs, const QmcLaunch *tmpl,
+                       int block, int ppt, int sm_count, unsigned long long *status_host, void *stream);
 }

@@ -795,3 +795,70 @@ extern "C" int qmc_k_occupancy(int cls, int block) {
     }
     return e == cudaSuccess ? v : 0;
 }
+
+// ---------------------------------------------------------------- no-allocation variant
+// Fixed scratch for qmc_eval_jobs_noalloc: [0, 256) queue counter and status
+// words, then the job table, then the tile partial sums. Every GPU that loads
+// the library holds it until the process exits; every call shares it.
+namespace {
+constexpr size_t kNoallocJobOff = 256;
+constexpr size_t kNoallocPartOff = kNoallocJobOff + (size_t)QMC_NOALLOC_MAX_JOBS * sizeof(QmcJobDev);
+static_assert(kNoallocPartOff % 256 == 0, "partials must stay 256-byte aligned");
+static_assert(QMC_NOALLOC_BYTES > kNoallocPartOff, "scratch too small");
+__device__ __align__(256) unsigned char qmc_noalloc_scratch[QMC_NOALLOC_BYTES];
+void *g_noalloc_ptr[64];  // device address of the array, per device (host stand-in is not one)
+}  // namespace
+
+extern "C" size_t qmc_k_noalloc_partial_capacity(void) {
+    return (QMC_NOALLOC_BYTES - kNoallocPartOff) / sizeof(double);
+}
+
+// Set-up once per device (the device must be current): look up the array's
+// device address. Not thread-safe against a concurrent first call on the
+// same device.
+extern "C" int qmc_k_noalloc_setup(int device, void **ptr) {
+    if (device < 0 || device >= 64) return -1;
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, qmc_noalloc_scratch) != cudaSuccess || !p) return -1;
+        g_noalloc_ptr[device] = p;
+    }
+    *ptr = g_noalloc_ptr[device];
+    return 0;
+}
+
+// Queue the evaluation of `njobs` host job records of one kernel class into
+// the fixed scratch, then copy the status words to `status_host`. The caller
+// synchronises the stream before reading `status_host`.
+extern "C" int qmc_k_noalloc_eval(int device, int cls, const QmcJobDev *jobs_host, int njobs,
+                                  const QmcLaunch *tmpl, int block, int ppt, int sm_count,
+                                  unsigned long long *status_host, void *stream) {
+    void *base = nullptr;
+    if (qmc_k_noalloc_setup(device, &base)) return -1;
+    if (njobs < 1 || njobs > QMC_NOALLOC_MAX_JOBS) return -2;
+    if (tmpl->ntiles * (uint64_t)(2 * tmpl->norders) > qmc_k_noalloc_partial_capacity()) return -2;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *b = (unsigned char *)base;
+    QmcLaunch L = *tmpl;
+    L.queue = (unsigned long long *)b;
+    L.status = (unsigned long long *)(b + 64);
+    L.jobs = (const QmcJobDev *)(b + kNoallocJobOff);
+    L.partials = (double *)(b + kNoallocPartOff);
+    L.njobs = njobs;
+    // what must start at zero: the tile counter and the status words
+    if (cudaMemsetAsync(b, 0, 128, st) != cudaSuccess) return -1;
+    if (cudaMemcpyAsync(b + kNoallocJobOff, jobs_host, (size_t)njobs * sizeof(QmcJobDev),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return -1;
+    int occ = qmc_k_occupancy(cls, block);
+    if (occ < 1) occ = 1;
+    uint64_t g = (uint64_t)sm_count * occ;
+    if (L.ntiles < g) g = L.ntiles;
+    const int grid = g < 1 ? 1 : (int)g;
+    if (L.ntiles > 0 && qmc_k_launch_eval(cls, &L, block, ppt, grid, stream)) return -1;
+    if (qmc_k_launch_finish(&L, stream)) return -1;
+    if (cudaMemcpyAsync(status_host, b + 64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return -1;
+    return 0;
+}

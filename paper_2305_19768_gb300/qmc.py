@@ -83,6 +83,7 @@ def lib():
                                         P(u64)], i32),
                 "qmc_shifts": ([vp, u64, u64, i32, i32, P(dbl)], i32),
                 "qmc_fp64_peak": ([vp, P(dbl)], i32),
+                "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -98,7 +99,7 @@ def exported_symbols():
             "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
-            "qmc_shifts", "qmc_fp64_peak"]
+            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc"]
 
 
 def _dp(a):
@@ -242,6 +243,13 @@ def qmc_shifts(ctx, seed: int, stream: int, m: int, d: int):
     out = np.zeros((m, d), dtype=np.float64)
     _check(ctx, lib().qmc_shifts(ctx, seed, stream, m, d, _dp(out)))
     return out
+
+
+def qmc_eval_jobs_noalloc(ctx, jobs, njobs: int, lo: int, norders: int, out_dev_ptr: int,
+                          stream_ptr=None):
+    """Evaluate into a caller-owned device buffer without allocating (see qmc.h)."""
+    _check(ctx, lib().qmc_eval_jobs_noalloc(ctx, jobs, njobs, lo, norders, ctypes.c_void_p(out_dev_ptr),
+                                            ctypes.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 def qmc_fp64_peak(ctx) -> float:

@@ -1,0 +1,64 @@
+"""The no-allocation entry point against the allocating one (GPU).
+
+qmc_eval_jobs_noalloc serves callers that cannot allocate device memory at
+evaluation time (inside a stream capture, in a real-time loop, under a
+fixed-budget allocator): it keeps its scratch in a fixed array in device
+memory instead of calling cudaMalloc. Here it must reproduce qmc_eval_jobs,
+within the parity tolerance of the other GPU tests, on two calls in a row
+(the second call sees the array the first one left behind). This file is
+collected last so a failure here leaves every other test already run.
+"""
+import numpy as np
+import pytest
+
+from paper_2305_19768_gb300 import qmc
+from paper_2305_19768_gb300.inputs import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+def _close(a, b):
+    scale = np.maximum(np.abs(b), np.abs(b).max())
+    assert np.all(np.abs(a - b) <= RTOL * scale), float(np.max(np.abs(a - b) / scale))
+
+
+def test_noalloc_matches_allocating_entry_point_twice():
+    import torch
+
+    ctx = qmc.qmc_create(0)
+    try:
+        qmc.load_lattice_table(ctx)
+        I = w.box_massless()
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0], [-5.0, -1.0]]))
+        specs = qmc.jobs_for_integral(iid, len(I.sectors), 2, 20011, 8, seed=3)
+        jobs, nj = qmc.make_jobs(specs)
+        size = nj * 8 * 3 * 2
+        ref = qmc.qmc_eval_jobs(ctx, jobs, nj, -2, 3, size)
+        out = torch.full((size,), float("nan"), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            qmc.qmc_eval_jobs_noalloc(ctx, jobs, nj, -2, 3, out.data_ptr())
+            _close(out.cpu().numpy(), ref)
+            out.fill_(float("nan"))
+        # a second workload through the same array: deformed sectors
+        Im = w.box_massive()
+        iid2 = qmc.qmc_load_sectors_mem(ctx, Im.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[12.0, -3.0], [7.5, -1.5]]))
+        specs2 = qmc.jobs_for_integral(iid2, len(Im.sectors), 2, 4001, 4, seed=5, lam=0.3)
+        jobs2, nj2 = qmc.make_jobs(specs2)
+        size2 = nj2 * 4 * 1 * 2
+        ref2 = qmc.qmc_eval_jobs(ctx, jobs2, nj2, 0, 1, size2)
+        out2 = torch.empty(size2, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            qmc.qmc_eval_jobs_noalloc(ctx, jobs2, nj2, 0, 1, out2.data_ptr())
+            _close(out2.cpu().numpy(), ref2)
+        # beyond the fixed scratch: rejected with a clear error, nothing run
+        big = qmc.jobs_for_integral(iid, len(I.sectors), 1, 1000003, 32)
+        jb, nb = qmc.make_jobs(big)
+        with pytest.raises(qmc.QmcError) as e:
+            qmc.qmc_eval_jobs_noalloc(ctx, jb, nb, -2, 3, out.data_ptr())
+        assert e.value.code == -1 and "fixed scratch" in str(e.value)
+    finally:
+        qmc.qmc_destroy(ctx)
