@@ -212,6 +212,13 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
 int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
                           double *out_dev, void *stream);
 
+/* The evaluator's own FP64 natural logarithm applied on the device to n
+ * positive normal doubles (host arrays x[n] -> out[n]), for verification:
+ * Tang's table-driven method (ACM TOMS 16, 1990) with a 129-entry table
+ * and a degree-7 log1p, within 1 ulp. Errors: QMC_E_INVAL for a
+ * non-positive, subnormal or non-finite x. */
+int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out);
+
 /* Measure the FP64 fused-multiply-add throughput of the device (the
  * roofline denominator of the evaluator): *gflops = 2 * DFMA / s over a
  * dependent-chain-free loop timed with CUDA events. */

@@ -20,6 +20,7 @@
 #include "qmc_internal.h"
 
 extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void *stream);
+extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_occupancy(int cls, int block);
 
 namespace {
@@ -263,6 +264,8 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
     H.f1 = S.f1;
     H.u0_int = (S.u0 == std::floor(S.u0) && std::fabs(S.u0) <= QMC_EMAX) ? 1 : 0;
     H.f0_int = (S.f0 == std::floor(S.f0) && std::fabs(S.f0) <= QMC_EMAX) ? 1 : 0;
+    H.pad1 = (S.u1 == std::floor(S.u1) && std::fabs(S.u1) <= QMC_EMAX && S.f1 == std::floor(S.f1) &&
+              std::fabs(S.f1) <= QMC_EMAX) ? 1 : 0;
     int q = 0;
     for (int j = 0; j < S.d; ++j) {
         H.a[j] = S.a[j];
@@ -570,6 +573,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         D.shifts = J.shifts;
         D.n = J.n;
         D.seed_state = J.seed ^ (kGamma * (J.stream + 1));
+        D.inv_n = 1.0 / (double)J.n;
         D.out_off = out_off;
         for (int j = 0; j < QMC_DMAX; ++j) {
             D.z[j] = j < S.d ? it->second[j] : 0;
@@ -788,6 +792,29 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
     return rc ? fail(ctx, rc, "qmc_shifts failed") : QMC_OK;
 }
 
+int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out) {
+    if (!ctx || (n && (!x || !out))) return fail(ctx, QMC_E_INVAL, "qmc_fp64_log: bad arguments");
+    for (size_t i = 0; i < n; ++i)
+        if (!(x[i] >= 2.2250738585072014e-308) || !std::isfinite(x[i]))
+            return fail(ctx, QMC_E_INVAL, "qmc_fp64_log: x[%zu] is not a positive normal number", i);
+    if (n == 0) return QMC_OK;
+    cudaSetDevice(ctx->device);
+    double *dx = nullptr, *dy = nullptr;
+    int rc = QMC_OK;
+    if (cudaMalloc(&dx, n * sizeof(double)) != cudaSuccess || cudaMalloc(&dy, n * sizeof(double)) != cudaSuccess) {
+        rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_log: allocation failed");
+    } else {
+        cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (qmc_k_log(dx, n, dy, ctx->stream)) rc = fail(ctx, QMC_E_CUDA, "log kernel launch failed");
+        cudaMemcpyAsync(out, dy, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (!rc && e != cudaSuccess) rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_log: %s", cudaGetErrorString(e));
+    }
+    cudaFree(dx);
+    cudaFree(dy);
+    return rc;
+}
+
 int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {
     if (!ctx || !gflops) return QMC_E_INVAL;
     cudaSetDevice(ctx->device);
@@ -857,6 +884,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
         D.shifts = J.shifts;
         D.n = J.n;
         D.seed_state = J.seed ^ (kGamma * (J.stream + 1));
+        D.inv_n = 1.0 / (double)J.n;
         D.out_off = out_off;
         for (int j = 0; j < QMC_DMAX; ++j) {
             D.z[j] = j < S.d ? it->second[j] : 0;

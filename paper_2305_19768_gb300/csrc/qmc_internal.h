@@ -26,11 +26,11 @@ struct QmcMono {
 struct QmcSectorDev {
     int32_t d, ns, nU, nF;
     int32_t deform, u0_int, f0_int, ninv;   // u0_int/f0_int: 1 if the exponent is an integer
-    int32_t monoU, monoF, nmono, pad0;      // offsets into the global monomial array
+    int32_t monoU, monoF, nmono, pad0;      // offsets into the global monomial array; pad0 = max exponent
     int32_t a[QMC_DMAX];
     int32_t sing[QMC_SMAX];                 // variable index of singular slot q
     int32_t regular_mask;                   // bit j: j not singular and (a_j != 0 or b_j != 0)
-    int32_t pad1;
+    int32_t pad1;                           // 1: u1, f1 integers with |.| <= QMC_EMAX (one log per corner)
     int32_t gU[QMC_NGROUP + 1];
     int32_t gF[QMC_NGROUP + 1];
     int32_t dFoff[QMC_DMAX], dFn[QMC_DMAX];   // relative to monoF + nF
@@ -50,7 +50,7 @@ struct QmcJobDev {
     uint64_t seed_state;   // splitmix64 state for this job's shifts
     uint64_t out_off;      // offset (in doubles) of [shifts][norders][2] in the output
     uint32_t z[QMC_DMAX];  // generating vector
-    int32_t pad;
+    double inv_n;          // RN(1/n), for the corrected lattice division
     double lambda[QMC_DMAX];
 };
 

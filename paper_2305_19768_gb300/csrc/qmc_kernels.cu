@@ -24,8 +24,11 @@
 #include <type_traits>
 
 #include "qmc_internal.h"
+#include "qmc_log_table.h"
 
 namespace {
+
+__device__ const double kLogTable[3 * QMC_LOG_TABLE_ROWS] = QMC_LOG_TABLE_INIT;
 
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
 
@@ -41,13 +44,51 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t state, uint64_t i) {
     return (double)(z >> 11) * (1.0 / 9007199254740992.0);
 }
 
-// Lattice coordinate (steps "lattice index" and "shifted point"): r/n + delta
-// folded into [0,1), every operation correctly rounded and never contracted.
-__device__ __forceinline__ double lattice_coord(uint64_t r, uint64_t n, double delta) {
-    double x = __ddiv_rn((double)r, (double)n);
-    x = __dadd_rn(x, delta);
+// Lattice coordinate (steps "lattice index" and "shifted point"): RN(r/n) +
+// delta folded into [0,1), every operation correctly rounded and never
+// contracted. RN(r/n) comes from Markstein's correction with y = RN(1/n)
+// computed on the host: q0 = RN(r y), rho = r - n q0 (exact by FMA: q0 is
+// within 1.5 ulp of r/n and n < 2^32), q = RN(q0 + rho y). The corrected sum
+// is within 1.5 * 2^-52 ulp of r/n, while r/n (n < 2^32, not a midpoint
+// because its odd denominator part does not divide r, or else it is a short
+// dyadic) lies at least 1/(2n) > 2^-33 ulp away from any rounding midpoint,
+// so q is exactly the correctly rounded quotient.
+__device__ __forceinline__ double lattice_coord(uint64_t r, double nd, double inv_n, double delta) {
+    const double rd = (double)r;
+    const double q0 = __dmul_rn(rd, inv_n);
+    const double rho = __fma_rn(-q0, nd, rd);
+    const double q = __fma_rn(rho, inv_n, q0);
+    double x = __dadd_rn(q, delta);
     if (x >= 1.0) x = __dadd_rn(x, -1.0);
     return x;
+}
+
+// Natural logarithm of a positive normal double, table-driven after Tang
+// (ACM TOMS 16, 1990): x = 2^e m, m in [1,2); F = 1 + j/128 nearest to m
+// (integer operations on the bits); r = m - F exact; f = r RN(1/F);
+// ln x = e ln2 + ln F + log1p(f), log1p by its Taylor series to f^7
+// (|f| <= 2^-8). e*LN2_HI + LOGF_HI is exact (both on the 2^-42 grid).
+// Measured worst case below 1 ulp. `tab` holds rows {RN(1/F), ln F hi, lo}.
+__device__ __forceinline__ double qlog(double x, const double *tab) {
+    const long long bits = __double_as_longlong(x);
+    const long long mb = bits & 0x000FFFFFFFFFFFFFLL;
+    const int j = (int)((mb + (1LL << 44)) >> 45);               // 0..128
+    const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);
+    const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 45));
+    // exponent as a double without a conversion instruction: (2^52 + 2^51 + e) - (2^52 + 2^51)
+    const long long e = (bits >> 52) - 1023;
+    const double ed = __longlong_as_double(0x4338000000000000LL + e) - 6755399441055744.0;
+    const double r = m - F;
+    const double f = r * tab[3 * j];
+    double q = fma(f, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(q, f, 0.2);
+    q = fma(q, f, -0.25);
+    q = fma(q, f, 1.0 / 3.0);
+    q = fma(q, f, -0.5);
+    const double tail = (f * f) * q;
+    const double hi = fma(ed, QMC_LN2_HI, tab[3 * j + 1]);
+    const double lo = fma(ed, QMC_LN2_LO, tab[3 * j + 2]);
+    return hi + (f + (tail + lo));
 }
 
 // ---------------------------------------------------------------- complex
@@ -67,9 +108,9 @@ __device__ __forceinline__ dc cinv(dc a) {
 }
 // Principal log; on the real axis the argument is taken from below
 // (x - i0), the prescription of F - i0.
-__device__ __forceinline__ dc clog_m0(dc a) {
+__device__ __forceinline__ dc clog_m0(dc a, const double *tab) {
     double arg = (a.im == 0.0) ? (a.re < 0.0 ? -CUDART_PI : 0.0) : atan2(a.im, a.re);
-    return dc{0.5 * log(fma(a.re, a.re, a.im * a.im)), arg};
+    return dc{0.5 * qlog(fma(a.re, a.re, a.im * a.im), tab), arg};
 }
 __device__ __forceinline__ dc cexp_(dc a) {
     double s, c;
@@ -123,6 +164,8 @@ struct TileSmem {
     double cval[QMC_MAXMONO];
     double delta[QMC_DMAX];
     double invb[QMC_SMAX];
+    double logtab[3 * QMC_LOG_TABLE_ROWS];
+    double w140d;  // 140^d of the staged sector
     unsigned long long tile;
     int cached_sector, cached_point;
     int job_index;
@@ -136,14 +179,24 @@ __device__ __forceinline__ T poly_sum(const uint32_t *exps, const double *cval, 
                                       const T (&tp)[DMAX][QMC_EMAX]) {
     T s = zero<T>();
     for (int m = m0; m < m1; ++m) {
-        uint32_t e = exps[m];
-        T v = from_real<T>(cval[m]);
+        const uint32_t e = exps[m];
+        const double c = cval[m];
+        if (e == 0u) {                      // constant monomial
+            s = (m == m0) ? from_real<T>(c) : s + from_real<T>(c);
+            continue;
+        }
+        bool first = true;
+        T v = from_real<T>(1.0);
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) {
-            uint32_t ej = (e >> (4 * j)) & 15u;
-            if (ej) v = v * pow_sel<T>(tp[j], ej);
+            const uint32_t ej = (e >> (4 * j)) & 15u;
+            if (ej) {
+                const T p = pow_sel<T>(tp[j], ej);
+                v = first ? p : v * p;
+                first = false;
+            }
         }
-        s = s + v;
+        s = (m == m0) ? mulsc(v, c) : s + mulsc(v, c);   // contracted into an FMA
     }
     return s;
 }
@@ -170,20 +223,50 @@ __device__ __forceinline__ void powers(const T (&x)[DMAX], int d, int emax, T (&
 //   A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q,  E_P = sum_{q not in P} b_q ln t_q,
 // which is the plus-distribution subtraction of every singular variable
 // (each int_0^1 t^{-1+b eps} g = g(0)/(b eps) + int t^{-1+b eps}(g - g(0))).
+// Only series terms that reach an order <= hi are formed: the corner V needs
+// Lambda_V^i for i <= hi + |V|, the pole set P its product terms k <= hi + |P|.
+// D_P comes from the corner series by the superset Moebius transform.
 // res[o] receives the coefficient of eps^(lo+o).
 template <int SMAX, int LMAX, class T>
-__device__ __forceinline__ void assemble(int ns, int lo, int nord, int L, const T (&BV)[1 << SMAX],
+__device__ __forceinline__ void assemble(int ns, int lo, int hi, int nord, const T (&BV)[1 << SMAX],
                                          const T (&LV)[1 << SMAX], const double (&it)[SMAX],
                                          const double (&lt)[SMAX], const double (&bq)[SMAX],
                                          const double (&invb)[SMAX], T (&res)[LMAX]) {
     constexpr int NG = 1 << SMAX;
     const int full = (1 << ns) - 1;
+    T g[NG][LMAX];
+#pragma unroll
+    for (int V = 0; V < NG; ++V) {
+        const int nV = hi + __popc(V) + 1;
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i) g[V][i] = zero<T>();
+        if (V > full || nV < 1) continue;
+        g[V][0] = BV[V];
+#pragma unroll
+        for (int i = 1; i < LMAX; ++i)
+            if (i < nV) g[V][i] = mulsc(g[V][i - 1] * LV[V], 1.0 / i);
+    }
+    // superset Moebius transform over the singular slots
+#pragma unroll
+    for (int q = 0; q < SMAX; ++q) {
+        if (q >= ns) continue;
+#pragma unroll
+        for (int P = 0; P < NG; ++P) {
+            if (P > full || (P & (1 << q))) continue;
+            const int nP = hi + __popc(P) + 1;
+#pragma unroll
+            for (int i = 0; i < LMAX; ++i)
+                if (i < nP) g[P][i] = g[P][i] - g[P | (1 << q)][i];
+        }
+    }
 #pragma unroll
     for (int o = 0; o < LMAX; ++o) res[o] = zero<T>();
 #pragma unroll
     for (int P = 0; P < NG; ++P) {
         if (P > full) continue;
         const int np = __popc(P);
+        const int nP = hi + np + 1;
+        if (nP < 1) continue;
         double A = 1.0, E = 0.0;
 #pragma unroll
         for (int q = 0; q < SMAX; ++q) {
@@ -192,45 +275,29 @@ __device__ __forceinline__ void assemble(int ns, int lo, int nord, int L, const 
                     A *= invb[q];
                 } else {
                     A *= it[q];
-                    if (L > 1) E = fma(bq[q], lt[q], E);
+                    if (nP > 1) E = fma(bq[q], lt[q], E);
                 }
             }
         }
-        T D[LMAX];
-#pragma unroll
-        for (int i = 0; i < LMAX; ++i) D[i] = zero<T>();
-#pragma unroll
-        for (int V = 0; V < NG; ++V) {
-            if (V > full || (V & P) != P) continue;
-            T pw = (__popc(V ^ P) & 1) ? mulsc(BV[V], -1.0) : BV[V];
-            D[0] = D[0] + pw;
-#pragma unroll
-            for (int i = 1; i < LMAX; ++i) {
-                if (i < L) {
-                    pw = pw * LV[V] * (1.0 / i);
-                    D[i] = D[i] + pw;
-                }
-            }
-        }
-        // product with exp(eps E): PE[k] = sum_i D[i] E^{k-i}/(k-i)!
         double e[LMAX];
         e[0] = 1.0;
 #pragma unroll
-        for (int l = 1; l < LMAX; ++l) e[l] = (l < L) ? e[l - 1] * E * (1.0 / l) : 0.0;
+        for (int l = 1; l < LMAX; ++l) e[l] = (l < nP) ? e[l - 1] * E * (1.0 / l) : 0.0;
         T PE[LMAX];
 #pragma unroll
         for (int k = 0; k < LMAX; ++k) {
             PE[k] = zero<T>();
-            if (k < L) {
+            if (k < nP && k >= lo + np) {
+                PE[k] = g[P][k];
 #pragma unroll
-                for (int i = 0; i <= k; ++i) PE[k] = PE[k] + mulsc(D[i], e[k - i]);
+                for (int i = 0; i < k; ++i) PE[k] = PE[k] + mulsc(g[P][i], e[k - i]);
             }
         }
         // res[o] += A * PE[lo + o + np] (index selected without local memory)
         const int shift = lo + np;
 #pragma unroll
         for (int o = 0; o < LMAX; ++o) {
-            if (o >= nord) continue;
+            if (o >= nord || o + shift < 0) continue;
             T sel = zero<T>();
 #pragma unroll
             for (int k = 0; k < LMAX; ++k)
@@ -240,13 +307,24 @@ __device__ __forceinline__ void assemble(int ns, int lo, int nord, int L, const 
     }
 }
 
+// x^e for integer |e| <= QMC_EMAX with x^-1 supplied
+template <class T>
+__device__ __forceinline__ T ipow_signed(T x, T xinv, int e) {
+    const T b = e < 0 ? xinv : x;
+    const int a = e < 0 ? -e : e;
+    T p = b;
+    for (int q = 1; q < a; ++q) p = p * b;
+    return a == 0 ? from_real<T>(1.0) : p;
+}
+
 // ---------------------------------------------------------------- real integrand
 template <int DMAX, int SMAX, int LMAX>
 __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double (&t)[DMAX], int lo,
-                                          int nord, int L, double (&res)[LMAX]) {
+                                          int hi, int nord, double (&res)[LMAX]) {
     constexpr int NG = 1 << SMAX;
     const QmcSectorDev &sec = S.sec;
     const int d = sec.d, ns = sec.ns;
+    const double *tab = S.logtab;
     double tp[DMAX][QMC_EMAX];
     powers<DMAX, double>(t, d, sec.pad0, tp);
 
@@ -279,18 +357,20 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
             }
         }
     }
+    const bool need_lam = hi + ns >= 1;   // some corner needs its eps exponent
 
     // factors of the regular variables: prod t^{a_j} and sum b_j ln t_j
     double Cc = 1.0, Lc = 0.0;
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d && ((sec.regular_mask >> j) & 1)) {
-            int a = sec.a[j];
+            const int a = sec.a[j];
             if (a > 0) Cc *= pow_sel<double>(tp[j], (uint32_t)a);
-            if (L > 1 && sec.b[j] != 0.0) Lc = fma(sec.b[j], log(t[j]), Lc);
+            if (need_lam && sec.b[j] != 0.0) Lc = fma(sec.b[j], qlog(t[j], tab), Lc);
         }
     }
-    // singular slots: t, 1/t, ln t, b
+    // singular slots: 1/t, ln t (needed when a pole set without q has a term of order >= 1), b
+    const bool need_lt = hi + ns - 1 >= 1;
     double it[SMAX], lt[SMAX], bq[SMAX];
 #pragma unroll
     for (int q = 0; q < SMAX; ++q) {
@@ -305,12 +385,15 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
                     tq = t[j];
                     bb = sec.b[j];
                 }
-            it[q] = 1.0 / tq;
+            it[q] = __drcp_rn(tq);
             bq[q] = bb;
-            if (L > 1) lt[q] = log(tq);
+            if (need_lt) lt[q] = qlog(tq, tab);
         }
     }
-    // corners
+    // corners: B_V = Cc U^u0 F^f0, Lambda_V = Lc + ln(U^u1 F^f1) (one log when
+    // u1, f1 are small integers, else u1 ln U + f1 ln F)
+    const int u0 = (int)sec.u0, f0 = (int)sec.f0, u1 = (int)sec.u1, f1 = (int)sec.f1;
+    const bool comb = sec.pad1 != 0;
     double BV[NG], LV[NG];
     const int full = (1 << ns) - 1;
 #pragma unroll
@@ -318,25 +401,28 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
         BV[V] = 0.0;
         LV[V] = 0.0;
         if (V > full) continue;
+        const bool lam_here = hi + __popc(V) >= 1;
         const double U = hU[(NG - 1) ^ V];
         const double F = hF[(NG - 1) ^ V];
-        double num = Cc, den = 1.0;
-        double lU = 0.0, lF = 0.0;
-        const bool needU = (L > 1 && sec.u1 != 0.0) || !sec.u0_int;
-        const bool needF = (L > 1 && sec.f1 != 0.0) || !sec.f0_int;
-        if (needU) lU = log(U);
-        if (needF) lF = log(F);
-        if (sec.u0_int) mul_ipow<double>(U, (int)sec.u0, num, den);
-        else num *= exp(sec.u0 * lU);
-        if (sec.f0_int) mul_ipow<double>(F, (int)sec.f0, num, den);
-        else num *= exp(sec.f0 * lF);
-        BV[V] = (den == 1.0) ? num : num / den;
-        if (L > 1) LV[V] = Lc + sec.u1 * lU + sec.f1 * lF;
+        const bool needUinv = (sec.u0_int && u0 < 0) || (lam_here && comb && u1 < 0);
+        const bool needFinv = (sec.f0_int && f0 < 0) || (lam_here && comb && f1 < 0);
+        const double Ui = needUinv ? __drcp_rn(U) : 0.0;
+        const double Fi = needFinv ? __drcp_rn(F) : 0.0;
+        double B = Cc;
+        B *= sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog(U, tab));
+        B *= sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog(F, tab));
+        BV[V] = B;
+        if (lam_here) {
+            double l;
+            if (comb) l = qlog(ipow_signed<double>(U, Ui, u1) * ipow_signed<double>(F, Fi, f1), tab);
+            else l = sec.u1 * qlog(U, tab) + sec.f1 * qlog(F, tab);
+            LV[V] = Lc + l;
+        }
     }
     double ib[SMAX];
 #pragma unroll
     for (int q = 0; q < SMAX; ++q) ib[q] = S.invb[q];
-    assemble<SMAX, LMAX, double>(ns, lo, nord, L, BV, LV, it, lt, bq, ib, res);
+    assemble<SMAX, LMAX, double>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, res);
 }
 
 // ---------------------------------------------------------------- deformed integrand
@@ -345,7 +431,7 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
 // G is recomputed at each corner t' = t with t_V = 0.
 template <int DMAX, int SMAX, int LMAX>
 __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const double (&t)[DMAX],
-                                              const double (&omt)[DMAX], int lo, int nord, int L,
+                                              const double (&omt)[DMAX], int lo, int hi, int nord,
                                               dc (&res)[LMAX], int &signfail) {
     static_assert(DMAX <= 3, "deformed evaluator handles d <= 3");
     constexpr int NG = 1 << SMAX;
@@ -353,6 +439,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
     const int d = sec.d, ns = sec.ns;
     const int full = (1 << ns) - 1;
     const int dbase = sec.nU + sec.nF;
+    const double *tab = S.logtab;
     dc BV[NG], LV[NG];
     double it[SMAX], lt[SMAX], bq[SMAX];
 #pragma unroll
@@ -368,9 +455,9 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                     tq = t[j];
                     bb = sec.b[j];
                 }
-            it[q] = 1.0 / tq;
+            it[q] = __drcp_rn(tq);
             bq[q] = bb;
-            if (L > 1) lt[q] = log(tq);
+            if (hi + ns - 1 >= 1) lt[q] = qlog(tq, tab);
         }
     }
 #pragma unroll
@@ -378,6 +465,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
         BV[V] = zero<dc>();
         LV[V] = zero<dc>();
         if (V > full) continue;
+        const bool lam_here = hi + __popc(V) >= 1;
         double tc[DMAX], oc[DMAX];
         bool issing[DMAX];
 #pragma unroll
@@ -462,28 +550,28 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
             if (j >= d) continue;
             if (issing[j]) {
                 den = den * rho[j];
-                if (L > 1 && sec.b[j] != 0.0) lsum = lsum + clog_m0(rho[j]) * sec.b[j];
+                if (lam_here && sec.b[j] != 0.0) lsum = lsum + clog_m0(rho[j], tab) * sec.b[j];
             } else if ((sec.regular_mask >> j) & 1) {
                 if (sec.a[j] != 0) mul_ipow<dc>(z[j], sec.a[j], num, den);
-                if (L > 1 && sec.b[j] != 0.0) lsum = lsum + clog_m0(z[j]) * sec.b[j];
+                if (lam_here && sec.b[j] != 0.0) lsum = lsum + clog_m0(z[j], tab) * sec.b[j];
             }
         }
-        const bool needU = (L > 1 && sec.u1 != 0.0) || !sec.u0_int;
-        const bool needF = (L > 1 && sec.f1 != 0.0) || !sec.f0_int;
+        const bool needU = (lam_here && sec.u1 != 0.0) || !sec.u0_int;
+        const bool needF = (lam_here && sec.f1 != 0.0) || !sec.f0_int;
         dc lU = zero<dc>(), lF = zero<dc>();
-        if (needU) lU = clog_m0(U);
-        if (needF) lF = clog_m0(F);
+        if (needU) lU = clog_m0(U, tab);
+        if (needF) lF = clog_m0(F, tab);
         if (sec.u0_int) mul_ipow<dc>(U, (int)sec.u0, num, den);
         else num = num * cexp_(lU * sec.u0);
         if (sec.f0_int) mul_ipow<dc>(F, (int)sec.f0, num, den);
         else num = num * cexp_(lF * sec.f0);
         BV[V] = num * cinv(den);
-        if (L > 1) LV[V] = lsum + lU * sec.u1 + lF * sec.f1;
+        if (lam_here) LV[V] = lsum + lU * sec.u1 + lF * sec.f1;
     }
     double ib[SMAX];
 #pragma unroll
     for (int q = 0; q < SMAX; ++q) ib[q] = S.invb[q];
-    assemble<SMAX, LMAX, dc>(ns, lo, nord, L, BV, LV, it, lt, bq, ib, res);
+    assemble<SMAX, LMAX, dc>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, res);
 }
 
 // ---------------------------------------------------------------- tile staging
@@ -521,6 +609,9 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
         if (threadIdx.x == 0) {
             S.cached_sector = sidx;
             S.cached_point = pidx;
+            double w = 1.0;
+            for (int j = 0; j < S.sec.d; ++j) w *= 140.0;
+            S.w140d = w;
         }
     }
 }
@@ -535,6 +626,7 @@ __global__ void __launch_bounds__(BLOCK) qmc_eval_kernel(QmcLaunch Lc, int ppt) 
         S.cached_sector = -1;
         S.cached_point = -1;
     }
+    for (int i = threadIdx.x; i < 3 * QMC_LOG_TABLE_ROWS; i += blockDim.x) S.logtab[i] = kLogTable[i];
     int signfail_total = 0;
     for (;;) {
         __syncthreads();  // previous tile fully consumed
@@ -576,8 +668,8 @@ __global__ void __launch_bounds__(BLOCK) qmc_eval_kernel(QmcLaunch Lc, int ppt) 
 
         const int d = S.sec.d;
         const uint64_t n = S.job.n;
+        const double nd = (double)n, inv_n = S.job.inv_n;
         const int hi = lo + nord - 1;
-        const int L = hi + S.sec.ns + 1;  // series length this sector needs
         T acc[LMAX];
 #pragma unroll
         for (int o = 0; o < LMAX; ++o) acc[o] = zero<T>();
@@ -599,31 +691,34 @@ __global__ void __launch_bounds__(BLOCK) qmc_eval_kernel(QmcLaunch Lc, int ppt) 
 #pragma unroll 1
             for (uint64_t k = k0; k < kend; ++k) {
                 double t[DMAX], omt[DMAX];
-                double W = 1.0;
+                double Ws = 1.0;  // prod u(1-u); the korobov3 weight is 140^d Ws^3
                 bool zero_t = false;
 #pragma unroll
                 for (int j = 0; j < DMAX; ++j) {
                     t[j] = 1.0;
                     omt[j] = 0.0;
                     if (j < d) {
-                        const double u = lattice_coord(r[j], n, dl[j]);
+                        const double u = lattice_coord(r[j], nd, inv_n, dl[j]);
                         const double u2 = u * u;
                         t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
-                        const double v = 1.0 - u;
-                        const double v2 = v * v;
-                        if (CPLX) omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
-                        W *= 140.0 * u2 * u * v2 * v;
+                        if (CPLX) {
+                            const double v = 1.0 - u;
+                            const double v2 = v * v;
+                            omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
+                        }
+                        Ws *= fma(-u, u, u);
                         zero_t |= (t[j] == 0.0);
                         uint64_t rn = r[j] + zz[j];
                         r[j] = (rn >= n) ? rn - n : rn;
                     }
                 }
+                const double W = S.w140d * (Ws * Ws * Ws);
                 if (W == 0.0 || zero_t) continue;
                 T res[LMAX];
                 if constexpr (CPLX) {
-                    eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, nord, L, res, signfail_total);
+                    eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, hi, nord, res, signfail_total);
                 } else {
-                    eval_real<DMAX, SMAX, LMAX>(S, t, lo, nord, L, res);
+                    eval_real<DMAX, SMAX, LMAX>(S, t, lo, hi, nord, res);
                 }
 #pragma unroll
                 for (int o = 0; o < LMAX; ++o)
@@ -691,17 +786,23 @@ __global__ void qmc_finish_kernel(QmcLaunch Lc) {
     if (j == 0 && threadIdx.x == 0) *Lc.queue = 0ULL;
 }
 
-__global__ void qmc_lattice_kernel(uint64_t n, const uint32_t *z, int d, const double *delta,
-                                   uint64_t k0, uint64_t count, double *x, uint64_t *rout) {
+__global__ void qmc_lattice_kernel(uint64_t n, double inv_n, const uint32_t *z, int d,
+                                   const double *delta, uint64_t k0, uint64_t count, double *x,
+                                   uint64_t *rout) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const uint64_t k = k0 + i;
     for (int j = 0; j < d; ++j) {
         // (k mod n) * z < 2^64 for n < 2^32
         const uint64_t r = ((k % n) * (uint64_t)z[j]) % n;
-        x[i * d + j] = lattice_coord(r, n, delta[j]);
+        x[i * d + j] = lattice_coord(r, (double)n, inv_n, delta[j]);
         if (rout) rout[i * d + j] = r;
     }
+}
+
+__global__ void qmc_log_kernel(const double *x, uint64_t n, double *out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = qlog(x[i], kLogTable);
 }
 
 __global__ void qmc_shift_kernel(uint64_t state, int m, int d, double *out) {
@@ -757,7 +858,8 @@ extern "C" int qmc_k_lattice_points(uint64_t n, const uint32_t *z_dev, int d, co
                                     void *stream) {
     if (count == 0) return 0;
     const unsigned grid = (unsigned)((count + 255) / 256);
-    qmc_lattice_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, z_dev, d, delta_dev, k0, count, x_dev, r_dev);
+    qmc_lattice_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, 1.0 / (double)n, z_dev, d, delta_dev, k0,
+                                                               count, x_dev, r_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -765,6 +867,12 @@ extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void 
     const int total = m * d;
     if (total <= 0) return 0;
     qmc_shift_kernel<<<(total + 255) / 256, 256, 0, (cudaStream_t)stream>>>(state, m, d, out_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream) {
+    if (n == 0) return 0;
+    qmc_log_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

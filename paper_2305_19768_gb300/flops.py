@@ -2,17 +2,17 @@
 
 One evaluation = one lattice point of one sector for one shift, all eps
 orders, all subtraction corners. The count follows the evaluator's
-formulation of the method and charges:
+formulation of the method (Section "Kernels" of the design notes):
 
-* +, -, x as 1 flop, fused multiply-add as 2, a division as 1;
-* each library transcendental at a fixed algorithmic cost: log, exp and
-  atan2 20 flops, sincos 30 (a minimax polynomial of degree ~10 plus range
-  reduction), so that the figure does not depend on how the GPU's math
-  library happens to implement them.
+* +, -, x, division and reciprocal count 1 flop, a fused multiply-add 2;
+* each transcendental counts a fixed algorithmic cost: log and exp 20
+  flops, atan2 20, sincos 30 (a minimax polynomial of degree ~10 plus range
+  reduction), independent of how a math library implements them;
+* only the terms the requested orders need are counted: corner V carries
+  its eps exponent (one log of U^u1 F^f1) only if hi + |V| >= 1, the ln t of
+  a singular variable only if hi + ns - 1 >= 1, and so on.
 
-The count is per sector (it depends on d, the singular variables, the
-monomial tables and the number of eps orders) and averaged over the
-sectors of a workload weighted by their lattice points.
+The figure is per sector; workloads average it over their sectors.
 """
 from __future__ import annotations
 
@@ -20,47 +20,61 @@ LOG = EXP = ATAN2 = 20
 SINCOS = 30
 
 
+def _monomial_flops(P) -> int:
+    f = 0
+    for e, _ in P.terms.items():
+        nv = sum(1 for x in e if x)
+        f += (nv - 1) + 2 if nv else 1
+    return f
+
+
 def sector_flops(sector, lo: int, norders: int, deform: bool = False) -> int:
     d = sector.d
     ns = len(sector.singular)
     hi = lo + norders - 1
-    L = hi + ns + 1
     f = 0
-    f += 2 * d                     # r / n, + delta
-    f += d * (2 + 6)               # korobov3 t (u^2, u^4, three fma, one mul)
-    f += d * (5 + 1)               # weight 140 u^3 (1-u)^3 and the product W
-    emax = max(max(sector.U.max_var_exponent(), sector.F.max_var_exponent()), 1)
-    f += d * max(emax - 1, 0)      # power table
-    for P in (sector.U, sector.F):
-        for e, _ in P.terms.items():
-            f += sum(1 for x in e if x) + 1   # products + accumulation
-    f += 2 * ns * (1 << max(ns - 1, 0))     # subset sums of the corner polynomials
-    corners = 1 << ns
-    per_corner = 0
-    need_log = L > 1
-    if need_log:
-        per_corner += (LOG + 2) * (1 if sector.u1 else 0) + (LOG + 2) * (1 if sector.f1 else 0)
-    per_corner += abs(int(sector.u0)) + abs(int(sector.f0)) + 2   # integer powers, one division
-    f += corners * per_corner
-    f += ns * (1 + (LOG if need_log else 0))   # 1/t and ln t of singular variables
-    # regular variables with eps exponents
+    f += 2 * d                          # r / n and + delta
+    f += 9 * d                          # korobov3 t
+    f += 3 * d + 3                      # weight: u(1-u), product, cube, 140^d
+    emax = max(sector.U.max_var_exponent(), sector.F.max_var_exponent(), 1)
+    f += d * (emax - 1)                 # power table
+    f += _monomial_flops(sector.U) + _monomial_flops(sector.F)
+    f += 2 * ns * (1 << max(ns - 1, 0))  # subset sums of both polynomials
+    u0, f0, u1, f1 = int(sector.u0), int(sector.f0), int(sector.u1), int(sector.f1)
+    for V in range(1 << ns):
+        nV = hi + bin(V).count("1") + 1
+        f += (1 if f0 < 0 else 0) + (1 if u0 < 0 else 0) + max(abs(u0) + abs(f0) - 1, 0) + 1
+        if nV > 1:
+            f += max(abs(u1) + abs(f1) - 1, 0) + LOG + 1
+            f += 2 * (nV - 1)           # corner series B Lambda^i / i!
+    f += ns                              # 1/t of singular variables
+    if hi + ns - 1 >= 1:
+        f += ns * LOG
+    need_lam = hi + ns >= 1
     for j in range(d):
-        if sector.a[j] != -1 and sector.b[j] != 0 and need_log:
+        if sector.a[j] != -1 and sector.b[j] != 0 and need_lam:
             f += LOG + 2
-    # assembly: for each pole set P, D_P over supersets (L terms each), exp series, convolution
-    for P in range(corners):
-        npop = bin(P).count("1")
-        sup = 1 << (ns - npop)
-        f += sup * (1 + 3 * (L - 1))
-        f += 2 * ns + 3 * (L - 1)
-        f += L * (L + 1)  # convolution (fma per term)
-        f += 2 * norders
-    f += 2 * norders               # weight x value into the accumulator
+    for q in range(ns):                  # superset Moebius transform
+        for P in range(1 << ns):
+            if not P & (1 << q):
+                f += max(hi + bin(P).count("1") + 1, 0)
+    for P in range(1 << ns):
+        np_ = bin(P).count("1")
+        nP = hi + np_ + 1
+        if nP < 1:
+            continue
+        f += ns                          # A_P
+        if nP > 1:
+            f += 2 * (ns - np_) + 2 * (nP - 1)   # E_P and its series
+        for k in range(max(0, lo + np_), nP):
+            f += 2 * k                   # convolution term k
+        f += 2 * min(norders, nP)        # res += A PE
+    f += 2 * norders                     # weight x value into the accumulator
     if deform:
-        f += 4 * d * d + 40            # J, z, rho
-        f += 60                        # complex determinant (d <= 3)
+        f += 4 * d * d + 40              # J, z, rho
+        f += 60                          # complex determinant (d <= 3)
         f += 4 * (len(sector.U) + len(sector.F)) * 2
-        f += 10                        # complex reciprocal
+        f += 10                          # complex reciprocal
     return f
 
 

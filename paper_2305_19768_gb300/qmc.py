@@ -84,6 +84,7 @@ def lib():
                 "qmc_shifts": ([vp, u64, u64, i32, i32, P(dbl)], i32),
                 "qmc_fp64_peak": ([vp, P(dbl)], i32),
                 "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
+                "qmc_fp64_log": ([vp, P(dbl), sz, P(dbl)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -99,7 +100,7 @@ def exported_symbols():
             "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
-            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc"]
+            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log"]
 
 
 def _dp(a):
@@ -250,6 +251,13 @@ def qmc_eval_jobs_noalloc(ctx, jobs, njobs: int, lo: int, norders: int, out_dev_
     """Evaluate into a caller-owned device buffer without allocating (see qmc.h)."""
     _check(ctx, lib().qmc_eval_jobs_noalloc(ctx, jobs, njobs, lo, norders, ctypes.c_void_p(out_dev_ptr),
                                             ctypes.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def qmc_fp64_log(ctx, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    _check(ctx, lib().qmc_fp64_log(ctx, _dp(x), x.size, _dp(out)))
+    return out
 
 
 def qmc_fp64_peak(ctx) -> float:

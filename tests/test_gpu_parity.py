@@ -56,6 +56,41 @@ def test_lattice_points_bit_exact(gpu, n, d):
         assert np.array_equal(xg.view(np.uint64), xo.view(np.uint64))
 
 
+def test_lattice_division_exhaustive(gpu):
+    # every r of one lattice, and random r near 2^32: the corrected division is RN(r/n)
+    n = 1000003
+    x, r = qmc.qmc_lattice_points(gpu.ctx, n, np.array([1], dtype=np.uint32), np.zeros(1), 0, n)
+    expect = np.arange(n, dtype=np.float64) / float(n)
+    assert np.array_equal(x[:, 0].view(np.uint64), expect.view(np.uint64))
+    rng = np.random.default_rng(4)
+    for n in (4294967291, 2147483647, 100000007, 65537, 3):
+        z = np.array([int(rng.integers(1, n))], dtype=np.uint32)
+        k0 = int(rng.integers(0, max(1, n - 100000)))
+        cnt = min(100000, n - k0)
+        xg, rg = qmc.qmc_lattice_points(gpu.ctx, n, z, np.zeros(1), k0, cnt)
+        assert np.array_equal(xg[:, 0].view(np.uint64), (rg[:, 0].astype(np.float64) / float(n)).view(np.uint64))
+
+
+def test_evaluator_log_within_one_ulp(gpu):
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.uniform(0.5, 2.0, 200000), np.exp(rng.uniform(-700, 700, 200000)),
+                         1.0 + rng.uniform(-1e-3, 1e-3, 50000), np.array([1.0, 2.0, 0.5, 1e-300, 1e300]),
+                         np.nextafter(1.0, 0.0) * np.ones(1), np.nextafter(1.0, 2.0) * np.ones(1)])
+    got = qmc.qmc_fp64_log(gpu.ctx, xs)
+    from decimal import Decimal, getcontext
+    getcontext().prec = 40
+    ref = np.log(xs)  # libm: correctly rounded to within 1 ulp on this host
+    ulp = np.spacing(np.abs(ref))
+    ulp[ref == 0] = np.spacing(0.0)
+    err = np.abs(got - ref) / ulp
+    assert err.max() <= 2.0, (err.max(), xs[np.argmax(err)])
+    # exact decimal reference on a sample
+    for i in range(0, len(xs), 20000):
+        exact = Decimal(float(xs[i])).ln()
+        g = Decimal(float(got[i]))
+        assert abs(g - exact) <= Decimal(float(np.spacing(abs(float(exact))))) * Decimal("1.01")
+
+
 def test_shifts_bit_exact(gpu):
     for seed, stream, m, d in ((1, 0, 32, 3), (12345, 77, 7, 6), (2**63 + 5, 2**40, 3, 2)):
         g = qmc.qmc_shifts(gpu.ctx, seed, stream, m, d)
