@@ -67,7 +67,8 @@ typedef struct {
     uint64_t min_points;   /* smallest lattice (pilot pass) [10000] */
     uint64_t max_points;   /* largest lattice qmc_integrate may use [largest tabulated] */
     int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
-    int reserved[8];
+    double lambda;         /* deformation parameter qmc_integrate uses for deformed sectors [0.3] */
+    int reserved[6];
 } qmc_options;
 
 /* One evaluation job: one sector of one loaded integral at one kinematic
@@ -182,6 +183,79 @@ int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d,
 /* Random shifts the evaluator draws for (seed, stream): Delta[s][j], host
  * array [m][d] (see qmc_job.stream). Computed on the device. */
 int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta);
+
+/* ------------------------------------------------------------------------
+ * Combination and allocation (host arithmetic, no GPU needed)
+ * ------------------------------------------------------------------------ */
+
+/* Statistics over m random shifts (section "Adaptive weighted sum
+ * evaluation": each integral is a normal variable whose variance the m
+ * shifts estimate): sums[m][norders][2] -> mean[norders][2] and
+ * var[norders][2] = the variance of the mean, (1/(m-1)) sum (Q_s - mean)^2 / m,
+ * separately for Re and Im (INFINITY if m = 1). Errors: QMC_E_INVAL. */
+int qmc_shift_stats(const double *sums, int m, int norders, double *mean, double *var);
+
+/* Laurent product: out[o] = coefficient of eps^(lo+o) in
+ * (sum_i a[i] eps^(a_lo+i)) (sum_j b[j] eps^(b_lo+j)), o < n (complex). */
+int qmc_series_mul(const qmc_c64 *a, int a_lo, int na, const qmc_c64 *b, int b_lo, int nb, int lo, int n,
+                   qmc_c64 *out);
+
+/* Variance through a fixed Laurent factor: out[o] = sum_{i+j = o'} |c[i]|^2 v[j]
+ * with v[j] = var Re + var Im of the eps^(v_lo+j) coefficient (independent
+ * shifts per sector, so variances add). */
+int qmc_series_var(const qmc_c64 *c, int c_lo, int nc, const double *v, int v_lo, int nv, int lo, int n,
+                   double *out);
+
+/* Lattice sizes of Eq. (adaptive-solution): for each of nsums sums k with
+ * requested variance V[k] > 0 and weights W[k][i] = |C_ki|^2 w_i (w_i the
+ * convergence constant of var(I_i) = w_i / n_i^alpha) minimise
+ * sum_i tau_i n_i subject to sum_i W[k][i] n_i^-alpha = V[k]:
+ *   lambda = (1/alpha) ((1/V) sum_i (W_i tau_i^alpha)^(1/(alpha+1)))^((alpha+1)/alpha),
+ *   n_i = (alpha lambda W_i / tau_i)^(1/(alpha+1)).
+ * Several sums are applied in turn and n_out[i] keeps the largest value,
+ * at least n_min (the paper's reading of its multiple-sum procedure).
+ * Integrals with W[k][i] = 0 do not enter sum k. tau[i] > 0 required. */
+int qmc_allocate(const double *W, const double *tau, const double *V, int nsums, int nint, double alpha,
+                 double n_min, double *n_out);
+
+/* What qmc_integrate sums: amplitudes A_k = sum_i C_ki I_i over the
+ * integrals integral_ids[0..nint-1], with complex Laurent coefficients
+ * coef[npoints][namp][nint][ncoef] of orders coef_lo.. (host). coef = NULL
+ * means every C_ki = 1. A NULL spec integrates the sum of all loaded
+ * integrals (namp = 1). */
+typedef struct {
+    const int *integral_ids;
+    int nint;
+    int namp;
+    const qmc_c64 *coef;
+    int coef_lo;
+    int ncoef;
+} qmc_sum_spec;
+
+typedef struct {
+    double evaluations;     /* lattice points x shifts evaluated */
+    double seconds;         /* wall time of the call */
+    double kernel_seconds;  /* device time of the evaluator kernels */
+    int iterations;         /* evaluation passes */
+    uint64_t max_lattice;   /* largest lattice any sector reached */
+} qmc_integrate_info;
+
+/* Adaptive integration of the sums (section "Adaptive weighted sum
+ * evaluation"): every sector at every kinematic point starts on the
+ * smallest tabulated lattice >= min_points (the pilot pass) with `shifts`
+ * random shifts; each pass evaluates the sectors whose lattice changed,
+ * combines prefactor, coefficients and sector means into value and
+ * variance per eps order, stops when every requested coefficient has
+ * sqrt(dR^2 + dI^2) <= max(epsrel |A|, epsabs), and otherwise re-sizes the
+ * lattices with qmc_allocate (alpha = 2, w_i = var_i n_i^2, tau_i from the
+ * measured kernel time split by a per-sector cost model), rounding up to
+ * tabulated lattices (<= max_points). Deformed sectors use options.lambda.
+ * Outputs (host, caller-owned): value[npoints][namp][norders] for orders
+ * lowest_order.., error[..] with re = sigma of Re, im = sigma of Im.
+ * Returns QMC_E_TIMEOUT (timeout_s > 0 exceeded), QMC_E_NOT_CONVERGED
+ * (largest lattice reached) or QMC_E_SIGN_CHECK with the outputs written. */
+int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
+                  int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info);
 
 /* Evaluation that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_host.cpp"]
+SOURCES = ["qmc_kernels.cu", "qmc_host.cpp", "qmc_integrate.cpp"]
 
 
 def _nvcc() -> str:
@@ -40,8 +40,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
+    extra = list(extra_flags) + os.environ.get("QMC_NVCC_FLAGS", "").split()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                     "-I", SRC] + list(extra_flags)
+                     "-I", SRC] + extra
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src) + ".o")

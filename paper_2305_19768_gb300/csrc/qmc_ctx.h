@@ -1,0 +1,86 @@
+// Host-side state of the C-ABI shared by qmc_host.cpp and qmc_integrate.cpp.
+// Not part of the public C-ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "qmc_internal.h"
+
+constexpr uint64_t kQmcGamma = 0x9E3779B97F4A7C15ULL;
+
+struct QmcTerm {
+    int e[QMC_DMAX];
+    double c[QMC_NCOEF];
+};
+
+struct QmcHostSector {
+    int d = 0;
+    bool deform = false;
+    int a[QMC_DMAX] = {0};
+    double b[QMC_DMAX] = {0};
+    double u0 = 0, u1 = 0, f0 = 0, f1 = 0;
+    std::vector<QmcTerm> U, F;
+    int ns = 0;
+    int cls = 0;
+    int global_index = 0;  // index in the device sector table
+};
+
+struct QmcHostIntegral {
+    std::string name;
+    int L = 0, N = 0, D0 = 0;
+    std::vector<std::string> invariants;
+    int pref_lo = 0;
+    std::vector<qmc_c64> pref;
+    std::vector<QmcHostSector> sectors;
+    int max_poles = 0;
+};
+
+struct qmc_plan;
+
+struct qmc_ctx {
+    int device = 0;
+    qmc_options opt{};
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    std::map<uint64_t, std::vector<uint32_t>> lattices;
+    std::vector<QmcHostIntegral> integrals;
+    // device tables (rebuilt when an integral is loaded)
+    QmcSectorDev *d_sectors = nullptr;
+    QmcMono *d_monos = nullptr;
+    int nsectors_dev = 0;
+    double *d_kin = nullptr;
+    int npoints = 0, ninv = 0;
+    std::vector<qmc_plan *> plans;
+};
+
+struct ClassLaunch {
+    int cls = 0;
+    QmcLaunch L{};
+    QmcJobDev *d_jobs = nullptr;
+    double *d_partials = nullptr;
+    unsigned long long *d_queue = nullptr;
+    int block = 128, ppt = 16, grid = 0;
+};
+
+struct qmc_plan {
+    qmc_ctx *ctx = nullptr;
+    int lo = 0, norders = 0, njobs = 0;
+    size_t out_size = 0;
+    double *d_out = nullptr;
+    unsigned long long *d_status = nullptr;
+    std::vector<ClassLaunch> launches;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> kev;   // [2 * class launch]: around each evaluator kernel
+    cudaStream_t last_stream = nullptr;
+    double *last_out = nullptr;
+    int last_launches = 0;
+};
+
+// Record `fmt` as the context's last error and return `code`.
+int qmc_fail(qmc_ctx *ctx, int code, const char *fmt, ...);

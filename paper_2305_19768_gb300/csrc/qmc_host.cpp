@@ -16,8 +16,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/qmc.h"
-#include "qmc_internal.h"
+#include "qmc_ctx.h"
 
 extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void *stream);
 extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream);
@@ -25,90 +24,11 @@ extern "C" int qmc_k_occupancy(int cls, int block);
 
 namespace {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
-
-struct Term {
-    int e[QMC_DMAX];
-    double c[QMC_NCOEF];
-};
-
-struct HostSector {
-    int d = 0;
-    bool deform = false;
-    int a[QMC_DMAX] = {0};
-    double b[QMC_DMAX] = {0};
-    double u0 = 0, u1 = 0, f0 = 0, f1 = 0;
-    std::vector<Term> U, F;
-    int ns = 0;
-    int cls = 0;
-    int global_index = 0;  // index in the device sector table
-};
-
-struct HostIntegral {
-    std::string name;
-    int L = 0, N = 0, D0 = 0;
-    std::vector<std::string> invariants;
-    int pref_lo = 0;
-    std::vector<qmc_c64> pref;
-    std::vector<HostSector> sectors;
-    int max_poles = 0;
-};
-
-}  // namespace
-
-struct qmc_plan;
-
-struct qmc_ctx {
-    int device = 0;
-    qmc_options opt{};
-    cudaStream_t stream = nullptr;
-    int sm_count = 0;
-    std::string err;
-    std::map<uint64_t, std::vector<uint32_t>> lattices;
-    std::vector<HostIntegral> integrals;
-    // device tables (rebuilt when an integral is loaded)
-    QmcSectorDev *d_sectors = nullptr;
-    QmcMono *d_monos = nullptr;
-    int nsectors_dev = 0;
-    double *d_kin = nullptr;
-    int npoints = 0, ninv = 0;
-    std::vector<qmc_plan *> plans;
-};
-
-struct ClassLaunch {
-    int cls = 0;
-    QmcLaunch L{};
-    QmcJobDev *d_jobs = nullptr;
-    double *d_partials = nullptr;
-    unsigned long long *d_queue = nullptr;
-    int block = 128, ppt = 4, grid = 0;
-};
-
-struct qmc_plan {
-    qmc_ctx *ctx = nullptr;
-    int lo = 0, norders = 0, njobs = 0;
-    size_t out_size = 0;
-    double *d_out = nullptr;
-    unsigned long long *d_status = nullptr;
-    std::vector<ClassLaunch> launches;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::vector<cudaEvent_t> kev;   // [2 * class launch]: around each evaluator kernel
-    cudaStream_t last_stream = nullptr;
-    double *last_out = nullptr;
-    int last_launches = 0;
-};
-
-namespace {
-
-int fail(qmc_ctx *ctx, int code, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    if (ctx) ctx->err = buf;
-    return code;
-}
+constexpr uint64_t kGamma = kQmcGamma;
+using Term = QmcTerm;
+using HostSector = QmcHostSector;
+using HostIntegral = QmcHostIntegral;
+#define fail qmc_fail
 
 #define CUDA_TRY(ctx, call)                                                                     \
     do {                                                                                        \
@@ -414,6 +334,16 @@ void free_plan_buffers(qmc_plan *p) {
 }  // namespace
 
 // ====================================================================== C-ABI
+int qmc_fail(qmc_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
 extern "C" {
 
 int qmc_create(qmc_ctx **out, int device, const qmc_options *opt) {
@@ -610,7 +540,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         ClassLaunch c;
         c.cls = cls;
         c.block = ctx->opt.block == 256 ? 256 : 128;
-        c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 4;
+        c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 16;
         const uint64_t tile_k = (uint64_t)c.block * c.ppt;
         uint64_t tiles = 0;
         for (QmcJobDev &D : v) {
@@ -853,7 +783,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, QMC_E_CUDA, "cudaSetDevice failed");
     QmcJobDev recs[QMC_NOALLOC_MAX_JOBS];
     const int block = ctx->opt.block == 256 ? 256 : 128;
-    const int ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 4;
+    const int ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 16;
     const uint64_t tile_k = (uint64_t)block * ppt;
     const int hi = lo + norders - 1;
     int cls = -1;

@@ -1,0 +1,385 @@
+// Combination and adaptive allocation (host side of the C-ABI):
+// per-shift statistics, Laurent products of coefficient/prefactor series with
+// sector series, variance propagation, the lattice-size allocation of
+// Eq. (adaptive-solution), and the iterative driver qmc_integrate
+// (section "Adaptive weighted sum evaluation" of arXiv:2305.19768).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qmc_ctx.h"
+
+#define fail qmc_fail
+
+namespace {
+
+// Relative evaluation cost of a sector (FP64 operations of the evaluator's
+// formulation, up to a constant): used to split a class's measured time per
+// evaluation between its sectors (the online tau_i estimate).
+double sector_cost(const QmcHostSector &S) {
+    return 20.0 * S.d + 3.0 * (double)(S.U.size() + S.F.size()) + 30.0 * (double)(1 << S.ns) +
+           15.0 * S.ns + (S.deform ? 300.0 : 0.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmc_shift_stats(const double *sums, int m, int norders, double *mean, double *var) {
+    if (!sums || !mean || !var || m < 1 || norders < 1) return QMC_E_INVAL;
+    for (int o = 0; o < norders; ++o) {
+        for (int c = 0; c < 2; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < m; ++k) s += sums[((size_t)k * norders + o) * 2 + c];
+            const double mu = s / m;
+            double v = 0.0;
+            for (int k = 0; k < m; ++k) {
+                const double dlt = sums[((size_t)k * norders + o) * 2 + c] - mu;
+                v += dlt * dlt;
+            }
+            mean[o * 2 + c] = mu;
+            var[o * 2 + c] = m > 1 ? v / (m - 1) / m : INFINITY;
+        }
+    }
+    return QMC_OK;
+}
+
+int qmc_series_mul(const qmc_c64 *a, int a_lo, int na, const qmc_c64 *b, int b_lo, int nb, int lo, int n,
+                   qmc_c64 *out) {
+    if ((na && !a) || (nb && !b) || !out || n < 0) return QMC_E_INVAL;
+    for (int o = 0; o < n; ++o) out[o].re = out[o].im = 0.0;
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) {
+            const int o = a_lo + i + b_lo + j - lo;
+            if (o < 0 || o >= n) continue;
+            out[o].re += a[i].re * b[j].re - a[i].im * b[j].im;
+            out[o].im += a[i].re * b[j].im + a[i].im * b[j].re;
+        }
+    return QMC_OK;
+}
+
+int qmc_series_var(const qmc_c64 *c, int c_lo, int nc, const double *v, int v_lo, int nv, int lo, int n,
+                   double *out) {
+    if ((nc && !c) || (nv && !v) || !out || n < 0) return QMC_E_INVAL;
+    for (int o = 0; o < n; ++o) out[o] = 0.0;
+    for (int i = 0; i < nc; ++i) {
+        const double c2 = c[i].re * c[i].re + c[i].im * c[i].im;
+        for (int j = 0; j < nv; ++j) {
+            const int o = c_lo + i + v_lo + j - lo;
+            if (o < 0 || o >= n) continue;
+            out[o] += c2 * v[j];
+        }
+    }
+    return QMC_OK;
+}
+
+int qmc_allocate(const double *W, const double *tau, const double *V, int nsums, int nint, double alpha,
+                 double n_min, double *n_out) {
+    if (!W || !tau || !V || !n_out || nsums < 0 || nint < 1 || !(alpha > 0)) return QMC_E_INVAL;
+    for (int i = 0; i < nint; ++i) {
+        if (!(tau[i] > 0)) return QMC_E_INVAL;
+        n_out[i] = n_min;
+    }
+    const double p = 1.0 / (alpha + 1.0);
+    for (int k = 0; k < nsums; ++k) {
+        const double *Wk = W + (size_t)k * nint;
+        if (!(V[k] > 0)) continue;
+        double s = 0.0;
+        for (int i = 0; i < nint; ++i)
+            if (Wk[i] > 0) s += std::pow(Wk[i] * std::pow(tau[i], alpha), p);
+        if (!(s > 0)) continue;
+        const double lam = (1.0 / alpha) * std::pow(s / V[k], (alpha + 1.0) / alpha);
+        for (int i = 0; i < nint; ++i)
+            if (Wk[i] > 0) n_out[i] = std::max(n_out[i], std::pow(alpha * lam * Wk[i] / tau[i], p));
+    }
+    return QMC_OK;
+}
+
+int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
+                  int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info) {
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    if (!ctx || !value || !error || norders < 1 || norders > 16 || !(epsrel >= 0) || !(epsabs >= 0))
+        return fail(ctx, QMC_E_INVAL, "qmc_integrate: bad arguments");
+    if (ctx->lattices.empty()) return fail(ctx, QMC_E_INVAL, "qmc_integrate: no lattice table");
+    // --- what to sum
+    std::vector<int> ids;
+    int namp = 1, coef_lo = 0, ncoef = 1;
+    const qmc_c64 *coef = nullptr;
+    if (spec && spec->nint > 0) {
+        ids.assign(spec->integral_ids, spec->integral_ids + spec->nint);
+        namp = spec->namp > 0 ? spec->namp : 1;
+        coef = spec->coef;
+        if (coef) {
+            coef_lo = spec->coef_lo;
+            ncoef = spec->ncoef;
+        }
+    } else {
+        for (size_t i = 0; i < ctx->integrals.size(); ++i) ids.push_back((int)i);
+    }
+    if (ids.empty()) return fail(ctx, QMC_E_INVAL, "qmc_integrate: nothing to integrate");
+    for (int id : ids)
+        if (id < 0 || id >= (int)ctx->integrals.size()) return fail(ctx, QMC_E_INVAL, "bad integral id %d", id);
+    const int nint = (int)ids.size();
+    bool any_inv = false;
+    for (int id : ids) any_inv |= !ctx->integrals[id].invariants.empty();
+    const int npts = any_inv ? ctx->npoints : std::max(1, ctx->npoints);
+    if (npts < 1) return fail(ctx, QMC_E_INVAL, "qmc_integrate: no kinematic points");
+    // --- sector order window
+    const int hiA = lowest_order + norders - 1;
+    int slo = 0, shi = -1000;
+    for (int id : ids) {
+        const QmcHostIntegral &I = ctx->integrals[id];
+        slo = std::min(slo, -I.max_poles);
+        shi = std::max(shi, hiA - coef_lo - I.pref_lo);
+    }
+    if (shi < slo) return fail(ctx, QMC_E_INVAL, "qmc_integrate: requested orders below every integral's series");
+    const int sn = shi - slo + 1;
+    // --- combined coefficient series G[p][k][i] = C_ki(p) (x) prefactor_i, orders glo..
+    int glo = 1 << 20, ghi = -(1 << 20);
+    for (int id : ids) {
+        glo = std::min(glo, coef_lo + ctx->integrals[id].pref_lo);
+        ghi = std::max(ghi, coef_lo + ncoef - 1 + ctx->integrals[id].pref_lo + (int)ctx->integrals[id].pref.size() - 1);
+    }
+    const int gn = ghi - glo + 1;
+    std::vector<qmc_c64> G((size_t)npts * namp * nint * gn);
+    for (int p = 0; p < npts; ++p)
+        for (int k = 0; k < namp; ++k)
+            for (int i = 0; i < nint; ++i) {
+                const QmcHostIntegral &I = ctx->integrals[ids[i]];
+                std::vector<qmc_c64> one(1, qmc_c64{1.0, 0.0});
+                const qmc_c64 *c = coef ? coef + (((size_t)p * namp + k) * nint + i) * ncoef : one.data();
+                qmc_series_mul(c, coef ? coef_lo : 0, coef ? ncoef : 1, I.pref.data(), I.pref_lo, (int)I.pref.size(),
+                               glo, gn, &G[(((size_t)p * namp + k) * nint + i) * gn]);
+            }
+    // --- slots (point, integral, sector)
+    struct Slot {
+        int p, i, s;
+        uint64_t n = 0;
+        bool have = false, dirty = true;
+        double mean[2 * 8], var[2 * 8];
+        double cost = 1.0;
+    };
+    std::vector<Slot> slots;
+    std::vector<uint64_t> sizes;
+    for (auto &kv : ctx->lattices) sizes.push_back(kv.first);
+    const uint64_t nmax_cap = ctx->opt.max_points ? ctx->opt.max_points : sizes.back();
+    auto round_up = [&](double n) -> uint64_t {
+        for (uint64_t v : sizes)
+            if ((double)v >= n && v <= nmax_cap) return v;
+        uint64_t best = sizes.front();
+        for (uint64_t v : sizes)
+            if (v <= nmax_cap) best = v;
+        return best;
+    };
+    const uint64_t n0 = round_up((double)ctx->opt.min_points);
+    if (sn > 8) return fail(ctx, QMC_E_INVAL, "qmc_integrate: %d sector orders exceed 8", sn);
+    for (int p = 0; p < npts; ++p)
+        for (int i = 0; i < nint; ++i) {
+            const QmcHostIntegral &I = ctx->integrals[ids[i]];
+            for (int s = 0; s < (int)I.sectors.size(); ++s) {
+                Slot sl;
+                sl.p = p;
+                sl.i = i;
+                sl.s = s;
+                sl.n = n0;
+                sl.cost = sector_cost(I.sectors[s]);
+                slots.push_back(sl);
+            }
+        }
+    const int m = ctx->opt.shifts;
+    const double alpha = 2.0;
+    double evals = 0.0, kernel_s = 0.0;
+    int iter = 0, rc_final = QMC_OK;
+    std::vector<double> tau(slots.size(), 1.0);
+    std::vector<double> amp_val((size_t)npts * namp * norders * 2), amp_var((size_t)npts * namp * norders);
+    std::vector<double> amp_vre((size_t)npts * namp * norders), amp_vim((size_t)npts * namp * norders);
+    for (;;) {
+        // ---- evaluate dirty slots in one plan
+        std::vector<qmc_job> jobs;
+        std::vector<size_t> jslot;
+        for (size_t q = 0; q < slots.size(); ++q) {
+            Slot &sl = slots[q];
+            if (!sl.dirty) continue;
+            const QmcHostIntegral &I = ctx->integrals[ids[sl.i]];
+            qmc_job J;
+            memset(&J, 0, sizeof J);
+            J.integral_id = ids[sl.i];
+            J.sector = sl.s;
+            J.point = I.invariants.empty() ? 0 : sl.p;
+            J.shifts = m;
+            J.n = sl.n;
+            J.seed = ctx->opt.seed;
+            J.stream = ((uint64_t)iter << 40) | q;
+            for (int j = 0; j < 6; ++j) J.lambda[j] = ctx->opt.lambda > 0 ? ctx->opt.lambda : 0.3;
+            jobs.push_back(J);
+            jslot.push_back(q);
+        }
+        if (!jobs.empty()) {
+            qmc_plan *plan = nullptr;
+            int rc = qmc_plan_create(ctx, jobs.data(), (int)jobs.size(), slo, sn, &plan);
+            if (rc) return rc;
+            std::vector<double> out(qmc_plan_output_size(plan));
+            rc = qmc_plan_run(plan, nullptr, nullptr);
+            uint64_t sf = 0;
+            if (!rc) rc = qmc_plan_results(plan, out.data(), &sf);
+            if (rc && rc != QMC_E_SIGN_CHECK) {
+                qmc_plan_destroy(plan);
+                return rc;
+            }
+            if (rc == QMC_E_SIGN_CHECK) rc_final = QMC_E_SIGN_CHECK;
+            // per-class time per evaluation -> tau of each slot (cost-weighted)
+            for (size_t c = 0; c < plan->launches.size(); ++c) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, plan->kev[2 * c], plan->kev[2 * c + 1]);
+                kernel_s += ms * 1e-3;
+                double ev = 0.0, cw = 0.0;
+                for (size_t j = 0; j < jobs.size(); ++j) {
+                    const QmcHostSector &S = ctx->integrals[jobs[j].integral_id].sectors[jobs[j].sector];
+                    if (S.cls != plan->launches[c].cls) continue;
+                    ev += (double)jobs[j].n * m;
+                    cw += (double)jobs[j].n * m * slots[jslot[j]].cost;
+                }
+                const double per_cost = cw > 0 ? ms * 1e-3 / cw : 1e-9;
+                for (size_t j = 0; j < jobs.size(); ++j) {
+                    const QmcHostSector &S = ctx->integrals[jobs[j].integral_id].sectors[jobs[j].sector];
+                    if (S.cls == plan->launches[c].cls) tau[jslot[j]] = per_cost * slots[jslot[j]].cost;
+                }
+                evals += ev;
+            }
+            qmc_plan_destroy(plan);
+            for (size_t j = 0; j < jobs.size(); ++j) {
+                Slot &sl = slots[jslot[j]];
+                qmc_shift_stats(&out[j * (size_t)m * sn * 2], m, sn, sl.mean, sl.var);
+                sl.have = true;
+                sl.dirty = false;
+            }
+        }
+        ++iter;
+        // ---- combine into the sums and check the requested accuracy
+        bool all_ok = true;
+        std::vector<char> sum_ok((size_t)npts * namp * norders, 1);
+        std::vector<double> target((size_t)npts * namp * norders, 0.0);
+        std::fill(amp_val.begin(), amp_val.end(), 0.0);
+        std::fill(amp_var.begin(), amp_var.end(), 0.0);
+        std::fill(amp_vre.begin(), amp_vre.end(), 0.0);
+        std::fill(amp_vim.begin(), amp_vim.end(), 0.0);
+        for (const Slot &sl : slots) {
+            qmc_c64 mu[8];
+            double vv[8];
+            for (int o = 0; o < sn; ++o) {
+                mu[o].re = sl.mean[2 * o];
+                mu[o].im = sl.mean[2 * o + 1];
+                vv[o] = sl.var[2 * o] + sl.var[2 * o + 1];
+            }
+            for (int k = 0; k < namp; ++k) {
+                const qmc_c64 *g = &G[(((size_t)sl.p * namp + k) * nint + sl.i) * gn];
+                qmc_c64 a[64];
+                double v[64];
+                qmc_series_mul(g, glo, gn, mu, slo, sn, lowest_order, norders, a);
+                qmc_series_var(g, glo, gn, vv, slo, sn, lowest_order, norders, v);
+                for (int o = 0; o < norders; ++o) {
+                    const size_t idx = ((size_t)sl.p * namp + k) * norders + o;
+                    amp_val[2 * idx] += a[o].re;
+                    amp_val[2 * idx + 1] += a[o].im;
+                    amp_var[idx] += v[o];
+                    // Re and Im separately: Re(g x) has variance g_r^2 v_r + g_i^2 v_i
+                    for (int so = 0; so < sn; ++so) {
+                        const int gi = (lowest_order + o) - (slo + so) - glo;
+                        if (gi < 0 || gi >= gn) continue;
+                        const double gr2 = g[gi].re * g[gi].re, gi2 = g[gi].im * g[gi].im;
+                        amp_vre[idx] += gr2 * sl.var[2 * so] + gi2 * sl.var[2 * so + 1];
+                        amp_vim[idx] += gi2 * sl.var[2 * so] + gr2 * sl.var[2 * so + 1];
+                    }
+                }
+            }
+        }
+        for (size_t idx = 0; idx < sum_ok.size(); ++idx) {
+            const double mag = std::hypot(amp_val[2 * idx], amp_val[2 * idx + 1]);
+            const double tgt = std::max(epsrel * mag, epsabs);
+            target[idx] = tgt;
+            if (!(std::sqrt(amp_var[idx]) <= tgt)) {
+                sum_ok[idx] = 0;
+                all_ok = false;
+            }
+        }
+        const double elapsed = std::chrono::duration<double>(clk::now() - t_start).count();
+        if (all_ok) break;
+        if (timeout_s > 0 && elapsed > timeout_s) {
+            rc_final = QMC_E_TIMEOUT;
+            break;
+        }
+        // ---- allocation (Eq. adaptive-solution), one sum at a time, keeping the largest n
+        bool grew = false;
+        for (int p = 0; p < npts; ++p)
+            for (int k = 0; k < namp; ++k)
+                for (int o = 0; o < norders; ++o) {
+                    const size_t idx = ((size_t)p * namp + k) * norders + o;
+                    if (sum_ok[idx] || !(target[idx] > 0)) continue;
+                    std::vector<size_t> members;
+                    std::vector<double> W, tv;
+                    for (size_t q = 0; q < slots.size(); ++q) {
+                        const Slot &sl = slots[q];
+                        if (sl.p != p) continue;
+                        const qmc_c64 *g = &G[(((size_t)p * namp + k) * nint + sl.i) * gn];
+                        // W = sum_{o'} |g^{(o - o')}|^2 w^{(o')},  w = var n^alpha
+                        double wsum = 0.0;
+                        for (int so = 0; so < sn; ++so) {
+                            const int gi = (lowest_order + o) - (slo + so) - glo;
+                            if (gi < 0 || gi >= gn) continue;
+                            const double c2 = g[gi].re * g[gi].re + g[gi].im * g[gi].im;
+                            const double w = (sl.var[2 * so] + sl.var[2 * so + 1]) * std::pow((double)sl.n, alpha);
+                            wsum += c2 * w;
+                        }
+                        if (wsum > 0) {
+                            members.push_back(q);
+                            W.push_back(wsum);
+                            tv.push_back(tau[q]);
+                        }
+                    }
+                    if (members.empty()) continue;
+                    const double V = target[idx] * target[idx];
+                    std::vector<double> nn(members.size());
+                    qmc_allocate(W.data(), tv.data(), &V, 1, (int)members.size(), alpha, 0.0, nn.data());
+                    for (size_t u = 0; u < members.size(); ++u) {
+                        Slot &sl = slots[members[u]];
+                        const uint64_t want = round_up(nn[u]);
+                        if (want > sl.n) {
+                            sl.n = want;
+                            sl.dirty = true;
+                            grew = true;
+                        }
+                    }
+                }
+        if (!grew) {
+            rc_final = QMC_E_NOT_CONVERGED;
+            break;
+        }
+    }
+    for (size_t idx = 0; idx < (size_t)npts * namp * norders; ++idx) {
+        value[idx].re = amp_val[2 * idx];
+        value[idx].im = amp_val[2 * idx + 1];
+        error[idx].re = std::sqrt(amp_vre[idx]);
+        error[idx].im = std::sqrt(amp_vim[idx]);
+    }
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->evaluations = evals;
+        info->seconds = std::chrono::duration<double>(clk::now() - t_start).count();
+        info->kernel_seconds = kernel_s;
+        info->iterations = iter;
+        uint64_t mx = 0;
+        for (const Slot &sl : slots) mx = std::max(mx, sl.n);
+        info->max_lattice = mx;
+    }
+    if (rc_final == QMC_E_TIMEOUT) return fail(ctx, QMC_E_TIMEOUT, "qmc_integrate: timeout after %d iterations", iter);
+    if (rc_final == QMC_E_NOT_CONVERGED)
+        return fail(ctx, QMC_E_NOT_CONVERGED, "qmc_integrate: largest lattice reached before the requested accuracy");
+    if (rc_final == QMC_E_SIGN_CHECK)
+        return fail(ctx, QMC_E_SIGN_CHECK, "qmc_integrate: deformed points had Im F > 0 (lambda too large)");
+    return QMC_OK;
+}
+
+}  // extern "C"

@@ -617,8 +617,12 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
 }
 
 // ---------------------------------------------------------------- the evaluator
+#ifndef QMC_MINB
+#define QMC_MINB 3   // resident 128-thread blocks per SM the real evaluator's registers must allow
+#endif
+
 template <int DMAX, int SMAX, int LMAX, bool CPLX, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
+__global__ void __launch_bounds__(BLOCK, CPLX ? 1 : QMC_MINB) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
     using T = typename std::conditional<CPLX, dc, double>::type;
     const int lo = Lc.lo, nord = Lc.norders;

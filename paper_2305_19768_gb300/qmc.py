@@ -35,7 +35,19 @@ class qmc_options(ctypes.Structure):
     _fields_ = [("shifts", ctypes.c_int), ("seed", ctypes.c_uint64), ("block", ctypes.c_int),
                 ("ppt", ctypes.c_int), ("min_points", ctypes.c_uint64),
                 ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("lambda_", ctypes.c_double), ("reserved", ctypes.c_int * 6)]
+
+
+class qmc_sum_spec(ctypes.Structure):
+    _fields_ = [("integral_ids", ctypes.POINTER(ctypes.c_int)), ("nint", ctypes.c_int),
+                ("namp", ctypes.c_int), ("coef", ctypes.c_void_p), ("coef_lo", ctypes.c_int),
+                ("ncoef", ctypes.c_int)]
+
+
+class qmc_integrate_info(ctypes.Structure):
+    _fields_ = [("evaluations", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("kernel_seconds", ctypes.c_double), ("iterations", ctypes.c_int),
+                ("max_lattice", ctypes.c_uint64)]
 
 
 class qmc_job(ctypes.Structure):
@@ -85,6 +97,12 @@ def lib():
                 "qmc_fp64_peak": ([vp, P(dbl)], i32),
                 "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
                 "qmc_fp64_log": ([vp, P(dbl), sz, P(dbl)], i32),
+                "qmc_shift_stats": ([P(dbl), i32, i32, P(dbl), P(dbl)], i32),
+                "qmc_series_mul": ([P(qmc_c64), i32, i32, P(qmc_c64), i32, i32, i32, i32, P(qmc_c64)], i32),
+                "qmc_series_var": ([P(qmc_c64), i32, i32, P(dbl), i32, i32, i32, i32, P(dbl)], i32),
+                "qmc_allocate": ([P(dbl), P(dbl), P(dbl), i32, i32, dbl, dbl, P(dbl)], i32),
+                "qmc_integrate": ([vp, P(qmc_sum_spec), dbl, dbl, dbl, i32, i32, P(qmc_c64), P(qmc_c64),
+                                   P(qmc_integrate_info)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -100,7 +118,8 @@ def exported_symbols():
             "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
-            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log"]
+            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log",
+            "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate"]
 
 
 def _dp(a):
@@ -117,7 +136,7 @@ def _check(ctx, rc):
 def qmc_create(device: int = 0, **opts):
     o = qmc_options()
     for k, v in opts.items():
-        setattr(o, k, v)
+        setattr(o, "lambda_" if k == "lambda" else k, v)
     h = ctypes.c_void_p()
     rc = lib().qmc_create(ctypes.byref(h), device, ctypes.byref(o))
     if rc != QMC_OK:
@@ -258,6 +277,80 @@ def qmc_fp64_log(ctx, x):
     out = np.zeros_like(x)
     _check(ctx, lib().qmc_fp64_log(ctx, _dp(x), x.size, _dp(out)))
     return out
+
+
+def _c64(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a, a.ctypes.data_as(P(qmc_c64))
+
+
+def qmc_shift_stats(sums):
+    """sums [m][norders][2] -> (mean [norders][2], variance of the mean [norders][2])."""
+    sums = np.ascontiguousarray(sums, dtype=np.float64)
+    m, no = sums.shape[0], sums.shape[1]
+    mean = np.zeros((no, 2))
+    var = np.zeros((no, 2))
+    _check(None, lib().qmc_shift_stats(_dp(sums), m, no, _dp(mean), _dp(var)))
+    return mean, var
+
+
+def qmc_series_mul(a, a_lo, b, b_lo, lo, n):
+    a, pa = _c64(a)
+    b, pb = _c64(b)
+    out = np.zeros(n, dtype=np.complex128)
+    _check(None, lib().qmc_series_mul(pa, a_lo, len(a), pb, b_lo, len(b), lo, n,
+                                      out.ctypes.data_as(P(qmc_c64))))
+    return out
+
+
+def qmc_series_var(c, c_lo, v, v_lo, lo, n):
+    c, pc = _c64(c)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(n)
+    _check(None, lib().qmc_series_var(pc, c_lo, len(c), _dp(v), v_lo, len(v), lo, n, _dp(out)))
+    return out
+
+
+def qmc_allocate(W, tau, V, alpha=2.0, n_min=0.0):
+    """W [nsums][nint], tau [nint], V [nsums] -> n [nint] (Eq. adaptive-solution)."""
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    V = np.ascontiguousarray(np.atleast_1d(V), dtype=np.float64)
+    out = np.zeros(W.shape[1])
+    _check(None, lib().qmc_allocate(_dp(W), _dp(tau), _dp(V), W.shape[0], W.shape[1], alpha, n_min,
+                                    _dp(out)))
+    return out
+
+
+def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, epsabs=0.0, timeout=0.0,
+                  lowest_order=0, norders=1, npoints=1, namp=1, check=True):
+    """Adaptive integration; returns (value, error, info dict, return code).
+    value/error: complex [npoints][namp][norders] (error = sigma_re + 1j sigma_im)."""
+    spec = None
+    keep = []
+    if integral_ids is not None:
+        ids = (ctypes.c_int * len(integral_ids))(*integral_ids)
+        keep.append(ids)
+        spec = qmc_sum_spec()
+        spec.integral_ids = ids
+        spec.nint = len(integral_ids)
+        spec.namp = namp
+        if coef is not None:
+            c = np.ascontiguousarray(coef, dtype=np.complex128)
+            keep.append(c)
+            spec.coef = c.ctypes.data
+            spec.coef_lo = coef_lo
+            spec.ncoef = c.shape[-1]
+    value = np.zeros((npoints, namp, norders), dtype=np.complex128)
+    error = np.zeros((npoints, namp, norders), dtype=np.complex128)
+    info = qmc_integrate_info()
+    rc = lib().qmc_integrate(ctx, ctypes.byref(spec) if spec is not None else None, epsrel, epsabs, timeout,
+                             lowest_order, norders, value.ctypes.data_as(P(qmc_c64)),
+                             error.ctypes.data_as(P(qmc_c64)), ctypes.byref(info))
+    if check and rc not in (0,):
+        _check(ctx, rc)
+    d = {k: getattr(info, k) for k, _ in qmc_integrate_info._fields_}
+    return value, error, d, rc
 
 
 def qmc_fp64_peak(ctx) -> float:

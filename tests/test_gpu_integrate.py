@@ -1,0 +1,104 @@
+"""The adaptive driver qmc_integrate on the GPU: the requested accuracy is
+reached and the values agree with the closed forms within their errors;
+amplitudes with coefficient series; timeout and lattice-limit statuses."""
+import numpy as np
+import pytest
+
+from golden_values import closed_form
+from paper_2305_19768_gb300 import qmc
+from paper_2305_19768_gb300.inputs import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(**opts):
+    ctx = qmc.qmc_create(0, **opts)
+    qmc.load_lattice_table(ctx)
+    return ctx
+
+
+def _within(val, err, exact, nsig=4.0):
+    sig = np.hypot(err.real, err.imag)
+    assert abs(val - exact) <= nsig * sig + 1e-13 * abs(exact), (val, exact, sig)
+
+
+def test_massless_box_to_1e_6():
+    ctx = _ctx()
+    try:
+        I = w.box_massless()
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-6, lowest_order=-2, norders=3)
+        assert rc == 0
+        ex = closed_form("box1L_massless", "s=-3,t=-2")
+        for o, order in enumerate((-2, -1, 0)):
+            _within(val[0, 0, o], err[0, 0, o], ex[order])
+            assert np.hypot(err[0, 0, o].real, err[0, 0, o].imag) <= 1e-6 * abs(val[0, 0, o]) * 1.0000001
+        assert info["iterations"] >= 1 and info["evaluations"] > 0
+    finally:
+        qmc.qmc_destroy(ctx)
+
+
+def test_amplitude_with_coefficient_series():
+    # A = (2 - eps) box(s,t) + 3 triangle: coefficients as Laurent series
+    ctx = _ctx()
+    try:
+        box = w.box_massless()
+        tri = w.triangle_massive()
+        ib = qmc.qmc_load_sectors_mem(ctx, box.to_text())
+        it = qmc.qmc_load_sectors_mem(ctx, tri.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+        coef = np.zeros((1, 1, 2, 2), dtype=complex)
+        coef[0, 0, 0] = [2.0, -1.0]
+        coef[0, 0, 1] = [3.0, 0.0]
+        val, err, info, rc = qmc.qmc_integrate(ctx, [ib, it], coef=coef, coef_lo=0, epsrel=1e-7,
+                                               lowest_order=-2, norders=3)
+        assert rc == 0
+        b = closed_form("box1L_massless", "s=-3,t=-2")
+        t0 = closed_form("triangle_m1_pm1")[0]
+        exact = [2 * b[-2], 2 * b[-1] - b[-2], 2 * b[0] - b[-1] + 3 * t0]
+        for o in range(3):
+            _within(val[0, 0, o], err[0, 0, o], exact[o])
+    finally:
+        qmc.qmc_destroy(ctx)
+
+
+def test_several_points_and_physical_deformed_bubble():
+    ctx = _ctx(**{"lambda": 0.5})
+    try:
+        I = w.bubble(1, "s")
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[10.0], [-3.0]]))
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-9, lowest_order=-1, norders=2,
+                                               npoints=2)
+        assert rc == 0
+        for p, s in enumerate((10, -3)):
+            ex = closed_form("bubble_m1", f"s={s}")
+            _within(val[p, 0, 0], err[p, 0, 0], ex[-1])
+            _within(val[p, 0, 1], err[p, 0, 1], ex[0])
+    finally:
+        qmc.qmc_destroy(ctx)
+
+
+def test_lattice_limit_and_timeout_statuses():
+    ctx = _ctx(max_points=20011)
+    try:
+        I = w.box_massless()
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-13, lowest_order=-2, norders=3,
+                                               check=False)
+        assert rc == -5 and info["max_lattice"] <= 20011
+        assert np.all(np.isfinite(val))
+    finally:
+        qmc.qmc_destroy(ctx)
+    ctx = _ctx()
+    try:
+        I = w.box_massless()
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-14, timeout=1e-9, lowest_order=-2,
+                                               norders=3, check=False)
+        assert rc == -4 and info["iterations"] == 1
+    finally:
+        qmc.qmc_destroy(ctx)
