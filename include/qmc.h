@@ -163,6 +163,16 @@ int qmc_plan_results(qmc_plan *plan, double *out, uint64_t *sign_failures);
  * it issued. Waits for the run to finish. Any output may be NULL. */
 int qmc_plan_last_time(qmc_plan *plan, float *ms_total, float *ms_eval, int *launches);
 
+/* Replay the plan's runs as one CUDA graph (enable != 0): the first run
+ * after enabling captures the sequence (status reset, per-class evaluator
+ * and finishing kernels, timing events) on the run's stream and later runs
+ * launch the instantiated graph; a different out_dev recaptures. */
+int qmc_plan_use_graph(qmc_plan *plan, int enable);
+
+/* Sign-check failures (deformed points with Im F > 0) of each job of the
+ * plan's last run, host array out[njobs] in the caller's job order. Waits. */
+int qmc_plan_job_failures(qmc_plan *plan, uint32_t *out);
+
 /* Free a plan. NULL is a no-op. */
 void qmc_plan_destroy(qmc_plan *plan);
 
@@ -183,6 +193,27 @@ int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d,
 /* Random shifts the evaluator draws for (seed, stream): Delta[s][j], host
  * array [m][d] (see qmc_job.stream). Computed on the device. */
 int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta);
+
+/* Choose the contour-deformation parameter of every deformed job by
+ * presampling (the paper's number_of_presamples): candidates
+ * lambda_max * 0.7^c, c < ncand (<= 32), are each evaluated on the smallest
+ * tabulated lattice with >= presamples/2 points and 2 shifts; a candidate
+ * qualifies if no sample has Im F(z) > 0, and among the qualifying ones the
+ * smallest shift-to-shift spread of the highest requested order wins (ties
+ * to the larger lambda). Writes jobs[i].lambda[0..5] (host array, in/out);
+ * undeformed jobs are untouched. QMC_E_SIGN_CHECK if some job has no
+ * qualifying candidate (it gets the smallest one). */
+int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int norders, double lambda_max,
+                         int ncand);
+
+/* Autotune the evaluator's launch shape per kernel class (real d <= 3,
+ * deformed d <= 3, real d <= 6): on up to 32 of the given jobs per class
+ * (at most 8 shifts each) every block size in {128, 256} and points per
+ * thread in {4, 8, 16, 32} is timed with CUDA events; the fastest is kept in
+ * the context and used by later plans whose options leave block/ppt at 0.
+ * best_block/best_ppt (may be NULL) receive [3] entries (0 = class absent). */
+int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
+                 int *best_ppt);
 
 /* ------------------------------------------------------------------------
  * Combination and allocation (host arithmetic, no GPU needed)

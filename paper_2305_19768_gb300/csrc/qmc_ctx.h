@@ -57,6 +57,8 @@ struct qmc_ctx {
     double *d_kin = nullptr;
     int npoints = 0, ninv = 0;
     std::vector<qmc_plan *> plans;
+    int tuned_block[QMC_NCLASS] = {0, 0, 0};   // autotuned launch shape per kernel class (0 = default)
+    int tuned_ppt[QMC_NCLASS] = {0, 0, 0};
 };
 
 struct ClassLaunch {
@@ -65,6 +67,8 @@ struct ClassLaunch {
     QmcJobDev *d_jobs = nullptr;
     double *d_partials = nullptr;
     unsigned long long *d_queue = nullptr;
+    unsigned int *d_jobfail = nullptr;   // per-job sign-check failures
+    std::vector<int> orig;               // caller's index of each class-local job
     int block = 128, ppt = 16, grid = 0;
 };
 
@@ -80,6 +84,9 @@ struct qmc_plan {
     cudaStream_t last_stream = nullptr;
     double *last_out = nullptr;
     int last_launches = 0;
+    bool use_graph = false;              // replay the run as one CUDA graph
+    cudaGraphExec_t gexec = nullptr;
+    double *graph_out = nullptr;         // output pointer the graph was captured with
 };
 
 // Record `fmt` as the context's last error and return `code`.

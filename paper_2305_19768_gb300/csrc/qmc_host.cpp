@@ -319,7 +319,10 @@ void free_plan_buffers(qmc_plan *p) {
         cudaFree(c.d_jobs);
         cudaFree(c.d_partials);
         cudaFree(c.d_queue);
+        cudaFree(c.d_jobfail);
     }
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
     p->launches.clear();
     cudaFree(p->d_out);
     cudaFree(p->d_status);
@@ -474,6 +477,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
     cudaSetDevice(ctx->device);
     const int hi = lo + norders - 1;
     std::vector<std::vector<QmcJobDev>> per(QMC_NCLASS);
+    std::vector<std::vector<int>> per_orig(QMC_NCLASS);
     uint64_t out_off = 0;
     for (int i = 0; i < njobs; ++i) {
         const qmc_job &J = jobs[i];
@@ -483,7 +487,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         if (J.sector < 0 || J.sector >= (int)I.sectors.size())
             return fail(ctx, QMC_E_INVAL, "job %d: bad sector %d", i, J.sector);
         const HostSector &S = I.sectors[J.sector];
-        if ((int)I.invariants.size() != ctx->ninv && ctx->ninv * ctx->npoints > 0)
+        if (!I.invariants.empty() && (int)I.invariants.size() != ctx->ninv)
             return fail(ctx, QMC_E_INVAL, "job %d: integral has %zu invariants, kinematics %d", i,
                         I.invariants.size(), ctx->ninv);
         if (J.point < 0 || (J.point >= ctx->npoints && !(I.invariants.empty() && J.point == 0)))
@@ -511,6 +515,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         }
         out_off += (uint64_t)J.shifts * norders * 2;
         per[S.cls].push_back(D);
+        per_orig[S.cls].push_back(i);
     }
     qmc_plan *p = new qmc_plan();
     p->ctx = ctx;
@@ -539,8 +544,9 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         if (v.empty()) continue;
         ClassLaunch c;
         c.cls = cls;
-        c.block = ctx->opt.block == 256 ? 256 : 128;
-        c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 16;
+        c.orig = per_orig[cls];
+        c.block = ctx->opt.block == 256 ? 256 : (ctx->opt.block == 128 ? 128 : (ctx->tuned_block[cls] ? ctx->tuned_block[cls] : 128));
+        c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : (ctx->tuned_ppt[cls] ? ctx->tuned_ppt[cls] : 16);
         const uint64_t tile_k = (uint64_t)c.block * c.ppt;
         uint64_t tiles = 0;
         for (QmcJobDev &D : v) {
@@ -553,6 +559,8 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         PLAN_TRY(cudaMalloc(&c.d_partials, std::max<uint64_t>(1, tiles) * 2 * norders * sizeof(double)));
         PLAN_TRY(cudaMalloc(&c.d_queue, sizeof(unsigned long long)));
         PLAN_TRY(cudaMemset(c.d_queue, 0, sizeof(unsigned long long)));
+        PLAN_TRY(cudaMalloc(&c.d_jobfail, v.size() * sizeof(unsigned int)));
+        PLAN_TRY(cudaMemset(c.d_jobfail, 0, v.size() * sizeof(unsigned int)));
         int occ = qmc_k_occupancy(cls, c.block);
         if (occ < 1) occ = 1;
         c.grid = (int)std::min<uint64_t>(tiles, (uint64_t)ctx->sm_count * occ);
@@ -572,6 +580,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         L.queue = c.d_queue;
         L.status = p->d_status;
         L.out = p->d_out;
+        L.job_fail = c.d_jobfail;
         p->launches.push_back(c);
     }
     for (size_t i = 0; i < 2 * p->launches.size(); ++i) {
@@ -587,12 +596,12 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
 
 size_t qmc_plan_output_size(const qmc_plan *plan) { return plan ? plan->out_size : 0; }
 
-int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
-    if (!plan) return QMC_E_INVAL;
+}  // extern "C"
+
+namespace {
+// Enqueue one evaluation of the plan on `st` writing to `out`.
+int plan_enqueue(qmc_plan *plan, double *out, cudaStream_t st) {
     qmc_ctx *ctx = plan->ctx;
-    cudaSetDevice(ctx->device);
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
-    double *out = out_dev ? out_dev : plan->d_out;
     CUDA_TRY(ctx, cudaMemsetAsync(plan->d_status, 0, 2 * sizeof(unsigned long long), st));
     CUDA_TRY(ctx, cudaEventRecord(plan->ev0, st));
     int launches = 0;
@@ -600,6 +609,7 @@ int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
         ClassLaunch &c = plan->launches[i];
         c.L.out = out;
         c.L.kin = ctx->d_kin;
+        CUDA_TRY(ctx, cudaMemsetAsync(c.d_jobfail, 0, c.orig.size() * sizeof(unsigned int), st));
         CUDA_TRY(ctx, cudaEventRecord(plan->kev[2 * i], st));
         if (c.L.ntiles > 0) {
             if (qmc_k_launch_eval(c.cls, &c.L, c.block, c.ppt, c.grid, st))
@@ -612,9 +622,67 @@ int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
         ++launches;
     }
     CUDA_TRY(ctx, cudaEventRecord(plan->ev1, st));
+    plan->last_launches = launches;
+    return QMC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
+    if (!plan) return QMC_E_INVAL;
+    qmc_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    double *out = out_dev ? out_dev : plan->d_out;
+    if (plan->use_graph) {
+        if (!plan->gexec || plan->graph_out != out) {
+            if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
+            plan->gexec = nullptr;
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int rc = plan_enqueue(plan, out, st);
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(ctx, QMC_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&plan->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(ctx, QMC_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            plan->graph_out = out;
+        }
+        CUDA_TRY(ctx, cudaGraphLaunch(plan->gexec, st));
+    } else {
+        int rc = plan_enqueue(plan, out, st);
+        if (rc) return rc;
+    }
     plan->last_stream = st;
     plan->last_out = out;
-    plan->last_launches = launches;
+    return QMC_OK;
+}
+
+int qmc_plan_use_graph(qmc_plan *plan, int enable) {
+    if (!plan) return QMC_E_INVAL;
+    plan->use_graph = enable != 0;
+    if (!plan->use_graph && plan->gexec) {
+        cudaGraphExecDestroy(plan->gexec);
+        plan->gexec = nullptr;
+    }
+    return QMC_OK;
+}
+
+int qmc_plan_job_failures(qmc_plan *plan, uint32_t *out) {
+    if (!plan || !out) return QMC_E_INVAL;
+    qmc_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    CUDA_TRY(ctx, cudaStreamSynchronize(plan->last_stream ? plan->last_stream : ctx->stream));
+    for (const ClassLaunch &c : plan->launches) {
+        std::vector<uint32_t> v(c.orig.size());
+        CUDA_TRY(ctx, cudaMemcpy(v.data(), c.d_jobfail, v.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        for (size_t j = 0; j < v.size(); ++j) out[c.orig[j]] = v[j];
+    }
     return QMC_OK;
 }
 

@@ -383,3 +383,148 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- presampling and autotuning
+extern "C" int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int norders,
+                                    double lambda_max, int ncand) {
+    if (!ctx || !jobs || njobs < 0 || norders < 1 || !(lambda_max > 0) || ncand < 1 || ncand > 32)
+        return fail(ctx, QMC_E_INVAL, "qmc_presample_lambda: bad arguments");
+    std::vector<uint64_t> sizes;
+    for (auto &kv : ctx->lattices) sizes.push_back(kv.first);
+    if (sizes.empty()) return fail(ctx, QMC_E_INVAL, "qmc_presample_lambda: no lattice table");
+    const int m_pre = 2;
+    const double want = std::max(2.0, (double)ctx->opt.presamples / m_pre);
+    uint64_t n_pre = sizes.back();
+    for (uint64_t v : sizes)
+        if ((double)v >= want) {
+            n_pre = v;
+            break;
+        }
+    std::vector<qmc_job> cand;
+    std::vector<int> owner;
+    std::vector<double> lam;
+    for (int i = 0; i < njobs; ++i) {
+        const qmc_job &J = jobs[i];
+        if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size())
+            return fail(ctx, QMC_E_INVAL, "job %d: bad integral id", i);
+        const QmcHostIntegral &I = ctx->integrals[J.integral_id];
+        if (J.sector < 0 || J.sector >= (int)I.sectors.size()) return fail(ctx, QMC_E_INVAL, "job %d: bad sector", i);
+        if (!I.sectors[J.sector].deform) continue;
+        double l = lambda_max;
+        for (int c = 0; c < ncand; ++c, l *= 0.7) {
+            qmc_job C = J;
+            C.shifts = m_pre;
+            C.n = n_pre;
+            C.stream = J.stream * 64 + (uint64_t)c + 0x7000000000000000ULL;
+            for (int j = 0; j < 6; ++j) C.lambda[j] = l;
+            cand.push_back(C);
+            owner.push_back(i);
+            lam.push_back(l);
+        }
+    }
+    if (cand.empty()) return QMC_OK;
+    qmc_plan *plan = nullptr;
+    int rc = qmc_plan_create(ctx, cand.data(), (int)cand.size(), lo, norders, &plan);
+    if (rc) return rc;
+    std::vector<double> out(qmc_plan_output_size(plan));
+    std::vector<uint32_t> fails(cand.size(), 0);
+    rc = qmc_plan_run(plan, nullptr, nullptr);
+    if (!rc) {
+        rc = qmc_plan_results(plan, out.data(), nullptr);
+        if (rc == QMC_E_SIGN_CHECK) rc = QMC_OK;
+    }
+    if (!rc) rc = qmc_plan_job_failures(plan, fails.data());
+    qmc_plan_destroy(plan);
+    if (rc) return rc;
+    // choose per job: zero failures, smallest shift spread of the highest order; ties -> larger lambda
+    bool all_found = true;
+    for (int i = 0; i < njobs; ++i) {
+        double best_var = INFINITY, best_l = -1.0, smallest = INFINITY;
+        bool any = false;
+        for (size_t c = 0; c < cand.size(); ++c) {
+            if (owner[c] != i) continue;
+            any = true;
+            smallest = std::min(smallest, lam[c]);
+            if (fails[c]) continue;
+            const double *q = &out[c * (size_t)m_pre * norders * 2];
+            const int o = norders - 1;
+            const double dr = q[o * 2] - q[(norders + o) * 2], di = q[o * 2 + 1] - q[(norders + o) * 2 + 1];
+            const double v = dr * dr + di * di;
+            if (v < best_var || (v == best_var && lam[c] > best_l)) {
+                best_var = v;
+                best_l = lam[c];
+            }
+        }
+        if (!any) continue;
+        if (best_l < 0) {
+            all_found = false;
+            best_l = smallest;
+        }
+        for (int j = 0; j < 6; ++j) jobs[i].lambda[j] = best_l;
+    }
+    if (!all_found)
+        return fail(ctx, QMC_E_SIGN_CHECK, "qmc_presample_lambda: some jobs fail the sign check for every candidate");
+    return QMC_OK;
+}
+
+extern "C" int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
+                            int *best_ppt) {
+    if (!ctx || !jobs || njobs < 1 || norders < 1) return fail(ctx, QMC_E_INVAL, "qmc_autotune: bad arguments");
+    // a sample of up to 32 jobs per kernel class, at most 8 shifts each
+    std::vector<std::vector<qmc_job>> per(QMC_NCLASS);
+    for (int i = 0; i < njobs; ++i) {
+        const qmc_job &J = jobs[i];
+        if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size()) continue;
+        const QmcHostIntegral &I = ctx->integrals[J.integral_id];
+        if (J.sector < 0 || J.sector >= (int)I.sectors.size()) continue;
+        const int cls = I.sectors[J.sector].cls;
+        if (per[cls].size() < 32) {
+            qmc_job C = J;
+            C.shifts = std::min(C.shifts, 8);
+            per[cls].push_back(C);
+        }
+    }
+    const int blocks[2] = {128, 256};
+    const int ppts[4] = {4, 8, 16, 32};
+    const qmc_options saved = ctx->opt;
+    for (int cls = 0; cls < QMC_NCLASS; ++cls) {
+        if (per[cls].empty()) continue;
+        double best = INFINITY;
+        int bb = 128, bp = 16;
+        for (int b : blocks)
+            for (int p : ppts) {
+                ctx->opt.block = b;
+                ctx->opt.ppt = p;
+                qmc_plan *plan = nullptr;
+                int rc = qmc_plan_create(ctx, per[cls].data(), (int)per[cls].size(), lo, norders, &plan);
+                if (rc) {
+                    ctx->opt = saved;
+                    return rc;
+                }
+                float ms = 0.f, best_ms = INFINITY;
+                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                    rc = qmc_plan_run(plan, nullptr, nullptr);
+                    if (!rc) rc = qmc_plan_last_time(plan, nullptr, &ms, nullptr);
+                    if (rep > 0) best_ms = std::min(best_ms, ms);
+                }
+                qmc_plan_destroy(plan);
+                if (rc) {
+                    ctx->opt = saved;
+                    return rc;
+                }
+                if (best_ms < best) {
+                    best = best_ms;
+                    bb = b;
+                    bp = p;
+                }
+            }
+        ctx->tuned_block[cls] = bb;
+        ctx->tuned_ppt[cls] = bp;
+    }
+    ctx->opt = saved;
+    for (int cls = 0; cls < QMC_NCLASS; ++cls) {
+        if (best_block) best_block[cls] = ctx->tuned_block[cls];
+        if (best_ppt) best_ppt[cls] = ctx->tuned_ppt[cls];
+    }
+    return QMC_OK;
+}

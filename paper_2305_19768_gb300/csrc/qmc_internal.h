@@ -70,6 +70,7 @@ struct QmcLaunch {
     unsigned long long *queue;   // tile counter (reset by the finish kernel)
     unsigned long long *status;  // [0]: sign-check failures, [1]: non-finite partials
     double *out;           // per-shift sums
+    unsigned int *job_fail;      // per-job sign-check failures (class-local job index) or null
 };
 
 // Fixed scratch of the no-allocation entry point (qmc_eval_jobs_noalloc).

@@ -631,8 +631,8 @@ __global__ void __launch_bounds__(BLOCK, CPLX ? 1 : QMC_MINB) qmc_eval_kernel(Qm
         S.cached_point = -1;
     }
     for (int i = threadIdx.x; i < 3 * QMC_LOG_TABLE_ROWS; i += blockDim.x) S.logtab[i] = kLogTable[i];
-    int signfail_total = 0;
     for (;;) {
+        int signfail_tile = 0;
         __syncthreads();  // previous tile fully consumed
         if (threadIdx.x == 0) {
             unsigned long long tile = atomicAdd(Lc.queue, 1ULL);
@@ -720,13 +720,21 @@ __global__ void __launch_bounds__(BLOCK, CPLX ? 1 : QMC_MINB) qmc_eval_kernel(Qm
                 if (W == 0.0 || zero_t) continue;
                 T res[LMAX];
                 if constexpr (CPLX) {
-                    eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, hi, nord, res, signfail_total);
+                    eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, hi, nord, res, signfail_tile);
                 } else {
                     eval_real<DMAX, SMAX, LMAX>(S, t, lo, hi, nord, res);
                 }
 #pragma unroll
                 for (int o = 0; o < LMAX; ++o)
                     if (o < nord) acc[o] = acc[o] + mulsc(res[o], W);
+            }
+        }
+        // sign-check failures of this tile: per job (if counted) and in total
+        if (CPLX && __ballot_sync(0xffffffffu, signfail_tile != 0)) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)signfail_tile);
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(Lc.status, (unsigned long long)v);
+                if (Lc.job_fail) atomicAdd(Lc.job_fail + jidx, v);
             }
         }
         // block reduction: warp shuffles, then warps in index order
@@ -752,16 +760,6 @@ __global__ void __launch_bounds__(BLOCK, CPLX ? 1 : QMC_MINB) qmc_eval_kernel(Qm
             for (int w = 0; w < BLOCK / 32; ++w) sum += S.red[w][threadIdx.x];
             Lc.partials[tile * (uint64_t)(2 * nord) + threadIdx.x] = sum;
             if (!isfinite(sum)) atomicAdd(Lc.status + 1, 1ULL);
-        }
-    }
-    if (CPLX) {
-        // one atomic per warp at most
-        unsigned mask = __ballot_sync(0xffffffffu, signfail_total != 0);
-        if (mask) {
-            int v = signfail_total;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0) atomicAdd(Lc.status, (unsigned long long)v);
         }
     }
 }

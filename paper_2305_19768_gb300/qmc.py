@@ -98,6 +98,10 @@ def lib():
                 "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
                 "qmc_fp64_log": ([vp, P(dbl), sz, P(dbl)], i32),
                 "qmc_shift_stats": ([P(dbl), i32, i32, P(dbl), P(dbl)], i32),
+                "qmc_plan_use_graph": ([vp, i32], i32),
+                "qmc_plan_job_failures": ([vp, P(ctypes.c_uint32)], i32),
+                "qmc_presample_lambda": ([vp, P(qmc_job), i32, i32, i32, dbl, i32], i32),
+                "qmc_autotune": ([vp, P(qmc_job), i32, i32, i32, P(i32), P(i32)], i32),
                 "qmc_series_mul": ([P(qmc_c64), i32, i32, P(qmc_c64), i32, i32, i32, i32, P(qmc_c64)], i32),
                 "qmc_series_var": ([P(qmc_c64), i32, i32, P(dbl), i32, i32, i32, i32, P(dbl)], i32),
                 "qmc_allocate": ([P(dbl), P(dbl), P(dbl), i32, i32, dbl, dbl, P(dbl)], i32),
@@ -119,7 +123,8 @@ def exported_symbols():
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
             "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log",
-            "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate"]
+            "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
+            "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune"]
 
 
 def _dp(a):
@@ -236,6 +241,31 @@ def qmc_plan_last_time(ctx, plan):
     ms, mse, nl = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
     _check(ctx, lib().qmc_plan_last_time(plan, ctypes.byref(ms), ctypes.byref(mse), ctypes.byref(nl)))
     return ms.value, mse.value, nl.value
+
+
+def qmc_plan_use_graph(ctx, plan, enable=True):
+    _check(ctx, lib().qmc_plan_use_graph(plan, 1 if enable else 0))
+
+
+def qmc_plan_job_failures(ctx, plan, njobs):
+    out = np.zeros(njobs, dtype=np.uint32)
+    _check(ctx, lib().qmc_plan_job_failures(plan, out.ctypes.data_as(P(ctypes.c_uint32))))
+    return out
+
+
+def qmc_presample_lambda(ctx, jobs, njobs, lo, norders, lambda_max=1.0, ncand=12, check=True):
+    """Choose lambda per deformed job in place (jobs is the ctypes array from make_jobs)."""
+    rc = lib().qmc_presample_lambda(ctx, jobs, njobs, lo, norders, lambda_max, ncand)
+    if check:
+        _check(ctx, rc)
+    return np.array([jobs[i].lambda_[0] for i in range(njobs)]), rc
+
+
+def qmc_autotune(ctx, jobs, njobs, lo, norders):
+    bb = (ctypes.c_int * 3)()
+    bp = (ctypes.c_int * 3)()
+    _check(ctx, lib().qmc_autotune(ctx, jobs, njobs, lo, norders, bb, bp))
+    return list(bb), list(bp)
 
 
 def qmc_plan_destroy(plan):
