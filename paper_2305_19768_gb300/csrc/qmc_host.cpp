@@ -599,29 +599,32 @@ size_t qmc_plan_output_size(const qmc_plan *plan) { return plan ? plan->out_size
 }  // extern "C"
 
 namespace {
-// Enqueue one evaluation of the plan on `st` writing to `out`.
-int plan_enqueue(qmc_plan *plan, double *out, cudaStream_t st) {
+// Enqueue one evaluation of the plan on `st` writing to `out`. While a graph
+// is being captured the timing events become external event-record nodes,
+// so that the host can still query them after each replay.
+int plan_enqueue(qmc_plan *plan, double *out, cudaStream_t st, bool capturing) {
     qmc_ctx *ctx = plan->ctx;
+    const unsigned evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CUDA_TRY(ctx, cudaMemsetAsync(plan->d_status, 0, 2 * sizeof(unsigned long long), st));
-    CUDA_TRY(ctx, cudaEventRecord(plan->ev0, st));
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->ev0, st, evflags));
     int launches = 0;
     for (size_t i = 0; i < plan->launches.size(); ++i) {
         ClassLaunch &c = plan->launches[i];
         c.L.out = out;
         c.L.kin = ctx->d_kin;
         CUDA_TRY(ctx, cudaMemsetAsync(c.d_jobfail, 0, c.orig.size() * sizeof(unsigned int), st));
-        CUDA_TRY(ctx, cudaEventRecord(plan->kev[2 * i], st));
+        CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->kev[2 * i], st, evflags));
         if (c.L.ntiles > 0) {
             if (qmc_k_launch_eval(c.cls, &c.L, c.block, c.ppt, c.grid, st))
                 return fail(ctx, QMC_E_CUDA, "evaluator launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             ++launches;
         }
-        CUDA_TRY(ctx, cudaEventRecord(plan->kev[2 * i + 1], st));
+        CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->kev[2 * i + 1], st, evflags));
         if (qmc_k_launch_finish(&c.L, st))
             return fail(ctx, QMC_E_CUDA, "finish launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ++launches;
     }
-    CUDA_TRY(ctx, cudaEventRecord(plan->ev1, st));
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->ev1, st, evflags));
     plan->last_launches = launches;
     return QMC_OK;
 }
@@ -641,7 +644,7 @@ int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
             plan->gexec = nullptr;
             cudaGraph_t g = nullptr;
             CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = plan_enqueue(plan, out, st);
+            int rc = plan_enqueue(plan, out, st, true);
             cudaError_t e = cudaStreamEndCapture(st, &g);
             if (rc) {
                 if (g) cudaGraphDestroy(g);
@@ -655,7 +658,7 @@ int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
         }
         CUDA_TRY(ctx, cudaGraphLaunch(plan->gexec, st));
     } else {
-        int rc = plan_enqueue(plan, out, st);
+        int rc = plan_enqueue(plan, out, st, false);
         if (rc) return rc;
     }
     plan->last_stream = st;

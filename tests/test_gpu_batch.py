@@ -50,6 +50,8 @@ def test_presampled_batch_of_1024_points_matches_oracle(batch):
             qmc.qmc_plan_run(ctx, plan)
             out2, _, _ = qmc.qmc_plan_results(ctx, plan)
             assert np.array_equal(out2.reshape(out.shape), out)
+            ms_g, ms_eval_g, nl_g = qmc.qmc_plan_last_time(ctx, plan)
+            assert nl_g == 2 and 0 < ms_eval_g <= ms_g
     finally:
         qmc.qmc_plan_destroy(plan)
 
