@@ -68,8 +68,16 @@ typedef struct {
     uint64_t max_points;   /* largest lattice qmc_integrate may use [largest tabulated] */
     int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
     double lambda;         /* deformation parameter qmc_integrate uses for deformed sectors [0.3] */
-    int reserved[6];
+    int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
+    int reserved[5];
 } qmc_options;
+
+/* Arithmetic of the evaluator for undeformed sectors. FP64: everything in
+ * FP64. MIXED: the monomial products of U and F and their group sums in
+ * FP32; the korobov3 weight, logs and powers of U and F, the series
+ * assembly and all reductions in FP64. Deformed sectors always run FP64. */
+#define QMC_PRECISION_FP64 0
+#define QMC_PRECISION_MIXED 1
 
 /* One evaluation job: one sector of one loaded integral at one kinematic
  * point, on one lattice, with `shifts` random shifts. */
@@ -113,7 +121,10 @@ int qmc_set_lattices(qmc_ctx *ctx, const uint64_t *n, const uint32_t *z, int cou
  * F^{f0+f1 eps}) is the one written by the Python input generators. Sector
  * limits: d <= 6, at most 4 variables with a_j = -1 (a_j >= -1 otherwise),
  * exponents <= 4 per variable, <= 3 invariants; deformed sectors d <= 3 with
- * at most 2 singular variables. *integral_id receives the new id.
+ * at most 2 singular variables. Sectors with d <= 3 and <= 2 singular
+ * variables run in the compact evaluator (series of <= 4 eps orders, i.e.
+ * highest requested order + singular variables + 1 <= 4), the others in the
+ * d <= 6 evaluator (<= 6). *integral_id receives the new id.
  * Errors: QMC_E_PARSE, QMC_E_INVAL (limits), QMC_E_CUDA. */
 int qmc_load_sectors_mem(qmc_ctx *ctx, const char *text, size_t len, int *integral_id);
 
@@ -206,12 +217,13 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
 int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int norders, double lambda_max,
                          int ncand);
 
-/* Autotune the evaluator's launch shape per kernel class (real d <= 3,
- * deformed d <= 3, real d <= 6): on up to 32 of the given jobs per class
+/* Autotune the evaluator's launch shape per kernel class (0: real d <= 3,
+ * 1: deformed d <= 3, 2: real d <= 6, 3 and 4: the mixed-precision variants
+ * of 0 and 2): on up to 32 of the given jobs per class
  * (at most 8 shifts each) every block size in {128, 256} and points per
  * thread in {4, 8, 16, 32} is timed with CUDA events; the fastest is kept in
  * the context and used by later plans whose options leave block/ppt at 0.
- * best_block/best_ppt (may be NULL) receive [3] entries (0 = class absent). */
+ * best_block/best_ppt (may be NULL) receive [5] entries (0 = class absent). */
 int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
                  int *best_ppt);
 

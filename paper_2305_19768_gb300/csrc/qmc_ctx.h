@@ -57,8 +57,8 @@ struct qmc_ctx {
     double *d_kin = nullptr;
     int npoints = 0, ninv = 0;
     std::vector<qmc_plan *> plans;
-    int tuned_block[QMC_NCLASS] = {0, 0, 0};   // autotuned launch shape per kernel class (0 = default)
-    int tuned_ppt[QMC_NCLASS] = {0, 0, 0};
+    int tuned_block[QMC_NCLASS] = {};   // autotuned launch shape per kernel class (0 = default)
+    int tuned_ppt[QMC_NCLASS] = {};
 };
 
 struct ClassLaunch {

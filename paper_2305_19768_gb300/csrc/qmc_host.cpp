@@ -496,11 +496,10 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         auto it = ctx->lattices.find(J.n);
         if (it == ctx->lattices.end())
             return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
-        if (norders > qmc_class_lmax(S.cls) || hi + S.ns + 1 > qmc_class_lmax(S.cls))
+        const int cls = ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(S.cls) : S.cls;
+        if (norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
             return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d with %d poles exceed the evaluator's series length %d",
-                        i, lo, hi, S.ns, qmc_class_lmax(S.cls));
-        if (S.cls == QMC_CLASS_REAL6)
-            return fail(ctx, QMC_E_INVAL, "job %d: sector needs the d<=6 evaluator, which this build lacks", i);
+                        i, lo, hi, S.ns, qmc_class_lmax(cls));
         QmcJobDev D{};
         D.sector = S.global_index;
         D.point = I.invariants.empty() ? 0 : J.point;
@@ -514,8 +513,8 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
             D.lambda[j] = (S.deform && j < S.d) ? J.lambda[j] : 0.0;
         }
         out_off += (uint64_t)J.shifts * norders * 2;
-        per[S.cls].push_back(D);
-        per_orig[S.cls].push_back(i);
+        per[cls].push_back(D);
+        per_orig[cls].push_back(i);
     }
     qmc_plan *p = new qmc_plan();
     p->ctx = ctx;

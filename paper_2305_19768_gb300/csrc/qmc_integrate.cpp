@@ -236,16 +236,19 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
                 cudaEventElapsedTime(&ms, plan->kev[2 * c], plan->kev[2 * c + 1]);
                 kernel_s += ms * 1e-3;
                 double ev = 0.0, cw = 0.0;
+                auto eff = [&](const QmcHostSector &S) {
+                    return ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(S.cls) : S.cls;
+                };
                 for (size_t j = 0; j < jobs.size(); ++j) {
                     const QmcHostSector &S = ctx->integrals[jobs[j].integral_id].sectors[jobs[j].sector];
-                    if (S.cls != plan->launches[c].cls) continue;
+                    if (eff(S) != plan->launches[c].cls) continue;
                     ev += (double)jobs[j].n * m;
                     cw += (double)jobs[j].n * m * slots[jslot[j]].cost;
                 }
                 const double per_cost = cw > 0 ? ms * 1e-3 / cw : 1e-9;
                 for (size_t j = 0; j < jobs.size(); ++j) {
                     const QmcHostSector &S = ctx->integrals[jobs[j].integral_id].sectors[jobs[j].sector];
-                    if (S.cls == plan->launches[c].cls) tau[jslot[j]] = per_cost * slots[jslot[j]].cost;
+                    if (eff(S) == plan->launches[c].cls) tau[jslot[j]] = per_cost * slots[jslot[j]].cost;
                 }
                 evals += ev;
             }
@@ -477,7 +480,8 @@ extern "C" int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo
         if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size()) continue;
         const QmcHostIntegral &I = ctx->integrals[J.integral_id];
         if (J.sector < 0 || J.sector >= (int)I.sectors.size()) continue;
-        const int cls = I.sectors[J.sector].cls;
+        const int base = I.sectors[J.sector].cls;
+        const int cls = ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(base) : base;
         if (per[cls].size() < 32) {
             qmc_job C = J;
             C.shifts = std::min(C.shifts, 8);

@@ -120,12 +120,15 @@ __device__ __forceinline__ dc cexp_(dc a) {
 }
 
 // scalar-generic helpers
+__device__ __forceinline__ float mulsc(float a, float s) { return a * s; }
 __device__ __forceinline__ double mulsc(double a, double s) { return a * s; }
 __device__ __forceinline__ dc mulsc(dc a, double s) { return a * s; }
 template <class T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
 template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
 template <> __device__ __forceinline__ dc zero<dc>() { return dc{0.0, 0.0}; }
 template <class T> __device__ __forceinline__ T from_real(double);
+template <> __device__ __forceinline__ float from_real<float>(double x) { return (float)x; }
 template <> __device__ __forceinline__ double from_real<double>(double x) { return x; }
 template <> __device__ __forceinline__ dc from_real<dc>(double x) { return dc{x, 0.0}; }
 template <class T> __device__ __forceinline__ T one() { return from_real<T>(1.0); }
@@ -162,6 +165,7 @@ struct TileSmem {
     QmcJobDev job;
     uint32_t exps[QMC_MAXMONO];
     double cval[QMC_MAXMONO];
+    float cvalf[QMC_MAXMONO];
     double delta[QMC_DMAX];
     double invb[QMC_SMAX];
     double logtab[3 * QMC_LOG_TABLE_ROWS];
@@ -174,13 +178,13 @@ struct TileSmem {
 
 // Polynomial value over monomials [m0, m1) of the staged table at a point given
 // by its power table (real or complex).
-template <int DMAX, class T>
-__device__ __forceinline__ T poly_sum(const uint32_t *exps, const double *cval, int m0, int m1,
+template <int DMAX, class T, class CT>
+__device__ __forceinline__ T poly_sum(const uint32_t *exps, const CT *cval, int m0, int m1,
                                       const T (&tp)[DMAX][QMC_EMAX]) {
     T s = zero<T>();
     for (int m = m0; m < m1; ++m) {
         const uint32_t e = exps[m];
-        const double c = cval[m];
+        const CT c = cval[m];
         if (e == 0u) {                      // constant monomial
             s = (m == m0) ? from_real<T>(c) : s + from_real<T>(c);
             continue;
@@ -318,7 +322,11 @@ __device__ __forceinline__ T ipow_signed(T x, T xinv, int e) {
 }
 
 // ---------------------------------------------------------------- real integrand
-template <int DMAX, int SMAX, int LMAX>
+// MIXED: the monomial products and their group sums in FP32 (coefficients
+// rounded to FP32), converted to FP64 before the subset sums; everything
+// else (korobov3 weight, logs and powers of U and F, the series assembly and
+// the reductions) stays FP64.
+template <int DMAX, int SMAX, int LMAX, bool MIXED>
 __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double (&t)[DMAX], int lo,
                                           int hi, int nord, double (&res)[LMAX]) {
     constexpr int NG = 1 << SMAX;
@@ -331,13 +339,29 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     // group sums by singular mask, then subset sums h[X] = sum_{M subset X} g[M];
     // the polynomial at corner V (t_V = 0) is h[(NG-1) ^ V].
     double hU[NG], hF[NG];
+    if constexpr (MIXED) {
+        float tf[DMAX], tpf[DMAX][QMC_EMAX];
 #pragma unroll
-    for (int g = 0; g < NG; ++g) {
-        hU[g] = 0.0;
-        hF[g] = 0.0;
-        if (g < (1 << ns)) {
-            hU[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.gU[g], sec.gU[g + 1], tp);
-            hF[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tp);
+        for (int j = 0; j < DMAX; ++j) tf[j] = __double2float_rn(t[j]);
+        powers<DMAX, float>(tf, d, sec.pad0, tpf);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            hU[g] = 0.0;
+            hF[g] = 0.0;
+            if (g < (1 << ns)) {
+                hU[g] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, sec.gU[g], sec.gU[g + 1], tpf);
+                hF[g] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tpf);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            hU[g] = 0.0;
+            hF[g] = 0.0;
+            if (g < (1 << ns)) {
+                hU[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.gU[g], sec.gU[g + 1], tp);
+                hF[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tp);
+            }
         }
     }
 #pragma unroll
@@ -594,6 +618,7 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
             double v = M.coef[0];
             for (int i = 0; i < Lc.ninv && i + 1 < QMC_NCOEF; ++i) v = fma(M.coef[i + 1], kin[i], v);
             S.cval[m] = v;
+            S.cvalf[m] = (float)v;
             S.exps[m] = M.exps;
         }
         __syncthreads();
@@ -621,8 +646,8 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
 #define QMC_MINB 3   // resident 128-thread blocks per SM the real evaluator's registers must allow
 #endif
 
-template <int DMAX, int SMAX, int LMAX, bool CPLX, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, CPLX ? 1 : QMC_MINB) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
     using T = typename std::conditional<CPLX, dc, double>::type;
     const int lo = Lc.lo, nord = Lc.norders;
@@ -722,7 +747,7 @@ __global__ void __launch_bounds__(BLOCK, CPLX ? 1 : QMC_MINB) qmc_eval_kernel(Qm
                 if constexpr (CPLX) {
                     eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, hi, nord, res, signfail_tile);
                 } else {
-                    eval_real<DMAX, SMAX, LMAX>(S, t, lo, hi, nord, res);
+                    eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
                 }
 #pragma unroll
                 for (int o = 0; o < LMAX; ++o)
@@ -829,13 +854,22 @@ __global__ void qmc_fp64_probe_kernel(double *out, int iters) {
     if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
 }
 
-template <int DMAX, int SMAX, int LMAX, bool CPLX>
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED>
 int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
     if (block == 256)
-        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, 256><<<grid, 256, 0, st>>>(*L, ppt);
+        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256><<<grid, 256, 0, st>>>(*L, ppt);
     else
-        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, 128><<<grid, 128, 0, st>>>(*L, ppt);
+        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128><<<grid, 128, 0, st>>>(*L, ppt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED>
+int occupancy_cls(int block) {
+    int v = 0;
+    cudaError_t e = block == 256
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256>, 256, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128>, 128, 0);
+    return e == cudaSuccess ? v : 0;
 }
 
 }  // namespace
@@ -843,8 +877,11 @@ int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st
 extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt, int grid, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (cls) {
-        case QMC_CLASS_REAL3: return launch_cls<3, 2, 4, false>(L, block, ppt, grid, st);
-        case QMC_CLASS_CPLX3: return launch_cls<3, 2, 4, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL3: return launch_cls<3, 2, 4, false, false>(L, block, ppt, grid, st);
+        case QMC_CLASS_CPLX3: return launch_cls<3, 2, 4, true, false>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6: return launch_cls<6, 4, 6, false, false>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL3M: return launch_cls<3, 2, 4, false, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6M: return launch_cls<6, 4, 6, false, true>(L, block, ppt, grid, st);
         default: return -2;
     }
 }
@@ -890,20 +927,14 @@ extern "C" int qmc_k_sm_count(int device) {
 }
 
 extern "C" int qmc_k_occupancy(int cls, int block) {
-    int v = 0;
-    cudaError_t e = cudaSuccess;
     switch (cls) {
-        case QMC_CLASS_REAL3:
-            e = block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<3, 2, 4, false, 256>, 256, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<3, 2, 4, false, 128>, 128, 0);
-            break;
-        case QMC_CLASS_CPLX3:
-            e = block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<3, 2, 4, true, 256>, 256, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<3, 2, 4, true, 128>, 128, 0);
-            break;
+        case QMC_CLASS_REAL3: return occupancy_cls<3, 2, 4, false, false>(block);
+        case QMC_CLASS_CPLX3: return occupancy_cls<3, 2, 4, true, false>(block);
+        case QMC_CLASS_REAL6: return occupancy_cls<6, 4, 6, false, false>(block);
+        case QMC_CLASS_REAL3M: return occupancy_cls<3, 2, 4, false, true>(block);
+        case QMC_CLASS_REAL6M: return occupancy_cls<6, 4, 6, false, true>(block);
         default: return 0;
     }
-    return e == cudaSuccess ? v : 0;
 }
 
 // ---------------------------------------------------------------- no-allocation variant

@@ -21,6 +21,8 @@ _lock = threading.Lock()
 _lib = None
 
 QMC_OK = 0
+QMC_PRECISION_FP64 = 0
+QMC_PRECISION_MIXED = 1
 ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIMEOUT",
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
@@ -35,7 +37,8 @@ class qmc_options(ctypes.Structure):
     _fields_ = [("shifts", ctypes.c_int), ("seed", ctypes.c_uint64), ("block", ctypes.c_int),
                 ("ppt", ctypes.c_int), ("min_points", ctypes.c_uint64),
                 ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
-                ("lambda_", ctypes.c_double), ("reserved", ctypes.c_int * 6)]
+                ("lambda_", ctypes.c_double), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class qmc_sum_spec(ctypes.Structure):
@@ -262,8 +265,8 @@ def qmc_presample_lambda(ctx, jobs, njobs, lo, norders, lambda_max=1.0, ncand=12
 
 
 def qmc_autotune(ctx, jobs, njobs, lo, norders):
-    bb = (ctypes.c_int * 3)()
-    bp = (ctypes.c_int * 3)()
+    bb = (ctypes.c_int * 5)()
+    bp = (ctypes.c_int * 5)()
     _check(ctx, lib().qmc_autotune(ctx, jobs, njobs, lo, norders, bb, bp))
     return list(bb), list(bp)
 

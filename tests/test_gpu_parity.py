@@ -145,6 +145,16 @@ def test_deformed_bubbles_and_triangle(gpu):
     _compare_integral(gpu, w.triangle_one_offshell(0, "s"), [[10.0]], 4001, 4, -2, 3, lam=0.3)
 
 
+def test_double_box_sectors_d6(gpu):
+    # the d <= 6 evaluator: sectors with 1, 2, 3 and 4 singular variables, eps^-4..eps^0
+    I = w.double_box_massless()
+    by_ns = {}
+    for i, s in enumerate(I.sectors):
+        by_ns.setdefault(len(s.singular), i)
+    sectors = [by_ns[k] for k in sorted(by_ns)]
+    _compare_integral(gpu, I, [[-3.0, -1.0]], 1009, 2, -4, 5, sectors=sectors)
+
+
 def test_tiny_lattices_below_one_tile(gpu):
     # n smaller than one tile and than one thread's PPT span; custom lattices
     I = w.box_massless()

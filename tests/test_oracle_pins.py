@@ -302,3 +302,24 @@ def test_prefactor_series_matches_gamma():
             approx = sum(c * eps ** (lo + i) for i, c in enumerate(cs))
             exact = (-1) ** N * math.gamma(N - L * D0 / 2 + L * eps)
             assert abs(approx - exact) <= 1e-12 * abs(exact)
+
+
+def test_double_box_leading_pole():
+    # planar massless double box: the eps^-4 coefficient is 4 / (s^2 t) in this
+    # normalisation (V.A. Smirnov, Phys. Lett. B460 (1999) 397: leading pole 4/eps^4
+    # times 1/(s^2 t)); only the sectors with four singular variables contribute
+    I = w.double_box_massless()
+    assert len(I.sectors) == 282 and I.max_poles == 4
+    sel = [i for i, s in enumerate(I.sectors) if len(s.singular) == 4]
+    s_, t_ = -2.0, -5.0
+    n, m = 4001, 8
+    z = cbc_fast(n, 6)
+    acc = np.zeros(m, dtype=complex)
+    for si in sel:
+        v = oracle.SectorView(I, si, [s_, t_])
+        out, _, _ = oracle.shift_sums(v, n, z, oracle.shifts(1, si, m, 6), -4, 1)
+        acc += out[:, 0, 0] + 1j * out[:, 0, 1]
+    c = I.prefactor[0] * acc * s_ * s_ * t_
+    mean, err = c.mean().real, c.real.std(ddof=1) / np.sqrt(m)
+    assert abs(mean - 4.0) <= 4 * err + 1e-6, (mean, err)
+    assert err < 1e-3
