@@ -69,8 +69,16 @@ typedef struct {
     int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
     double lambda;         /* deformation parameter qmc_integrate uses for deformed sectors [0.3] */
     int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
-    int reserved[5];
+    int transform;         /* QMC_TRANSFORM_KOROBOV3 [default], _BAKER or _NONE */
+    int reserved[4];
 } qmc_options;
+
+/* Periodizing transforms (timings section: korobov3 by default, baker for
+ * some examples): korobov3 t = u^4 (35 - 84u + 70u^2 - 20u^3) with weight
+ * 140 u^3 (1-u)^3; baker t = 1 - |2u - 1| with weight 1; none t = u. */
+#define QMC_TRANSFORM_KOROBOV3 0
+#define QMC_TRANSFORM_BAKER 1
+#define QMC_TRANSFORM_NONE 2
 
 /* Arithmetic of the evaluator for undeformed sectors. FP64: everything in
  * FP64. MIXED: the monomial products of U and F and their group sums in
@@ -92,7 +100,12 @@ typedef struct {
                               splitmix64 started at seed ^ (0x9E3779B97F4A7C15 * (stream + 1)),
                               as (out >> 11) * 2^-53 */
     double lambda[6];      /* deformation parameter per variable (deformed sectors) */
+    uint32_t z[6];         /* explicit generating vector, each z_j in U_n (z[0] = 0: the table's) */
+    int32_t flags;         /* QMC_JOB_UNSHIFTED: evaluate the unshifted rule (Delta = 0) */
+    int32_t pad;
 } qmc_job;
+
+#define QMC_JOB_UNSHIFTED 1
 
 /* Create a context on CUDA device `device`. `opt` may be NULL (defaults).
  * On success *out owns all device memory the context allocates; free with
@@ -226,6 +239,24 @@ int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int nor
  * best_block/best_ppt (may be NULL) receive [5] entries (0 = class absent). */
 int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
                  int *best_ppt);
+
+/* Median QMC rule candidates (section "Median Quasi-Monte Carlo rules"):
+ * r generating vectors with components uniform in U_n = {1 <= z <= n-1,
+ * gcd(z, n) = 1}: component j of candidate i is 1 + (x mod (n-1)) for the
+ * next splitmix64 output x (state started at `seed`) that gives a value
+ * coprime to n, drawn candidate-major; components d..5 are set to 1.
+ * z: host array [r][6]. Pure host arithmetic. */
+int qmc_median_candidates(uint64_t n, int d, int r, uint64_t seed, uint32_t *z);
+
+/* Median QMC rule for one job (Eq. (median)): evaluates the unshifted rank-1
+ * rule Q_{n,z_i} of the job's sector with each of r (odd) candidates from
+ * qmc_median_candidates(job->n, d, r, seed) in one plan and returns in
+ * z_out[6] the candidate whose estimate is the median, ranked by the real
+ * part of order lo+norders-1 (ties keep the lower candidate index).
+ * `estimates` (may be NULL): host [r][norders][2] per-candidate values. The
+ * uncertainty then comes from random shifts of this lattice (set job.z). */
+int qmc_median_lattice(qmc_ctx *ctx, const qmc_job *job, int lo, int norders, int r, uint64_t seed,
+                       uint32_t *z_out, double *estimates);
 
 /* ------------------------------------------------------------------------
  * Combination and allocation (host arithmetic, no GPU needed)

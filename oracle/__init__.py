@@ -36,7 +36,8 @@ class OrcSector(ctypes.Structure):
                 ("f1", ctypes.c_double), ("nU", ctypes.c_int), ("nF", ctypes.c_int),
                 ("Ue", ctypes.POINTER(ctypes.c_int)), ("Uc", ctypes.POINTER(ctypes.c_double)),
                 ("Fe", ctypes.POINTER(ctypes.c_int)), ("Fc", ctypes.POINTER(ctypes.c_double)),
-                ("deform", ctypes.c_int), ("lam", ctypes.c_double * DMAX)]
+                ("deform", ctypes.c_int), ("lam", ctypes.c_double * DMAX),
+                ("transform", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +66,8 @@ def lib():
                                              P(ctypes.c_double), P(ctypes.c_uint64)]
             L.orc_korobov3.argtypes = [ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double),
                                        P(ctypes.c_double)]
+            L.orc_baker.argtypes = [ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double),
+                                    P(ctypes.c_double)]
             L.orc_point_value.argtypes = [P(OrcSector), P(ctypes.c_double), ctypes.c_int,
                                           ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
             L.orc_point_value.restype = ctypes.c_int
@@ -87,7 +90,7 @@ def _dptr(a):
 class SectorView:
     """An ``OrcSector`` plus the numpy arrays it points into."""
 
-    def __init__(self, integral, sector: int, inv, lam=None):
+    def __init__(self, integral, sector: int, inv, lam=None, transform: int = 0):
         s = integral.sectors[sector]
         self.d = s.d
         self.Ue, self.Uc = integral.coefficients_at(sector, "U", inv)
@@ -110,6 +113,7 @@ class SectorView:
             lam = np.broadcast_to(np.asarray(lam, dtype=np.float64), (s.d,))
             for j in range(s.d):
                 st.lam[j] = float(lam[j])
+        st.transform = transform
         self.st = st
         self.nsing = len(s.singular)
 
@@ -134,6 +138,12 @@ def lattice_points(n: int, z, delta, k0: int, count: int):
 def korobov3(u: float):
     t, omt, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().orc_korobov3(u, ctypes.byref(t), ctypes.byref(omt), ctypes.byref(w))
+    return t.value, omt.value, w.value
+
+
+def baker(u: float):
+    t, omt, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().orc_baker(u, ctypes.byref(t), ctypes.byref(omt), ctypes.byref(w))
     return t.value, omt.value, w.value
 
 

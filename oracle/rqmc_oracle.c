@@ -55,6 +55,7 @@ typedef struct {
     const double *Fc;    /* [nF] */
     int deform;
     double lambda[ORC_DMAX];
+    int transform;       /* 0 korobov3, 1 baker, 2 none */
 } orc_sector;
 
 /* ---------------- splitmix64 (Steele, Lea & Flood 2014) ---------------- */
@@ -103,6 +104,26 @@ void orc_korobov3(double u, double *t, double *omt, double *w) {
     *t = korobov_phi(u);
     *omt = korobov_phi(1.0 - u);
     *w = korobov_w(u);
+}
+
+/* baker (tent) transform: t = 1 - |2u - 1|, weight 1 (the map is two-to-one
+ * and each branch has |dt/du| = 2); t and 1 - t are formed piecewise so that
+ * both are exact for u >= 1/2 and t is exact for u < 1/2. */
+void orc_baker(double u, double *t, double *omt, double *w) {
+    if (u < 0.5) {
+        *t = 2.0 * u;
+        *omt = 1.0 - 2.0 * u;
+    } else {
+        *t = 2.0 * (1.0 - u);
+        *omt = 2.0 * u - 1.0;
+    }
+    *w = 1.0;
+}
+
+static void transform_point(int transform, double u, double *t, double *omt, double *w) {
+    if (transform == 1) orc_baker(u, t, omt, w);
+    else if (transform == 2) { *t = u; *omt = 1.0 - u; *w = 1.0; }
+    else orc_korobov3(u, t, omt, w);
 }
 
 /* ---------------- truncated Laurent series in eps ---------------- */
@@ -360,7 +381,7 @@ static int point_value_cond(const orc_sector *S, const double *u, int lo, int no
     for (int o = 0; o < 2 * norders; ++o) out[o] = 0.0;
     for (int j = 0; j < d; ++j) {
         double w;
-        orc_korobov3(u[j], &t[j], &omt[j], &w);
+        transform_point(S->transform, u[j], &t[j], &omt[j], &w);
         W *= w;
     }
     if (W == 0.0) return 0;

@@ -363,6 +363,10 @@ int qmc_create(qmc_ctx **out, int device, const qmc_options *opt) {
     if (ctx->opt.seed == 0) ctx->opt.seed = 1;
     if (ctx->opt.min_points == 0) ctx->opt.min_points = 10000;
     if (ctx->opt.presamples <= 0) ctx->opt.presamples = 10000;
+    if (ctx->opt.transform < 0 || ctx->opt.transform > 2) {
+        delete ctx;
+        return QMC_E_INVAL;
+    }
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete ctx;
@@ -493,9 +497,22 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         if (J.point < 0 || (J.point >= ctx->npoints && !(I.invariants.empty() && J.point == 0)))
             return fail(ctx, QMC_E_INVAL, "job %d: bad kinematic point %d", i, J.point);
         if (J.shifts < 1) return fail(ctx, QMC_E_INVAL, "job %d: shifts < 1", i);
-        auto it = ctx->lattices.find(J.n);
-        if (it == ctx->lattices.end())
-            return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
+        std::vector<uint32_t> zvec;
+        if (J.z[0] != 0) {
+            if (J.n < 2 || J.n >= (1ULL << 32)) return fail(ctx, QMC_E_INVAL, "job %d: n outside 2..2^32-1", i);
+            for (int j = 0; j < S.d; ++j) {
+                uint64_t a = J.z[j], b = J.n;
+                while (b) { uint64_t r = a % b; a = b; b = r; }
+                if (J.z[j] == 0 || J.z[j] >= J.n || a != 1)
+                    return fail(ctx, QMC_E_INVAL, "job %d: z_%d = %u not in U_n", i, j, J.z[j]);
+            }
+            zvec.assign(J.z, J.z + 6);
+        } else {
+            auto it = ctx->lattices.find(J.n);
+            if (it == ctx->lattices.end())
+                return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
+            zvec = it->second;
+        }
         const int cls = ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(S.cls) : S.cls;
         if (norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
             return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d with %d poles exceed the evaluator's series length %d",
@@ -509,9 +526,10 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         D.inv_n = 1.0 / (double)J.n;
         D.out_off = out_off;
         for (int j = 0; j < QMC_DMAX; ++j) {
-            D.z[j] = j < S.d ? it->second[j] : 0;
+            D.z[j] = j < S.d ? zvec[j] : 0;
             D.lambda[j] = (S.deform && j < S.d) ? J.lambda[j] : 0.0;
         }
+        D.flags = J.flags & QMC_JOB_UNSHIFTED;
         out_off += (uint64_t)J.shifts * norders * 2;
         per[cls].push_back(D);
         per_orig[cls].push_back(i);
@@ -575,6 +593,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         L.norders = norders;
         L.ntiles = tiles;
         L.tile_k = (uint32_t)tile_k;
+        L.transform = ctx->opt.transform;
         L.partials = c.d_partials;
         L.queue = c.d_queue;
         L.status = p->d_status;
@@ -869,6 +888,8 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
         if (J.point < 0 || (J.point >= ctx->npoints && !(I.invariants.empty() && J.point == 0)))
             return fail(ctx, QMC_E_INVAL, "job %d: bad kinematic point %d", i, J.point);
         if (J.shifts < 1) return fail(ctx, QMC_E_INVAL, "job %d: shifts < 1", i);
+        if (J.z[0] != 0 || J.flags)
+            return fail(ctx, QMC_E_INVAL, "job %d: explicit generating vectors and job flags need qmc_eval_jobs", i);
         auto it = ctx->lattices.find(J.n);
         if (it == ctx->lattices.end())
             return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
@@ -911,6 +932,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
     L.norders = norders;
     L.ntiles = tiles;
     L.tile_k = (uint32_t)tile_k;
+    L.transform = ctx->opt.transform;
     L.out = out_dev;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     unsigned long long status[2] = {0, 0};

@@ -532,3 +532,78 @@ extern "C" int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo
     }
     return QMC_OK;
 }
+
+// ---------------------------------------------------------------- median QMC rules
+namespace {
+uint64_t sm64_next(uint64_t &state) {
+    uint64_t z = (state += kQmcGamma);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        const uint64_t r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+}  // namespace
+
+extern "C" int qmc_median_candidates(uint64_t n, int d, int r, uint64_t seed, uint32_t *z) {
+    if (!z || n < 2 || n >= (1ULL << 32) || d < 1 || d > 6 || r < 1) return QMC_E_INVAL;
+    uint64_t st = seed;
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < 6; ++j) {
+            if (j >= d) {
+                z[i * 6 + j] = 1;
+                continue;
+            }
+            for (;;) {
+                const uint64_t c = 1 + sm64_next(st) % (n - 1);
+                if (gcd64(c, n) == 1) {
+                    z[i * 6 + j] = (uint32_t)c;
+                    break;
+                }
+            }
+        }
+    return QMC_OK;
+}
+
+extern "C" int qmc_median_lattice(qmc_ctx *ctx, const qmc_job *job, int lo, int norders, int r, uint64_t seed,
+                                  uint32_t *z_out, double *estimates) {
+    if (!ctx || !job || !z_out || r < 1 || r > 1024 || !(r & 1) || norders < 1)
+        return fail(ctx, QMC_E_INVAL, "qmc_median_lattice: bad arguments (r must be odd)");
+    if (job->integral_id < 0 || job->integral_id >= (int)ctx->integrals.size() || job->sector < 0 ||
+        job->sector >= (int)ctx->integrals[job->integral_id].sectors.size())
+        return fail(ctx, QMC_E_INVAL, "qmc_median_lattice: bad job");
+    const int d = ctx->integrals[job->integral_id].sectors[job->sector].d;
+    std::vector<uint32_t> cand((size_t)r * 6);
+    int rc = qmc_median_candidates(job->n, d, r, seed, cand.data());
+    if (rc) return fail(ctx, rc, "qmc_median_lattice: bad lattice size");
+    std::vector<qmc_job> jobs((size_t)r, *job);
+    for (int i = 0; i < r; ++i) {
+        memcpy(jobs[i].z, &cand[(size_t)i * 6], sizeof jobs[i].z);
+        jobs[i].shifts = 1;
+        jobs[i].flags |= QMC_JOB_UNSHIFTED;
+    }
+    qmc_plan *plan = nullptr;
+    rc = qmc_plan_create(ctx, jobs.data(), r, lo, norders, &plan);
+    if (rc) return rc;
+    std::vector<double> out(qmc_plan_output_size(plan));
+    rc = qmc_plan_run(plan, nullptr, nullptr);
+    if (!rc) rc = qmc_plan_results(plan, out.data(), nullptr);
+    qmc_plan_destroy(plan);
+    if (rc) return rc;
+    // Eq. (median): the candidate whose estimate (Re of the highest order) is the median
+    std::vector<int> idx((size_t)r);
+    for (int i = 0; i < r; ++i) idx[i] = i;
+    const int o = norders - 1;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return out[(size_t)a * norders * 2 + 2 * o] <
+                                                                         out[(size_t)b * norders * 2 + 2 * o]; });
+    const int med = idx[r / 2];
+    memcpy(z_out, &cand[(size_t)med * 6], 6 * sizeof(uint32_t));
+    if (estimates) memcpy(estimates, out.data(), out.size() * sizeof(double));
+    return QMC_OK;
+}

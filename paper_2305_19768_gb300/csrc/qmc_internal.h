@@ -52,6 +52,8 @@ struct QmcJobDev {
     uint32_t z[QMC_DMAX];  // generating vector
     double inv_n;          // RN(1/n), for the corrected lattice division
     double lambda[QMC_DMAX];
+    int32_t flags;         // bit 0: no random shift (Delta = 0)
+    int32_t pad2;
 };
 
 struct QmcLaunch {
@@ -65,7 +67,7 @@ struct QmcLaunch {
     int32_t norders;
     uint64_t ntiles;
     uint32_t tile_k;       // points per tile = block * ppt
-    uint32_t pad;
+    int32_t transform;     // 0 korobov3, 1 baker, 2 none
     double *partials;      // [ntiles][norders][2]
     unsigned long long *queue;   // tile counter (reset by the finish kernel)
     unsigned long long *status;  // [0]: sign-check failures, [1]: non-finite partials

@@ -691,7 +691,8 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
         const uint64_t chunk = local % (uint64_t)S.job.tiles_per_shift;
         if (threadIdx.x < QMC_DMAX) {
             int j = threadIdx.x;
-            S.delta[j] = (j < S.sec.d) ? splitmix_uniform(S.job.seed_state, (uint64_t)s * S.sec.d + j) : 0.0;
+            S.delta[j] = (j < S.sec.d && !(S.job.flags & 1))
+                             ? splitmix_uniform(S.job.seed_state, (uint64_t)s * S.sec.d + j) : 0.0;
         }
         __syncthreads();
 
@@ -728,20 +729,28 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
                     omt[j] = 0.0;
                     if (j < d) {
                         const double u = lattice_coord(r[j], nd, inv_n, dl[j]);
-                        const double u2 = u * u;
-                        t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
-                        if (CPLX) {
-                            const double v = 1.0 - u;
-                            const double v2 = v * v;
-                            omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
+                        if (Lc.transform == 0) {          // korobov3
+                            const double u2 = u * u;
+                            t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
+                            if (CPLX) {
+                                const double v = 1.0 - u;
+                                const double v2 = v * v;
+                                omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
+                            }
+                            Ws *= fma(-u, u, u);
+                        } else if (Lc.transform == 1) {   // baker: t = 1 - |2u - 1|, weight 1
+                            t[j] = u < 0.5 ? 2.0 * u : 2.0 * (1.0 - u);
+                            omt[j] = u < 0.5 ? 1.0 - 2.0 * u : 2.0 * u - 1.0;
+                        } else {                          // no transform
+                            t[j] = u;
+                            omt[j] = 1.0 - u;
                         }
-                        Ws *= fma(-u, u, u);
                         zero_t |= (t[j] == 0.0);
                         uint64_t rn = r[j] + zz[j];
                         r[j] = (rn >= n) ? rn - n : rn;
                     }
                 }
-                const double W = S.w140d * (Ws * Ws * Ws);
+                const double W = Lc.transform == 0 ? S.w140d * (Ws * Ws * Ws) : 1.0;
                 if (W == 0.0 || zero_t) continue;
                 T res[LMAX];
                 if constexpr (CPLX) {

@@ -23,6 +23,8 @@ _lib = None
 QMC_OK = 0
 QMC_PRECISION_FP64 = 0
 QMC_PRECISION_MIXED = 1
+QMC_TRANSFORM_KOROBOV3, QMC_TRANSFORM_BAKER, QMC_TRANSFORM_NONE = 0, 1, 2
+QMC_JOB_UNSHIFTED = 1
 ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIMEOUT",
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
@@ -38,7 +40,7 @@ class qmc_options(ctypes.Structure):
                 ("ppt", ctypes.c_int), ("min_points", ctypes.c_uint64),
                 ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("precision", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("transform", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class qmc_sum_spec(ctypes.Structure):
@@ -57,7 +59,8 @@ class qmc_job(ctypes.Structure):
     _fields_ = [("integral_id", ctypes.c_int32), ("sector", ctypes.c_int32),
                 ("point", ctypes.c_int32), ("shifts", ctypes.c_int32), ("n", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint64),
-                ("lambda_", ctypes.c_double * 6)]
+                ("lambda_", ctypes.c_double * 6), ("z", ctypes.c_uint32 * 6), ("flags", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class qmc_c64(ctypes.Structure):
@@ -105,6 +108,8 @@ def lib():
                 "qmc_plan_job_failures": ([vp, P(ctypes.c_uint32)], i32),
                 "qmc_presample_lambda": ([vp, P(qmc_job), i32, i32, i32, dbl, i32], i32),
                 "qmc_autotune": ([vp, P(qmc_job), i32, i32, i32, P(i32), P(i32)], i32),
+                "qmc_median_candidates": ([u64, i32, i32, u64, P(ctypes.c_uint32)], i32),
+                "qmc_median_lattice": ([vp, P(qmc_job), i32, i32, i32, u64, P(ctypes.c_uint32), P(dbl)], i32),
                 "qmc_series_mul": ([P(qmc_c64), i32, i32, P(qmc_c64), i32, i32, i32, i32, P(qmc_c64)], i32),
                 "qmc_series_var": ([P(qmc_c64), i32, i32, P(dbl), i32, i32, i32, i32, P(dbl)], i32),
                 "qmc_allocate": ([P(dbl), P(dbl), P(dbl), i32, i32, dbl, dbl, P(dbl)], i32),
@@ -127,7 +132,8 @@ def exported_symbols():
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
             "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
-            "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune"]
+            "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
+            "qmc_median_candidates", "qmc_median_lattice"]
 
 
 def _dp(a):
@@ -211,6 +217,11 @@ def make_jobs(specs):
         lam = np.broadcast_to(np.asarray(s.get("lambda", 0.0), dtype=np.float64), (6,))
         for j in range(6):
             arr[i].lambda_[j] = float(lam[j])
+        z = s.get("z")
+        if z is not None:
+            for j in range(6):
+                arr[i].z[j] = int(z[j]) if j < len(z) else 1
+        arr[i].flags = int(s.get("flags", 0))
     return arr, len(specs)
 
 
@@ -269,6 +280,22 @@ def qmc_autotune(ctx, jobs, njobs, lo, norders):
     bp = (ctypes.c_int * 5)()
     _check(ctx, lib().qmc_autotune(ctx, jobs, njobs, lo, norders, bb, bp))
     return list(bb), list(bp)
+
+
+def qmc_median_candidates(n, d, r, seed):
+    z = np.zeros((r, 6), dtype=np.uint32)
+    _check(None, lib().qmc_median_candidates(n, d, r, seed, z.ctypes.data_as(P(ctypes.c_uint32))))
+    return z
+
+
+def qmc_median_lattice(ctx, job_spec, lo, norders, r, seed):
+    """(z [6], per-candidate estimates [r][norders][2]) for one job spec dict."""
+    jobs, _ = make_jobs([job_spec])
+    z = np.zeros(6, dtype=np.uint32)
+    est = np.zeros((r, norders, 2))
+    _check(ctx, lib().qmc_median_lattice(ctx, jobs, lo, norders, r, seed, z.ctypes.data_as(P(ctypes.c_uint32)),
+                                         _dp(est)))
+    return z, est
 
 
 def qmc_plan_destroy(plan):

@@ -155,6 +155,49 @@ def test_double_box_sectors_d6(gpu):
     _compare_integral(gpu, I, [[-3.0, -1.0]], 1009, 2, -4, 5, sectors=sectors)
 
 
+def test_baker_transform_sums():
+    g = Gpu(transform=qmc.QMC_TRANSFORM_BAKER)
+    try:
+        I = w.box_massless()
+        iid = g.load(I)
+        qmc.qmc_set_kinematics(g.ctx, np.array([[-3.0, -2.0]]))
+        specs = _specs(iid, [0, 4, 9], [0], 4001, 3, nsec_total=12)
+        out, _, rc = g.eval(iid, specs, -2, 3)
+        assert rc == 0
+        out = out.reshape(3, 3, 3, 2)
+        for i, sp in enumerate(specs):
+            _, z = lattice_for(4001, 3)
+            view = oracle.SectorView(I, sp["sector"], [-3.0, -2.0], transform=1)
+            o, a, _, c = oracle.shift_sums(view, 4001, z, oracle.shifts(1, sp["stream"], 3, 3), -2, 3,
+                                           with_cond=True)
+            assert_close(out[i], o, a, c, what=f"baker sector {sp['sector']}")
+    finally:
+        g.close()
+
+
+def test_median_rule_and_explicit_vectors(gpu):
+    I = w.box_massless()
+    iid = gpu.load(I)
+    qmc.qmc_set_kinematics(gpu.ctx, np.array([[-3.0, -2.0]]))
+    n, r, sector = 20011, 11, 5
+    spec = dict(integral_id=iid, sector=sector, point=0, shifts=1, n=n, seed=1, stream=5)
+    z, est = qmc.qmc_median_lattice(gpu.ctx, spec, -2, 3, r, 99)
+    cands = qmc.qmc_median_candidates(n, 3, r, 99)
+    view = oracle.SectorView(I, sector, [-3.0, -2.0])
+    o_est = []
+    for i in range(r):
+        o, a, _, c = oracle.shift_sums(view, n, cands[i, :3], np.zeros((1, 3)), -2, 3, with_cond=True)
+        assert_close(est[i][None], o, a, c, what=f"candidate {i}")
+        o_est.append(o[0, 2, 0])
+    assert list(z[:3]) == list(cands[int(np.argsort(o_est, kind="stable")[r // 2]), :3])
+    # random shifts of the chosen lattice through an explicit generating vector
+    spec2 = dict(spec, shifts=4, z=list(z))
+    out, _, rc = gpu.eval(iid, [spec2], -2, 3)
+    assert rc == 0
+    o, a, _, c = oracle.shift_sums(view, n, z[:3], oracle.shifts(1, 5, 4, 3), -2, 3, with_cond=True)
+    assert_close(out.reshape(4, 3, 2), o, a, c, what="median lattice with shifts")
+
+
 def test_tiny_lattices_below_one_tile(gpu):
     # n smaller than one tile and than one thread's PPT span; custom lattices
     I = w.box_massless()

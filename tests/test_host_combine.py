@@ -46,3 +46,15 @@ def test_allocate_matches_oracle_one_and_several_sums():
     n, _ = combine.allocate_one_sum(W[0], tau, V[0])
     assert np.allclose(one, n, rtol=1e-12)
     assert abs(np.sum(W[0] * one ** -2.0) - V[0]) <= 1e-10 * V[0]
+
+
+def test_median_candidates_match_the_input_generator():
+    from math import gcd
+
+    from paper_2305_19768_gb300.inputs.lattice import median_candidates
+
+    for n, d, r, seed in ((1000003, 3, 11, 42), (20011, 6, 5, 7), (1024, 2, 7, 1)):
+        z = qmc.qmc_median_candidates(n, d, r, seed)
+        assert np.array_equal(z[:, :d], median_candidates(n, d, r, seed))
+        assert np.all(z[:, d:] == 1)
+        assert all(gcd(int(c), n) == 1 and 1 <= c < n for c in z[:, :d].ravel())

@@ -323,3 +323,32 @@ def test_double_box_leading_pole():
     mean, err = c.mean().real, c.real.std(ddof=1) / np.sqrt(m)
     assert abs(mean - 4.0) <= 4 * err + 1e-6, (mean, err)
     assert err < 1e-3
+
+
+def test_baker_transform_moments_and_triangle():
+    # the tent map is measure preserving: int_0^1 g(phi(u)) du = int_0^1 g(t) dt, weight 1
+    xs, ws = leggauss(20)
+    for lo_, hi_ in ((0.0, 0.5), (0.5, 1.0)):
+        u = lo_ + (hi_ - lo_) * 0.5 * (xs + 1)
+        vals = np.array([oracle.baker(float(v)) for v in u])
+        assert np.all(vals[:, 2] == 1.0)
+        assert np.max(np.abs(vals[:, 0] + vals[:, 1] - 1.0)) == 0.0
+    for p in range(5):
+        tot = 0.0
+        for lo_, hi_ in ((0.0, 0.5), (0.5, 1.0)):
+            u = lo_ + (hi_ - lo_) * 0.5 * (xs + 1)
+            t = np.array([oracle.baker(float(v))[0] for v in u])
+            tot += np.sum((hi_ - lo_) * 0.5 * ws * t ** p)
+        assert abs(tot - 1.0 / (p + 1)) < 1e-14
+    # the triangle through the baker transform reproduces its closed form
+    I = w.triangle_massive()
+    n, m = next_prime(20000), 8
+    z = cbc_fast(n, 2)
+    acc = np.zeros(m)
+    for si in range(3):
+        v = oracle.SectorView(I, si, [], transform=1)
+        out, _, _ = oracle.shift_sums(v, n, z, oracle.shifts(1, si, m, 2), 0, 1)
+        acc += out[:, 0, 0]
+    acc *= I.prefactor[0].real
+    err = acc.std(ddof=1) / np.sqrt(m)
+    assert abs(acc.mean() - closed_form("triangle_m1_pm1")[0].real) <= 4 * err + 1e-12
