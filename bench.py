@@ -36,6 +36,23 @@ METRIC = "integrand evals/s"
 UNIT = "evals/s"
 LO, NORD = -2, 3
 INV = [-3.0, -2.0]
+JOB_RECORD_BYTES = 136   # device job record (QmcJobDev) copied per job
+
+# DRAM traffic per evaluator launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) for the kernel source with this SHA-1; any other
+# kernel source reports null.
+PROFILED_TRAFFIC = {
+    # full-size launch (n = 1000003, m = 32), ncu 1 pass: 780.80 KB read, 0 B written
+    "3ad063322ef9b25731cc82b1f0154dac917122b1": 780800,
+}
+
+
+def kernel_sha1():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_2305_19768_gb300", "csrc", "qmc_kernels.cu")
+    with open(path, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()
 
 
 def _env_int(name, default):
@@ -148,6 +165,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -229,7 +247,7 @@ def main():
     # end to end through the public API with host buffers: kinematics and the
     # job table in, per-shift sums out, every step
     e2e_val = None
-    h2d = kin.nbytes + nj * 128
+    h2d = kin.nbytes + nj * JOB_RECORD_BYTES
     d2h = out_n * 8
     host_out = np.zeros(out_n)
     t_e2e = 0.0
@@ -244,9 +262,43 @@ def main():
     fl_per_eval = flopmod.workload_flops(I, LO, NORD)
     avg_eval_ms = float(np.mean(eval_ms))
     achieved = fl_per_eval * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
+    sha = kernel_sha1()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s (fp64)",
-            "frac": achieved / peak_gflops, "traffic": None,
-            "flops_per_eval": fl_per_eval, "peak_source": "DFMA probe in this run"}
+            "frac": achieved / peak_gflops, "traffic": PROFILED_TRAFFIC.get(sha),
+            "flops_per_eval": fl_per_eval, "peak_source": "DFMA probe in this run",
+            "kernel_sha1": sha}
+
+    # secondary: time to 1e-4 relative error per eps-coefficient through
+    # qmc_integrate (pilot lattice 1e4, adaptive), FP64 and mixed precision,
+    # and the mixed-precision throughput of the same evaluation pass
+    extra = {}
+    if not args.no_extra:
+        t0 = time.perf_counter()
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-4, lowest_order=LO, norders=NORD,
+                                               check=False)
+        extra["time_to_1e-4_s"] = time.perf_counter() - t0
+        extra["time_to_1e-4_rc"] = rc
+        ctxm = qmc.qmc_create(local, precision=qmc.QMC_PRECISION_MIXED, **opts)
+        qmc.load_lattice_table(ctxm)
+        iidm = qmc.qmc_load_sectors_mem(ctxm, I.to_text())
+        qmc.qmc_set_kinematics(ctxm, kin)
+        t0 = time.perf_counter()
+        qmc.qmc_integrate(ctxm, [iidm], epsrel=1e-4, lowest_order=LO, norders=NORD, check=False)
+        extra["time_to_1e-4_mixed_s"] = time.perf_counter() - t0
+        jobs_m, nj_m = qmc.make_jobs(qmc.jobs_for_integral(iidm, nsec, 1, args.n, args.shifts, seed=seed))
+        plan_m = qmc.qmc_plan_create(ctxm, jobs_m, nj_m, LO, NORD)
+        ms_m = []
+        for i in range(4):
+            qmc.qmc_plan_run(ctxm, plan_m, None, sptr)
+            _, me, _ = qmc.qmc_plan_last_time(ctxm, plan_m)
+            if i:
+                ms_m.append(me)
+        out_m, _, _ = qmc.qmc_plan_results(ctxm, plan_m, check=False)
+        ref = out_dev.cpu().numpy()
+        extra["mixed_evals_per_s"] = evals_per_step / (float(np.mean(ms_m)) * 1e-3)
+        extra["mixed_max_abs_diff_vs_fp64"] = float(np.max(np.abs(out_m - ref)))
+        qmc.qmc_plan_destroy(plan_m)
+        qmc.qmc_destroy(ctxm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -262,7 +314,8 @@ def main():
             "config": {"workload": WORKLOAD.format(n=args.n, m=args.shifts), "evals_per_step": evals_per_step,
                        "l2": "flushed between timed steps (256 MB write)", "wall_s": wall},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "extra": extra}
     if rank == 0:
         print(json.dumps(line), flush=True)
     qmc.qmc_plan_destroy(plan)
