@@ -372,6 +372,18 @@ int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out);
  * dependent-chain-free loop timed with CUDA events. */
 int qmc_fp64_peak(qmc_ctx *ctx, double *gflops);
 
+/* ------------------------------------------------------------------------
+ * Learned part: tensor-core MLP kernels
+ * ------------------------------------------------------------------------ */
+
+/* BF16 GEMM on the tensor cores (tcgen05.mma, FP32 accumulation in tensor
+ * memory): C[M][N] = sum_k A[M][K] B[N][K] with A, B row-major bf16 (raw
+ * 16-bit patterns) and C row-major float, host buffers, current CUDA device.
+ * M % 128 == 0, K % 16 == 0, N % 16 == 0 and 16 <= N <= 256.
+ * Errors: QMC_E_INVAL (shape), QMC_E_CUDA (launch, or a completion wait
+ * that ran out). */
+int qmc_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int M, int N, int K);
+
 #ifdef __cplusplus
 }
 #endif

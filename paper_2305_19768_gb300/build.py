@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_host.cpp", "qmc_integrate.cpp"]
+SOURCES = ["qmc_kernels.cu", "qmc_mlp.cu", "qmc_host.cpp", "qmc_integrate.cpp"]
 
 
 def _nvcc() -> str:

@@ -109,6 +109,7 @@ def lib():
                 "qmc_presample_lambda": ([vp, P(qmc_job), i32, i32, i32, dbl, i32], i32),
                 "qmc_autotune": ([vp, P(qmc_job), i32, i32, i32, P(i32), P(i32)], i32),
                 "qmc_median_candidates": ([u64, i32, i32, u64, P(ctypes.c_uint32)], i32),
+                "qmc_gemm_bf16": ([P(ctypes.c_uint16), P(ctypes.c_uint16), P(ctypes.c_float), i32, i32, i32], i32),
                 "qmc_median_lattice": ([vp, P(qmc_job), i32, i32, i32, u64, P(ctypes.c_uint32), P(dbl)], i32),
                 "qmc_series_mul": ([P(qmc_c64), i32, i32, P(qmc_c64), i32, i32, i32, i32, P(qmc_c64)], i32),
                 "qmc_series_var": ([P(qmc_c64), i32, i32, P(dbl), i32, i32, i32, i32, P(dbl)], i32),
@@ -133,7 +134,7 @@ def exported_symbols():
             "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
-            "qmc_median_candidates", "qmc_median_lattice"]
+            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16"]
 
 
 def _dp(a):
@@ -296,6 +297,31 @@ def qmc_median_lattice(ctx, job_spec, lo, norders, r, seed):
     _check(ctx, lib().qmc_median_lattice(ctx, jobs, lo, norders, r, seed, z.ctypes.data_as(P(ctypes.c_uint32)),
                                          _dp(est)))
     return z, est
+
+
+def to_bf16_bits(x):
+    """Round float32 values to bfloat16 (nearest even) and return the 16-bit patterns."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    return r
+
+
+def from_bf16_bits(b):
+    return (np.ascontiguousarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def qmc_gemm_bf16(A_bits, B_bits):
+    """C = A B^T on the tensor cores; A [M][K], B [N][K] bf16 bit patterns."""
+    A_bits = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B_bits = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    M, K = A_bits.shape
+    N = B_bits.shape[0]
+    C = np.zeros((M, N), dtype=np.float32)
+    _check(None, lib().qmc_gemm_bf16(A_bits.ctypes.data_as(P(ctypes.c_uint16)),
+                                     B_bits.ctypes.data_as(P(ctypes.c_uint16)),
+                                     C.ctypes.data_as(P(ctypes.c_float)), M, N, K))
+    return C
 
 
 def qmc_plan_destroy(plan):
