@@ -384,6 +384,34 @@ int qmc_fp64_peak(qmc_ctx *ctx, double *gflops);
  * that ran out). */
 int qmc_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int M, int N, int K);
 
+/* A multilayer perceptron trained and evaluated on the GPU (the learned
+ * sizing/surrogate model): x (nin) -> tanh(W0 x + b0) -> (depth - 1) layers
+ * tanh(Wl h + bl) of `width` units -> Wout h + bout (nout). Layer 0 runs on
+ * the CUDA cores in FP32; all other layers and all gradient products run on
+ * the tensor cores through the BF16 GEMM above (bf16 operands, FP32
+ * accumulation); master weights, gradients and Adam moments are FP32.
+ * width must be 128 or 256; nin <= 64, nout <= 256, depth 1..16. Weights
+ * start uniform in +-1/sqrt(fan_in) from splitmix64(seed), biases 0.
+ * Parameters are one flat FP32 vector: for l = 0..depth, W_l [rows][fan_in]
+ * row-major then b_l [rows] (rows = width, and nout for l = depth). */
+typedef struct qmc_mlp qmc_mlp;
+int qmc_mlp_create(qmc_mlp **out, int device, int nin, int width, int depth, int nout, uint64_t seed);
+void qmc_mlp_destroy(qmc_mlp *mlp);
+int qmc_mlp_num_params(const qmc_mlp *mlp, size_t *n);
+/* Copy the FP32 master parameters out of / into the model (host [n]). */
+int qmc_mlp_get_params(qmc_mlp *mlp, float *params, size_t n);
+int qmc_mlp_set_params(qmc_mlp *mlp, const float *params, size_t n);
+/* y[B][nout] = model(x[B][nin]) (host buffers). */
+int qmc_mlp_forward(qmc_mlp *mlp, const float *x, int B, float *y);
+/* Loss (1/B) sum_b sum_o wt[o] (model(x_b)_o - y_b,o)^2 (wt may be NULL = 1)
+ * and its gradient with respect to the parameters (host grad[n], may be NULL). */
+int qmc_mlp_grad(qmc_mlp *mlp, const float *x, const float *y, const float *wt, int B, float *loss,
+                 float *grad);
+/* `steps` full-batch Adam steps (beta 0.9/0.999, eps 1e-8) on the same loss;
+ * losses[steps] (may be NULL) receives the loss before each step. */
+int qmc_mlp_train(qmc_mlp *mlp, const float *x, const float *y, const float *wt, int B, int steps, float lr,
+                  float *losses);
+
 #ifdef __cplusplus
 }
 #endif

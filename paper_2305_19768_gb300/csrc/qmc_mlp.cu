@@ -15,10 +15,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/qmc.h"
+
 #include "qmc_internal.h"
 
-#define QMC_E_INVAL_LOCAL (-1)
-#define QMC_E_CUDA_LOCAL (-3)
+#define QMC_E_INVAL_LOCAL QMC_E_INVAL
+#define QMC_E_CUDA_LOCAL QMC_E_CUDA
 
 namespace {
 
@@ -212,3 +218,463 @@ extern "C" int qmc_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
     cudaFree(derr);
     return rc;
 }
+
+// ============================================================================
+// The MLP: x (nin) -> tanh(W0 x + b0) -> [tanh(Wk h + bk)] x (depth-1) -> Wout h + bout
+// Layer 0 (K = nin, tiny) runs on the CUDA cores in FP32; every other layer and
+// every weight/activation gradient product runs through qmc_gemm_bf16_tc with
+// bf16 operands and FP32 accumulation. FP32 master weights, Adam in FP32.
+// Batches are padded to a multiple of 128 rows with zero loss weight.
+// ============================================================================
+namespace {
+
+__device__ __forceinline__ __nv_bfloat16 bf(float x) { return __float2bfloat16_rn(x); }
+
+// h0 = tanh(x W0^T + b0): f32 [Bp][H], bf16 [Bp][H] and [H][Bp]
+__global__ void mlp_layer0_fwd(const float *x, const float *W0, const float *b0, int nin, int H, int Bp,
+                               float *h, __nv_bfloat16 *hb, __nv_bfloat16 *hbT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp * H) return;
+    const int b = i / H, o = i % H;
+    float z = b0[o];
+    for (int k = 0; k < nin; ++k) z = fmaf(W0[o * nin + k], x[b * nin + k], z);
+    const float a = tanhf(z);
+    h[i] = a;
+    hb[i] = bf(a);
+    hbT[(size_t)o * Bp + b] = bf(a);
+}
+
+// a = act(C + bias) for a GEMM output C [Bp][ldc] (columns < N used)
+__global__ void mlp_bias_act(const float *C, const float *bias, int N, int ldc, int Bp, int act, float *h,
+                             __nv_bfloat16 *hb, __nv_bfloat16 *hbT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp * N) return;
+    const int b = i / N, o = i % N;
+    float z = C[(size_t)b * ldc + o] + bias[o];
+    if (act) z = tanhf(z);
+    h[i] = z;
+    if (hb) hb[i] = bf(z);
+    if (hbT) hbT[(size_t)o * Bp + b] = bf(z);
+}
+
+// weighted squared error: loss += wt_o mask_b (out - y)^2 / B; dout = 2 wt_o mask_b (out - y) / B
+__global__ void mlp_loss(const float *out, const float *y, const float *wt, const float *mask, int No, int Nop,
+                         int Bp, float invB, __nv_bfloat16 *dob, __nv_bfloat16 *dobT, float *dof, double *loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp * Nop) return;
+    const int b = i / Nop, o = i % Nop;
+    float g = 0.f;
+    if (o < No) {
+        const float r = out[(size_t)b * No + o] - y[(size_t)b * No + o];
+        const float w = wt[o] * mask[b];
+        g = 2.f * w * r * invB;
+        if (w != 0.f) atomicAdd(loss, (double)(w * r * r * invB));
+    }
+    dob[i] = bf(g);
+    dobT[(size_t)o * Bp + b] = bf(g);
+    dof[i] = g;
+}
+
+// dz = dh (1 - h^2) for tanh layers: bf16 [Bp][H], bf16 [H][Bp], f32 [Bp][H]
+__global__ void mlp_tanh_bwd(const float *dh, const float *h, int H, int Bp, __nv_bfloat16 *dzb,
+                             __nv_bfloat16 *dzbT, float *dzf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp * H) return;
+    const int b = i / H, o = i % H;
+    const float a = h[i];
+    const float g = dh[i] * (1.f - a * a);
+    dzb[i] = bf(g);
+    dzbT[(size_t)o * Bp + b] = bf(g);
+    dzf[i] = g;
+}
+
+// column sums: db[o] = sum_b dz[b][o]  (one block per column, fixed order)
+__global__ void mlp_colsum(const float *dz, int N, int ld, int Bp, float *db) {
+    const int o = blockIdx.x;
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int b = threadIdx.x; b < Bp; b += blockDim.x) s += dz[(size_t)b * ld + o];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[o] = red[0];
+}
+
+// dW0[o][k] = sum_b dz0[b][o] x[b][k]
+__global__ void mlp_layer0_bwd(const float *dz, const float *x, int nin, int H, int Bp, float *dW0) {
+    const int o = blockIdx.x, k = blockIdx.y;
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int b = threadIdx.x; b < Bp; b += blockDim.x) s = fmaf(dz[(size_t)b * H + o], x[b * nin + k], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dW0[o * nin + k] = red[0];
+}
+
+// copy a [H][Nop] GEMM result (dWout^T) into dWout [No][H]
+__global__ void mlp_untranspose(const float *src, int H, int Nop, int No, float *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= No * H) return;
+    const int o = i / H, k = i % H;
+    dst[i] = src[(size_t)k * Nop + o];
+}
+
+// bf16 copies of a weight matrix W [R][C] (rows >= R of the padded copy are 0)
+__global__ void mlp_weights_bf16(const float *W, int R, int Rp, int C, __nv_bfloat16 *Wb, __nv_bfloat16 *WbT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Rp * C) return;
+    const int r = i / C, c = i % C;
+    const float v = r < R ? W[(size_t)r * C + c] : 0.f;
+    Wb[i] = bf(v);
+    WbT[(size_t)c * Rp + r] = bf(v);
+}
+
+__global__ void mlp_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, float b1, float b2,
+                         float eps, float c1, float c2) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+uint64_t mlp_sm64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct qmc_mlp {
+    int device = 0, nin = 0, H = 0, D = 0, No = 0, Nop = 0;
+    cudaStream_t stream = nullptr;
+    size_t nparams = 0;
+    std::vector<size_t> offW, offb;     // per layer (0..D-1 hidden, D = output)
+    float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+    std::vector<__nv_bfloat16 *> Wb, WbT;   // layers 1..D (index by layer)
+    int Bcap = 0;
+    float *x = nullptr, *y = nullptr, *mask = nullptr, *C = nullptr, *tmp = nullptr;
+    std::vector<float *> hf;                 // [D] f32 activations
+    std::vector<__nv_bfloat16 *> hb, hbT;    // [D]
+    float *out = nullptr, *dof = nullptr, *dz = nullptr;
+    __nv_bfloat16 *dob = nullptr, *dobT = nullptr, *dzb = nullptr, *dzbT = nullptr;
+    float *wt = nullptr;
+    double *loss = nullptr;
+    unsigned *err = nullptr;
+    int t = 0;
+};
+
+namespace {
+
+int mlp_free_batch(qmc_mlp *m) {
+    cudaFree(m->x);
+    cudaFree(m->y);
+    cudaFree(m->mask);
+    cudaFree(m->C);
+    cudaFree(m->tmp);
+    cudaFree(m->out);
+    cudaFree(m->dof);
+    cudaFree(m->dz);
+    cudaFree(m->dob);
+    cudaFree(m->dobT);
+    cudaFree(m->dzb);
+    cudaFree(m->dzbT);
+    for (float *p : m->hf) cudaFree(p);
+    for (auto *p : m->hb) cudaFree(p);
+    for (auto *p : m->hbT) cudaFree(p);
+    m->hf.assign(m->D, nullptr);
+    m->hb.assign(m->D, nullptr);
+    m->hbT.assign(m->D, nullptr);
+    m->x = m->y = m->mask = m->C = m->tmp = m->out = m->dof = m->dz = nullptr;
+    m->dob = m->dobT = m->dzb = m->dzbT = nullptr;
+    m->Bcap = 0;
+    return 0;
+}
+
+int mlp_ensure_batch(qmc_mlp *m, int Bp) {
+    if (Bp <= m->Bcap) return 0;
+    mlp_free_batch(m);
+    const size_t H = m->H, No = m->No, Nop = m->Nop;
+    bool bad = false;
+    auto A = [&](void **p, size_t bytes) { bad |= cudaMalloc(p, bytes) != cudaSuccess; };
+    A((void **)&m->x, (size_t)Bp * m->nin * 4);
+    A((void **)&m->y, (size_t)Bp * No * 4);
+    A((void **)&m->mask, (size_t)Bp * 4);
+    A((void **)&m->C, (size_t)Bp * std::max(H, Nop) * 4);
+    A((void **)&m->tmp, (size_t)std::max(H * Nop, (size_t)Bp * H) * 4);
+    A((void **)&m->out, (size_t)Bp * No * 4);
+    A((void **)&m->dof, (size_t)Bp * Nop * 4);
+    A((void **)&m->dz, (size_t)Bp * H * 4);
+    A((void **)&m->dob, (size_t)Bp * Nop * 2);
+    A((void **)&m->dobT, (size_t)Bp * Nop * 2);
+    A((void **)&m->dzb, (size_t)Bp * H * 2);
+    A((void **)&m->dzbT, (size_t)Bp * H * 2);
+    for (int l = 0; l < m->D; ++l) {
+        A((void **)&m->hf[l], (size_t)Bp * H * 4);
+        A((void **)&m->hb[l], (size_t)Bp * H * 2);
+        A((void **)&m->hbT[l], (size_t)Bp * H * 2);
+    }
+    if (bad) {
+        mlp_free_batch(m);
+        return -1;
+    }
+    m->Bcap = Bp;
+    return 0;
+}
+
+// refresh the bf16 weight copies of the GEMM layers from the FP32 master weights
+int mlp_sync_weights(qmc_mlp *m) {
+    for (int l = 1; l <= m->D; ++l) {
+        const int R = l == m->D ? m->No : m->H, Rp = l == m->D ? m->Nop : m->H;
+        mlp_weights_bf16<<<nblk((size_t)Rp * m->H), 256, 0, m->stream>>>(m->params + m->offW[l], R, Rp, m->H,
+                                                                        m->Wb[l], m->WbT[l]);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// forward for Bp rows already in m->x; output in m->out [Bp][No]
+int mlp_forward_dev(qmc_mlp *m, int Bp) {
+    const int H = m->H;
+    mlp_layer0_fwd<<<nblk((size_t)Bp * H), 256, 0, m->stream>>>(m->x, m->params + m->offW[0], m->params + m->offb[0],
+                                                               m->nin, H, Bp, m->hf[0], m->hb[0], m->hbT[0]);
+    for (int l = 1; l < m->D; ++l) {
+        if (qmc_k_gemm_bf16(m->hb[l - 1], m->Wb[l], m->C, Bp, H, H, m->err, m->stream)) return -1;
+        mlp_bias_act<<<nblk((size_t)Bp * H), 256, 0, m->stream>>>(m->C, m->params + m->offb[l], H, H, Bp, 1,
+                                                                 m->hf[l], m->hb[l], m->hbT[l]);
+    }
+    if (qmc_k_gemm_bf16(m->hb[m->D - 1], m->Wb[m->D], m->C, Bp, m->Nop, H, m->err, m->stream)) return -1;
+    mlp_bias_act<<<nblk((size_t)Bp * m->No), 256, 0, m->stream>>>(m->C, m->params + m->offb[m->D], m->No, m->Nop,
+                                                                 Bp, 0, m->out, nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// loss and gradients (into m->grads) for Bp rows with x, y, mask, wt in place
+int mlp_backward_dev(qmc_mlp *m, int Bp, int B) {
+    const int H = m->H, D = m->D, Nop = m->Nop, No = m->No;
+    cudaMemsetAsync(m->loss, 0, sizeof(double), m->stream);
+    mlp_loss<<<nblk((size_t)Bp * Nop), 256, 0, m->stream>>>(m->out, m->y, m->wt, m->mask, No, Nop, Bp, 1.f / B,
+                                                            m->dob, m->dobT, m->dof, m->loss);
+    // output layer: dWout^T = h_{D-1}^T dout  ([H][Nop]), dbout, dh = dout Wout
+    if (qmc_k_gemm_bf16(m->hbT[D - 1], m->dobT, m->tmp, H, Nop, Bp, m->err, m->stream)) return -1;
+    mlp_untranspose<<<nblk((size_t)No * H), 256, 0, m->stream>>>(m->tmp, H, Nop, No, m->grads + m->offW[D]);
+    mlp_colsum<<<No, 256, 0, m->stream>>>(m->dof, No, Nop, Bp, m->grads + m->offb[D]);
+    if (qmc_k_gemm_bf16(m->dob, m->WbT[D], m->C, Bp, H, Nop, m->err, m->stream)) return -1;
+    for (int l = D - 1; l >= 0; --l) {
+        mlp_tanh_bwd<<<nblk((size_t)Bp * H), 256, 0, m->stream>>>(m->C, m->hf[l], H, Bp, m->dzb, m->dzbT, m->dz);
+        mlp_colsum<<<H, 256, 0, m->stream>>>(m->dz, H, H, Bp, m->grads + m->offb[l]);
+        if (l == 0) {
+            mlp_layer0_bwd<<<dim3(H, m->nin), 256, 0, m->stream>>>(m->dz, m->x, m->nin, H, Bp, m->grads + m->offW[0]);
+        } else {
+            // dW_l = dz^T h_{l-1}  ([H][H]); dh_{l-1} = dz W_l
+            if (qmc_k_gemm_bf16(m->dzbT, m->hbT[l - 1], m->grads + m->offW[l], H, H, Bp, m->err, m->stream))
+                return -1;
+            if (qmc_k_gemm_bf16(m->dzb, m->WbT[l], m->C, Bp, H, H, m->err, m->stream)) return -1;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// stage a host batch (B rows) padded to Bp rows
+int mlp_stage(qmc_mlp *m, const float *x, const float *y, const float *wt, int B, int Bp) {
+    if (mlp_ensure_batch(m, Bp)) return -1;
+    cudaMemsetAsync(m->x, 0, (size_t)Bp * m->nin * 4, m->stream);
+    cudaMemcpyAsync(m->x, x, (size_t)B * m->nin * 4, cudaMemcpyHostToDevice, m->stream);
+    if (y) {
+        cudaMemsetAsync(m->y, 0, (size_t)Bp * m->No * 4, m->stream);
+        cudaMemcpyAsync(m->y, y, (size_t)B * m->No * 4, cudaMemcpyHostToDevice, m->stream);
+        std::vector<float> mk(Bp, 0.f);
+        for (int b = 0; b < B; ++b) mk[b] = 1.f;
+        cudaMemcpyAsync(m->mask, mk.data(), (size_t)Bp * 4, cudaMemcpyHostToDevice, m->stream);
+        std::vector<float> w(m->No, 1.f);
+        if (wt) w.assign(wt, wt + m->No);
+        cudaMemcpyAsync(m->wt, w.data(), (size_t)m->No * 4, cudaMemcpyHostToDevice, m->stream);
+        return cudaStreamSynchronize(m->stream) == cudaSuccess ? 0 : -1;   // host vectors go out of scope
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int mlp_check_err(qmc_mlp *m) {
+    unsigned e = 0;
+    if (cudaMemcpyAsync(&e, m->err, 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return -1;
+    return e ? -1 : 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmc_mlp_create(qmc_mlp **out, int device, int nin, int width, int depth, int nout, uint64_t seed) {
+    if (!out || nin < 1 || nin > 64 || width % 128 || width < 128 || width > 256 || depth < 1 || depth > 16 ||
+        nout < 1 || nout > 256)
+        return QMC_E_INVAL_LOCAL;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return QMC_E_CUDA_LOCAL;
+    qmc_mlp *m = new qmc_mlp();
+    m->device = device;
+    m->nin = nin;
+    m->H = width;
+    m->D = depth;
+    m->No = nout;
+    m->Nop = (nout + 15) / 16 * 16;
+    m->hf.assign(depth, nullptr);
+    m->hb.assign(depth, nullptr);
+    m->hbT.assign(depth, nullptr);
+    size_t off = 0;
+    for (int l = 0; l <= depth; ++l) {
+        const size_t fan_in = l == 0 ? nin : width, rows = l == depth ? nout : width;
+        m->offW.push_back(off);
+        off += rows * fan_in;
+        m->offb.push_back(off);
+        off += rows;
+    }
+    m->nparams = off;
+    bool bad = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess;
+    bad |= cudaMalloc(&m->params, off * 4) != cudaSuccess;
+    bad |= cudaMalloc(&m->grads, off * 4) != cudaSuccess;
+    bad |= cudaMalloc(&m->am, off * 4) != cudaSuccess;
+    bad |= cudaMalloc(&m->av, off * 4) != cudaSuccess;
+    bad |= cudaMalloc(&m->wt, 256 * 4) != cudaSuccess;
+    bad |= cudaMalloc(&m->loss, sizeof(double)) != cudaSuccess;
+    bad |= cudaMalloc(&m->err, 4) != cudaSuccess;
+    m->Wb.assign(depth + 1, nullptr);
+    m->WbT.assign(depth + 1, nullptr);
+    for (int l = 1; l <= depth; ++l) {
+        const size_t Rp = l == depth ? m->Nop : width;
+        bad |= cudaMalloc(&m->Wb[l], Rp * width * 2) != cudaSuccess;
+        bad |= cudaMalloc(&m->WbT[l], Rp * width * 2) != cudaSuccess;
+    }
+    if (bad) {
+        qmc_mlp_destroy(m);
+        return QMC_E_CUDA_LOCAL;
+    }
+    // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, from splitmix64
+    std::vector<float> p(off, 0.f);
+    uint64_t st = seed;
+    for (int l = 0; l <= depth; ++l) {
+        const size_t fan_in = l == 0 ? nin : width, rows = l == depth ? nout : width;
+        const double a = 1.0 / std::sqrt((double)fan_in);
+        for (size_t i = 0; i < rows * fan_in; ++i)
+            p[m->offW[l] + i] = (float)(a * (2.0 * ((mlp_sm64(st) >> 11) * (1.0 / 9007199254740992.0)) - 1.0));
+    }
+    cudaMemcpy(m->params, p.data(), off * 4, cudaMemcpyHostToDevice);
+    cudaMemset(m->am, 0, off * 4);
+    cudaMemset(m->av, 0, off * 4);
+    cudaMemset(m->grads, 0, off * 4);
+    cudaMemset(m->err, 0, 4);
+    if (mlp_sync_weights(m) || cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        qmc_mlp_destroy(m);
+        return QMC_E_CUDA_LOCAL;
+    }
+    *out = m;
+    return 0;
+}
+
+void qmc_mlp_destroy(qmc_mlp *m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    mlp_free_batch(m);
+    cudaFree(m->params);
+    cudaFree(m->grads);
+    cudaFree(m->am);
+    cudaFree(m->av);
+    cudaFree(m->wt);
+    cudaFree(m->loss);
+    cudaFree(m->err);
+    for (auto *p : m->Wb) cudaFree(p);
+    for (auto *p : m->WbT) cudaFree(p);
+    if (m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+int qmc_mlp_num_params(const qmc_mlp *m, size_t *n) {
+    if (!m || !n) return QMC_E_INVAL_LOCAL;
+    *n = m->nparams;
+    return 0;
+}
+
+int qmc_mlp_get_params(qmc_mlp *m, float *host, size_t n) {
+    if (!m || !host || n != m->nparams) return QMC_E_INVAL_LOCAL;
+    cudaSetDevice(m->device);
+    if (cudaMemcpyAsync(host, m->params, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return QMC_E_CUDA_LOCAL;
+    return 0;
+}
+
+int qmc_mlp_set_params(qmc_mlp *m, const float *host, size_t n) {
+    if (!m || !host || n != m->nparams) return QMC_E_INVAL_LOCAL;
+    cudaSetDevice(m->device);
+    if (cudaMemcpyAsync(m->params, host, n * 4, cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
+        mlp_sync_weights(m) || cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return QMC_E_CUDA_LOCAL;
+    return 0;
+}
+
+int qmc_mlp_forward(qmc_mlp *m, const float *x, int B, float *y) {
+    if (!m || !x || !y || B < 1) return QMC_E_INVAL_LOCAL;
+    cudaSetDevice(m->device);
+    cudaMemsetAsync(m->err, 0, 4, m->stream);
+    const int Bp = (B + 127) / 128 * 128;
+    if (mlp_stage(m, x, nullptr, nullptr, B, Bp) || mlp_forward_dev(m, Bp)) return QMC_E_CUDA_LOCAL;
+    if (cudaMemcpyAsync(y, m->out, (size_t)B * m->No * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
+        return QMC_E_CUDA_LOCAL;
+    return mlp_check_err(m) ? QMC_E_CUDA_LOCAL : 0;
+}
+
+int qmc_mlp_grad(qmc_mlp *m, const float *x, const float *y, const float *wt, int B, float *loss, float *grad) {
+    if (!m || !x || !y || B < 1) return QMC_E_INVAL_LOCAL;
+    cudaSetDevice(m->device);
+    cudaMemsetAsync(m->err, 0, 4, m->stream);
+    const int Bp = (B + 127) / 128 * 128;
+    if (mlp_stage(m, x, y, wt, B, Bp) || mlp_forward_dev(m, Bp) || mlp_backward_dev(m, Bp, B))
+        return QMC_E_CUDA_LOCAL;
+    double l = 0.0;
+    cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+    if (grad) cudaMemcpyAsync(grad, m->grads, m->nparams * 4, cudaMemcpyDeviceToHost, m->stream);
+    if (mlp_check_err(m)) return QMC_E_CUDA_LOCAL;
+    if (loss) *loss = (float)l;
+    return 0;
+}
+
+int qmc_mlp_train(qmc_mlp *m, const float *x, const float *y, const float *wt, int B, int steps, float lr,
+                  float *losses) {
+    if (!m || !x || !y || B < 1 || steps < 0 || !(lr > 0)) return QMC_E_INVAL_LOCAL;
+    cudaSetDevice(m->device);
+    cudaMemsetAsync(m->err, 0, 4, m->stream);
+    const int Bp = (B + 127) / 128 * 128;
+    if (mlp_stage(m, x, y, wt, B, Bp)) return QMC_E_CUDA_LOCAL;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int s = 0; s < steps; ++s) {
+        if (mlp_forward_dev(m, Bp) || mlp_backward_dev(m, Bp, B)) return QMC_E_CUDA_LOCAL;
+        ++m->t;
+        const float c1 = 1.f - std::pow(b1, (float)m->t), c2 = 1.f - std::pow(b2, (float)m->t);
+        mlp_adam<<<nblk(m->nparams), 256, 0, m->stream>>>(m->params, m->grads, m->am, m->av, m->nparams, lr, b1,
+                                                           b2, eps, c1, c2);
+        if (mlp_sync_weights(m)) return QMC_E_CUDA_LOCAL;
+        if (losses) {
+            double l = 0.0;
+            cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+            cudaStreamSynchronize(m->stream);
+            losses[s] = (float)l;
+        }
+    }
+    return mlp_check_err(m) ? QMC_E_CUDA_LOCAL : 0;
+}
+
+}  // extern "C"

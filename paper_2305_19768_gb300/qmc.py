@@ -110,6 +110,16 @@ def lib():
                 "qmc_autotune": ([vp, P(qmc_job), i32, i32, i32, P(i32), P(i32)], i32),
                 "qmc_median_candidates": ([u64, i32, i32, u64, P(ctypes.c_uint32)], i32),
                 "qmc_gemm_bf16": ([P(ctypes.c_uint16), P(ctypes.c_uint16), P(ctypes.c_float), i32, i32, i32], i32),
+                "qmc_mlp_create": ([P(vp), i32, i32, i32, i32, i32, u64], i32),
+                "qmc_mlp_destroy": ([vp], None),
+                "qmc_mlp_num_params": ([vp, P(sz)], i32),
+                "qmc_mlp_get_params": ([vp, P(ctypes.c_float), sz], i32),
+                "qmc_mlp_set_params": ([vp, P(ctypes.c_float), sz], i32),
+                "qmc_mlp_forward": ([vp, P(ctypes.c_float), i32, P(ctypes.c_float)], i32),
+                "qmc_mlp_grad": ([vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float), i32,
+                                  P(ctypes.c_float), P(ctypes.c_float)], i32),
+                "qmc_mlp_train": ([vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float), i32, i32,
+                                   ctypes.c_float, P(ctypes.c_float)], i32),
                 "qmc_median_lattice": ([vp, P(qmc_job), i32, i32, i32, u64, P(ctypes.c_uint32), P(dbl)], i32),
                 "qmc_series_mul": ([P(qmc_c64), i32, i32, P(qmc_c64), i32, i32, i32, i32, P(qmc_c64)], i32),
                 "qmc_series_var": ([P(qmc_c64), i32, i32, P(dbl), i32, i32, i32, i32, P(dbl)], i32),
@@ -134,7 +144,9 @@ def exported_symbols():
             "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
-            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16"]
+            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_mlp_create",
+            "qmc_mlp_destroy", "qmc_mlp_num_params", "qmc_mlp_get_params", "qmc_mlp_set_params",
+            "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train"]
 
 
 def _dp(a):
@@ -322,6 +334,63 @@ def qmc_gemm_bf16(A_bits, B_bits):
                                      B_bits.ctypes.data_as(P(ctypes.c_uint16)),
                                      C.ctypes.data_as(P(ctypes.c_float)), M, N, K))
     return C
+
+
+def _fp(a):
+    return a.ctypes.data_as(P(ctypes.c_float))
+
+
+class Mlp:
+    """The C-ABI's tensor-core MLP (qmc_mlp_*), host numpy in and out."""
+
+    def __init__(self, nin, width, depth, nout, seed=1, device=0):
+        self.h = ctypes.c_void_p()
+        rc = lib().qmc_mlp_create(ctypes.byref(self.h), device, nin, width, depth, nout, seed)
+        if rc:
+            raise QmcError(rc, "qmc_mlp_create failed")
+        self.shape = (nin, width, depth, nout)
+        n = ctypes.c_size_t()
+        lib().qmc_mlp_num_params(self.h, ctypes.byref(n))
+        self.nparams = n.value
+
+    def close(self):
+        if self.h:
+            lib().qmc_mlp_destroy(self.h)
+            self.h = None
+
+    def params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        _check(None, lib().qmc_mlp_get_params(self.h, _fp(p), self.nparams))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(None, lib().qmc_mlp_set_params(self.h, _fp(p), self.nparams))
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros((x.shape[0], self.shape[3]), dtype=np.float32)
+        _check(None, lib().qmc_mlp_forward(self.h, _fp(x), x.shape[0], _fp(y)))
+        return y
+
+    def grad(self, x, y, wt=None):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        w = None if wt is None else np.ascontiguousarray(wt, dtype=np.float32)
+        loss = ctypes.c_float()
+        g = np.zeros(self.nparams, dtype=np.float32)
+        _check(None, lib().qmc_mlp_grad(self.h, _fp(x), _fp(y), _fp(w) if w is not None else None, x.shape[0],
+                                        ctypes.byref(loss), _fp(g)))
+        return loss.value, g
+
+    def train(self, x, y, steps, lr, wt=None):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        w = None if wt is None else np.ascontiguousarray(wt, dtype=np.float32)
+        losses = np.zeros(max(1, steps), dtype=np.float32)
+        _check(None, lib().qmc_mlp_train(self.h, _fp(x), _fp(y), _fp(w) if w is not None else None, x.shape[0],
+                                         steps, lr, _fp(losses)))
+        return losses[:steps]
 
 
 def qmc_plan_destroy(plan):

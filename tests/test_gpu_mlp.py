@@ -31,3 +31,55 @@ def test_gemm_rejects_bad_shapes():
     A = np.zeros((100, 16), dtype=np.uint16)
     with pytest.raises(qmc.QmcError):
         qmc.qmc_gemm_bf16(A, np.zeros((16, 16), dtype=np.uint16))
+
+
+def _net():
+    return qmc.Mlp(2, 256, 4, 42, seed=7)
+
+
+def test_mlp_forward_and_gradient_match_oracle():
+    from oracle import mlp as omlp
+
+    net = _net()
+    try:
+        rng = np.random.default_rng(11)
+        B = 300
+        x = rng.uniform(-1, 1, size=(B, 2)).astype(np.float32)
+        y = rng.normal(size=(B, 42)).astype(np.float32)
+        wt = rng.uniform(0.5, 2.0, size=42).astype(np.float32)
+        p = net.params()
+        out = net.forward(x)
+        ref, _ = omlp.forward(p, x, 2, 256, 4, 42, bf16=True)
+        scale = np.abs(ref).max()
+        # identical bf16 rounding points; differences come from FP32 accumulation and the
+        # occasional bf16 rounding flip that this causes (one bf16 ulp = 2^-8 relative)
+        assert np.abs(out - ref).max() <= 5e-3 * scale
+        assert np.abs(out - ref).mean() <= 5e-4 * scale
+        loss, g = net.grad(x, y, wt)
+        rloss, rg = omlp.loss_and_grad(p, x, y, wt, 2, 256, 4, 42, bf16=True)
+        assert abs(loss - rloss) <= 1e-3 * abs(rloss)
+        cos = float(g @ rg / (np.linalg.norm(g) * np.linalg.norm(rg)))
+        assert cos > 0.9999, cos
+        assert np.abs(g - rg).max() <= 2e-2 * np.abs(rg).max()
+        # against the unrounded FP64 gradient the bf16 model is still close
+        _, g64 = omlp.loss_and_grad(p, x, y, wt, 2, 256, 4, 42, bf16=False)
+        cos64 = float(g @ g64 / (np.linalg.norm(g) * np.linalg.norm(g64)))
+        assert cos64 > 0.999, cos64
+    finally:
+        net.close()
+
+
+def test_mlp_training_fits_a_smooth_map():
+    net = _net()
+    try:
+        rng = np.random.default_rng(12)
+        x = rng.uniform(-1, 1, size=(2000, 2)).astype(np.float32)
+        cols = [np.sin(2 * x[:, 0] + k * x[:, 1]) * (1 + 0.1 * k) for k in range(42)]
+        y = np.stack(cols, axis=1).astype(np.float32)
+        losses = net.train(x, y, 400, 1e-3)
+        assert losses[-1] < losses[0] / 100, (losses[0], losses[-1])
+        xt = rng.uniform(-1, 1, size=(500, 2)).astype(np.float32)
+        yt = np.stack([np.sin(2 * xt[:, 0] + k * xt[:, 1]) * (1 + 0.1 * k) for k in range(42)], axis=1)
+        assert np.sqrt(np.mean((net.forward(xt) - yt) ** 2)) < 0.05
+    finally:
+        net.close()
