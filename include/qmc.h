@@ -67,7 +67,9 @@ typedef struct {
     uint64_t min_points;   /* smallest lattice (pilot pass) [10000] */
     uint64_t max_points;   /* largest lattice qmc_integrate may use [largest tabulated] */
     int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
-    double lambda;         /* deformation parameter qmc_integrate uses for deformed sectors [0.3] */
+    double lambda;         /* deformation parameter of qmc_integrate for deformed sectors; 0 = choose
+                              per (point, sector) by presampling (qmc_presample_lambda,
+                              lambda_max 1, 8 candidates) [0] */
     int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
     int transform;         /* QMC_TRANSFORM_KOROBOV3 [default], _BAKER or _NONE */
     int reserved[4];
@@ -323,13 +325,27 @@ typedef struct {
  * sqrt(dR^2 + dI^2) <= max(epsrel |A|, epsabs), and otherwise re-sizes the
  * lattices with qmc_allocate (alpha = 2, w_i = var_i n_i^2, tau_i from the
  * measured kernel time split by a per-sector cost model), rounding up to
- * tabulated lattices (<= max_points). Deformed sectors use options.lambda.
+ * tabulated lattices (<= max_points). Deformed sectors use options.lambda,
+ * or, when it is 0, a lambda per (point, sector) chosen once by presampling.
  * Outputs (host, caller-owned): value[npoints][namp][norders] for orders
  * lowest_order.., error[..] with re = sigma of Re, im = sigma of Im.
  * Returns QMC_E_TIMEOUT (timeout_s > 0 exceeded), QMC_E_NOT_CONVERGED
  * (largest lattice reached) or QMC_E_SIGN_CHECK with the outputs written. */
 int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                   int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info);
+
+/* qmc_integrate with control over the start and per-slot outputs. Slots are
+ * the (kinematic point, integral, sector) triples in that nesting order.
+ * n_init (host [nslots], may be NULL): starting lattice size of every slot,
+ * rounded up to a tabulated lattice, replacing the pilot pass (the learned
+ * sizing hands its predicted sizes in here). shifts > 1 overrides the
+ * context's shift count. w_out (host [nslots], may be NULL) receives each
+ * slot's convergence constant w = n^2 sum_orders (var Re + var Im) from its
+ * last evaluation (Eq. (varscaling) with alpha = 2), n_out its final lattice
+ * size. Everything else as qmc_integrate. */
+int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
+                     int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
+                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out);
 
 /* Evaluation that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the

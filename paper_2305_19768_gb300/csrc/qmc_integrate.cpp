@@ -97,8 +97,19 @@ int qmc_allocate(const double *W, const double *tau, const double *V, int nsums,
     return QMC_OK;
 }
 
+int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
+                     int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
+                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out);
+
 int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                   int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info) {
+    return qmc_integrate_ex(ctx, spec, epsrel, epsabs, timeout_s, lowest_order, norders, value, error, info,
+                            nullptr, 0, nullptr, nullptr);
+}
+
+int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
+                     int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
+                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out) {
     using clk = std::chrono::steady_clock;
     const auto t_start = clk::now();
     if (!ctx || !value || !error || norders < 1 || norders > 16 || !(epsrel >= 0) || !(epsabs >= 0))
@@ -161,6 +172,7 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
         bool have = false, dirty = true;
         double mean[2 * 8], var[2 * 8];
         double cost = 1.0;
+        double lambda = 0.3;
     };
     std::vector<Slot> slots;
     std::vector<uint64_t> sizes;
@@ -184,13 +196,44 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
                 sl.p = p;
                 sl.i = i;
                 sl.s = s;
-                sl.n = n0;
+                sl.n = n_init ? round_up((double)n_init[slots.size()]) : n0;
                 sl.cost = sector_cost(I.sectors[s]);
                 slots.push_back(sl);
             }
         }
-    const int m = ctx->opt.shifts;
+    const int m = shifts > 1 ? shifts : ctx->opt.shifts;
     const double alpha = 2.0;
+    // contour-deformation parameter per deformed slot: fixed by the options, or
+    // chosen by presampling (number_of_presamples points per candidate)
+    {
+        std::vector<qmc_job> pre;
+        std::vector<size_t> pre_slot;
+        for (size_t q = 0; q < slots.size(); ++q) {
+            Slot &sl = slots[q];
+            const QmcHostIntegral &I = ctx->integrals[ids[sl.i]];
+            if (!I.sectors[sl.s].deform) continue;
+            if (ctx->opt.lambda > 0) {
+                sl.lambda = ctx->opt.lambda;
+                continue;
+            }
+            qmc_job J;
+            memset(&J, 0, sizeof J);
+            J.integral_id = ids[sl.i];
+            J.sector = sl.s;
+            J.point = I.invariants.empty() ? 0 : sl.p;
+            J.shifts = 2;
+            J.n = sizes.front();
+            J.seed = ctx->opt.seed;
+            J.stream = q;
+            pre.push_back(J);
+            pre_slot.push_back(q);
+        }
+        if (!pre.empty()) {
+            const int rc = qmc_presample_lambda(ctx, pre.data(), (int)pre.size(), slo, sn, 1.0, 8);
+            if (rc && rc != QMC_E_SIGN_CHECK) return rc;
+            for (size_t j = 0; j < pre.size(); ++j) slots[pre_slot[j]].lambda = pre[j].lambda[0];
+        }
+    }
     double evals = 0.0, kernel_s = 0.0;
     int iter = 0, rc_final = QMC_OK;
     std::vector<double> tau(slots.size(), 1.0);
@@ -213,7 +256,7 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
             J.n = sl.n;
             J.seed = ctx->opt.seed;
             J.stream = ((uint64_t)iter << 40) | q;
-            for (int j = 0; j < 6; ++j) J.lambda[j] = ctx->opt.lambda > 0 ? ctx->opt.lambda : 0.3;
+            for (int j = 0; j < 6; ++j) J.lambda[j] = sl.lambda;
             jobs.push_back(J);
             jslot.push_back(q);
         }
@@ -366,6 +409,15 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
         value[idx].im = amp_val[2 * idx + 1];
         error[idx].re = std::sqrt(amp_vre[idx]);
         error[idx].im = std::sqrt(amp_vim[idx]);
+    }
+    for (size_t q = 0; q < slots.size(); ++q) {
+        const Slot &sl = slots[q];
+        if (n_out) n_out[q] = sl.n;
+        if (w_out) {
+            double v = 0.0;
+            for (int so = 0; so < sn; ++so) v += sl.var[2 * so] + sl.var[2 * so + 1];
+            w_out[q] = v * std::pow((double)sl.n, alpha);
+        }
     }
     if (info) {
         memset(info, 0, sizeof *info);

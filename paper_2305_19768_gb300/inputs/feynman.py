@@ -84,29 +84,34 @@ def kin_massless_4pt() -> Kinematics:
     return Kinematics(["s", "t"], 4, square)
 
 
-def kin_2pt(name: str) -> Kinematics:
-    """Two-point kinematics p^2 = <name>."""
+def _unit(names, which) -> Coef:
+    return (Fraction(0),) + tuple(Fraction(1 if n == which else 0) for n in names)
+
+
+def kin_2pt(name: str, names=None) -> Kinematics:
+    """Two-point kinematics p^2 = <name>, over the invariant list ``names``
+    (default: just <name>)."""
+    names = list(names) if names else [name]
+    one, zero = _unit(names, name), (Fraction(0),) * (len(names) + 1)
 
     def square(legs: FrozenSet[int]) -> Coef:
-        if len(frozenset(legs)) == 1:
-            return (Fraction(0), Fraction(1))
-        return (Fraction(0), Fraction(0))
+        return one if len(frozenset(legs)) == 1 else zero
 
-    return Kinematics([name], 2, square)
+    return Kinematics(names, 2, square)
 
 
-def kin_3pt_one_offshell(name: str) -> Kinematics:
+def kin_3pt_one_offshell(name: str, names=None) -> Kinematics:
     """Three-point kinematics with p_0^2 = <name>, p_1^2 = p_2^2 = 0."""
+    names = list(names) if names else [name]
+    one, zero = _unit(names, name), (Fraction(0),) * (len(names) + 1)
 
     def square(legs: FrozenSet[int]) -> Coef:
         legs = frozenset(legs)
         if len(legs) == 2:
             legs = frozenset({0, 1, 2}) - legs
-        if legs == frozenset({0}):
-            return (Fraction(0), Fraction(1))
-        return (Fraction(0), Fraction(0))
+        return one if legs == frozenset({0}) else zero
 
-    return Kinematics([name], 3, square)
+    return Kinematics(names, 3, square)
 
 
 @dataclass

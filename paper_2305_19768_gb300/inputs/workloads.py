@@ -89,15 +89,15 @@ def double_box_massless() -> Integral:
     return _integral_from_graph(g, 4, deform=False)
 
 
-def bubble(msq=0, inv="s", deform: bool = True) -> Integral:
+def bubble(msq=0, inv="s", deform: bool = True, names=None) -> Integral:
     g = Graph(edges=[(0, 1), (1, 0)], masses_sq=[Fraction(msq)] * 2, legs=[0, 1],
-              kin=kin_2pt(inv), name=f"bubble_m{msq}_{inv}")
+              kin=kin_2pt(inv, names), name=f"bubble_m{msq}_{inv}")
     return _integral_from_graph(g, 4, deform=deform)
 
 
-def triangle_one_offshell(msq=0, inv="s", deform: bool = True) -> Integral:
+def triangle_one_offshell(msq=0, inv="s", deform: bool = True, names=None) -> Integral:
     g = Graph(edges=[(0, 1), (1, 2), (2, 0)], masses_sq=[Fraction(msq)] * 3, legs=[0, 1, 2],
-              kin=kin_3pt_one_offshell(inv), name=f"triangle_m{msq}_{inv}")
+              kin=kin_3pt_one_offshell(inv, names), name=f"triangle_m{msq}_{inv}")
     return _integral_from_graph(g, 4, deform=deform)
 
 
@@ -113,3 +113,46 @@ def amplitude_grid(ns: int = 100, nt: int = 100) -> np.ndarray:
     t = -8.0 + 7.0 * (np.arange(nt) + 0.5) / nt
     S, T = np.meshgrid(s, t, indexing="ij")
     return np.stack([S.ravel(), T.ravel()], axis=1)
+
+
+def amplitude_integrals():
+    """The ten one-loop integrals of the synthetic amplitude, all over the
+    invariants (s, t): massless and massive (m^2 = 1) bubbles and one-mass
+    triangles in s (physical, deformed) and in t (Euclidean), and the massless
+    and massive boxes in (s, t) (physical, deformed)."""
+    st = ["s", "t"]
+    out = []
+    for msq in (0, 1):
+        out.append(bubble(msq, "s", deform=True, names=st))
+        out.append(bubble(msq, "t", deform=False, names=st))
+    for msq in (0, 1):
+        out.append(triangle_one_offshell(msq, "s", deform=True, names=st))
+        out.append(triangle_one_offshell(msq, "t", deform=False, names=st))
+    out.append(box_massless(deform=True))
+    out.append(box_massive(deform=True))
+    return out
+
+
+def amplitude_coefficients(nint: int = 10, seed: int = 5):
+    """Coefficient polynomials C_i(s, t) = sum_{a+b<=2} c_iab s^a t^b with
+    c = p/q, p uniform in [-9, 9], q in [1, 9] (splitmix64 from ``seed``;
+    drawn integral by integral, monomials in the order 1, s, t, s^2, s t, t^2).
+    Returns an array [nint][6] of Fractions."""
+    st = seed & MASK64
+    rows = []
+    for _ in range(nint):
+        row = []
+        for _m in range(6):
+            st, a = splitmix64_next(st)
+            st, b = splitmix64_next(st)
+            row.append(Fraction(int(a % 19) - 9, int(b % 9) + 1))
+        rows.append(row)
+    return rows
+
+
+def amplitude_coefficient_values(points: np.ndarray, coefs) -> np.ndarray:
+    """C_i at each (s, t): float64 [npoints][nint]."""
+    s, t = points[:, 0], points[:, 1]
+    mons = np.stack([np.ones_like(s), s, t, s * s, s * t, t * t], axis=1)
+    C = np.array([[float(c) for c in row] for row in coefs])
+    return mons @ C.T

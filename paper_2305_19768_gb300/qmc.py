@@ -126,6 +126,8 @@ def lib():
                 "qmc_allocate": ([P(dbl), P(dbl), P(dbl), i32, i32, dbl, dbl, P(dbl)], i32),
                 "qmc_integrate": ([vp, P(qmc_sum_spec), dbl, dbl, dbl, i32, i32, P(qmc_c64), P(qmc_c64),
                                    P(qmc_integrate_info)], i32),
+                "qmc_integrate_ex": ([vp, P(qmc_sum_spec), dbl, dbl, dbl, i32, i32, P(qmc_c64), P(qmc_c64),
+                                      P(qmc_integrate_info), P(u64), i32, P(dbl), P(u64)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -146,7 +148,7 @@ def exported_symbols():
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
             "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_mlp_create",
             "qmc_mlp_destroy", "qmc_mlp_num_params", "qmc_mlp_get_params", "qmc_mlp_set_params",
-            "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train"]
+            "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train", "qmc_integrate_ex"]
 
 
 def _dp(a):
@@ -478,8 +480,10 @@ def qmc_allocate(W, tau, V, alpha=2.0, n_min=0.0):
 
 
 def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, epsabs=0.0, timeout=0.0,
-                  lowest_order=0, norders=1, npoints=1, namp=1, check=True):
-    """Adaptive integration; returns (value, error, info dict, return code).
+                  lowest_order=0, norders=1, npoints=1, namp=1, check=True, n_init=None, shifts=0,
+                  nslots=0):
+    """Adaptive integration; returns (value, error, info dict, return code), and with
+    ``nslots`` > 0 also (w_out, n_out) per (point, integral, sector) slot.
     value/error: complex [npoints][namp][norders] (error = sigma_re + 1j sigma_im)."""
     spec = None
     keep = []
@@ -499,12 +503,23 @@ def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, eps
     value = np.zeros((npoints, namp, norders), dtype=np.complex128)
     error = np.zeros((npoints, namp, norders), dtype=np.complex128)
     info = qmc_integrate_info()
-    rc = lib().qmc_integrate(ctx, ctypes.byref(spec) if spec is not None else None, epsrel, epsabs, timeout,
-                             lowest_order, norders, value.ctypes.data_as(P(qmc_c64)),
-                             error.ctypes.data_as(P(qmc_c64)), ctypes.byref(info))
+    w_out = np.zeros(max(1, nslots))
+    n_out = np.zeros(max(1, nslots), dtype=np.uint64)
+    ni = None
+    if n_init is not None:
+        ni = np.ascontiguousarray(n_init, dtype=np.uint64)
+        keep.append(ni)
+    rc = lib().qmc_integrate_ex(ctx, ctypes.byref(spec) if spec is not None else None, epsrel, epsabs, timeout,
+                                lowest_order, norders, value.ctypes.data_as(P(qmc_c64)),
+                                error.ctypes.data_as(P(qmc_c64)), ctypes.byref(info),
+                                ni.ctypes.data_as(P(ctypes.c_uint64)) if ni is not None else None, shifts,
+                                _dp(w_out) if nslots else None,
+                                n_out.ctypes.data_as(P(ctypes.c_uint64)) if nslots else None)
     if check and rc not in (0,):
         _check(ctx, rc)
     d = {k: getattr(info, k) for k, _ in qmc_integrate_info._fields_}
+    if nslots:
+        return value, error, d, rc, w_out[:nslots], n_out[:nslots]
     return value, error, d, rc
 
 

@@ -1,0 +1,33 @@
+"""The amplitude scan on a small grid: plain (per point), batched and learned
+(MLP-sized, spot-checked, mixed precision) agree within their errors and meet
+the requested accuracy; the learned form reports its surrogate acceptances."""
+import numpy as np
+import pytest
+
+from paper_2305_19768_gb300 import scan
+
+pytestmark = pytest.mark.gpu
+
+
+def test_scan_modes_agree_on_a_small_grid():
+    P = scan.Problem(npoints=144, grid=(12, 12))
+    eps = 1e-4
+    plain = scan.run_plain(P, eps, sel=np.arange(0, 144, 12))
+    batched = scan.run_batched(P, eps)
+    learned = scan.run_learned(P, eps, ntrain=64, steps=600)
+    assert batched["rc"] == 0 and plain["failures"] == 0
+    rel = scan.relative_errors(batched["values"], batched["errors"])
+    assert rel.max() <= eps * 1.0000001
+    # plain and batched estimate the same sums: differences within 5 combined sigma
+    sel = np.arange(0, 144, 12)
+    d = np.abs(plain["values"] - batched["values"][sel])
+    comb = np.hypot(np.abs(plain["errors"]), np.abs(batched["errors"][sel]))
+    assert np.all(d <= 5 * comb + 1e-12 * np.abs(plain["values"]))
+    # learned: every point meets the request (surrogate or QMC) and agrees with batched
+    rel_l = scan.relative_errors(learned["values"], learned["errors"])
+    assert rel_l.max() <= eps * 1.0000001
+    d = np.abs(learned["values"] - batched["values"])
+    comb = np.hypot(np.abs(learned["errors"]), np.abs(batched["errors"]))
+    assert np.all(d <= 5 * comb + 1e-12 * np.abs(batched["values"]))
+    print("learned accepted", learned["accepted"], "of", 144 - 64, "times", learned["seconds"],
+          batched["seconds"])
