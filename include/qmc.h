@@ -72,8 +72,18 @@ typedef struct {
                               lambda_max 1, 8 candidates) [0] */
     int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
     int transform;         /* QMC_TRANSFORM_KOROBOV3 [default], _BAKER or _NONE */
-    int reserved[4];
+    int target_mode;       /* QMC_TARGET_COEFFICIENT [default] or QMC_TARGET_AMPLITUDE */
+    int reserved[3];
 } qmc_options;
+
+/* What epsrel refers to in qmc_integrate. COEFFICIENT: each eps coefficient
+ * A^(o) separately, sqrt(dR^2 + dI^2) <= epsrel |A^(o)| (the paper's
+ * definition, timings section). AMPLITUDE: every coefficient of an amplitude
+ * at a point against the amplitude's largest coefficient there,
+ * sqrt(dR^2 + dI^2) <= epsrel max_o |A^(o)| (reachable where one coefficient
+ * passes through zero). */
+#define QMC_TARGET_COEFFICIENT 0
+#define QMC_TARGET_AMPLITUDE 1
 
 /* Periodizing transforms (timings section: korobov3 by default, baker for
  * some examples): korobov3 t = u^4 (35 - 84u + 70u^2 - 20u^3) with weight

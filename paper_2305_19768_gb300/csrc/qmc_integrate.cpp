@@ -203,6 +203,9 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
         }
     const int m = shifts > 1 ? shifts : ctx->opt.shifts;
     const double alpha = 2.0;
+    std::vector<size_t> pbegin(npts + 1, slots.size());   // slots of point p: [pbegin[p], pbegin[p+1])
+    for (size_t q = slots.size(); q-- > 0;) pbegin[slots[q].p] = q;
+    for (int p = npts - 1; p >= 0; --p) pbegin[p] = std::min(pbegin[p], pbegin[p + 1]);
     // contour-deformation parameter per deformed slot: fixed by the options, or
     // chosen by presampling (number_of_presamples points per candidate)
     {
@@ -343,7 +346,13 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             }
         }
         for (size_t idx = 0; idx < sum_ok.size(); ++idx) {
-            const double mag = std::hypot(amp_val[2 * idx], amp_val[2 * idx + 1]);
+            double mag = std::hypot(amp_val[2 * idx], amp_val[2 * idx + 1]);
+            if (ctx->opt.target_mode == QMC_TARGET_AMPLITUDE) {
+                // relative to the largest coefficient of this amplitude at this point
+                const size_t base = idx - idx % norders;
+                for (int o = 0; o < norders; ++o)
+                    mag = std::max(mag, std::hypot(amp_val[2 * (base + o)], amp_val[2 * (base + o) + 1]));
+            }
             const double tgt = std::max(epsrel * mag, epsabs);
             target[idx] = tgt;
             if (!(std::sqrt(amp_var[idx]) <= tgt)) {
@@ -366,9 +375,8 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
                     if (sum_ok[idx] || !(target[idx] > 0)) continue;
                     std::vector<size_t> members;
                     std::vector<double> W, tv;
-                    for (size_t q = 0; q < slots.size(); ++q) {
+                    for (size_t q = pbegin[p]; q < pbegin[p + 1]; ++q) {
                         const Slot &sl = slots[q];
-                        if (sl.p != p) continue;
                         const qmc_c64 *g = &G[(((size_t)p * namp + k) * nint + sl.i) * gn];
                         // W = sum_{o'} |g^{(o - o')}|^2 w^{(o')},  w = var n^alpha
                         double wsum = 0.0;

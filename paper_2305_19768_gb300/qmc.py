@@ -25,6 +25,7 @@ QMC_PRECISION_FP64 = 0
 QMC_PRECISION_MIXED = 1
 QMC_TRANSFORM_KOROBOV3, QMC_TRANSFORM_BAKER, QMC_TRANSFORM_NONE = 0, 1, 2
 QMC_JOB_UNSHIFTED = 1
+QMC_TARGET_COEFFICIENT, QMC_TARGET_AMPLITUDE = 0, 1
 ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIMEOUT",
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
@@ -40,7 +41,8 @@ class qmc_options(ctypes.Structure):
                 ("ppt", ctypes.c_int), ("min_points", ctypes.c_uint64),
                 ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("precision", ctypes.c_int),
-                ("transform", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("transform", ctypes.c_int), ("target_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class qmc_sum_spec(ctypes.Structure):

@@ -22,7 +22,7 @@ def test_scan_modes_agree_on_a_small_grid():
     sel = np.arange(0, 144, 12)
     d = np.abs(plain["values"] - batched["values"][sel])
     comb = np.hypot(np.abs(plain["errors"]), np.abs(batched["errors"][sel]))
-    assert np.all(d <= 5 * comb + 1e-12 * np.abs(plain["values"]))
+    assert np.all(d <= 5 * comb + 1e-12 * np.abs(plain["values"]).max(axis=1, keepdims=True))
     # learned: every point meets the request (surrogate or QMC) and agrees with batched
     # within 5 combined sigma plus the requested error (its mixed-precision QMC carries
     # a ~1e-7 relative FP32-product bias that only shows where sigma is far below it)
@@ -30,6 +30,6 @@ def test_scan_modes_agree_on_a_small_grid():
     assert rel_l.max() <= eps * 1.0000001
     d = np.abs(learned["values"] - batched["values"])
     comb = np.hypot(np.abs(learned["errors"]), np.abs(batched["errors"]))
-    assert np.all(d <= 5 * comb + eps * np.abs(batched["values"]))
+    assert np.all(d <= 5 * comb + eps * np.abs(batched["values"]).max(axis=1, keepdims=True))
     print("learned accepted", learned["accepted"], "of", 144 - 64, "times", learned["seconds"],
           batched["seconds"])
