@@ -69,7 +69,7 @@ typedef struct {
     int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
     double lambda;         /* deformation parameter of qmc_integrate for deformed sectors; 0 = choose
                               per (point, sector) by presampling (qmc_presample_lambda,
-                              lambda_max 1, 8 candidates) [0] */
+                              lambda_max 1, 12 candidates) [0] */
     int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
     int transform;         /* QMC_TRANSFORM_KOROBOV3 [default], _BAKER or _NONE */
     int target_mode;       /* QMC_TARGET_COEFFICIENT [default] or QMC_TARGET_AMPLITUDE */
@@ -234,9 +234,9 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
  * presampling (the paper's number_of_presamples): candidates
  * lambda_max * 0.7^c, c < ncand (<= 32), are each evaluated on the smallest
  * tabulated lattice with >= presamples/2 points and 2 shifts; a candidate
- * qualifies if no sample has Im F(z) > 0, and among the qualifying ones the
- * smallest shift-to-shift spread of the highest requested order wins (ties
- * to the larger lambda). Writes jobs[i].lambda[0..5] (host array, in/out);
+ * qualifies if no sample has Im F(z) > 0 and its estimates are finite, and
+ * the largest qualifying candidate wins (the decreasing-lambda search of
+ * pySecDec's presampling). Writes jobs[i].lambda[0..5] (host array, in/out);
  * undeformed jobs are untouched. QMC_E_SIGN_CHECK if some job has no
  * qualifying candidate (it gets the smallest one). */
 int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int norders, double lambda_max,

@@ -232,7 +232,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             pre_slot.push_back(q);
         }
         if (!pre.empty()) {
-            const int rc = qmc_presample_lambda(ctx, pre.data(), (int)pre.size(), slo, sn, 1.0, 8);
+            const int rc = qmc_presample_lambda(ctx, pre.data(), (int)pre.size(), slo, sn, 1.0, 12);
             if (rc && rc != QMC_E_SIGN_CHECK) return rc;
             for (size_t j = 0; j < pre.size(); ++j) slots[pre_slot[j]].lambda = pre[j].lambda[0];
         }
@@ -499,10 +499,11 @@ extern "C" int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int 
     if (!rc) rc = qmc_plan_job_failures(plan, fails.data());
     qmc_plan_destroy(plan);
     if (rc) return rc;
-    // choose per job: zero failures, smallest shift spread of the highest order; ties -> larger lambda
+    // choose per job: the largest candidate with no sign-check failure (the
+    // spread between the two shifts is far too noisy to rank candidates by)
     bool all_found = true;
     for (int i = 0; i < njobs; ++i) {
-        double best_var = INFINITY, best_l = -1.0, smallest = INFINITY;
+        double best_l = -1.0, smallest = INFINITY;
         bool any = false;
         for (size_t c = 0; c < cand.size(); ++c) {
             if (owner[c] != i) continue;
@@ -510,13 +511,9 @@ extern "C" int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int 
             smallest = std::min(smallest, lam[c]);
             if (fails[c]) continue;
             const double *q = &out[c * (size_t)m_pre * norders * 2];
-            const int o = norders - 1;
-            const double dr = q[o * 2] - q[(norders + o) * 2], di = q[o * 2 + 1] - q[(norders + o) * 2 + 1];
-            const double v = dr * dr + di * di;
-            if (v < best_var || (v == best_var && lam[c] > best_l)) {
-                best_var = v;
-                best_l = lam[c];
-            }
+            bool finite = true;
+            for (int k = 0; k < m_pre * norders * 2; ++k) finite &= std::isfinite(q[k]);
+            if (finite && lam[c] > best_l) best_l = lam[c];
         }
         if (!any) continue;
         if (best_l < 0) {

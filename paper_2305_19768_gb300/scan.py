@@ -51,10 +51,11 @@ class Problem:
         self.nsec = [len(I.sectors) for I in self.integrals]
         self.nslot = sum(self.nsec)
 
-    def context(self, precision=qmc.QMC_PRECISION_FP64, shifts=32):
+    def context(self, precision=qmc.QMC_PRECISION_FP64, shifts=32, max_points=0):
         # lambda chosen per (point, sector) by presampling; epsrel against each
         # amplitude's largest eps coefficient (QMC_TARGET_AMPLITUDE)
-        ctx = qmc.qmc_create(0, precision=precision, shifts=shifts, target_mode=qmc.QMC_TARGET_AMPLITUDE)
+        ctx = qmc.qmc_create(0, precision=precision, shifts=shifts, target_mode=qmc.QMC_TARGET_AMPLITUDE,
+                             max_points=max_points)
         qmc.load_lattice_table(ctx)
         ids = [qmc.qmc_load_sectors_mem(ctx, I.to_text()) for I in self.integrals]
         return ctx, ids
@@ -86,9 +87,9 @@ def run_plain(P: Problem, epsrel: float, sel=None):
 
 
 def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION_FP64, n_init=None,
-                shifts=0, want_slots=False):
+                shifts=0, want_slots=False, max_points=0):
     sel = np.arange(len(P.points)) if sel is None else np.asarray(sel)
-    ctx, ids = P.context(precision)
+    ctx, ids = P.context(precision, max_points=max_points)
     t0 = time.perf_counter()
     try:
         qmc.qmc_set_kinematics(ctx, P.points[sel])
