@@ -107,10 +107,14 @@ def massive_box_points(count: int = 1024, seed: int = 3) -> np.ndarray:
     return np.stack([5.0 + 15.0 * u[:, 0], -8.0 + 7.0 * u[:, 1]], axis=1)
 
 
-def amplitude_grid(ns: int = 100, nt: int = 100) -> np.ndarray:
-    """Row-major (s, t) grid over s in [5, 20], t in [-8, -1] (cell centres)."""
+def amplitude_grid(ns: int = 100, nt: int = 100, t_offset: float = 0.137) -> np.ndarray:
+    """Row-major (s, t) grid over s in [5, 20], t in [-8, -1]: s at cell centres,
+    t at cell centres moved by ``t_offset`` of a cell, so that no point lies on
+    u = -s - t = 0 (on that line the massless box's sector polynomials vanish
+    along a line through a sector corner, where the deformation vanishes too,
+    and the sector integrands are not integrable)."""
     s = 5.0 + 15.0 * (np.arange(ns) + 0.5) / ns
-    t = -8.0 + 7.0 * (np.arange(nt) + 0.5) / nt
+    t = -8.0 + 7.0 * (np.arange(nt) + 0.5 + t_offset) / nt
     S, T = np.meshgrid(s, t, indexing="ij")
     return np.stack([S.ravel(), T.ravel()], axis=1)
 

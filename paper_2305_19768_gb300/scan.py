@@ -51,11 +51,11 @@ class Problem:
         self.nsec = [len(I.sectors) for I in self.integrals]
         self.nslot = sum(self.nsec)
 
-    def context(self, precision=qmc.QMC_PRECISION_FP64, shifts=32, max_points=0):
+    def context(self, precision=qmc.QMC_PRECISION_FP64, shifts=32, max_points=0, min_points=10000):
         # lambda chosen per (point, sector) by presampling; epsrel against each
         # amplitude's largest eps coefficient (QMC_TARGET_AMPLITUDE)
         ctx = qmc.qmc_create(0, precision=precision, shifts=shifts, target_mode=qmc.QMC_TARGET_AMPLITUDE,
-                             max_points=max_points)
+                             max_points=max_points, min_points=min_points)
         qmc.load_lattice_table(ctx)
         ids = [qmc.qmc_load_sectors_mem(ctx, I.to_text()) for I in self.integrals]
         return ctx, ids
@@ -87,9 +87,9 @@ def run_plain(P: Problem, epsrel: float, sel=None):
 
 
 def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION_FP64, n_init=None,
-                shifts=0, want_slots=False, max_points=0):
+                shifts=0, want_slots=False, max_points=0, min_points=10000):
     sel = np.arange(len(P.points)) if sel is None else np.asarray(sel)
-    ctx, ids = P.context(precision, max_points=max_points)
+    ctx, ids = P.context(precision, max_points=max_points, min_points=min_points)
     t0 = time.perf_counter()
     try:
         qmc.qmc_set_kinematics(ctx, P.points[sel])
@@ -116,8 +116,9 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     t0 = time.perf_counter()
     train = np.arange(min(ntrain, len(P.points)))
     rest = np.arange(len(train), len(P.points))
-    # 1. the method's own outputs on the training points
-    tr = run_batched(P, epsrel, train, precision, want_slots=True)
+    # 1. the method's own outputs on the training points: batched, adaptive,
+    #    from a small pilot (n = spot_n, `shifts` shifts) instead of 10^4 x 32
+    tr = run_batched(P, epsrel, train, precision, want_slots=True, shifts=shifts, min_points=spot_n)
     # 2. the model: (s, t) -> log w per slot, Re/Im per eps coefficient
     x = _features(P.points[train])
     logw = np.log(np.maximum(tr["w"], 1e-300))
