@@ -32,6 +32,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import sys
 import time
 
 import numpy as np
@@ -110,15 +111,24 @@ def _features(points):
     return np.stack([(s - 12.5) / 7.5, (t + 4.5) / 3.5], axis=1).astype(np.float32)
 
 
+def _log(msg):
+    print(f"[scan] {msg}", file=sys.stderr, flush=True)
+
+
 def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC_PRECISION_MIXED,
-                steps: int = 1500, spot_n: int = 1009, spot_shifts: int = 8, shifts: int = 16):
-    """Learned sizing + spot-checked surrogate + batched QMC (see module doc)."""
+                steps: int = 1500, spot_n: int = 1009, spot_shifts: int = 8, shifts: int = 16,
+                max_points: int = 1000003):
+    """Learned sizing + spot-checked surrogate + batched QMC (see module doc).
+    Lattices are capped at `max_points` (sizes beyond it come from a model error)."""
     t0 = time.perf_counter()
     train = np.arange(min(ntrain, len(P.points)))
     rest = np.arange(len(train), len(P.points))
     # 1. the method's own outputs on the training points: batched, adaptive,
     #    from a small pilot (n = spot_n, `shifts` shifts) instead of 10^4 x 32
-    tr = run_batched(P, epsrel, train, precision, want_slots=True, shifts=shifts, min_points=spot_n)
+    tr = run_batched(P, epsrel, train, precision, want_slots=True, shifts=shifts, min_points=spot_n,
+                     max_points=max_points)
+    _log(f"training QMC: {tr['seconds']:.2f} s, {tr['evaluations']:.3g} evals, rc {tr['rc']}, "
+         f"{tr['iterations']} passes, n quartiles {np.percentile(tr['n'], [50, 90, 99, 100]).tolist()}")
     # 2. the model: (s, t) -> log w per slot, Re/Im per eps coefficient
     x = _features(P.points[train])
     logw = np.log(np.maximum(tr["w"], 1e-300))
@@ -134,6 +144,7 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     finally:
         net.close()
     t_model = time.perf_counter() - t0
+    _log(f"model trained and evaluated: {t_model:.2f} s since start, final loss {losses[-1]:.4g}")
     res_vals = np.zeros((len(P.points), NORD), complex)
     res_errs = np.zeros((len(P.points), NORD), complex)
     res_vals[train], res_errs[train] = tr["values"], tr["errors"]
@@ -142,7 +153,9 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     w_pred = np.exp(pred[:, :P.nslot])
     a_pred = pred[:, P.nslot:P.nslot + NORD] + 1j * pred[:, P.nslot + NORD:]
     # 3. spot check: one small-lattice pass for every remaining point
-    sp = run_batched(P, 1e9, rest, precision, n_init=np.full(len(rest) * P.nslot, spot_n), shifts=spot_shifts)
+    sp = run_batched(P, 1e9, rest, precision, n_init=np.full(len(rest) * P.nslot, spot_n), shifts=spot_shifts,
+                     min_points=spot_n)
+    _log(f"spot check: {sp['seconds']:.2f} s, {sp['evaluations']:.3g} evals")
     target = epsrel * np.abs(sp["values"]).max(axis=1, keepdims=True)
     sig = np.abs(sp["errors"])
     accept = np.all((sig <= target) & (np.abs(a_pred - sp["values"]) <= target), axis=1)
@@ -162,7 +175,12 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
             W = (np.abs(P.C[p, slot_int]) ** 2 * wp[k])[None, :]
             V = np.array([(epsrel * max(np.max(np.abs(ap[k])), 1e-12)) ** 2])
             n_init[k] = qmc.qmc_allocate(W, np.ones(P.nslot), V, 2.0, float(spot_n))
-        run = run_batched(P, epsrel, todo, precision, n_init=n_init.ravel(), shifts=shifts)
+        n_init = np.minimum(n_init, max_points)
+        _log(f"sized lattices: quartiles {np.percentile(n_init, [50, 90, 99, 100]).tolist()}")
+        run = run_batched(P, epsrel, todo, precision, n_init=n_init.ravel(), shifts=shifts, min_points=spot_n,
+                          max_points=max_points)
+        _log(f"sized QMC: {run['seconds']:.2f} s, {run['evaluations']:.3g} evals, rc {run['rc']}, "
+             f"{run['iterations']} passes")
         res_vals[todo], res_errs[todo] = run["values"], run["errors"]
         evals += run["evaluations"]
     return dict(seconds=time.perf_counter() - t0, values=res_vals, errors=res_errs, evaluations=evals,
