@@ -69,7 +69,7 @@ typedef struct {
     int presamples;        /* points per lambda candidate in the deformation presampling [10000] */
     double lambda;         /* deformation parameter of qmc_integrate for deformed sectors; 0 = choose
                               per (point, sector) by presampling (qmc_presample_lambda,
-                              lambda_max 1, 12 candidates) [0] */
+                              lambda_max 1, 16 candidates) [0] */
     int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
     int transform;         /* QMC_TRANSFORM_KOROBOV3 [default], _BAKER or _NONE */
     int target_mode;       /* QMC_TARGET_COEFFICIENT [default] or QMC_TARGET_AMPLITUDE */
@@ -231,12 +231,12 @@ int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d,
 int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta);
 
 /* Choose the contour-deformation parameter of every deformed job by
- * presampling (the paper's number_of_presamples): candidates
- * lambda_max * 0.7^c, c < ncand (<= 32), are each evaluated on the smallest
- * tabulated lattice with >= presamples/2 points and 2 shifts; a candidate
- * qualifies if no sample has Im F(z) > 0 and its estimates are finite, and
- * the largest qualifying candidate wins (the decreasing-lambda search of
- * pySecDec's presampling). Writes jobs[i].lambda[0..5] (host array, in/out);
+ * presampling (the paper's number_of_presamples): a decreasing search over
+ * lambda_max * 0.7^c, c < ncand (<= 32); round c evaluates candidate c, on
+ * the smallest tabulated lattice with >= presamples/2 points and 2 shifts,
+ * for the jobs that have not qualified yet, and a job keeps the first
+ * candidate with no sample at Im F(z) > 0 and finite estimates (the largest
+ * qualifying lambda). Writes jobs[i].lambda[0..5] (host array, in/out);
  * undeformed jobs are untouched. QMC_E_SIGN_CHECK if some job has no
  * qualifying candidate (it gets the smallest one). */
 int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int norders, double lambda_max,
@@ -352,10 +352,13 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
  * context's shift count. w_out (host [nslots], may be NULL) receives each
  * slot's convergence constant w = n^2 sum_orders (var Re + var Im) from its
  * last evaluation (Eq. (varscaling) with alpha = 2), n_out its final lattice
- * size. Everything else as qmc_integrate. */
+ * size. lambda_io (host [nslots], may be NULL): on input a positive entry
+ * fixes the deformation parameter of that (deformed) slot and skips its
+ * presampling; on output every deformed slot's lambda (0 for the others).
+ * Everything else as qmc_integrate. */
 int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                      int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
-                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out);
+                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out, double *lambda_io);
 
 /* Evaluation that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the

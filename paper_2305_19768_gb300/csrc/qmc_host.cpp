@@ -564,6 +564,13 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         c.orig = per_orig[cls];
         c.block = ctx->opt.block == 256 ? 256 : (ctx->opt.block == 128 ? 128 : (ctx->tuned_block[cls] ? ctx->tuned_block[cls] : 128));
         c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : (ctx->tuned_ppt[cls] ? ctx->tuned_ppt[cls] : 16);
+        if (ctx->opt.ppt <= 0 && !ctx->tuned_ppt[cls]) {
+            // small lattices: tiles of 512 points instead of 2048, so that a
+            // lattice of a few thousand points does not leave most threads idle
+            uint64_t nmax = 0;
+            for (const QmcJobDev &D : v) nmax = std::max<uint64_t>(nmax, D.n);
+            if (nmax < 16384) c.ppt = 4;
+        }
         const uint64_t tile_k = (uint64_t)c.block * c.ppt;
         uint64_t tiles = 0;
         for (QmcJobDev &D : v) {

@@ -99,17 +99,17 @@ int qmc_allocate(const double *W, const double *tau, const double *V, int nsums,
 
 int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                      int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
-                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out);
+                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out, double *lambda_io);
 
 int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                   int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info) {
     return qmc_integrate_ex(ctx, spec, epsrel, epsabs, timeout_s, lowest_order, norders, value, error, info,
-                            nullptr, 0, nullptr, nullptr);
+                            nullptr, 0, nullptr, nullptr, nullptr);
 }
 
 int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                      int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
-                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out) {
+                     const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out, double *lambda_io) {
     using clk = std::chrono::steady_clock;
     const auto t_start = clk::now();
     if (!ctx || !value || !error || norders < 1 || norders > 16 || !(epsrel >= 0) || !(epsabs >= 0))
@@ -215,6 +215,10 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             Slot &sl = slots[q];
             const QmcHostIntegral &I = ctx->integrals[ids[sl.i]];
             if (!I.sectors[sl.s].deform) continue;
+            if (lambda_io && lambda_io[q] > 0) {
+                sl.lambda = lambda_io[q];
+                continue;
+            }
             if (ctx->opt.lambda > 0) {
                 sl.lambda = ctx->opt.lambda;
                 continue;
@@ -232,7 +236,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             pre_slot.push_back(q);
         }
         if (!pre.empty()) {
-            const int rc = qmc_presample_lambda(ctx, pre.data(), (int)pre.size(), slo, sn, 1.0, 12);
+            const int rc = qmc_presample_lambda(ctx, pre.data(), (int)pre.size(), slo, sn, 1.0, 16);
             if (rc && rc != QMC_E_SIGN_CHECK) return rc;
             for (size_t j = 0; j < pre.size(); ++j) slots[pre_slot[j]].lambda = pre[j].lambda[0];
         }
@@ -420,6 +424,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
     }
     for (size_t q = 0; q < slots.size(); ++q) {
         const Slot &sl = slots[q];
+        if (lambda_io) lambda_io[q] = ctx->integrals[ids[sl.i]].sectors[sl.s].deform ? sl.lambda : 0.0;
         if (n_out) n_out[q] = sl.n;
         if (w_out) {
             double v = 0.0;
@@ -463,67 +468,56 @@ extern "C" int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int 
             n_pre = v;
             break;
         }
-    std::vector<qmc_job> cand;
-    std::vector<int> owner;
-    std::vector<double> lam;
+    // decreasing-lambda search: round c evaluates candidate lambda_max * 0.7^c for
+    // the jobs that have not passed yet; a job takes the first candidate with no
+    // sign-check failure and finite estimates
+    std::vector<int> pending;
     for (int i = 0; i < njobs; ++i) {
         const qmc_job &J = jobs[i];
         if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size())
             return fail(ctx, QMC_E_INVAL, "job %d: bad integral id", i);
         const QmcHostIntegral &I = ctx->integrals[J.integral_id];
         if (J.sector < 0 || J.sector >= (int)I.sectors.size()) return fail(ctx, QMC_E_INVAL, "job %d: bad sector", i);
-        if (!I.sectors[J.sector].deform) continue;
-        double l = lambda_max;
-        for (int c = 0; c < ncand; ++c, l *= 0.7) {
-            qmc_job C = J;
+        if (I.sectors[J.sector].deform) pending.push_back(i);
+    }
+    double l = lambda_max;
+    for (int c = 0; c < ncand && !pending.empty(); ++c, l *= 0.7) {
+        std::vector<qmc_job> cand;
+        for (int i : pending) {
+            qmc_job C = jobs[i];
             C.shifts = m_pre;
             C.n = n_pre;
-            C.stream = J.stream * 64 + (uint64_t)c + 0x7000000000000000ULL;
+            C.stream = jobs[i].stream * 64 + (uint64_t)c + 0x7000000000000000ULL;
             for (int j = 0; j < 6; ++j) C.lambda[j] = l;
             cand.push_back(C);
-            owner.push_back(i);
-            lam.push_back(l);
         }
-    }
-    if (cand.empty()) return QMC_OK;
-    qmc_plan *plan = nullptr;
-    int rc = qmc_plan_create(ctx, cand.data(), (int)cand.size(), lo, norders, &plan);
-    if (rc) return rc;
-    std::vector<double> out(qmc_plan_output_size(plan));
-    std::vector<uint32_t> fails(cand.size(), 0);
-    rc = qmc_plan_run(plan, nullptr, nullptr);
-    if (!rc) {
-        rc = qmc_plan_results(plan, out.data(), nullptr);
-        if (rc == QMC_E_SIGN_CHECK) rc = QMC_OK;
-    }
-    if (!rc) rc = qmc_plan_job_failures(plan, fails.data());
-    qmc_plan_destroy(plan);
-    if (rc) return rc;
-    // choose per job: the largest candidate with no sign-check failure (the
-    // spread between the two shifts is far too noisy to rank candidates by)
-    bool all_found = true;
-    for (int i = 0; i < njobs; ++i) {
-        double best_l = -1.0, smallest = INFINITY;
-        bool any = false;
-        for (size_t c = 0; c < cand.size(); ++c) {
-            if (owner[c] != i) continue;
-            any = true;
-            smallest = std::min(smallest, lam[c]);
-            if (fails[c]) continue;
-            const double *q = &out[c * (size_t)m_pre * norders * 2];
-            bool finite = true;
-            for (int k = 0; k < m_pre * norders * 2; ++k) finite &= std::isfinite(q[k]);
-            if (finite && lam[c] > best_l) best_l = lam[c];
+        qmc_plan *plan = nullptr;
+        int rc = qmc_plan_create(ctx, cand.data(), (int)cand.size(), lo, norders, &plan);
+        if (rc) return rc;
+        std::vector<double> out(qmc_plan_output_size(plan));
+        std::vector<uint32_t> fails(cand.size(), 0);
+        rc = qmc_plan_run(plan, nullptr, nullptr);
+        if (!rc) {
+            rc = qmc_plan_results(plan, out.data(), nullptr);
+            if (rc == QMC_E_SIGN_CHECK || rc == QMC_E_NONFINITE) rc = QMC_OK;
         }
-        if (!any) continue;
-        if (best_l < 0) {
-            all_found = false;
-            best_l = smallest;
+        if (!rc) rc = qmc_plan_job_failures(plan, fails.data());
+        qmc_plan_destroy(plan);
+        if (rc) return rc;
+        std::vector<int> still;
+        for (size_t k = 0; k < cand.size(); ++k) {
+            bool ok = fails[k] == 0;
+            const double *q = &out[k * (size_t)m_pre * norders * 2];
+            for (int u = 0; u < m_pre * norders * 2; ++u) ok &= std::isfinite(q[u]) != 0;
+            const int i = pending[k];
+            for (int j = 0; j < 6; ++j) jobs[i].lambda[j] = l;   // the last tried stays if none passes
+            if (!ok) still.push_back(i);
         }
-        for (int j = 0; j < 6; ++j) jobs[i].lambda[j] = best_l;
+        pending.swap(still);
     }
-    if (!all_found)
-        return fail(ctx, QMC_E_SIGN_CHECK, "qmc_presample_lambda: some jobs fail the sign check for every candidate");
+    if (!pending.empty())
+        return fail(ctx, QMC_E_SIGN_CHECK, "qmc_presample_lambda: %zu jobs fail the sign check for every candidate",
+                    pending.size());
     return QMC_OK;
 }
 

@@ -129,7 +129,7 @@ def lib():
                 "qmc_integrate": ([vp, P(qmc_sum_spec), dbl, dbl, dbl, i32, i32, P(qmc_c64), P(qmc_c64),
                                    P(qmc_integrate_info)], i32),
                 "qmc_integrate_ex": ([vp, P(qmc_sum_spec), dbl, dbl, dbl, i32, i32, P(qmc_c64), P(qmc_c64),
-                                      P(qmc_integrate_info), P(u64), i32, P(dbl), P(u64)], i32),
+                                      P(qmc_integrate_info), P(u64), i32, P(dbl), P(u64), P(dbl)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -483,7 +483,7 @@ def qmc_allocate(W, tau, V, alpha=2.0, n_min=0.0):
 
 def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, epsabs=0.0, timeout=0.0,
                   lowest_order=0, norders=1, npoints=1, namp=1, check=True, n_init=None, shifts=0,
-                  nslots=0):
+                  nslots=0, lambda_io=None):
     """Adaptive integration; returns (value, error, info dict, return code), and with
     ``nslots`` > 0 also (w_out, n_out) per (point, integral, sector) slot.
     value/error: complex [npoints][namp][norders] (error = sigma_re + 1j sigma_im)."""
@@ -516,7 +516,8 @@ def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, eps
                                 error.ctypes.data_as(P(qmc_c64)), ctypes.byref(info),
                                 ni.ctypes.data_as(P(ctypes.c_uint64)) if ni is not None else None, shifts,
                                 _dp(w_out) if nslots else None,
-                                n_out.ctypes.data_as(P(ctypes.c_uint64)) if nslots else None)
+                                n_out.ctypes.data_as(P(ctypes.c_uint64)) if nslots else None,
+                                _dp(lambda_io) if lambda_io is not None else None)
     if check and rc not in (0,):
         _check(ctx, rc)
     d = {k: getattr(info, k) for k, _ in qmc_integrate_info._fields_}

@@ -88,7 +88,10 @@ def run_plain(P: Problem, epsrel: float, sel=None):
 
 
 def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION_FP64, n_init=None,
-                shifts=0, want_slots=False, max_points=0, min_points=10000):
+                shifts=0, want_slots=False, max_points=0, min_points=10000, lambdas=None):
+    """All points of `sel` in one adaptive qmc_integrate_ex. `lambdas` (float64
+    [len(sel) * nslot], in/out) carries the deformation parameters: positive
+    entries are used, the rest presampled and written back."""
     sel = np.arange(len(P.points)) if sel is None else np.asarray(sel)
     ctx, ids = P.context(precision, max_points=max_points, min_points=min_points)
     t0 = time.perf_counter()
@@ -96,7 +99,7 @@ def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION
         qmc.qmc_set_kinematics(ctx, P.points[sel])
         res = qmc.qmc_integrate(ctx, ids, coef=P.coef(sel), epsrel=epsrel, lowest_order=LO, norders=NORD,
                                 npoints=len(sel), check=False, n_init=n_init, shifts=shifts,
-                                nslots=len(sel) * P.nslot if want_slots else 0)
+                                nslots=len(sel) * P.nslot if want_slots else 0, lambda_io=lambdas)
     finally:
         qmc.qmc_destroy(ctx)
     out = dict(seconds=time.perf_counter() - t0, values=res[0][:, 0], errors=res[1][:, 0],
@@ -153,8 +156,9 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     w_pred = np.exp(pred[:, :P.nslot])
     a_pred = pred[:, P.nslot:P.nslot + NORD] + 1j * pred[:, P.nslot + NORD:]
     # 3. spot check: one small-lattice pass for every remaining point
+    lam_rest = np.zeros(len(rest) * P.nslot)      # presampled once, reused by the sized run
     sp = run_batched(P, 1e9, rest, precision, n_init=np.full(len(rest) * P.nslot, spot_n), shifts=spot_shifts,
-                     min_points=spot_n)
+                     min_points=spot_n, lambdas=lam_rest)
     _log(f"spot check: {sp['seconds']:.2f} s, {sp['evaluations']:.3g} evals")
     target = epsrel * np.abs(sp["values"]).max(axis=1, keepdims=True)
     sig = np.abs(sp["errors"])
@@ -177,8 +181,9 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
             n_init[k] = qmc.qmc_allocate(W, np.ones(P.nslot), V, 2.0, float(spot_n))
         n_init = np.minimum(n_init, max_points)
         _log(f"sized lattices: quartiles {np.percentile(n_init, [50, 90, 99, 100]).tolist()}")
+        lam_todo = lam_rest.reshape(len(rest), P.nslot)[~accept].ravel().copy()
         run = run_batched(P, epsrel, todo, precision, n_init=n_init.ravel(), shifts=shifts, min_points=spot_n,
-                          max_points=max_points)
+                          max_points=max_points, lambdas=lam_todo)
         _log(f"sized QMC: {run['seconds']:.2f} s, {run['evaluations']:.3g} evals, rc {run['rc']}, "
              f"{run['iterations']} passes")
         res_vals[todo], res_errs[todo] = run["values"], run["errors"]
