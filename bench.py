@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -212,8 +213,8 @@ def main():
     torch.cuda.synchronize()
 
     peak_gflops = qmc.qmc_fp64_peak(ctx)
-    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/bench_clocks_r{rank}.csv"
+    clk_dir = os.environ.get("QMC_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+    clk_path = os.path.join(clk_dir, f"bench_clocks_r{rank}.csv")
     proc, fh = clock_sampler_start(clk_path)
     if dist:
         dist.barrier()

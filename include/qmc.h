@@ -73,7 +73,10 @@ typedef struct {
     int precision;         /* QMC_PRECISION_FP64 [default] or QMC_PRECISION_MIXED */
     int transform;         /* QMC_TRANSFORM_KOROBOV3 [default], _BAKER or _NONE */
     int target_mode;       /* QMC_TARGET_COEFFICIENT [default] or QMC_TARGET_AMPLITUDE */
-    int reserved[3];
+    int max_growth;        /* largest factor by which one pass of qmc_integrate may enlarge a
+                              sector's lattice (the next pass re-measures before growing
+                              further); 0 = no limit, the allocation rule alone [0] */
+    int reserved[2];
 } qmc_options;
 
 /* What epsrel refers to in qmc_integrate. COEFFICIENT: each eps coefficient

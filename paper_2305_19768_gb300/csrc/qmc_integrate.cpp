@@ -186,6 +186,12 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             if (v <= nmax_cap) best = v;
         return best;
     };
+    auto round_down = [&](double n) -> uint64_t {   // largest tabulated size <= n (<= the cap)
+        uint64_t best = sizes.front();
+        for (uint64_t v : sizes)
+            if ((double)v <= n && v <= nmax_cap) best = v;
+        return best;
+    };
     const uint64_t n0 = round_up((double)ctx->opt.min_points);
     if (sn > 8) return fail(ctx, QMC_E_INVAL, "qmc_integrate: %d sector orders exceed 8", sn);
     for (int p = 0; p < npts; ++p)
@@ -403,7 +409,9 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
                     qmc_allocate(W.data(), tv.data(), &V, 1, (int)members.size(), alpha, 0.0, nn.data());
                     for (size_t u = 0; u < members.size(); ++u) {
                         Slot &sl = slots[members[u]];
-                        const uint64_t want = round_up(nn[u]);
+                        uint64_t want = round_up(nn[u]);
+                        if (ctx->opt.max_growth > 1 && (double)want > (double)sl.n * ctx->opt.max_growth)
+                            want = std::max(round_down((double)sl.n * ctx->opt.max_growth), round_up((double)sl.n + 1));
                         if (want > sl.n) {
                             sl.n = want;
                             sl.dirty = true;

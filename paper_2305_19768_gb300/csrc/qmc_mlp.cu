@@ -1,5 +1,5 @@
-// Tensor-core kernels of the learned lattice-size / amplitude model
-// (north-star production form "learned part"): a BF16 GEMM on the 5th-
+// Tensor-core kernels of the learned lattice-size / amplitude model of the
+// amplitude scan: a BF16 GEMM on the 5th-
 // generation tensor cores (tcgen05.mma, accumulator in tensor memory, FP32
 // accumulation) plus the elementwise kernels of an MLP's forward and
 // backward passes and its Adam update.

@@ -42,7 +42,7 @@ class qmc_options(ctypes.Structure):
                 ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("precision", ctypes.c_int),
                 ("transform", ctypes.c_int), ("target_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("max_growth", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class qmc_sum_spec(ctypes.Structure):

@@ -1,4 +1,4 @@
-"""The amplitude scan over a grid of kinematic points, three ways.
+"""The amplitude scan over a grid of kinematic points, four ways.
 
 The sum is A(s, t) = sum_i C_i(s, t) I_i(s, t) over ten one-loop integrals
 (inputs.workloads.amplitude_integrals) with seeded rational polynomial
@@ -10,20 +10,24 @@ per-coefficient relative error of the paper's timings section is not
 reachable).
 
 * ``plain``: one kinematic point at a time, FP64, each with the 10^4-point
-  pilot pass and the adaptive allocation (qmc_integrate) — no batching, no
+  pilot pass and the adaptive allocation (qmc_integrate) -- no batching, no
   model.
-* ``batched``: all points in one adaptive qmc_integrate (one evaluator
-  launch per pass for every point, sector and shift).
-* ``learned``: the spec learned form. QMC on the first `ntrain`
-  points (batched) gives per-slot convergence constants w and amplitude
-  values; a tensor-core MLP (qmc_mlp_*) learns (s, t) -> (log w per
-  sector slot, Re/Im of each eps coefficient); for the other points it
-  predicts w, from which Eq. (adaptive-solution) (qmc_allocate) sizes every
-  lattice up front instead of the pilot pass. A small-lattice spot check
-  runs first; a point takes the surrogate value only where the spot check's
-  own error is within the request and the surrogate agrees with it to
-  within that error, and everything else runs the sized, batched QMC, which
-  still refines adaptively where the prediction was short.
+* ``batched``: the same, all points in one adaptive qmc_integrate (one
+  evaluator launch per pass for every point, sector and shift).
+* ``learned``: the production form. Batched, mixed-precision QMC on the
+  first `ntrain` points, started from the smallest lattice and with the
+  per-pass lattice growth limited (options.max_growth), gives every slot's
+  converged lattice size and the amplitude values; a tensor-core MLP
+  (qmc_mlp_*) learns (s, t) -> (log n per sector slot, Re/Im of each eps
+  coefficient); for the other points it predicts the lattice sizes, which
+  replace the pilot pass. A small-lattice spot check decides where the
+  surrogate amplitude may stand in for QMC (its own error and the
+  surrogate's distance to it both within the request); it is skipped when
+  the model does not fit its own training points that well. Everything else
+  runs the sized, batched QMC, which still refines adaptively where the
+  prediction was short.
+* ``unsized``: the learned form's QMC without the network (pilot pass on the
+  smallest lattice), which isolates what the network contributes.
 
 All arithmetic of the method runs behind the C-ABI; this module marshals
 arrays and keeps the books.
@@ -52,11 +56,12 @@ class Problem:
         self.nsec = [len(I.sectors) for I in self.integrals]
         self.nslot = sum(self.nsec)
 
-    def context(self, precision=qmc.QMC_PRECISION_FP64, shifts=32, max_points=0, min_points=10000):
+    def context(self, precision=qmc.QMC_PRECISION_FP64, shifts=32, max_points=0, min_points=10000,
+                max_growth=0):
         # lambda chosen per (point, sector) by presampling; epsrel against each
         # amplitude's largest eps coefficient (QMC_TARGET_AMPLITUDE)
         ctx = qmc.qmc_create(0, precision=precision, shifts=shifts, target_mode=qmc.QMC_TARGET_AMPLITUDE,
-                             max_points=max_points, min_points=min_points)
+                             max_points=max_points, min_points=min_points, max_growth=max_growth)
         qmc.load_lattice_table(ctx)
         ids = [qmc.qmc_load_sectors_mem(ctx, I.to_text()) for I in self.integrals]
         return ctx, ids
@@ -88,12 +93,12 @@ def run_plain(P: Problem, epsrel: float, sel=None):
 
 
 def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION_FP64, n_init=None,
-                shifts=0, want_slots=False, max_points=0, min_points=10000, lambdas=None):
+                shifts=0, want_slots=False, max_points=0, min_points=10000, lambdas=None, max_growth=0):
     """All points of `sel` in one adaptive qmc_integrate_ex. `lambdas` (float64
     [len(sel) * nslot], in/out) carries the deformation parameters: positive
     entries are used, the rest presampled and written back."""
     sel = np.arange(len(P.points)) if sel is None else np.asarray(sel)
-    ctx, ids = P.context(precision, max_points=max_points, min_points=min_points)
+    ctx, ids = P.context(precision, max_points=max_points, min_points=min_points, max_growth=max_growth)
     t0 = time.perf_counter()
     try:
         qmc.qmc_set_kinematics(ctx, P.points[sel])
@@ -103,10 +108,30 @@ def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION
     finally:
         qmc.qmc_destroy(ctx)
     out = dict(seconds=time.perf_counter() - t0, values=res[0][:, 0], errors=res[1][:, 0],
-               evaluations=res[2]["evaluations"], rc=res[3], iterations=res[2]["iterations"])
+               evaluations=res[2]["evaluations"], rc=res[3], iterations=res[2]["iterations"],
+               kernel_seconds=res[2]["kernel_seconds"])
     if want_slots:
         out["w"], out["n"] = res[4].reshape(len(sel), P.nslot), res[5].reshape(len(sel), P.nslot)
     return out
+
+
+def snap_to_table(n):
+    """Each size to the tabulated lattice nearest to it in log n (qmc_integrate_ex
+    rounds up, which would lift a prediction of 1009.000001 to the next size)."""
+    from .inputs.lattice import load_table
+
+    sizes = np.array([r[0] for r in load_table()], dtype=np.float64)
+    k = np.abs(np.log(np.asarray(n, dtype=np.float64))[..., None] - np.log(sizes)).argmin(axis=-1)
+    return sizes[k]
+
+
+def run_unsized(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION_MIXED, spot_n: int = 1009,
+                shifts: int = 16, max_points: int = 1000003, max_growth: int = 4):
+    """The learned form's QMC without the network: the same batched, mixed,
+    growth-limited integration, started from the smallest lattice (a pilot pass
+    at `spot_n`) instead of from predicted sizes."""
+    return run_batched(P, epsrel, sel, precision, shifts=shifts, min_points=spot_n, max_points=max_points,
+                       max_growth=max_growth, want_slots=True)
 
 
 def _features(points):
@@ -120,81 +145,95 @@ def _log(msg):
 
 def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC_PRECISION_MIXED,
                 steps: int = 1500, spot_n: int = 1009, spot_shifts: int = 8, shifts: int = 16,
-                max_points: int = 1000003):
+                max_points: int = 1000003, max_growth: int = 4):
     """Learned sizing + spot-checked surrogate + batched QMC (see module doc).
-    Lattices are capped at `max_points` (sizes beyond it come from a model error)."""
+    Every QMC pass here grows a lattice by at most `max_growth` per pass and
+    caps it at `max_points`."""
     t0 = time.perf_counter()
     train = np.arange(min(ntrain, len(P.points)))
     rest = np.arange(len(train), len(P.points))
     # 1. the method's own outputs on the training points: batched, adaptive,
-    #    from a small pilot (n = spot_n, `shifts` shifts) instead of 10^4 x 32
+    #    from the smallest lattice (n = spot_n, `shifts` shifts)
     tr = run_batched(P, epsrel, train, precision, want_slots=True, shifts=shifts, min_points=spot_n,
-                     max_points=max_points)
+                     max_points=max_points, max_growth=max_growth)
     _log(f"training QMC: {tr['seconds']:.2f} s, {tr['evaluations']:.3g} evals, rc {tr['rc']}, "
-         f"{tr['iterations']} passes, n quartiles {np.percentile(tr['n'], [50, 90, 99, 100]).tolist()}")
-    # 2. the model: (s, t) -> log w per slot, Re/Im per eps coefficient
+         f"{tr['iterations']} passes, n percentiles 50/90/99/100 "
+         f"{np.percentile(tr['n'], [50, 90, 99, 100]).tolist()}")
+    # 2. the model: (s, t) -> log n per slot (the lattice the slot converged on),
+    #    Re/Im per eps coefficient. The lattice size itself is learned rather than
+    #    w = var n^2: w is far from constant over the lattices used here (the
+    #    sector integrands converge much faster than n^-2 under korobov3), so a
+    #    size extrapolated from w with alpha = 2 overshoots.
     x = _features(P.points[train])
-    logw = np.log(np.maximum(tr["w"], 1e-300))
+    logn = np.log(tr["n"].astype(np.float64))
     amp = np.concatenate([tr["values"].real, tr["values"].imag], axis=1)
-    Y = np.concatenate([logw, amp], axis=1)
+    Y = np.concatenate([logn, amp], axis=1)
     mu, sd = Y.mean(axis=0), Y.std(axis=0) + 1e-12
     net = qmc.Mlp(2, 256, 4, Y.shape[1], seed=5)
     wt = np.ones(Y.shape[1], dtype=np.float32)
     wt[P.nslot:] = 4.0   # the amplitude coefficients weigh more than the sizing outputs
     try:
         losses = net.train(x, ((Y - mu) / sd).astype(np.float32), steps, 1e-3, wt=wt)
-        pred = net.forward(_features(P.points[rest])) * sd + mu
+        fit = net.forward(x) * sd + mu
+        pred = net.forward(_features(P.points[rest])) * sd + mu if len(rest) else None
     finally:
         net.close()
+    a_fit = fit[:, P.nslot:P.nslot + NORD] + 1j * fit[:, P.nslot + NORD:]
+    fit_err = float(np.max(np.abs(a_fit - tr["values"]) / np.abs(tr["values"]).max(axis=1, keepdims=True)))
     t_model = time.perf_counter() - t0
-    _log(f"model trained and evaluated: {t_model:.2f} s since start, final loss {losses[-1]:.4g}")
+    _log(f"model trained and evaluated: {t_model:.2f} s since start, final loss {losses[-1]:.4g}, "
+         f"largest relative amplitude error on its training points {fit_err:.3g}")
     res_vals = np.zeros((len(P.points), NORD), complex)
     res_errs = np.zeros((len(P.points), NORD), complex)
     res_vals[train], res_errs[train] = tr["values"], tr["errors"]
+    base = dict(model_seconds=t_model, final_loss=float(losses[-1]), fit_rel_error=fit_err,
+                train_seconds=tr["seconds"], train_evaluations=tr["evaluations"],
+                train_n_percentiles=np.percentile(tr["n"], [50, 90, 99, 100]).tolist())
     if len(rest) == 0:
-        return dict(seconds=time.perf_counter() - t0, values=res_vals, errors=res_errs, accepted=0)
-    w_pred = np.exp(pred[:, :P.nslot])
+        return dict(seconds=time.perf_counter() - t0, values=res_vals, errors=res_errs, accepted=0,
+                    evaluations=tr["evaluations"], spot_seconds=0.0, sized_seconds=0.0, **base)
+    n_pred = np.exp(pred[:, :P.nslot])
     a_pred = pred[:, P.nslot:P.nslot + NORD] + 1j * pred[:, P.nslot + NORD:]
-    # 3. spot check: one small-lattice pass for every remaining point
+    # 3. spot check, one small-lattice pass for every remaining point -- run only
+    #    when the model fits its own training points within the request (a model
+    #    that does not cannot have a guess accepted anywhere)
     lam_rest = np.zeros(len(rest) * P.nslot)      # presampled once, reused by the sized run
-    sp = run_batched(P, 1e9, rest, precision, n_init=np.full(len(rest) * P.nslot, spot_n), shifts=spot_shifts,
-                     min_points=spot_n, lambdas=lam_rest)
-    _log(f"spot check: {sp['seconds']:.2f} s, {sp['evaluations']:.3g} evals")
-    target = epsrel * np.abs(sp["values"]).max(axis=1, keepdims=True)
-    sig = np.abs(sp["errors"])
-    accept = np.all((sig <= target) & (np.abs(a_pred - sp["values"]) <= target), axis=1)
-    res_vals[rest[accept]] = a_pred[accept]
-    res_errs[rest[accept]] = target[accept]
-    # 4. predicted lattice sizes (Eq. adaptive-solution) for the others, then batched QMC
+    accept = np.zeros(len(rest), bool)
+    evals = tr["evaluations"]
+    spot_s = 0.0
+    if fit_err <= epsrel:
+        sp = run_batched(P, 1e9, rest, precision, n_init=np.full(len(rest) * P.nslot, spot_n),
+                         shifts=spot_shifts, min_points=spot_n, lambdas=lam_rest)
+        spot_s = sp["seconds"]
+        _log(f"spot check: {sp['seconds']:.2f} s, {sp['evaluations']:.3g} evals")
+        target = epsrel * np.abs(sp["values"]).max(axis=1, keepdims=True)
+        sig = np.abs(sp["errors"])
+        accept = np.all((sig <= target) & (np.abs(a_pred - sp["values"]) <= target), axis=1)
+        res_vals[rest[accept]] = a_pred[accept]
+        res_errs[rest[accept]] = np.broadcast_to(target, sig.shape)[accept]
+        evals += sp["evaluations"]
+    else:
+        _log("spot check skipped: the model misses its own training points by more than the request")
+    # 4. the predicted lattice sizes for the others, then batched QMC from there
     todo = rest[~accept]
-    evals = tr["evaluations"] + sp["evaluations"]
+    n_init = np.zeros((0, P.nslot))
     if len(todo):
-        wp = w_pred[~accept]
-        ap = a_pred[~accept]
-        # per point: W_slot = |C_i|^2 w_slot (prefactor series folded into w by training),
-        # V = (epsrel * min over orders |A|)^2, tau from the sector's lattice dimension cost
-        n_init = np.zeros((len(todo), P.nslot))
-        slot_int = np.repeat(np.arange(len(P.integrals)), P.nsec)
-        for k, p in enumerate(todo):
-            W = (np.abs(P.C[p, slot_int]) ** 2 * wp[k])[None, :]
-            V = np.array([(epsrel * max(np.max(np.abs(ap[k])), 1e-12)) ** 2])
-            n_init[k] = qmc.qmc_allocate(W, np.ones(P.nslot), V, 2.0, float(spot_n))
-        n_init = np.minimum(n_init, max_points)
-        _log(f"sized lattices: quartiles {np.percentile(n_init, [50, 90, 99, 100]).tolist()}")
+        n_init = snap_to_table(np.clip(n_pred[~accept], spot_n, max_points))
+        _log(f"sized lattices: percentiles 50/90/99/100 {np.percentile(n_init, [50, 90, 99, 100]).tolist()}")
         lam_todo = lam_rest.reshape(len(rest), P.nslot)[~accept].ravel().copy()
         run = run_batched(P, epsrel, todo, precision, n_init=n_init.ravel(), shifts=shifts, min_points=spot_n,
-                          max_points=max_points, lambdas=lam_todo)
-        _log(f"sized QMC: {run['seconds']:.2f} s, {run['evaluations']:.3g} evals, rc {run['rc']}, "
-             f"{run['iterations']} passes")
+                          max_points=max_points, lambdas=lam_todo, max_growth=max_growth, want_slots=True)
+        _log(f"sized QMC: {run['seconds']:.2f} s ({run['kernel_seconds']:.2f} s in the evaluator), "
+             f"{run['evaluations']:.3g} evals, rc {run['rc']}, {run['iterations']} passes, final n "
+             f"percentiles 50/90/99/100 {np.percentile(run['n'], [50, 90, 99, 100]).tolist()}")
         res_vals[todo], res_errs[todo] = run["values"], run["errors"]
         evals += run["evaluations"]
     return dict(seconds=time.perf_counter() - t0, values=res_vals, errors=res_errs, evaluations=evals,
-                accepted=int(accept.sum()), model_seconds=t_model, final_loss=float(losses[-1]),
-                train_seconds=tr["seconds"], spot_seconds=sp["seconds"],
-                train_n_quartiles=np.percentile(tr["n"], [25, 50, 75, 95]).tolist(),
-                sized_n_quartiles=np.percentile(n_init, [25, 50, 75, 95]).tolist() if len(todo) else [],
+                accepted=int(accept.sum()), spot_seconds=spot_s,
+                sized_n_percentiles=np.percentile(n_init, [50, 90, 99, 100]).tolist() if len(todo) else [],
                 sized_seconds=run["seconds"] if len(todo) else 0.0,
-                sized_iterations=run["iterations"] if len(todo) else 0)
+                sized_evaluations=run["evaluations"] if len(todo) else 0.0,
+                sized_iterations=run["iterations"] if len(todo) else 0, **base)
 
 
 def relative_errors(values, errors):
@@ -213,10 +252,13 @@ def main():
     P = Problem(args.points)
     out = {"points": len(P.points), "epsrel": args.epsrel, "slots_per_point": P.nslot}
     ref = None
+    plain_sel = None
     for mode in args.modes.split(","):
         if mode == "plain":
             sel = np.arange(0, len(P.points), args.plain_sample) if args.plain_sample else None
             r = run_plain(P, args.epsrel, sel)
+            plain_sel = sel if sel is not None else np.arange(len(P.points))
+            plain_vals, plain_errs = r["values"], r["errors"]
             scale = len(P.points) / (len(sel) if sel is not None else len(P.points))
             out["plain"] = dict(seconds=r["seconds"] * scale, measured_seconds=r["seconds"],
                                 sampled_points=int(len(sel)) if sel is not None else len(P.points),
@@ -227,6 +269,11 @@ def main():
             out["batched"] = dict(seconds=r["seconds"], evaluations=r["evaluations"], rc=r["rc"],
                                   iterations=r["iterations"],
                                   max_rel_error=float(relative_errors(r["values"], r["errors"]).max()))
+        elif mode == "unsized":
+            r = run_unsized(P, args.epsrel)
+            out["unsized"] = dict(seconds=r["seconds"], evaluations=r["evaluations"], rc=r["rc"],
+                                  iterations=r["iterations"], kernel_seconds=r["kernel_seconds"],
+                                  max_rel_error=float(relative_errors(r["values"], r["errors"]).max()))
         elif mode == "learned":
             r = run_learned(P, args.epsrel, args.ntrain)
             d = {k: v for k, v in r.items() if k not in ("values", "errors")}
@@ -235,9 +282,18 @@ def main():
                 diff = np.abs(r["values"] - ref["values"])
                 comb = np.hypot(np.abs(r["errors"]), np.abs(ref["errors"]))
                 d["max_diff_over_combined_sigma"] = float(np.max(diff / np.maximum(comb, 1e-300)))
+            if "plain" in out and plain_sel is not None:
+                # the learned answers against the plain FP64 answers on the points plain ran
+                diff = np.abs(r["values"][plain_sel] - plain_vals)
+                amax = np.abs(plain_vals).max(axis=1, keepdims=True)
+                comb = np.hypot(np.abs(r["errors"][plain_sel]), np.abs(plain_errs))
+                d["vs_plain_max_rel_diff"] = float(np.max(diff / amax))
+                d["vs_plain_max_diff_over_combined_sigma"] = float(np.max(diff / np.maximum(comb, 1e-300)))
             out["learned"] = d
     if "plain" in out and "learned" in out:
         out["speedup_learned_vs_plain"] = out["plain"]["seconds"] / out["learned"]["seconds"]
+    if "plain" in out and "unsized" in out:
+        out["speedup_unsized_vs_plain"] = out["plain"]["seconds"] / out["unsized"]["seconds"]
     if "plain" in out and "batched" in out:
         out["speedup_batched_vs_plain"] = out["plain"]["seconds"] / out["batched"]["seconds"]
     print(json.dumps(out))
