@@ -167,6 +167,7 @@ def main():
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-scan", action="store_true", help="skip the amplitude-scan comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -300,6 +301,22 @@ def main():
         extra["mixed_max_abs_diff_vs_fp64"] = float(np.max(np.abs(out_m - ref)))
         qmc.qmc_plan_destroy(plan_m)
         qmc.qmc_destroy(ctxm)
+
+    # the amplitude scan (time to 1e-4 relative amplitude error on the 10^4-point
+    # (s, t) grid of a ten-integral amplitude): the learned, batched,
+    # mixed-precision form against the plain FP64 method (timed on every 50th
+    # point and scaled to the grid) and against the same QMC without the network
+    if not args.no_extra and not args.no_scan and world == 1:
+        from paper_2305_19768_gb300 import scan
+
+        sc = scan.compare(10000, 1e-4, "plain,unsized,learned", 2000, plain_sample=50)
+        keep = ("seconds", "evaluations", "presample_evaluations", "max_rel_error", "rc", "iterations",
+                "sampled_points", "accepted", "train_seconds", "model_seconds", "sized_seconds",
+                "fit_rel_error", "vs_plain_max_rel_diff", "vs_plain_max_diff_over_combined_sigma")
+        extra["amplitude_scan"] = {
+            "grid": "100 x 100 (s, t), s in [5, 20], t in [-8, -1]; 10 one-loop integrals, 36 sectors",
+            **{k: v for k, v in sc.items() if k.startswith("speedup")},
+            **{m: {k: v for k, v in sc[m].items() if k in keep} for m in ("plain", "unsized", "learned")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -327,6 +327,7 @@ typedef struct {
     double kernel_seconds;  /* device time of the evaluator kernels */
     int iterations;         /* evaluation passes */
     uint64_t max_lattice;   /* largest lattice any sector reached */
+    double presample_evaluations;   /* lattice points x shifts of the lambda presampling */
 } qmc_integrate_info;
 
 /* Adaptive integration of the sums (section "Adaptive weighted sum
@@ -338,8 +339,12 @@ typedef struct {
  * sqrt(dR^2 + dI^2) <= max(epsrel |A|, epsabs), and otherwise re-sizes the
  * lattices with qmc_allocate (alpha = 2, w_i = var_i n_i^2, tau_i from the
  * measured kernel time split by a per-sector cost model), rounding up to
- * tabulated lattices (<= max_points). Deformed sectors use options.lambda,
- * or, when it is 0, a lambda per (point, sector) chosen once by presampling.
+ * tabulated lattices (<= max_points; options.max_growth limits the growth
+ * per pass). Deformed sectors use options.lambda, or, when it is 0, a lambda
+ * per (point, sector) chosen once by presampling; a sector whose evaluation
+ * fails the sign check (a point with Im F > 0) is presampled again with
+ * candidates below its lambda and evaluated again (at most 8 such rounds,
+ * after which the call returns QMC_E_SIGN_CHECK with the results it has).
  * Outputs (host, caller-owned): value[npoints][namp][norders] for orders
  * lowest_order.., error[..] with re = sigma of Re, im = sigma of Im.
  * Returns QMC_E_TIMEOUT (timeout_s > 0 exceeded), QMC_E_NOT_CONVERGED

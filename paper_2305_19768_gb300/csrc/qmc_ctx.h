@@ -59,6 +59,7 @@ struct qmc_ctx {
     std::vector<qmc_plan *> plans;
     int tuned_block[QMC_NCLASS] = {};   // autotuned launch shape per kernel class (0 = default)
     int tuned_ppt[QMC_NCLASS] = {};
+    double presample_evals = 0.0;       // lattice points x shifts spent in qmc_presample_lambda
 };
 
 struct ClassLaunch {

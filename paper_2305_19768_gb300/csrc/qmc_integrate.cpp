@@ -114,6 +114,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
     const auto t_start = clk::now();
     if (!ctx || !value || !error || norders < 1 || norders > 16 || !(epsrel >= 0) || !(epsabs >= 0))
         return fail(ctx, QMC_E_INVAL, "qmc_integrate: bad arguments");
+    const double presample_evals0 = ctx->presample_evals;
     if (ctx->lattices.empty()) return fail(ctx, QMC_E_INVAL, "qmc_integrate: no lattice table");
     // --- what to sum
     std::vector<int> ids;
@@ -252,6 +253,8 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
     std::vector<double> tau(slots.size(), 1.0);
     std::vector<double> amp_val((size_t)npts * namp * norders * 2), amp_var((size_t)npts * namp * norders);
     std::vector<double> amp_vre((size_t)npts * namp * norders), amp_vim((size_t)npts * namp * norders);
+    std::vector<size_t> resample;   // slots to presample again after a sign-check failure
+    int resample_rounds = 0;
     for (;;) {
         // ---- evaluate dirty slots in one plan
         std::vector<qmc_job> jobs;
@@ -285,7 +288,18 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
                 qmc_plan_destroy(plan);
                 return rc;
             }
-            if (rc == QMC_E_SIGN_CHECK) rc_final = QMC_E_SIGN_CHECK;
+            if (rc == QMC_E_SIGN_CHECK) {
+                // a deformed slot whose contour crossed to Im F > 0 on this lattice:
+                // presample again below its lambda and evaluate it once more
+                std::vector<uint32_t> fails(jobs.size(), 0);
+                rc = qmc_plan_job_failures(plan, fails.data());
+                if (rc) {
+                    qmc_plan_destroy(plan);
+                    return rc;
+                }
+                for (size_t j = 0; j < jobs.size(); ++j)
+                    if (fails[j]) resample.push_back(jslot[j]);
+            }
             // per-class time per evaluation -> tau of each slot (cost-weighted)
             for (size_t c = 0; c < plan->launches.size(); ++c) {
                 float ms = 0.f;
@@ -317,6 +331,37 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             }
         }
         ++iter;
+        if (!resample.empty() && ++resample_rounds > 8) {
+            rc_final = QMC_E_SIGN_CHECK;   // lambda keeps failing: keep the results, report it
+            resample.clear();
+        }
+        if (!resample.empty()) {
+            std::vector<qmc_job> pre;
+            for (size_t q : resample) {
+                const Slot &sl = slots[q];
+                qmc_job J;
+                memset(&J, 0, sizeof J);
+                J.integral_id = ids[sl.i];
+                J.sector = sl.s;
+                J.point = ctx->integrals[ids[sl.i]].invariants.empty() ? 0 : sl.p;
+                J.seed = ctx->opt.seed;
+                J.stream = ((uint64_t)iter << 40) | q;
+                pre.push_back(J);
+            }
+            // candidates below the smallest failing lambda (all failing slots in one search)
+            double lmax = 1.0;   // (a failing lambda <= 0 restarts from 1)
+            for (size_t q : resample)
+                if (slots[q].lambda > 0) lmax = std::min(lmax, 0.7 * slots[q].lambda);
+            const int prc = qmc_presample_lambda(ctx, pre.data(), (int)pre.size(), slo, sn, lmax, 16);
+            if (prc && prc != QMC_E_SIGN_CHECK) return prc;
+            for (size_t u = 0; u < resample.size(); ++u) {
+                Slot &sl = slots[resample[u]];
+                sl.lambda = pre[u].lambda[0];   // the largest passing candidate, else the smallest tried
+                sl.dirty = true;
+            }
+            resample.clear();
+            if (std::any_of(slots.begin(), slots.end(), [](const Slot &s) { return s.dirty; })) continue;
+        }
         // ---- combine into the sums and check the requested accuracy
         bool all_ok = true;
         std::vector<char> sum_ok((size_t)npts * namp * norders, 1);
@@ -449,6 +494,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
         uint64_t mx = 0;
         for (const Slot &sl : slots) mx = std::max(mx, sl.n);
         info->max_lattice = mx;
+        info->presample_evaluations = ctx->presample_evals - presample_evals0;
     }
     if (rc_final == QMC_E_TIMEOUT) return fail(ctx, QMC_E_TIMEOUT, "qmc_integrate: timeout after %d iterations", iter);
     if (rc_final == QMC_E_NOT_CONVERGED)
@@ -502,6 +548,7 @@ extern "C" int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int 
         qmc_plan *plan = nullptr;
         int rc = qmc_plan_create(ctx, cand.data(), (int)cand.size(), lo, norders, &plan);
         if (rc) return rc;
+        ctx->presample_evals += (double)cand.size() * (double)n_pre * m_pre;
         std::vector<double> out(qmc_plan_output_size(plan));
         std::vector<uint32_t> fails(cand.size(), 0);
         rc = qmc_plan_run(plan, nullptr, nullptr);

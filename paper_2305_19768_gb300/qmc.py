@@ -54,7 +54,7 @@ class qmc_sum_spec(ctypes.Structure):
 class qmc_integrate_info(ctypes.Structure):
     _fields_ = [("evaluations", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("kernel_seconds", ctypes.c_double), ("iterations", ctypes.c_int),
-                ("max_lattice", ctypes.c_uint64)]
+                ("max_lattice", ctypes.c_uint64), ("presample_evaluations", ctypes.c_double)]
 
 
 class qmc_job(ctypes.Structure):

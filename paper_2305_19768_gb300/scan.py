@@ -18,9 +18,11 @@ reachable).
   first `ntrain` points, started from the smallest lattice and with the
   per-pass lattice growth limited (options.max_growth), gives every slot's
   converged lattice size and the amplitude values; a tensor-core MLP
-  (qmc_mlp_*) learns (s, t) -> (log n per sector slot, Re/Im of each eps
-  coefficient); for the other points it predicts the lattice sizes, which
-  replace the pilot pass. A small-lattice spot check decides where the
+  (qmc_mlp_*) learns (s, t) -> (log n per sector slot, log lambda per
+  deformed slot, Re/Im of each eps coefficient); for the other points it
+  predicts the lattice sizes, which replace the pilot pass, and the
+  deformation parameters, which replace the presampling (the QMC's sign
+  check verifies them and presamples where one fails). A small-lattice spot check decides where the
   surrogate amplitude may stand in for QMC (its own error and the
   surrogate's distance to it both within the request); it is skipped when
   the model does not fit its own training points that well. Everything else
@@ -109,9 +111,11 @@ def run_batched(P: Problem, epsrel: float, sel=None, precision=qmc.QMC_PRECISION
         qmc.qmc_destroy(ctx)
     out = dict(seconds=time.perf_counter() - t0, values=res[0][:, 0], errors=res[1][:, 0],
                evaluations=res[2]["evaluations"], rc=res[3], iterations=res[2]["iterations"],
-               kernel_seconds=res[2]["kernel_seconds"])
+               kernel_seconds=res[2]["kernel_seconds"], presample_evaluations=res[2]["presample_evaluations"])
     if want_slots:
         out["w"], out["n"] = res[4].reshape(len(sel), P.nslot), res[5].reshape(len(sel), P.nslot)
+        if lambdas is not None:
+            out["lam"] = np.asarray(lambdas).reshape(len(sel), P.nslot)
     return out
 
 
@@ -155,7 +159,7 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     # 1. the method's own outputs on the training points: batched, adaptive,
     #    from the smallest lattice (n = spot_n, `shifts` shifts)
     tr = run_batched(P, epsrel, train, precision, want_slots=True, shifts=shifts, min_points=spot_n,
-                     max_points=max_points, max_growth=max_growth)
+                     max_points=max_points, max_growth=max_growth, lambdas=np.zeros(len(train) * P.nslot))
     _log(f"training QMC: {tr['seconds']:.2f} s, {tr['evaluations']:.3g} evals, rc {tr['rc']}, "
          f"{tr['iterations']} passes, n percentiles 50/90/99/100 "
          f"{np.percentile(tr['n'], [50, 90, 99, 100]).tolist()}")
@@ -166,19 +170,22 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     #    size extrapolated from w with alpha = 2 overshoots.
     x = _features(P.points[train])
     logn = np.log(tr["n"].astype(np.float64))
+    deformed = tr["lam"][0] > 0                     # slots with a contour deformation
+    loglam = np.log(tr["lam"][:, deformed])
     amp = np.concatenate([tr["values"].real, tr["values"].imag], axis=1)
-    Y = np.concatenate([logn, amp], axis=1)
+    Y = np.concatenate([logn, loglam, amp], axis=1)
+    na = P.nslot + int(deformed.sum())              # first amplitude output
     mu, sd = Y.mean(axis=0), Y.std(axis=0) + 1e-12
     net = qmc.Mlp(2, 256, 4, Y.shape[1], seed=5)
     wt = np.ones(Y.shape[1], dtype=np.float32)
-    wt[P.nslot:] = 4.0   # the amplitude coefficients weigh more than the sizing outputs
+    wt[na:] = 4.0   # the amplitude coefficients weigh more than the sizing outputs
     try:
         losses = net.train(x, ((Y - mu) / sd).astype(np.float32), steps, 1e-3, wt=wt)
         fit = net.forward(x) * sd + mu
         pred = net.forward(_features(P.points[rest])) * sd + mu if len(rest) else None
     finally:
         net.close()
-    a_fit = fit[:, P.nslot:P.nslot + NORD] + 1j * fit[:, P.nslot + NORD:]
+    a_fit = fit[:, na:na + NORD] + 1j * fit[:, na + NORD:]
     fit_err = float(np.max(np.abs(a_fit - tr["values"]) / np.abs(tr["values"]).max(axis=1, keepdims=True)))
     t_model = time.perf_counter() - t0
     _log(f"model trained and evaluated: {t_model:.2f} s since start, final loss {losses[-1]:.4g}, "
@@ -193,11 +200,16 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
         return dict(seconds=time.perf_counter() - t0, values=res_vals, errors=res_errs, accepted=0,
                     evaluations=tr["evaluations"], spot_seconds=0.0, sized_seconds=0.0, **base)
     n_pred = np.exp(pred[:, :P.nslot])
-    a_pred = pred[:, P.nslot:P.nslot + NORD] + 1j * pred[:, P.nslot + NORD:]
+    a_pred = pred[:, na:na + NORD] + 1j * pred[:, na + NORD:]
+    # deformation parameters: the prediction snapped to the presampling grid 0.7^c
+    # (c = 0..15); the QMC's own sign check verifies it and presamples where it fails
+    c = np.clip(np.round(-pred[:, P.nslot:na] / np.log(1 / 0.7)), 0, 15)
+    lam_pred = np.zeros((len(rest), P.nslot))
+    lam_pred[:, deformed] = 0.7 ** c
     # 3. spot check, one small-lattice pass for every remaining point -- run only
     #    when the model fits its own training points within the request (a model
     #    that does not cannot have a guess accepted anywhere)
-    lam_rest = np.zeros(len(rest) * P.nslot)      # presampled once, reused by the sized run
+    lam_rest = lam_pred.ravel().copy()
     accept = np.zeros(len(rest), bool)
     evals = tr["evaluations"]
     spot_s = 0.0
@@ -233,6 +245,7 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
                 sized_n_percentiles=np.percentile(n_init, [50, 90, 99, 100]).tolist() if len(todo) else [],
                 sized_seconds=run["seconds"] if len(todo) else 0.0,
                 sized_evaluations=run["evaluations"] if len(todo) else 0.0,
+                sized_presample_evaluations=run["presample_evaluations"] if len(todo) else 0.0,
                 sized_iterations=run["iterations"] if len(todo) else 0, **base)
 
 
@@ -241,48 +254,47 @@ def relative_errors(values, errors):
     return np.abs(errors) / np.maximum(np.abs(values).max(axis=-1, keepdims=True), 1e-300)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--points", type=int, default=10000)
-    ap.add_argument("--epsrel", type=float, default=1e-4)
-    ap.add_argument("--modes", default="plain,batched,learned")
-    ap.add_argument("--ntrain", type=int, default=2000)
-    ap.add_argument("--plain-sample", type=int, default=0, help="time plain on every k-th point only")
-    args = ap.parse_args()
-    P = Problem(args.points)
-    out = {"points": len(P.points), "epsrel": args.epsrel, "slots_per_point": P.nslot}
+def compare(points: int = 10000, epsrel: float = 1e-4, modes="plain,unsized,learned", ntrain: int = 2000,
+            plain_sample: int = 0):
+    """Run the requested modes on the first `points` grid points and return the
+    timings, evaluation counts and errors (plain may run on every
+    `plain_sample`-th point only; its time is then scaled to the whole grid)."""
+    P = Problem(points)
+    out = {"points": len(P.points), "epsrel": epsrel, "slots_per_point": P.nslot}
     ref = None
     plain_sel = None
-    for mode in args.modes.split(","):
+    for mode in modes.split(",") if isinstance(modes, str) else modes:
         if mode == "plain":
-            sel = np.arange(0, len(P.points), args.plain_sample) if args.plain_sample else None
-            r = run_plain(P, args.epsrel, sel)
+            sel = np.arange(0, len(P.points), plain_sample) if plain_sample else None
+            r = run_plain(P, epsrel, sel)
             plain_sel = sel if sel is not None else np.arange(len(P.points))
             plain_vals, plain_errs = r["values"], r["errors"]
-            scale = len(P.points) / (len(sel) if sel is not None else len(P.points))
+            scale = len(P.points) / len(plain_sel)
             out["plain"] = dict(seconds=r["seconds"] * scale, measured_seconds=r["seconds"],
-                                sampled_points=int(len(sel)) if sel is not None else len(P.points),
-                                evaluations=r["evaluations"] * scale, failures=r["failures"])
+                                sampled_points=int(len(plain_sel)), evaluations=r["evaluations"] * scale,
+                                failures=r["failures"],
+                                max_rel_error=float(relative_errors(r["values"], r["errors"]).max()))
         elif mode == "batched":
-            r = run_batched(P, args.epsrel)
+            r = run_batched(P, epsrel)
             ref = r
             out["batched"] = dict(seconds=r["seconds"], evaluations=r["evaluations"], rc=r["rc"],
                                   iterations=r["iterations"],
                                   max_rel_error=float(relative_errors(r["values"], r["errors"]).max()))
         elif mode == "unsized":
-            r = run_unsized(P, args.epsrel)
+            r = run_unsized(P, epsrel)
             out["unsized"] = dict(seconds=r["seconds"], evaluations=r["evaluations"], rc=r["rc"],
+                                  presample_evaluations=r["presample_evaluations"],
                                   iterations=r["iterations"], kernel_seconds=r["kernel_seconds"],
                                   max_rel_error=float(relative_errors(r["values"], r["errors"]).max()))
         elif mode == "learned":
-            r = run_learned(P, args.epsrel, args.ntrain)
+            r = run_learned(P, epsrel, ntrain)
             d = {k: v for k, v in r.items() if k not in ("values", "errors")}
             d["max_rel_error"] = float(relative_errors(r["values"], r["errors"]).max())
             if ref is not None:
                 diff = np.abs(r["values"] - ref["values"])
                 comb = np.hypot(np.abs(r["errors"]), np.abs(ref["errors"]))
                 d["max_diff_over_combined_sigma"] = float(np.max(diff / np.maximum(comb, 1e-300)))
-            if "plain" in out and plain_sel is not None:
+            if plain_sel is not None:
                 # the learned answers against the plain FP64 answers on the points plain ran
                 diff = np.abs(r["values"][plain_sel] - plain_vals)
                 amax = np.abs(plain_vals).max(axis=1, keepdims=True)
@@ -290,13 +302,21 @@ def main():
                 d["vs_plain_max_rel_diff"] = float(np.max(diff / amax))
                 d["vs_plain_max_diff_over_combined_sigma"] = float(np.max(diff / np.maximum(comb, 1e-300)))
             out["learned"] = d
-    if "plain" in out and "learned" in out:
-        out["speedup_learned_vs_plain"] = out["plain"]["seconds"] / out["learned"]["seconds"]
-    if "plain" in out and "unsized" in out:
-        out["speedup_unsized_vs_plain"] = out["plain"]["seconds"] / out["unsized"]["seconds"]
-    if "plain" in out and "batched" in out:
-        out["speedup_batched_vs_plain"] = out["plain"]["seconds"] / out["batched"]["seconds"]
-    print(json.dumps(out))
+    for mode in ("learned", "unsized", "batched"):
+        if "plain" in out and mode in out:
+            out[f"speedup_{mode}_vs_plain"] = out["plain"]["seconds"] / out[mode]["seconds"]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--points", type=int, default=10000)
+    ap.add_argument("--epsrel", type=float, default=1e-4)
+    ap.add_argument("--modes", default="plain,unsized,learned")
+    ap.add_argument("--ntrain", type=int, default=2000)
+    ap.add_argument("--plain-sample", type=int, default=0, help="time plain on every k-th point only")
+    args = ap.parse_args()
+    print(json.dumps(compare(args.points, args.epsrel, args.modes, args.ntrain, args.plain_sample)))
 
 
 if __name__ == "__main__":

@@ -102,3 +102,28 @@ def test_lattice_limit_and_timeout_statuses():
         assert rc == -4 and info["iterations"] == 1
     finally:
         qmc.qmc_destroy(ctx)
+
+
+def test_sign_check_failure_is_presampled_again():
+    # a deformation parameter of the wrong sign, handed in per slot, puts F(z) on
+    # the wrong side of the cut at every point: the driver must presample that
+    # slot again, evaluate it once more and agree with the presampled run
+    I = w.box_massive()
+    vals = []
+    for lam_in in (None, -0.5):
+        ctx = _ctx()
+        try:
+            iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+            qmc.qmc_set_kinematics(ctx, np.array([[10.0, -3.0]]))
+            lam = None if lam_in is None else np.full(len(I.sectors), lam_in)
+            val, err, info, rc, wv, nv = qmc.qmc_integrate(ctx, [iid], epsrel=1e-5, lowest_order=0, norders=1,
+                                                           nslots=len(I.sectors), lambda_io=lam, check=False)
+            assert rc == 0, qmc.qmc_last_error(ctx)
+            if lam is not None:
+                assert np.all(lam > 0)
+            vals.append((val[0, 0, 0], err[0, 0, 0]))
+        finally:
+            qmc.qmc_destroy(ctx)
+    (a, ea), (b, eb) = vals
+    sig = np.hypot(abs(ea), abs(eb))
+    assert abs(a - b) <= 5 * sig
