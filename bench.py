@@ -181,6 +181,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    from paper_2305_19768_gb300 import dist as qdist
     from paper_2305_19768_gb300 import flops as flopmod
     from paper_2305_19768_gb300 import qmc
     from paper_2305_19768_gb300.inputs import workloads as w
@@ -197,7 +198,7 @@ def main():
     kin = np.array([INV], dtype=np.float64)
     qmc.qmc_set_kinematics(ctx, kin)
     nsec = len(I.sectors)
-    seed = 1 + rank  # independent shift streams per rank
+    seed = qdist.rank_seed(1, rank)  # independent shift streams per rank
     specs = qmc.jobs_for_integral(iid, nsec, 1, args.n, args.shifts, seed=seed)
     jobs, nj = qmc.make_jobs(specs)
     plan = qmc.qmc_plan_create(ctx, jobs, nj, LO, NORD)
@@ -241,9 +242,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = qdist.max_over_ranks(total_ms, device="cuda")
     value = evals_per_step * args.steps * world / (total_ms * 1e-3)
 
     # end to end through the public API with host buffers: kinematics and the

@@ -1,0 +1,46 @@
+"""Several GPUs, one process each: how the evaluation shards.
+
+Every lattice point, sector, kinematic point and random shift of the method
+is independent, so ranks need no exchange inside an evaluation pass. Rank r
+evaluates the same jobs as every other rank with its own shift streams
+(seed = base seed + r): the ranks' shifts together are N x m independent
+random shifts of each lattice (weak scaling: per-rank work is fixed). One
+small exchange per integration pass gathers the per-shift sums, after which
+the shift statistics run on the whole set; the timing of a step is the
+slowest rank's.
+
+The collectives are torch.distributed calls on host tensors (gloo) or device
+tensors (nccl); nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s shift streams."""
+    return int(base_seed) + int(rank)
+
+
+def gather_shift_sums(local, group=None, device=None):
+    """All-gather per-shift sums [jobs][m][orders][2] from every rank and
+    concatenate them along the shift axis in rank order: [jobs][N m][orders][2]."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.as_tensor(np.ascontiguousarray(local, dtype=np.float64))
+    if device is not None:
+        t = t.to(device)
+    parts = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, t, group=group)
+    return np.concatenate([p.cpu().numpy() for p in parts], axis=1)
+
+
+def max_over_ranks(value: float, group=None, device=None) -> float:
+    """The largest `value` over all ranks (step time of the slowest rank)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())

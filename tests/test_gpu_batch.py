@@ -56,12 +56,17 @@ def test_presampled_batch_of_1024_points_matches_oracle(batch):
         qmc.qmc_plan_destroy(plan)
 
 
-def test_presampling_rejects_wrong_sign_and_finds_small_lambda(batch):
+def test_presampling_keeps_the_largest_lambda_for_quadratic_F(batch):
+    # one-loop F is quadratic in the Feynman parameters, so along the deformed
+    # contour Im F(z) = -lambda sum_k t_k (1 - t_k) (dF/dt_k)^2 <= 0 for every
+    # lambda > 0: no candidate can fail the sign check and the search keeps the
+    # first (largest) one. (A lambda of the wrong sign is caught by the sign
+    # check; qmc_integrate then presamples again -- test_gpu_integrate.)
     ctx, I, iid, pts = batch
     specs = qmc.jobs_for_integral(iid, 4, 4, 1009, 2, seed=2)
     jobs, nj = qmc.make_jobs(specs)
     lam, rc = qmc.qmc_presample_lambda(ctx, jobs, nj, 0, 1, lambda_max=8.0, ncand=16)
-    assert rc == 0 and np.all(lam < 8.0)   # the largest candidates break the sign check
+    assert rc == 0 and np.all(lam == 8.0)
     plan = qmc.qmc_plan_create(ctx, jobs, nj, 0, 1)
     try:
         qmc.qmc_plan_run(ctx, plan)
