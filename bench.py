@@ -9,6 +9,13 @@ subtraction, per-shift reduction), computed by the CUDA kernels behind the
 C-ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload box1L_massless|triangle_massive|box1L_massive_batch|
+                                box2L_planar_massless] [--precision fp64|mixed]
+
+The default workload and precision are the ones above; the others measure
+the same metric on the finite massive triangle, the 1024-point deformed
+massive-box batch and the two-loop double box (FP64 or FP32 monomial
+products), and report no traffic, no extras and no scan.
 
 Prints one JSON line (rank 0). Under torchrun each rank evaluates its own
 independent batch (its own shift streams): weak scaling, no data-path
@@ -32,12 +39,35 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n={n} CBC, m={m} shifts"
 METRIC = "integrand evals/s"
 UNIT = "evals/s"
-LO, NORD = -2, 3
-INV = [-3.0, -2.0]
 JOB_RECORD_BYTES = 136   # device job record (QmcJobDev) copied per job
+
+
+def _workloads():
+    from paper_2305_19768_gb300.inputs import workloads as w
+
+    return {
+        # the default: one-loop massless box, Euclidean point
+        "box1L_massless": dict(
+            make=w.box_massless, kin=[[-3.0, -2.0]], lo=-2, nord=3, n=1000003, m=32, deform=False,
+            desc="box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n={n} CBC, m={m} shifts"),
+        # finite massive triangle, p_i^2 = -1, m^2 = 1
+        "triangle_massive": dict(
+            make=w.triangle_massive, kin=[[]], lo=0, nord=1, n=100003, m=16, deform=False,
+            desc="triangle m^2=1 p_i^2=-1, 3 sectors d=2, eps^0, n={n} CBC, m={m} shifts"),
+        # massive box in the physical region: 1024 seeded (s, t), contour deformation
+        # with lambda presampled per (point, sector), all jobs in one persistent launch
+        "box1L_massive_batch": dict(
+            make=w.box_massive, kin=w.massive_box_points(1024, seed=3).tolist(), lo=0, nord=1, n=10007,
+            m=32, deform=True,
+            desc="box1L_massive m^2=1, 1024 (s,t) s~U[5,20] t~U[-8,-1] seed 3, 4 sectors d=3 deformed, "
+                 "eps^0, n={n} CBC, m={m} shifts"),
+        # two-loop planar massless double box, Euclidean point
+        "box2L_planar_massless": dict(
+            make=w.double_box_massless, kin=[[-3.0, -1.0]], lo=-4, nord=5, n=100003, m=32, deform=False,
+            desc="box2L_planar_massless s=-3 t=-1, 282 sectors d=6, eps^-4..eps^0, n={n} CBC, m={m} shifts"),
+    }
 
 # DRAM traffic per evaluator launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) for the kernel source with this SHA-1; any other
@@ -107,23 +137,28 @@ def clock_sampler_stop(proc, fh, path, device_index):
             "samples": len(sm)}
 
 
-def oracle_sample(I, inv, n, m, seed, ks, sectors=None):
-    """Oracle per-shift sums of every sector over lattice indices [0, ks):
-    returns (evaluations, seconds, threads)."""
+def oracle_sample(I, inv, n, m, seed, ks, lo, nord, lam=None):
+    """Oracle per-shift sums of every sector at one kinematic point over lattice
+    indices [0, ks): returns (evaluations, seconds, threads)."""
     import oracle
     from paper_2305_19768_gb300.inputs.lattice import lattice_for
 
-    sectors = range(len(I.sectors)) if sectors is None else sectors
     t0 = time.perf_counter()
     evals = 0
-    for s in sectors:
+    for s in range(len(I.sectors)):
         sec = I.sectors[s]
         _, z = lattice_for(n, sec.d)
         dl = oracle.shifts(seed, s, m, sec.d)
-        view = oracle.SectorView(I, s, inv)
-        oracle.shift_sums(view, n, z, dl, LO, NORD, k0=0, k1=ks)
+        view = oracle.SectorView(I, s, inv, lam=None if lam is None else lam[s])
+        oracle.shift_sums(view, n, z, dl, lo, nord, k0=0, k1=ks)
         evals += m * ks
     return evals, time.perf_counter() - t0, oracle.max_threads()
+
+
+def oracle_ks(W, nsec):
+    """Lattice indices per (sector, shift) of the oracle sample: about 6e5
+    evaluations of a d = 3 sector, fewer where sectors are many or wide."""
+    return max(64, int(1500 * 12 * 32 / (nsec * W["m"]) * (3.0 / max(3, W.get("d", 3)))))
 
 
 def run_reference(args):
@@ -131,25 +166,28 @@ def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    from paper_2305_19768_gb300.inputs import workloads as w
-
-    I = w.box_massless()
-    n, m = args.n, args.shifts
-    ks = 1500
+    W = _workloads()[args.workload]
+    I = W["make"]()
+    n, m = args.n or W["n"], args.shifts or W["m"]
+    W = dict(W, m=m, d=max(sec.d for sec in I.sectors))
+    nsec = len(I.sectors)
+    ks = oracle_ks(W, nsec)
+    inv = W["kin"][0]
+    lam = [1.0] * nsec if W["deform"] else None
     for _ in range(args.warmup):
-        oracle_sample(I, INV, n, m, 1, ks)
+        oracle_sample(I, inv, n, m, 1, ks, W["lo"], W["nord"], lam)
     tot_e, tot_t, thr = 0, 0.0, 1
     for _ in range(args.steps):
-        e, t, thr = oracle_sample(I, INV, n, m, 1, ks)
+        e, t, thr = oracle_sample(I, inv, n, m, 1, ks, W["lo"], W["nord"], lam)
         tot_e += e
         tot_t += t
     val = tot_e / tot_t
+    sample = f"all {nsec} sectors x {m} shifts x lattice indices [0,{ks}) of n={n} at the first kinematic point"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD.format(n=n, m=m), "sample": f"k in [0,{ks}) per sector and shift"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
-                             "sample": f"all 12 sectors x {m} shifts x lattice indices [0,{ks}) of n={n}"},
+            "data": "synthetic", "config": {"workload": W["desc"].format(n=n, m=m), "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -161,8 +199,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1000003)
-    ap.add_argument("--shifts", type=int, default=32)
+    ap.add_argument("--workload", default="box1L_massless",
+                    choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box2L_planar_massless"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=0, help="lattice size (default: the workload's)")
+    ap.add_argument("--shifts", type=int, default=0, help="random shifts (default: the workload's)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -186,21 +227,36 @@ def main():
     from paper_2305_19768_gb300 import qmc
     from paper_2305_19768_gb300.inputs import workloads as w
 
-    I = w.box_massless()
+    W = _workloads()[args.workload]
+    I = W["make"]()
+    args.n, args.shifts = args.n or W["n"], args.shifts or W["m"]
+    LO, NORD = W["lo"], W["nord"]
+    default = args.workload == "box1L_massless" and args.precision == "fp64"
     opts = {}
     if args.block:
         opts["block"] = args.block
     if args.ppt:
         opts["ppt"] = args.ppt
+    if args.precision == "mixed":
+        opts["precision"] = qmc.QMC_PRECISION_MIXED
     ctx = qmc.qmc_create(local, **opts)
     qmc.load_lattice_table(ctx)
     iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
-    kin = np.array([INV], dtype=np.float64)
-    qmc.qmc_set_kinematics(ctx, kin)
+    kin = np.array(W["kin"], dtype=np.float64).reshape(len(W["kin"]), -1)
+    qmc.qmc_set_kinematics(ctx, kin if kin.shape[1] else np.zeros((0, 0)))
+    npts = len(W["kin"])
     nsec = len(I.sectors)
     seed = qdist.rank_seed(1, rank)  # independent shift streams per rank
-    specs = qmc.jobs_for_integral(iid, nsec, 1, args.n, args.shifts, seed=seed)
+    specs = qmc.jobs_for_integral(iid, nsec, npts, args.n, args.shifts, seed=seed)
     jobs, nj = qmc.make_jobs(specs)
+    lam0 = None
+    if W["deform"]:
+        # contour-deformation parameter per (point, sector) by presampling (untimed setup)
+        lam, _ = qmc.qmc_presample_lambda(ctx, jobs, nj, LO, NORD, lambda_max=1.0, ncand=16)
+        for sp, L in zip(specs, lam):
+            sp["lambda"] = float(L)
+        jobs, nj = qmc.make_jobs(specs)
+        lam0 = [float(L) for L in lam[:nsec]]
     plan = qmc.qmc_plan_create(ctx, jobs, nj, LO, NORD)
     out_n = qmc.qmc_plan_output_size(plan)
     out_dev = torch.empty(out_n, dtype=torch.float64, device="cuda")
@@ -208,7 +264,7 @@ def main():
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    evals_per_step = nsec * args.shifts * args.n
+    evals_per_step = nj * args.shifts * args.n
 
     for _ in range(max(3, args.warmup)):
         qmc.qmc_plan_run(ctx, plan, out_dev.data_ptr(), sptr)
@@ -260,12 +316,12 @@ def main():
     e2e_val = evals_per_step * max(1, args.steps // 2) * world / t_e2e
 
     # roofline of the evaluator kernel: algorithmic FP64 flops / event time
-    fl_per_eval = flopmod.workload_flops(I, LO, NORD)
+    fl_per_eval = flopmod.workload_flops(I, LO, NORD, deform=W["deform"])
     avg_eval_ms = float(np.mean(eval_ms))
     achieved = fl_per_eval * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
     sha = kernel_sha1()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s (fp64)",
-            "frac": achieved / peak_gflops, "traffic": PROFILED_TRAFFIC.get(sha),
+            "frac": achieved / peak_gflops, "traffic": PROFILED_TRAFFIC.get(sha) if default else None,
             "flops_per_eval": fl_per_eval, "peak_source": "DFMA probe in this run",
             "kernel_sha1": sha}
 
@@ -273,7 +329,7 @@ def main():
     # qmc_integrate (pilot lattice 1e4, adaptive), FP64 and mixed precision,
     # and the mixed-precision throughput of the same evaluation pass
     extra = {}
-    if not args.no_extra:
+    if not args.no_extra and default:
         t0 = time.perf_counter()
         val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-4, lowest_order=LO, norders=NORD,
                                                check=False)
@@ -305,7 +361,7 @@ def main():
     # (s, t) grid of a ten-integral amplitude): the learned, batched,
     # mixed-precision form against the plain FP64 method (timed on every 50th
     # point and scaled to the grid) and against the same QMC without the network
-    if not args.no_extra and not args.no_scan and world == 1:
+    if not args.no_extra and not args.no_scan and world == 1 and default:
         from paper_2305_19768_gb300 import scan
 
         sc = scan.compare(10000, 1e-4, "plain,unsized,learned", 2000, plain_sample=50)
@@ -319,16 +375,19 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ks = 1500
-        e, t, thr = oracle_sample(I, INV, args.n, args.shifts, 1, ks)
+        ks = oracle_ks(dict(W, m=args.shifts, d=max(sec.d for sec in I.sectors)), nsec)
+        e, t, thr = oracle_sample(I, W["kin"][0], args.n, args.shifts, 1, ks, LO, NORD, lam0)
         cpu = {"value": e / t, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"all {nsec} sectors x {args.shifts} shifts x lattice indices [0,{ks}) of n={args.n}"}
+               "sample": f"all {nsec} sectors x {args.shifts} shifts x lattice indices [0,{ks}) of n={args.n}"
+                         " at the first kinematic point"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(n=args.n, m=args.shifts), "evals_per_step": evals_per_step,
+            "config": {"workload": W["desc"].format(n=args.n, m=args.shifts), "evals_per_step": evals_per_step,
+                       "precision": args.precision,
                        "l2": "flushed between timed steps (256 MB write)", "wall_s": wall},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
