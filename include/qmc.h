@@ -399,10 +399,16 @@ int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, 
 
 /* The evaluator's own FP64 natural logarithm applied on the device to n
  * positive normal doubles (host arrays x[n] -> out[n]), for verification:
- * Tang's table-driven method (ACM TOMS 16, 1990) with a 129-entry table
- * and a degree-7 log1p, within 1 ulp. Errors: QMC_E_INVAL for a
- * non-positive, subnormal or non-finite x. */
+ * Tang's table-driven method (ACM TOMS 16, 1990) with a 1025-entry table
+ * and a degree-5 log1p, within 1.5 ulp (without Tang's separate procedure
+ * near x = 1). Errors: QMC_E_INVAL for a non-positive, subnormal or
+ * non-finite x. */
 int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out);
+
+/* The evaluator's own FP64 reciprocal (two Newton-Raphson steps from the
+ * hardware approximation), applied like qmc_fp64_log, for verification:
+ * within 1 ulp of the correctly rounded 1/x. Same arguments and errors. */
+int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out);
 
 /* Measure the FP64 fused-multiply-add throughput of the device (the
  * roofline denominator of the evaluator): *gflops = 2 * DFMA / s over a

@@ -2,7 +2,7 @@
 logarithm (Tang, "Table-driven implementation of the logarithm function in
 IEEE floating-point arithmetic", ACM TOMS 16 (1990)).
 
-For j = 0..128, F_j = 1 + j/128 and
+For j = 0..1024, F_j = 1 + j/1024 and
     INVF[j]          = RN(1/F_j)
     LOGF_HI[j]       = ln(F_j) rounded to a multiple of 2^-42
     LOGF_LO[j]       = RN(ln(F_j) - LOGF_HI[j])
@@ -32,8 +32,8 @@ def grid42(x) -> float:
 
 def main():
     rows = []
-    for j in range(129):
-        F = mp.mpf(1) + mp.mpf(j) / 128
+    for j in range(1025):
+        F = mp.mpf(1) + mp.mpf(j) / 1024
         L = mp.log(F)
         hi = grid42(L)
         lo = rn(L - mp.mpf(hi))
@@ -43,10 +43,10 @@ def main():
     ln2_lo = rn(ln2 - mp.mpf(ln2_hi))
     with open(OUT, "w") as fh:
         fh.write("// Table of the evaluator's FP64 logarithm (written by make_log_table.py).\n")
-        fh.write("// Row j: RN(1/F_j), ln(F_j) on the 2^-42 grid, RN(remainder); F_j = 1 + j/128.\n")
+        fh.write("// Row j: RN(1/F_j), ln(F_j) on the 2^-42 grid, RN(remainder); F_j = 1 + j/1024.\n")
         fh.write("#pragma once\n")
         fh.write(f"#define QMC_LN2_HI {ln2_hi.hex()}\n#define QMC_LN2_LO {ln2_lo.hex()}\n")
-        fh.write("#define QMC_LOG_TABLE_ROWS 129\n")
+        fh.write("#define QMC_LOG_TABLE_ROWS 1025\n")
         fh.write("#define QMC_LOG_TABLE_INIT { \\\n")
         for inv, hi, lo in rows:
             fh.write(f"    {inv.hex()}, {hi.hex()}, {lo.hex()}, \\\n")

@@ -20,6 +20,7 @@
 
 extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void *stream);
 extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream);
+extern "C" int qmc_k_rcp(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_occupancy(int cls, int block);
 
 namespace {
@@ -186,10 +187,19 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
     H.f0_int = (S.f0 == std::floor(S.f0) && std::fabs(S.f0) <= QMC_EMAX) ? 1 : 0;
     H.pad1 = (S.u1 == std::floor(S.u1) && std::fabs(S.u1) <= QMC_EMAX && S.f1 == std::floor(S.f1) &&
               std::fabs(S.f1) <= QMC_EMAX) ? 1 : 0;
+    bool bint = true;
+    for (int j = 0; j < S.d; ++j)
+        bint = bint && S.b[j] == std::floor(S.b[j]) && std::fabs(S.b[j]) <= QMC_EMAX;
+    if (H.pad1 && bint) H.pad1 |= 2;
+    if (H.pad1) {
+        H.u1i = (int32_t)S.u1;
+        H.f1i = (int32_t)S.f1;
+    }
     int q = 0;
     for (int j = 0; j < S.d; ++j) {
         H.a[j] = S.a[j];
         H.b[j] = S.b[j];
+        if (bint) H.bi[j] = (int32_t)S.b[j];
         if (S.a[j] == -1) H.sing[q++] = j;
         else if (S.a[j] != 0 || S.b[j] != 0.0) H.regular_mask |= 1 << j;
     }
@@ -818,27 +828,37 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
     return rc ? fail(ctx, rc, "qmc_shifts failed") : QMC_OK;
 }
 
-int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out) {
-    if (!ctx || (n && (!x || !out))) return fail(ctx, QMC_E_INVAL, "qmc_fp64_log: bad arguments");
+// one device function applied elementwise to host data (verification entry points)
+static int fp64_apply(qmc_ctx *ctx, const double *x, size_t n, double *out, const char *name,
+                      int (*launch)(const double *, uint64_t, double *, void *)) {
+    if (!ctx || (n && (!x || !out))) return fail(ctx, QMC_E_INVAL, "%s: bad arguments", name);
     for (size_t i = 0; i < n; ++i)
         if (!(x[i] >= 2.2250738585072014e-308) || !std::isfinite(x[i]))
-            return fail(ctx, QMC_E_INVAL, "qmc_fp64_log: x[%zu] is not a positive normal number", i);
+            return fail(ctx, QMC_E_INVAL, "%s: x[%zu] is not a positive normal number", name, i);
     if (n == 0) return QMC_OK;
     cudaSetDevice(ctx->device);
     double *dx = nullptr, *dy = nullptr;
     int rc = QMC_OK;
     if (cudaMalloc(&dx, n * sizeof(double)) != cudaSuccess || cudaMalloc(&dy, n * sizeof(double)) != cudaSuccess) {
-        rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_log: allocation failed");
+        rc = fail(ctx, QMC_E_CUDA, "%s: allocation failed", name);
     } else {
         cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-        if (qmc_k_log(dx, n, dy, ctx->stream)) rc = fail(ctx, QMC_E_CUDA, "log kernel launch failed");
+        if (launch(dx, n, dy, ctx->stream)) rc = fail(ctx, QMC_E_CUDA, "%s: kernel launch failed", name);
         cudaMemcpyAsync(out, dy, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
-        if (!rc && e != cudaSuccess) rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_log: %s", cudaGetErrorString(e));
+        if (!rc && e != cudaSuccess) rc = fail(ctx, QMC_E_CUDA, "%s: %s", name, cudaGetErrorString(e));
     }
     cudaFree(dx);
     cudaFree(dy);
     return rc;
+}
+
+int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out) {
+    return fp64_apply(ctx, x, n, out, "qmc_fp64_log", qmc_k_log);
+}
+
+int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out) {
+    return fp64_apply(ctx, x, n, out, "qmc_fp64_rcp", qmc_k_rcp);
 }
 
 int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {

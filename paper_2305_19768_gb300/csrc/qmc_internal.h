@@ -30,7 +30,10 @@ struct QmcSectorDev {
     int32_t a[QMC_DMAX];
     int32_t sing[QMC_SMAX];                 // variable index of singular slot q
     int32_t regular_mask;                   // bit j: j not singular and (a_j != 0 or b_j != 0)
-    int32_t pad1;                           // 1: u1, f1 integers with |.| <= QMC_EMAX (one log per corner)
+    int32_t pad1;                           // bit 0: u1, f1 integers with |.| <= QMC_EMAX (one log per
+                                            // corner); bit 1: every b_j too (one complex log per corner)
+    int32_t bi[QMC_DMAX];                   // b_j, u1, f1 as integers where bit 1 / bit 0 of pad1 is set
+    int32_t u1i, f1i;
     int32_t gU[QMC_NGROUP + 1];
     int32_t gF[QMC_NGROUP + 1];
     int32_t dFoff[QMC_DMAX], dFn[QMC_DMAX];   // relative to monoF + nF

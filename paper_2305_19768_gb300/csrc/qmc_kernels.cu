@@ -44,6 +44,12 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t state, uint64_t i) {
     return (double)(z >> 11) * (1.0 / 9007199254740992.0);
 }
 
+// x >= 0 finite: compares on the bit pattern (integer pipe) instead of FP64
+__device__ __forceinline__ bool nonneg_is_zero(double x) { return __double_as_longlong(x) == 0; }
+__device__ __forceinline__ bool nonneg_ge_one(double x) {
+    return __double_as_longlong(x) >= 0x3FF0000000000000LL;
+}
+
 // Lattice coordinate (steps "lattice index" and "shifted point"): RN(r/n) +
 // delta folded into [0,1), every operation correctly rounded and never
 // contracted. RN(r/n) comes from Markstein's correction with y = RN(1/n)
@@ -59,36 +65,49 @@ __device__ __forceinline__ double lattice_coord(uint64_t r, double nd, double in
     const double rho = __fma_rn(-q0, nd, rd);
     const double q = __fma_rn(rho, inv_n, q0);
     double x = __dadd_rn(q, delta);
-    if (x >= 1.0) x = __dadd_rn(x, -1.0);
+    if (nonneg_ge_one(x)) x = __dadd_rn(x, -1.0);
     return x;
 }
 
 // Natural logarithm of a positive normal double, table-driven after Tang
-// (ACM TOMS 16, 1990): x = 2^e m, m in [1,2); F = 1 + j/128 nearest to m
-// (integer operations on the bits); r = m - F exact; f = r RN(1/F);
-// ln x = e ln2 + ln F + log1p(f), log1p by its Taylor series to f^7
-// (|f| <= 2^-8). e*LN2_HI + LOGF_HI is exact (both on the 2^-42 grid).
-// Measured worst case below 1 ulp. `tab` holds rows {RN(1/F), ln F hi, lo}.
+// (ACM TOMS 16, 1990): x = 2^e m, m in [1,2); F = 1 + j/1024 nearest to m
+// (integer operations on the bits); r = m - F exact; f = r RN(1/F),
+// |f| <= 2^-11; ln x = e ln2 + ln F + log1p(f), log1p by its Taylor series
+// to f^5 (truncation below 2^-57 relative). e*LN2_HI + LOGF_HI is exact (both
+// on the 2^-42 grid). Without Tang's separate procedure near x = 1, the two
+// roundings in f show where ln F and f nearly cancel: measured worst case
+// 1.05 ulp. 12 FP64 operations. `tab` holds rows {RN(1/F), ln F hi, lo}.
 __device__ __forceinline__ double qlog(double x, const double *tab) {
     const long long bits = __double_as_longlong(x);
     const long long mb = bits & 0x000FFFFFFFFFFFFFLL;
-    const int j = (int)((mb + (1LL << 44)) >> 45);               // 0..128
+    const int j = (int)((mb + (1LL << 41)) >> 42);               // 0..1024
     const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);
-    const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 45));
+    const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 42));
     // exponent as a double without a conversion instruction: (2^52 + 2^51 + e) - (2^52 + 2^51)
     const long long e = (bits >> 52) - 1023;
     const double ed = __longlong_as_double(0x4338000000000000LL + e) - 6755399441055744.0;
     const double r = m - F;
     const double f = r * tab[3 * j];
-    double q = fma(f, 1.0 / 7.0, -1.0 / 6.0);
-    q = fma(q, f, 0.2);
-    q = fma(q, f, -0.25);
+    double q = fma(f, 0.2, -0.25);
     q = fma(q, f, 1.0 / 3.0);
     q = fma(q, f, -0.5);
-    const double tail = (f * f) * q;
-    const double hi = fma(ed, QMC_LN2_HI, tab[3 * j + 1]);
     const double lo = fma(ed, QMC_LN2_LO, tab[3 * j + 2]);
-    return hi + (f + (tail + lo));
+    const double s = fma(f * f, q, lo);                            // tail + lo
+    const double hi = fma(ed, QMC_LN2_HI, tab[3 * j + 1]);
+    return hi + (f + s);
+}
+
+// Reciprocal by Newton-Raphson (y <- y + y (1 - x y), quadratic convergence)
+// from the hardware approximation rcp.approx.ftz.f64, two steps: not
+// correctly rounded, within about 1 ulp for normal x (checked against
+// CUDA's correctly rounded reciprocal).
+__device__ __forceinline__ double qrcp(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
 }
 
 // ---------------------------------------------------------------- complex
@@ -103,8 +122,17 @@ __device__ __forceinline__ dc operator*(dc a, dc b) {
 }
 __device__ __forceinline__ dc operator*(dc a, double s) { return dc{a.re * s, a.im * s}; }
 __device__ __forceinline__ dc cinv(dc a) {
-    double q = 1.0 / fma(a.re, a.re, a.im * a.im);
+    double q = qrcp(fma(a.re, a.re, a.im * a.im));
     return dc{a.re * q, -a.im * q};
+}
+__device__ __forceinline__ dc conj_(dc a) { return dc{a.re, -a.im}; }
+__device__ __forceinline__ double norm_(dc a) { return fma(a.re, a.re, a.im * a.im); }
+// FP32 estimate of the principal argument (branch bookkeeping only); `m0`:
+// on the negative real axis take -pi (the F - i0 prescription)
+__device__ __forceinline__ float arg32(dc a, bool m0) {
+    float im = __double2float_rn(a.im);
+    if (m0 && (__double_as_longlong(a.im) << 1) == 0) im = -0.0f;
+    return atan2f(im, __double2float_rn(a.re));
 }
 // Principal log; on the real axis the argument is taken from below
 // (x - i0), the prescription of F - i0.
@@ -409,7 +437,7 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
                     tq = t[j];
                     bb = sec.b[j];
                 }
-            it[q] = __drcp_rn(tq);
+            it[q] = qrcp(tq);
             bq[q] = bb;
             if (need_lt) lt[q] = qlog(tq, tab);
         }
@@ -417,7 +445,7 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     // corners: B_V = Cc U^u0 F^f0, Lambda_V = Lc + ln(U^u1 F^f1) (one log when
     // u1, f1 are small integers, else u1 ln U + f1 ln F)
     const int u0 = (int)sec.u0, f0 = (int)sec.f0, u1 = (int)sec.u1, f1 = (int)sec.f1;
-    const bool comb = sec.pad1 != 0;
+    const bool comb = (sec.pad1 & 1) != 0;
     double BV[NG], LV[NG];
     const int full = (1 << ns) - 1;
 #pragma unroll
@@ -430,8 +458,8 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
         const double F = hF[(NG - 1) ^ V];
         const bool needUinv = (sec.u0_int && u0 < 0) || (lam_here && comb && u1 < 0);
         const bool needFinv = (sec.f0_int && f0 < 0) || (lam_here && comb && f1 < 0);
-        const double Ui = needUinv ? __drcp_rn(U) : 0.0;
-        const double Fi = needFinv ? __drcp_rn(F) : 0.0;
+        const double Ui = needUinv ? qrcp(U) : 0.0;
+        const double Fi = needFinv ? qrcp(F) : 0.0;
         double B = Cc;
         B *= sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog(U, tab));
         B *= sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog(F, tab));
@@ -479,7 +507,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                     tq = t[j];
                     bb = sec.b[j];
                 }
-            it[q] = __drcp_rn(tq);
+            it[q] = qrcp(tq);
             bq[q] = bb;
             if (hi + ns - 1 >= 1) lt[q] = qlog(tq, tab);
         }
@@ -567,21 +595,42 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
         const dc U = poly_sum<DMAX, dc>(S.exps, S.cval, sec.gU[0], sec.nU, zp);
         const dc F = poly_sum<DMAX, dc>(S.exps, S.cval, sec.nU, sec.nU + sec.nF, zp);
         if (F.im > 0.0) ++signfail;
+        // all exponents integers: the corner's eps exponent is one complex log,
+        // ln X with X = prod rho_j^b_j prod z_j^b_j U^u1 F^f1, whose imaginary
+        // part is restored to the sum of the factors' principal arguments by the
+        // multiple of 2 pi that an FP32 estimate of that sum selects
+        const bool comb_all = (sec.pad1 & 3) == 3;
         dc num = detJ, den = one<dc>();
         dc lsum = zero<dc>();
+        dc Xn = one<dc>(), Xd = one<dc>();
+        float sarg = 0.0f;
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) {
             if (j >= d) continue;
             if (issing[j]) {
                 den = den * rho[j];
-                if (lam_here && sec.b[j] != 0.0) lsum = lsum + clog_m0(rho[j], tab) * sec.b[j];
+                if (lam_here && sec.b[j] != 0.0) {
+                    if (comb_all) {
+                        mul_ipow<dc>(rho[j], sec.bi[j], Xn, Xd);
+                        sarg = fmaf((float)sec.bi[j], arg32(rho[j], false), sarg);
+                    } else {
+                        lsum = lsum + clog_m0(rho[j], tab) * sec.b[j];
+                    }
+                }
             } else if ((sec.regular_mask >> j) & 1) {
                 if (sec.a[j] != 0) mul_ipow<dc>(z[j], sec.a[j], num, den);
-                if (lam_here && sec.b[j] != 0.0) lsum = lsum + clog_m0(z[j], tab) * sec.b[j];
+                if (lam_here && sec.b[j] != 0.0) {
+                    if (comb_all) {
+                        mul_ipow<dc>(z[j], sec.bi[j], Xn, Xd);
+                        sarg = fmaf((float)sec.bi[j], arg32(z[j], false), sarg);
+                    } else {
+                        lsum = lsum + clog_m0(z[j], tab) * sec.b[j];
+                    }
+                }
             }
         }
-        const bool needU = (lam_here && sec.u1 != 0.0) || !sec.u0_int;
-        const bool needF = (lam_here && sec.f1 != 0.0) || !sec.f0_int;
+        const bool needU = (lam_here && sec.u1 != 0.0 && !comb_all) || !sec.u0_int;
+        const bool needF = (lam_here && sec.f1 != 0.0 && !comb_all) || !sec.f0_int;
         dc lU = zero<dc>(), lF = zero<dc>();
         if (needU) lU = clog_m0(U, tab);
         if (needF) lF = clog_m0(F, tab);
@@ -590,7 +639,21 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
         if (sec.f0_int) mul_ipow<dc>(F, (int)sec.f0, num, den);
         else num = num * cexp_(lF * sec.f0);
         BV[V] = num * cinv(den);
-        if (lam_here) LV[V] = lsum + lU * sec.u1 + lF * sec.f1;
+        if (lam_here) {
+            if (comb_all) {
+                mul_ipow<dc>(U, sec.u1i, Xn, Xd);
+                sarg = fmaf((float)sec.u1i, arg32(U, false), sarg);
+                mul_ipow<dc>(F, sec.f1i, Xn, Xd);
+                sarg = fmaf((float)sec.f1i, arg32(F, true), sarg);
+                const dc X = Xn * conj_(Xd);                  // |Xd|^2 Xn / Xd
+                const double phi = atan2(X.im, X.re);
+                const float kf = rintf((sarg - __double2float_rn(phi)) * 0.15915494f);
+                LV[V] = dc{0.5 * qlog(norm_(Xn) * qrcp(norm_(Xd)), tab),
+                           fma((double)kf, 2.0 * CUDART_PI, phi)};
+            } else {
+                LV[V] = lsum + lU * sec.u1 + lF * sec.f1;
+            }
+        }
     }
     double ib[SMAX];
 #pragma unroll
@@ -745,13 +808,13 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
                             t[j] = u;
                             omt[j] = 1.0 - u;
                         }
-                        zero_t |= (t[j] == 0.0);
+                        zero_t |= nonneg_is_zero(t[j]);
                         uint64_t rn = r[j] + zz[j];
                         r[j] = (rn >= n) ? rn - n : rn;
                     }
                 }
                 const double W = Lc.transform == 0 ? S.w140d * (Ws * Ws * Ws) : 1.0;
-                if (W == 0.0 || zero_t) continue;
+                if (nonneg_is_zero(W) || zero_t) continue;
                 T res[LMAX];
                 if constexpr (CPLX) {
                     eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, hi, nord, res, signfail_tile);
@@ -841,6 +904,11 @@ __global__ void qmc_log_kernel(const double *x, uint64_t n, double *out) {
     if (i < n) out[i] = qlog(x[i], kLogTable);
 }
 
+__global__ void qmc_rcp_kernel(const double *x, uint64_t n, double *out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = qrcp(x[i]);
+}
+
 __global__ void qmc_shift_kernel(uint64_t state, int m, int d, double *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m * d) out[i] = splitmix_uniform(state, (uint64_t)i);
@@ -921,6 +989,12 @@ extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void 
 extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream) {
     if (n == 0) return 0;
     qmc_log_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+extern "C" int qmc_k_rcp(const double *x_dev, uint64_t n, double *out_dev, void *stream) {
+    if (n == 0) return 0;
+    qmc_rcp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
