@@ -59,14 +59,29 @@ __device__ __forceinline__ bool nonneg_ge_one(double x) {
 // because its odd denominator part does not divide r, or else it is a short
 // dyadic) lies at least 1/(2n) > 2^-33 ulp away from any rounding midpoint,
 // so q is exactly the correctly rounded quotient.
+// Exact doubles from integer operations on the bits (integer pipe):
+// u32_to_double(r) = r for r < 2^32; frac_of_one_two(x) = x - 1 for x in [1, 2).
+__device__ __forceinline__ double u32_to_double(uint64_t r) {
+    if (r == 0) return 0.0;
+    const int p = 63 - __clzll((long long)r);                          // leading bit, 0..31
+    const uint64_t mant = (r << (52 - p)) & 0x000FFFFFFFFFFFFFULL;
+    return __longlong_as_double((long long)(((uint64_t)(1023 + p) << 52) | mant));
+}
+__device__ __forceinline__ double frac_of_one_two(double x) {
+    const uint64_t f = (uint64_t)__double_as_longlong(x) & 0x000FFFFFFFFFFFFFULL;   // (x - 1) 2^52
+    if (f == 0) return 0.0;
+    const int p = 63 - __clzll((long long)f);                          // 0..51
+    const uint64_t mant = (f << (52 - p)) & 0x000FFFFFFFFFFFFFULL;
+    return __longlong_as_double((long long)(((uint64_t)(1023 + p - 52) << 52) | mant));
+}
+
 __device__ __forceinline__ double lattice_coord(uint64_t r, double nd, double inv_n, double delta) {
-    const double rd = (double)r;
+    const double rd = u32_to_double(r);
     const double q0 = __dmul_rn(rd, inv_n);
     const double rho = __fma_rn(-q0, nd, rd);
     const double q = __fma_rn(rho, inv_n, q0);
-    double x = __dadd_rn(q, delta);
-    if (nonneg_ge_one(x)) x = __dadd_rn(x, -1.0);
-    return x;
+    const double x = __dadd_rn(q, delta);
+    return nonneg_ge_one(x) ? frac_of_one_two(x) : x;   // x - 1 is exact for x in [1, 2)
 }
 
 // Natural logarithm of a positive normal double, table-driven after Tang
@@ -413,11 +428,15 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
 
     // factors of the regular variables: prod t^{a_j} and sum b_j ln t_j
     double Cc = 1.0, Lc = 0.0;
+    bool hasCc = false;
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d && ((sec.regular_mask >> j) & 1)) {
             const int a = sec.a[j];
-            if (a > 0) Cc *= pow_sel<double>(tp[j], (uint32_t)a);
+            if (a > 0) {
+                Cc = hasCc ? Cc * pow_sel<double>(tp[j], (uint32_t)a) : pow_sel<double>(tp[j], (uint32_t)a);
+                hasCc = true;
+            }
             if (need_lam && sec.b[j] != 0.0) Lc = fma(sec.b[j], qlog(t[j], tab), Lc);
         }
     }
@@ -460,9 +479,23 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
         const bool needFinv = (sec.f0_int && f0 < 0) || (lam_here && comb && f1 < 0);
         const double Ui = needUinv ? qrcp(U) : 0.0;
         const double Fi = needFinv ? qrcp(F) : 0.0;
-        double B = Cc;
-        B *= sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog(U, tab));
-        B *= sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog(F, tab));
+        // B = Cc U^u0 F^f0 without multiplications by unit factors (the
+        // conditions are uniform over the tile's sector)
+        double B = 1.0;
+        bool unit = true;
+        if (hasCc) {
+            B = Cc;
+            unit = false;
+        }
+        if (!sec.u0_int || u0 != 0) {
+            const double pu = sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog(U, tab));
+            B = unit ? pu : B * pu;
+            unit = false;
+        }
+        if (!sec.f0_int || f0 != 0) {
+            const double pf = sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog(F, tab));
+            B = unit ? pf : B * pf;
+        }
         BV[V] = B;
         if (lam_here) {
             double l;
@@ -813,7 +846,7 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
                         r[j] = (rn >= n) ? rn - n : rn;
                     }
                 }
-                const double W = Lc.transform == 0 ? S.w140d * (Ws * Ws * Ws) : 1.0;
+                const double W = Lc.transform == 0 ? Ws * Ws * Ws : 1.0;   // 140^d: per tile
                 if (nonneg_is_zero(W) || zero_t) continue;
                 T res[LMAX];
                 if constexpr (CPLX) {
@@ -855,6 +888,7 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
         if (threadIdx.x < 2 * nord) {
             double sum = 0.0;
             for (int w = 0; w < BLOCK / 32; ++w) sum += S.red[w][threadIdx.x];
+            if (Lc.transform == 0) sum *= S.w140d;   // the korobov3 weight's constant 140^d
             Lc.partials[tile * (uint64_t)(2 * nord) + threadIdx.x] = sum;
             if (!isfinite(sum)) atomicAdd(Lc.status + 1, 1ULL);
         }
