@@ -419,13 +419,22 @@ int qmc_fp64_peak(qmc_ctx *ctx, double *gflops);
  * Learned part: tensor-core MLP kernels
  * ------------------------------------------------------------------------ */
 
-/* BF16 GEMM on the tensor cores (tcgen05.mma, FP32 accumulation in tensor
- * memory): C[M][N] = sum_k A[M][K] B[N][K] with A, B row-major bf16 (raw
- * 16-bit patterns) and C row-major float, host buffers, current CUDA device.
+/* BF16 GEMM on the tensor cores (TMA-fed tcgen05.mma, FP32 accumulation in
+ * tensor memory, split-K over the SMs when the M tiles are few):
+ * C[M][N] = sum_k A[M][K] B[N][K] with A, B row-major bf16 (raw 16-bit
+ * patterns) and C row-major float, host buffers, current CUDA device.
  * M % 128 == 0, K % 16 == 0, N % 16 == 0 and 16 <= N <= 256.
  * Errors: QMC_E_INVAL (shape), QMC_E_CUDA (launch, or a completion wait
  * that ran out). */
 int qmc_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int M, int N, int K);
+
+/* The same GEMM on device buffers (A, B 16-byte aligned), enqueued on
+ * `stream` (NULL: the legacy default stream); err_dev (device, one unsigned,
+ * caller-zeroed) is incremented by every CTA whose completion wait ran out.
+ * Returns at once (no synchronisation). Errors: QMC_E_INVAL (shape,
+ * alignment, NULL pointers), QMC_E_CUDA (launch). */
+int qmc_gemm_bf16_device(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
+                         void *stream);
 
 /* A multilayer perceptron trained and evaluated on the GPU (the learned
  * sizing/surrogate model): x (nin) -> tanh(W0 x + b0) -> (depth - 1) layers

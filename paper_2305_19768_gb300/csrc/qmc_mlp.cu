@@ -1,22 +1,31 @@
 // Tensor-core kernels of the learned lattice-size / amplitude model of the
-// amplitude scan: a BF16 GEMM on the 5th-
-// generation tensor cores (tcgen05.mma, accumulator in tensor memory, FP32
-// accumulation) plus the elementwise kernels of an MLP's forward and
-// backward passes and its Adam update.
+// amplitude scan: a BF16 GEMM on the 5th-generation tensor cores and the
+// elementwise kernels of an MLP's forward and backward passes and its Adam
+// update.
 //
 // gemm: C[M][N] (fp32) = A[M][K] . B[N][K]^T with A, B bf16 and K-major
 // (row-major [rows][K]). One CTA of 128 threads computes a 128 x N tile
-// (N <= 256, multiple of 16; M, K multiples of 128 and 16): K is staged in
-// chunks of 64 through shared memory in the canonical no-swizzle K-major
-// layout (8 x 16-byte core matrices), one elected thread issues four
-// tcgen05.mma (K = 16 each) per chunk, tcgen05.commit signals an mbarrier,
-// and the 4 warps read the 128 x N accumulator back with tcgen05.ld.
+// (N <= 256, multiple of 16; M a multiple of 128, K of 16) over a range of
+// K (split-K when the M tiles alone cannot fill the GPU):
+//  * thread 0 streams 64-wide K chunks of A (128 rows) and B (N rows) into a
+//    4-stage shared-memory ring with TMA (cp.async.bulk.tensor, 128-byte
+//    swizzle), each stage completing on a transaction-count mbarrier;
+//  * thread 32 issues four tcgen05.mma (K = 16 each) per stage into an FP32
+//    accumulator in tensor memory and frees the stage with tcgen05.commit;
+//  * after the last commit all 4 warps read the accumulator back with
+//    tcgen05.ld and store it.
+// Split-K partials go to a workspace and a second kernel adds them in split
+// order (deterministic). Every mbarrier wait has an iteration limit, after
+// which the CTA records an error, waits for its copies in flight, frees its
+// tensor memory and exits.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "../../include/qmc.h"
@@ -29,29 +38,32 @@
 namespace {
 
 constexpr int kGemmThreads = 128;
-constexpr int kChunkK = 64;                       // K elements staged per round
+constexpr int kStages = 4;
+constexpr int kBK = 64;                                  // K elements per stage: one 128-byte swizzle span
 constexpr int kTileM = 128;
 constexpr int kMaxN = 256;
-constexpr int kAChunkBytes = kTileM * kChunkK * 2;  // 16 KB
-constexpr int kBChunkBytes = kMaxN * kChunkK * 2;   // 32 KB
-// Dynamic shared memory reserved per CTA: the operand chunks plus headroom, so
-// that every address the descriptors can describe stays inside the allocation.
-constexpr int kGemmSmem = 200 * 1024;
+constexpr int kAStageBytes = kTileM * kBK * 2;           // 16 KB
+constexpr int kBStageBytes = kMaxN * kBK * 2;            // 32 KB
+constexpr int kStageBytes = kAStageBytes + kBStageBytes;
+constexpr int kGemmSmem = kStages * kStageBytes + 1024;  // + slack to align the ring to 1024 B
 constexpr unsigned kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor (tcgen05): start address, leading byte
-// offset (K-direction core-matrix stride), stride byte offset (M/N-direction
-// core-matrix stride), version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor (tcgen05) of a K-major operand in the
+// 128-byte-swizzled layout that TMA writes: start address, stride between
+// 8-row core-matrix groups 1024 B, fixed field 0b001 at bit 46, swizzle mode
+// 2 (128 B) at bit 61; the leading-dimension offset is unused for swizzled
+// K-major operands (set to 1).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -76,81 +88,109 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     return false;
 }
 
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
 __global__ void __launch_bounds__(kGemmThreads, 1)
-qmc_gemm_bf16_tc(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B, float *__restrict__ C,
-                 int M, int N, int K, int ldc, unsigned *err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar;
+qmc_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float *C,
+                 int N, int K, int chunks_per_split, size_t split_stride, unsigned *err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base;
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + kAChunkBytes;
+    __shared__ int issued, consumed;
+    unsigned char *ring = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kTileM;
+    const int nchunks = (K + kBK - 1) / kBK;
+    const int c0 = blockIdx.y * chunks_per_split;
+    const int nc = min(nchunks, c0 + chunks_per_split) - c0;   // >= 1 by the host's split choice
+    float *Cs = C + (size_t)blockIdx.y * split_stride;
 
     if (warp == 0) {
-        const uint32_t dst = smem_u32(&tmem_base);
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kMaxN));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kMaxN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::);
+        issued = 0;
+        consumed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
     const uint32_t tmem = tmem_base;
-    const uint32_t mb = smem_u32(&mbar);
-    const uint32_t idesc = instr_desc_bf16(kTileM, N);
-    const int ngroups = N >> 3;
+    const uint32_t bytes_stage = (uint32_t)((kTileM + N) * kBK * 2);
     bool ok = true;
-    uint32_t phase = 0;
 
-    for (int k0 = 0; k0 < K; k0 += kChunkK) {
-        const int kc = min(kChunkK, K - k0);   // multiple of 16
-        const int cgroups = kc >> 3;
-        // stage A[m0 .. m0+127][k0 .. k0+kc) : core matrix (g, c) at (c * 16 + g) * 128 bytes
-        for (int idx = tid; idx < kTileM * cgroups; idx += kGemmThreads) {
-            const int row = idx / cgroups, c = idx % cgroups;
-            const uint4 v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + row) * K + k0 + c * 8);
-            *reinterpret_cast<uint4 *>(sA + ((c * 16 + (row >> 3)) * 128 + (row & 7) * 16)) = v;
+    if (tid == 0) {
+        // producer: TMA into the ring, each stage reused once the MMAs reading it committed
+        for (int i = 0; i < nc; ++i) {
+            const int s = i % kStages;
+            if (i >= kStages && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / kStages - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const uint32_t fb = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes_stage)
+                         : "memory");
+            const uint32_t sa = smem_u32(ring + s * kStageBytes);
+            tma_load_2d(sa, &mapA, (c0 + i) * kBK, m0, fb);
+            tma_load_2d(sa + kAStageBytes, &mapB, (c0 + i) * kBK, 0, fb);
+            issued = i + 1;
         }
-        // stage B[0 .. N)[k0 .. k0+kc): core matrix (g, c) at (c * N/8 + g) * 128 bytes
-        for (int idx = tid; idx < N * cgroups; idx += kGemmThreads) {
-            const int row = idx / cgroups, c = idx % cgroups;
-            const uint4 v = *reinterpret_cast<const uint4 *>(B + (size_t)row * K + k0 + c * 8);
-            *reinterpret_cast<uint4 *>(sB + ((c * ngroups + (row >> 3)) * 128 + (row & 7) * 16)) = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (tid == 32) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc_bf16(kTileM, N);
+        for (int i = 0; i < nc; ++i) {
+            const int s = i % kStages;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / kStages) & 1))) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::);
-            for (int ks = 0; ks < kc / 16; ++ks) {
-                const uint64_t da = smem_desc(smem_u32(sA) + ks * 2 * 16 * 128, 16 * 128, 128);
-                const uint64_t db = smem_desc(smem_u32(sB) + ks * 2 * ngroups * 128, ngroups * 128, 128);
-                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t sa = smem_u32(ring + s * kStageBytes);
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks) {
+                const uint64_t da = smem_desc_sw128(sa + ks * 32);
+                const uint64_t db = smem_desc_sw128(sa + kAStageBytes + ks * 32);
+                const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
                     "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
                          : "memory");
+            consumed = i + 1;
         }
-        // the MMAs must finish reading this chunk before it is overwritten
-        if (!mbar_wait(mb, phase)) ok = false;
-        phase ^= 1u;
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
+        // completion of every MMA issued so far
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
     }
+    if (!mbar_wait(smem_u32(&done), 0)) ok = false;
+    ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
     if (ok) {
         // warp w owns TMEM lanes 32w..32w+31 = rows m0 + 32w + lane
         const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < N; c0 += 16) {
+        for (int c = 0; c < N; c += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                 "%13, %14, %15}, [%16];"
@@ -159,27 +199,84 @@ qmc_gemm_bf16_tc(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__res
                   "=r"(r[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
-                float *dst = C + (size_t)row * ldc + c0;
+            float *dst = Cs + (size_t)row * N + c;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) dst[q] = __uint_as_float(r[q]);
-            }
+            for (int q = 0; q < 16; ++q) dst[q] = __uint_as_float(r[q]);
         }
-    } else if (tid == 0) {
-        atomicAdd(err, 1u);
+    } else {
+        if (tid == 0) {
+            atomicAdd(err, 1u);
+            // copies still in flight land before the CTA's shared memory goes away
+            for (int i = consumed; i < issued; ++i)
+                mbar_wait(smem_u32(&full[i % kStages]), (uint32_t)((i / kStages) & 1));
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::);
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMaxN));
 }
 
+// C = sum over splits of W[s] (in split order)
+__global__ void qmc_gemm_splitk_sum(const float *W, int splits, size_t stride, float *C, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float acc = W[i];
+        for (int s = 1; s < splits; ++s) acc += W[(size_t)s * stride + i];
+        C[i] = acc;
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2-D bf16 tensor [rows][K] (row stride K), box {64, box_rows}, 128-byte swizzle,
+// zero fill beyond K
+bool make_map(CUtensorMap *map, const void *ptr, int rows, int K, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// split-K workspace, grown on demand (one per process; calls on one device)
+struct SplitWorkspace {
+    std::mutex mu;
+    float *ptr = nullptr;
+    size_t cap = 0;
+};
+SplitWorkspace &workspace() {
+    static SplitWorkspace w;
+    return w;
+}
+
 }  // namespace
 
 // C[M][N] = A[M][K] B[N][K]^T, device pointers; M % 128 == 0, K % 16 == 0,
-// N % 16 == 0 and 16 <= N <= 256; rows/cols contiguous (ldc = N).
+// N % 16 == 0 and 16 <= N <= 256; A, B 16-byte aligned; C rows contiguous
+// (ldc = N). Split-K when the M tiles leave most SMs idle.
 extern "C" int qmc_k_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
                                void *stream) {
     if (M <= 0 || M % 128 || K <= 0 || K % 16 || N < 16 || N > 256 || N % 16) return -2;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return -2;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(qmc_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem) !=
@@ -187,9 +284,45 @@ extern "C" int qmc_k_gemm_bf16(const void *A, const void *B, float *C, int M, in
             return -1;
         attr_set = true;
     }
-    qmc_gemm_bf16_tc<<<M / 128, kGemmThreads, kGemmSmem, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, C, M, N, K, N, err_dev);
+    CUtensorMap mapA, mapB;
+    if (!make_map(&mapA, A, M, K, kTileM) || !make_map(&mapB, B, N, K, N)) return -1;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int mt = M / kTileM, nchunks = (K + kBK - 1) / kBK;
+    int splits = std::max(1, std::min(nchunks, sms / mt));
+    const int per = (nchunks + splits - 1) / splits;
+    splits = (nchunks + per - 1) / per;   // every split has at least one chunk
+    const size_t mn = (size_t)M * N;
+    float *out = C;
+    std::unique_lock<std::mutex> lock(workspace().mu, std::defer_lock);
+    if (splits > 1) {
+        lock.lock();
+        SplitWorkspace &w = workspace();
+        if (w.cap < (size_t)splits * mn) {
+            cudaStreamSynchronize((cudaStream_t)stream);
+            cudaFree(w.ptr);
+            w.ptr = nullptr;
+            w.cap = 0;
+            if (cudaMalloc(&w.ptr, (size_t)splits * mn * sizeof(float)) != cudaSuccess) return -1;
+            w.cap = (size_t)splits * mn;
+        }
+        out = w.ptr;
+    }
+    qmc_gemm_bf16_tc<<<dim3(mt, splits), kGemmThreads, kGemmSmem, (cudaStream_t)stream>>>(mapA, mapB, out, N, K,
+                                                                                           per, mn, err_dev);
+    if (splits > 1) {
+        const unsigned blocks = (unsigned)std::min<size_t>((mn + 255) / 256, 4096);
+        qmc_gemm_splitk_sum<<<blocks, 256, 0, (cudaStream_t)stream>>>(out, splits, mn, C, mn);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+extern "C" int qmc_gemm_bf16_device(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
+                                    void *stream) {
+    if (!A || !B || !C || !err_dev) return QMC_E_INVAL_LOCAL;
+    const int rc = qmc_k_gemm_bf16(A, B, C, M, N, K, err_dev, stream);
+    return rc == -2 ? QMC_E_INVAL_LOCAL : (rc ? QMC_E_CUDA_LOCAL : 0);
 }
 
 // Host-buffer wrapper (tests and small callers): copies in, runs, copies out.
@@ -462,12 +595,12 @@ int mlp_forward_dev(qmc_mlp *m, int Bp) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// loss and gradients (into m->grads) for Bp rows with x, y, mask, wt in place
-int mlp_backward_dev(qmc_mlp *m, int Bp, int B) {
+// loss (into *loss_dst) and gradients (into m->grads) for Bp rows with x, y, mask, wt in place
+int mlp_backward_dev(qmc_mlp *m, int Bp, int B, double *loss_dst) {
     const int H = m->H, D = m->D, Nop = m->Nop, No = m->No;
-    cudaMemsetAsync(m->loss, 0, sizeof(double), m->stream);
+    cudaMemsetAsync(loss_dst, 0, sizeof(double), m->stream);
     mlp_loss<<<nblk((size_t)Bp * Nop), 256, 0, m->stream>>>(m->out, m->y, m->wt, m->mask, No, Nop, Bp, 1.f / B,
-                                                            m->dob, m->dobT, m->dof, m->loss);
+                                                            m->dob, m->dobT, m->dof, loss_dst);
     // output layer: dWout^T = h_{D-1}^T dout  ([H][Nop]), dbout, dh = dout Wout
     if (qmc_k_gemm_bf16(m->hbT[D - 1], m->dobT, m->tmp, H, Nop, Bp, m->err, m->stream)) return -1;
     mlp_untranspose<<<nblk((size_t)No * H), 256, 0, m->stream>>>(m->tmp, H, Nop, No, m->grads + m->offW[D]);
@@ -642,7 +775,7 @@ int qmc_mlp_grad(qmc_mlp *m, const float *x, const float *y, const float *wt, in
     cudaSetDevice(m->device);
     cudaMemsetAsync(m->err, 0, 4, m->stream);
     const int Bp = (B + 127) / 128 * 128;
-    if (mlp_stage(m, x, y, wt, B, Bp) || mlp_forward_dev(m, Bp) || mlp_backward_dev(m, Bp, B))
+    if (mlp_stage(m, x, y, wt, B, Bp) || mlp_forward_dev(m, Bp) || mlp_backward_dev(m, Bp, B, m->loss))
         return QMC_E_CUDA_LOCAL;
     double l = 0.0;
     cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
@@ -660,20 +793,32 @@ int qmc_mlp_train(qmc_mlp *m, const float *x, const float *y, const float *wt, i
     const int Bp = (B + 127) / 128 * 128;
     if (mlp_stage(m, x, y, wt, B, Bp)) return QMC_E_CUDA_LOCAL;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    for (int s = 0; s < steps; ++s) {
-        if (mlp_forward_dev(m, Bp) || mlp_backward_dev(m, Bp, B)) return QMC_E_CUDA_LOCAL;
+    // per-step losses stay on the device until the end (no host round trip per step)
+    double *hist = nullptr;
+    if (cudaMalloc(&hist, (size_t)std::max(steps, 1) * sizeof(double)) != cudaSuccess) return QMC_E_CUDA_LOCAL;
+    int rc = 0;
+    for (int s = 0; s < steps && !rc; ++s) {
+        if (mlp_forward_dev(m, Bp) || mlp_backward_dev(m, Bp, B, hist + s)) {
+            rc = QMC_E_CUDA_LOCAL;
+            break;
+        }
         ++m->t;
         const float c1 = 1.f - std::pow(b1, (float)m->t), c2 = 1.f - std::pow(b2, (float)m->t);
         mlp_adam<<<nblk(m->nparams), 256, 0, m->stream>>>(m->params, m->grads, m->am, m->av, m->nparams, lr, b1,
                                                            b2, eps, c1, c2);
-        if (mlp_sync_weights(m)) return QMC_E_CUDA_LOCAL;
-        if (losses) {
-            double l = 0.0;
-            cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
-            cudaStreamSynchronize(m->stream);
-            losses[s] = (float)l;
-        }
+        if (mlp_sync_weights(m)) rc = QMC_E_CUDA_LOCAL;
     }
+    if (!rc && losses && steps > 0) {
+        std::vector<double> h(steps);
+        if (cudaMemcpyAsync(h.data(), hist, steps * sizeof(double), cudaMemcpyDeviceToHost, m->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(m->stream) != cudaSuccess)
+            rc = QMC_E_CUDA_LOCAL;
+        for (int s = 0; s < steps && !rc; ++s) losses[s] = (float)h[s];
+    }
+    cudaStreamSynchronize(m->stream);
+    cudaFree(hist);
+    if (rc) return rc;
     return mlp_check_err(m) ? QMC_E_CUDA_LOCAL : 0;
 }
 

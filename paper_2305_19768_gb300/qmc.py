@@ -113,6 +113,7 @@ def lib():
                 "qmc_autotune": ([vp, P(qmc_job), i32, i32, i32, P(i32), P(i32)], i32),
                 "qmc_median_candidates": ([u64, i32, i32, u64, P(ctypes.c_uint32)], i32),
                 "qmc_gemm_bf16": ([P(ctypes.c_uint16), P(ctypes.c_uint16), P(ctypes.c_float), i32, i32, i32], i32),
+                "qmc_gemm_bf16_device": ([vp, vp, vp, i32, i32, i32, vp, vp], i32),
                 "qmc_mlp_create": ([P(vp), i32, i32, i32, i32, i32, u64], i32),
                 "qmc_mlp_destroy": ([vp], None),
                 "qmc_mlp_num_params": ([vp, P(sz)], i32),
@@ -149,7 +150,7 @@ def exported_symbols():
             "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
-            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_mlp_create",
+            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_gemm_bf16_device", "qmc_mlp_create",
             "qmc_mlp_destroy", "qmc_mlp_num_params", "qmc_mlp_get_params", "qmc_mlp_set_params",
             "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train", "qmc_integrate_ex"]
 
@@ -339,6 +340,14 @@ def qmc_gemm_bf16(A_bits, B_bits):
                                      B_bits.ctypes.data_as(P(ctypes.c_uint16)),
                                      C.ctypes.data_as(P(ctypes.c_float)), M, N, K))
     return C
+
+
+def qmc_gemm_bf16_device(A_ptr, B_ptr, C_ptr, M, N, K, err_ptr, stream_ptr=0):
+    """The same GEMM on device pointers (e.g. torch data_ptr()), enqueued on
+    `stream_ptr`; err_ptr points at a caller-zeroed device unsigned."""
+    _check(None, lib().qmc_gemm_bf16_device(ctypes.c_void_p(A_ptr), ctypes.c_void_p(B_ptr), ctypes.c_void_p(C_ptr),
+                                            M, N, K, ctypes.c_void_p(err_ptr),
+                                            ctypes.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 def _fp(a):

@@ -85,3 +85,23 @@ def test_mlp_training_fits_a_smooth_map():
         assert np.sqrt(np.mean((net.forward(xt) - target(xt)) ** 2)) < 0.05
     finally:
         net.close()
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 2048), (2048, 48, 256), (19456, 256, 1024)])
+def test_gemm_bf16_device_buffers_and_split_k(M, N, K):
+    # device-pointer entry point: split-K (few M tiles, long K) and a grid of
+    # one M tile per SM; reference = FP64 product of the same bf16 operands
+    torch = pytest.importorskip("torch")
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda", dtype=torch.float32)
+    err = torch.zeros(1, device="cuda", dtype=torch.int32)
+    qmc.qmc_gemm_bf16_device(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, err.data_ptr())
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    a, b = A.double(), B.double()
+    ref = a @ b.T
+    bound = (K / 16 + 2) * 2.0 ** -24 * (a.abs() @ b.abs().T) + 1e-30
+    worst = float(((C.double() - ref).abs() / bound).max())
+    assert worst <= 1.0, worst
