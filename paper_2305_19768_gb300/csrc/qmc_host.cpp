@@ -165,6 +165,8 @@ int classify(qmc_ctx *ctx, HostSector &S, int si) {
         S.cls = QMC_CLASS_CPLX3;
     } else if (S.d <= 3 && S.ns <= 2) {
         S.cls = QMC_CLASS_REAL3;
+    } else if (S.ns <= 2) {
+        S.cls = QMC_CLASS_REAL6S;
     } else {
         S.cls = QMC_CLASS_REAL6;
     }
@@ -923,7 +925,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
         if (cls < 0) cls = S.cls;
         if (S.cls != cls)
             return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: all jobs must use one evaluator class");
-        if (cls == QMC_CLASS_REAL6 || norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
+        if (qmc_class_big(cls) || norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
             return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d not supported by the evaluator", i, lo, hi);
         QmcJobDev &D = recs[i];
         memset(&D, 0, sizeof D);

@@ -11,6 +11,8 @@
 
 #include "qmc_ctx.h"
 
+static_assert(QMC_NCLASS == QMC_NUM_CLASSES, "evaluator class count of the C-ABI");
+
 #define fail qmc_fail
 
 namespace {

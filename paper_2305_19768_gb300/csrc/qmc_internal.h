@@ -86,20 +86,29 @@ struct QmcLaunch {
 enum QmcClass {
     QMC_CLASS_REAL3 = 0,   // real integrand, d <= 3, <= 2 singular variables
     QMC_CLASS_CPLX3 = 1,   // contour-deformed, d <= 3, <= 2 singular variables
-    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6, <= 4 singular variables
+    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6, 3 or 4 singular variables
     QMC_CLASS_REAL3M = 3,  // REAL3 with FP32 monomial products
     QMC_CLASS_REAL6M = 4,  // REAL6 with FP32 monomial products
-    QMC_NCLASS = 5
+    QMC_CLASS_REAL6S = 5,  // real integrand, d <= 6, <= 2 singular variables (4 corners)
+    QMC_CLASS_REAL6SM = 6, // REAL6S with FP32 monomial products
+    QMC_NCLASS = 7
 };
 
-static inline bool qmc_class_big(int cls) { return cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M; }
+static inline bool qmc_class_big(int cls) {
+    return cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M || cls == QMC_CLASS_REAL6S || cls == QMC_CLASS_REAL6SM;
+}
 // Series length (orders) each class supports: K + ns + 1 <= class_lmax.
 static inline int qmc_class_lmax(int cls) { return qmc_class_big(cls) ? 6 : 4; }
 static inline int qmc_class_dmax(int cls) { return qmc_class_big(cls) ? 6 : 3; }
-static inline int qmc_class_smax(int cls) { return qmc_class_big(cls) ? 4 : 2; }
+static inline int qmc_class_smax(int cls) { return (cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M) ? 4 : 2; }
 // The mixed-precision variant of a real class (deformed sectors stay FP64).
 static inline int qmc_class_mixed(int cls) {
-    return cls == QMC_CLASS_REAL3 ? QMC_CLASS_REAL3M : (cls == QMC_CLASS_REAL6 ? QMC_CLASS_REAL6M : cls);
+    switch (cls) {
+        case QMC_CLASS_REAL3: return QMC_CLASS_REAL3M;
+        case QMC_CLASS_REAL6: return QMC_CLASS_REAL6M;
+        case QMC_CLASS_REAL6S: return QMC_CLASS_REAL6SM;
+        default: return cls;
+    }
 }
 
 extern "C" {

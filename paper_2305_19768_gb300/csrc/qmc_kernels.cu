@@ -326,18 +326,24 @@ __device__ __forceinline__ void assemble(int ns, int lo, int hi, int nord, const
                 }
             }
         }
-        double e[LMAX];
-        e[0] = 1.0;
-#pragma unroll
-        for (int l = 1; l < LMAX; ++l) e[l] = (l < nP) ? e[l - 1] * E * (1.0 / l) : 0.0;
         T PE[LMAX];
+        if (P == full) {
+            // every singular variable in the pole set: no exp(eps E_P) factor
 #pragma unroll
-        for (int k = 0; k < LMAX; ++k) {
-            PE[k] = zero<T>();
-            if (k < nP && k >= lo + np) {
-                PE[k] = g[P][k];
+            for (int k = 0; k < LMAX; ++k) PE[k] = (k < nP && k >= lo + np) ? g[P][k] : zero<T>();
+        } else {
+            double e[LMAX];
+            e[0] = 1.0;
 #pragma unroll
-                for (int i = 0; i < k; ++i) PE[k] = PE[k] + mulsc(g[P][i], e[k - i]);
+            for (int l = 1; l < LMAX; ++l) e[l] = (l < nP) ? e[l - 1] * E * (1.0 / l) : 0.0;
+#pragma unroll
+            for (int k = 0; k < LMAX; ++k) {
+                PE[k] = zero<T>();
+                if (k < nP && k >= lo + np) {
+                    PE[k] = g[P][k];
+#pragma unroll
+                    for (int i = 0; i < k; ++i) PE[k] = PE[k] + mulsc(g[P][i], e[k - i]);
+                }
             }
         }
         // res[o] += A * PE[lo + o + np] (index selected without local memory)
@@ -993,6 +999,8 @@ extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt
         case QMC_CLASS_REAL6: return launch_cls<6, 4, 6, false, false>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL3M: return launch_cls<3, 2, 4, false, true>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL6M: return launch_cls<6, 4, 6, false, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6S: return launch_cls<6, 2, 6, false, false>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6SM: return launch_cls<6, 2, 6, false, true>(L, block, ppt, grid, st);
         default: return -2;
     }
 }
@@ -1050,6 +1058,8 @@ extern "C" int qmc_k_occupancy(int cls, int block) {
         case QMC_CLASS_REAL6: return occupancy_cls<6, 4, 6, false, false>(block);
         case QMC_CLASS_REAL3M: return occupancy_cls<3, 2, 4, false, true>(block);
         case QMC_CLASS_REAL6M: return occupancy_cls<6, 4, 6, false, true>(block);
+        case QMC_CLASS_REAL6S: return occupancy_cls<6, 2, 6, false, false>(block);
+        case QMC_CLASS_REAL6SM: return occupancy_cls<6, 2, 6, false, true>(block);
         default: return 0;
     }
 }

@@ -30,6 +30,9 @@ ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIM
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
 
+QMC_NUM_CLASSES = 7   # evaluator classes (include/qmc.h)
+
+
 class QmcError(RuntimeError):
     def __init__(self, code, msg=""):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -295,8 +298,8 @@ def qmc_presample_lambda(ctx, jobs, njobs, lo, norders, lambda_max=1.0, ncand=12
 
 
 def qmc_autotune(ctx, jobs, njobs, lo, norders):
-    bb = (ctypes.c_int * 5)()
-    bp = (ctypes.c_int * 5)()
+    bb = (ctypes.c_int * QMC_NUM_CLASSES)()
+    bp = (ctypes.c_int * QMC_NUM_CLASSES)()
     _check(ctx, lib().qmc_autotune(ctx, jobs, njobs, lo, norders, bb, bp))
     return list(bb), list(bp)
 
