@@ -211,6 +211,7 @@ struct TileSmem {
     float cvalf[QMC_MAXMONO];
     double delta[QMC_DMAX];
     double invb[QMC_SMAX];
+    double invb_full;  // prod over the singular slots of 1/b_q (A of the full pole set)
     double logtab[3 * QMC_LOG_TABLE_ROWS];
     double w140d;  // 140^d of the staged sector
     unsigned long long tile;
@@ -278,7 +279,8 @@ template <int SMAX, int LMAX, class T>
 __device__ __forceinline__ void assemble(int ns, int lo, int hi, int nord, const T (&BV)[1 << SMAX],
                                          const T (&LV)[1 << SMAX], const double (&it)[SMAX],
                                          const double (&lt)[SMAX], const double (&bq)[SMAX],
-                                         const double (&invb)[SMAX], T (&res)[LMAX]) {
+                                         const double (&invb)[SMAX], double A_empty, double A_full,
+                                         T (&res)[LMAX]) {
     constexpr int NG = 1 << SMAX;
     const int full = (1 << ns) - 1;
     T g[NG][LMAX];
@@ -314,14 +316,17 @@ __device__ __forceinline__ void assemble(int ns, int lo, int hi, int nord, const
         const int np = __popc(P);
         const int nP = hi + np + 1;
         if (nP < 1) continue;
-        double A = 1.0, E = 0.0;
+        // A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q; the empty and the
+        // full pole set come precomputed
+        const bool Aknown = (P == 0) || (P == full);
+        double A = P == 0 ? A_empty : (P == full ? A_full : 1.0), E = 0.0;
 #pragma unroll
         for (int q = 0; q < SMAX; ++q) {
             if (q < ns) {
                 if (P & (1 << q)) {
-                    A *= invb[q];
+                    if (!Aknown) A *= invb[q];
                 } else {
-                    A *= it[q];
+                    if (!Aknown) A *= it[q];
                     if (nP > 1) E = fma(bq[q], lt[q], E);
                 }
             }
@@ -462,9 +467,30 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
                     tq = t[j];
                     bb = sec.b[j];
                 }
-            it[q] = qrcp(tq);
+            it[q] = tq;   // the reciprocal follows below, in pairs
             bq[q] = bb;
             if (need_lt) lt[q] = qlog(tq, tab);
+        }
+    }
+    // 1/t_q in pairs: 1/a = b / (a b), one reciprocal per pair; for two
+    // singular variables that reciprocal is also A of the empty pole set
+    double A_empty = 1.0;
+    if (ns == 2) {
+        const double r = qrcp(it[0] * it[1]);
+        const double t0 = it[0];
+        it[0] = it[1] * r;
+        it[1] = t0 * r;
+        A_empty = r;
+    } else {
+#pragma unroll
+        for (int q = 0; q < SMAX; ++q)
+            if (q < ns) it[q] = qrcp(it[q]);
+        if (ns == 1) A_empty = it[0];
+        else if (ns > 2) {
+            A_empty = it[0];
+#pragma unroll
+            for (int q = 1; q < SMAX; ++q)
+                if (q < ns) A_empty *= it[q];
         }
     }
     // corners: B_V = Cc U^u0 F^f0, Lambda_V = Lc + ln(U^u1 F^f1) (one log when
@@ -473,6 +499,25 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     const bool comb = (sec.pad1 & 1) != 0;
     double BV[NG], LV[NG];
     const int full = (1 << ns) - 1;
+    // 1/F at the corners that need it, in pairs of corners (V, V + 1)
+    double FiV[NG];
+#pragma unroll
+    for (int V = 0; V < NG; V += 2) {
+        const double Fa = hF[(NG - 1) ^ V], Fb = hF[(NG - 1) ^ (V + 1)];
+        const bool na = V <= full && ((sec.f0_int && f0 < 0) || (hi + __popc(V) >= 1 && comb && f1 < 0));
+        const bool nb = V + 1 <= full && ((sec.f0_int && f0 < 0) || (hi + __popc(V + 1) >= 1 && comb && f1 < 0));
+        FiV[V] = 0.0;
+        FiV[V + 1] = 0.0;
+        if (na && nb) {
+            const double r = qrcp(Fa * Fb);
+            FiV[V] = Fb * r;
+            FiV[V + 1] = Fa * r;
+        } else if (na) {
+            FiV[V] = qrcp(Fa);
+        } else if (nb) {
+            FiV[V + 1] = qrcp(Fb);
+        }
+    }
 #pragma unroll
     for (int V = 0; V < NG; ++V) {
         BV[V] = 0.0;
@@ -482,9 +527,8 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
         const double U = hU[(NG - 1) ^ V];
         const double F = hF[(NG - 1) ^ V];
         const bool needUinv = (sec.u0_int && u0 < 0) || (lam_here && comb && u1 < 0);
-        const bool needFinv = (sec.f0_int && f0 < 0) || (lam_here && comb && f1 < 0);
         const double Ui = needUinv ? qrcp(U) : 0.0;
-        const double Fi = needFinv ? qrcp(F) : 0.0;
+        const double Fi = FiV[V];
         // B = Cc U^u0 F^f0 without multiplications by unit factors (the
         // conditions are uniform over the tile's sector)
         double B = 1.0;
@@ -513,7 +557,7 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     double ib[SMAX];
 #pragma unroll
     for (int q = 0; q < SMAX; ++q) ib[q] = S.invb[q];
-    assemble<SMAX, LMAX, double>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, res);
+    assemble<SMAX, LMAX, double>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, A_empty, S.invb_full, res);
 }
 
 // ---------------------------------------------------------------- deformed integrand
@@ -697,7 +741,11 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
     double ib[SMAX];
 #pragma unroll
     for (int q = 0; q < SMAX; ++q) ib[q] = S.invb[q];
-    assemble<SMAX, LMAX, dc>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, res);
+    double A_empty = 1.0;
+#pragma unroll
+    for (int q = 0; q < SMAX; ++q)
+        if (q < ns) A_empty = q == 0 ? it[0] : A_empty * it[q];
+    assemble<SMAX, LMAX, dc>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, A_empty, S.invb_full, res);
 }
 
 // ---------------------------------------------------------------- tile staging
@@ -736,6 +784,9 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
         if (threadIdx.x == 0) {
             S.cached_sector = sidx;
             S.cached_point = pidx;
+            double af = 1.0;
+            for (int q = 0; q < S.sec.ns; ++q) af *= 1.0 / S.sec.b[S.sec.sing[q]];
+            S.invb_full = af;
             double w = 1.0;
             for (int j = 0; j < S.sec.d; ++j) w *= 140.0;
             S.w140d = w;
