@@ -65,7 +65,7 @@ def _workloads():
                  "eps^0, n={n} CBC, m={m} shifts"),
         # two-loop planar massless double box, Euclidean point
         "box2L_planar_massless": dict(
-            make=w.double_box_massless, kin=[[-3.0, -1.0]], lo=-4, nord=5, n=100003, m=32, deform=False,
+            make=w.double_box_massless, kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
             desc="box2L_planar_massless s=-3 t=-1, 282 sectors d=6, eps^-4..eps^0, n={n} CBC, m={m} shifts"),
     }
 
