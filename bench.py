@@ -10,7 +10,8 @@ C-ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload box1L_massless|triangle_massive|box1L_massive_batch|
-                                box2L_planar_massless] [--precision fp64|mixed]
+                                box1L_massless_physical|box2L_planar_massless]
+                    [--precision fp64|mixed]
 
 The default workload and precision are the ones above; the others measure
 the same metric on the finite massive triangle, the 1024-point deformed
@@ -63,6 +64,13 @@ def _workloads():
             m=32, deform=True,
             desc="box1L_massive m^2=1, 1024 (s,t) s~U[5,20] t~U[-8,-1] seed 3, 4 sectors d=3 deformed, "
                  "eps^0, n={n} CBC, m={m} shifts"),
+        # massless box in the physical region at the same 1024 points: deformed
+        # sectors with subtraction corners (the amplitude scan's costliest class)
+        "box1L_massless_physical": dict(
+            make=lambda: w.box_massless(deform=True), kin=w.massive_box_points(1024, seed=3).tolist(), lo=-2,
+            nord=3, n=10007, m=32, deform=True,
+            desc="box1L_massless deformed, 1024 (s,t) s~U[5,20] t~U[-8,-1] seed 3, 12 sectors d=3, "
+                 "eps^-2..eps^0, n={n} CBC, m={m} shifts"),
         # two-loop planar massless double box, Euclidean point
         "box2L_planar_massless": dict(
             make=w.double_box_massless, kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
@@ -200,7 +208,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box1L_massless",
-                    choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box2L_planar_massless"])
+                    choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box1L_massless_physical",
+                             "box2L_planar_massless"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--n", type=int, default=0, help="lattice size (default: the workload's)")
     ap.add_argument("--shifts", type=int, default=0, help="random shifts (default: the workload's)")

@@ -413,6 +413,13 @@ int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out);
  * within 1 ulp of the correctly rounded 1/x. Same arguments and errors. */
 int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out);
 
+/* The evaluator's own two-argument arctangent (table-driven reduction by
+ * atan(j/64), one division, a degree-7 series; IEEE sign conventions for
+ * signed zeros) applied on the device to host arrays y[n], x[n] -> out[n],
+ * for verification: within 4 ulp. Errors: QMC_E_INVAL for non-finite
+ * input or (0, 0). */
+int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, double *out);
+
 /* Measure the FP64 fused-multiply-add throughput of the device (the
  * roofline denominator of the evaluator): *gflops = 2 * DFMA / s over a
  * dependent-chain-free loop timed with CUDA events. */

@@ -11,6 +11,10 @@ Rounding the leading parts to the 2^-42 grid makes e * LN2_HI + LOGF_HI[j]
 exact for every binary exponent |e| < 2^10. Values come from mpmath at 60
 digits and are written as C99 hexadecimal floating constants.
 
+The same header carries the table of the evaluator's two-argument arctangent:
+for j = 0..64, ATAN_HI[j] = RN(atan(j/64)), ATAN_LO[j] = RN(atan(j/64) -
+ATAN_HI[j]), and pi/2, pi as (RN, RN(remainder)) pairs.
+
 Usage: python make_log_table.py   (rewrites qmc_log_table.h beside it)
 """
 import os
@@ -41,6 +45,16 @@ def main():
     ln2 = mp.log(2)
     ln2_hi = grid42(ln2)
     ln2_lo = rn(ln2 - mp.mpf(ln2_hi))
+    atan_rows = []
+    for j in range(65):
+        a = mp.atan(mp.mpf(j) / 64)
+        ah = rn(a)
+        atan_rows.append((ah, rn(a - mp.mpf(ah))))
+    pio2 = mp.pi / 2
+    pio2_hi = rn(pio2)
+    pio2_lo = rn(pio2 - mp.mpf(pio2_hi))
+    pi_hi = rn(mp.pi)
+    pi_lo = rn(mp.pi - mp.mpf(pi_hi))
     with open(OUT, "w") as fh:
         fh.write("// Table of the evaluator's FP64 logarithm (written by make_log_table.py).\n")
         fh.write("// Row j: RN(1/F_j), ln(F_j) on the 2^-42 grid, RN(remainder); F_j = 1 + j/1024.\n")
@@ -50,6 +64,14 @@ def main():
         fh.write("#define QMC_LOG_TABLE_INIT { \\\n")
         for inv, hi, lo in rows:
             fh.write(f"    {inv.hex()}, {hi.hex()}, {lo.hex()}, \\\n")
+        fh.write("}\n")
+        fh.write("// Row j: RN(atan(j/64)), RN(remainder).\n")
+        fh.write(f"#define QMC_PIO2_HI {pio2_hi.hex()}\n#define QMC_PIO2_LO {pio2_lo.hex()}\n")
+        fh.write(f"#define QMC_PI_HI {pi_hi.hex()}\n#define QMC_PI_LO {pi_lo.hex()}\n")
+        fh.write("#define QMC_ATAN_TABLE_ROWS 65\n")
+        fh.write("#define QMC_ATAN_TABLE_INIT { \\\n")
+        for hi, lo in atan_rows:
+            fh.write(f"    {hi.hex()}, {lo.hex()}, \\\n")
         fh.write("}\n")
 
 

@@ -21,6 +21,7 @@
 extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void *stream);
 extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_rcp(const double *x_dev, uint64_t n, double *out_dev, void *stream);
+extern "C" int qmc_k_atan2(const double *yx_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_occupancy(int cls, int block);
 
 namespace {
@@ -861,6 +862,33 @@ int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out) {
 
 int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out) {
     return fp64_apply(ctx, x, n, out, "qmc_fp64_rcp", qmc_k_rcp);
+}
+
+int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, double *out) {
+    if (!ctx || (n && (!x || !y || !out))) return fail(ctx, QMC_E_INVAL, "qmc_fp64_atan2: bad arguments");
+    std::vector<double> yx(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || (x[i] == 0.0 && y[i] == 0.0))
+            return fail(ctx, QMC_E_INVAL, "qmc_fp64_atan2: (y, x)[%zu] is not finite or is (0, 0)", i);
+        yx[2 * i] = y[i];
+        yx[2 * i + 1] = x[i];
+    }
+    if (n == 0) return QMC_OK;
+    cudaSetDevice(ctx->device);
+    double *dyx = nullptr, *dout = nullptr;
+    int rc = QMC_OK;
+    if (cudaMalloc(&dyx, 2 * n * sizeof(double)) != cudaSuccess || cudaMalloc(&dout, n * sizeof(double)) != cudaSuccess) {
+        rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_atan2: allocation failed");
+    } else {
+        cudaMemcpyAsync(dyx, yx.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (qmc_k_atan2(dyx, n, dout, ctx->stream)) rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_atan2: kernel launch failed");
+        cudaMemcpyAsync(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (!rc && e != cudaSuccess) rc = fail(ctx, QMC_E_CUDA, "qmc_fp64_atan2: %s", cudaGetErrorString(e));
+    }
+    cudaFree(dyx);
+    cudaFree(dout);
+    return rc;
 }
 
 int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {

@@ -29,6 +29,7 @@
 namespace {
 
 __device__ const double kLogTable[3 * QMC_LOG_TABLE_ROWS] = QMC_LOG_TABLE_INIT;
+__device__ const double kAtanTable[2 * QMC_ATAN_TABLE_ROWS] = QMC_ATAN_TABLE_INIT;
 
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
 
@@ -125,6 +126,41 @@ __device__ __forceinline__ double qrcp(double x) {
     return fma(y, e, y);
 }
 
+// Two-argument arctangent of finite (y, x), not both zero, table-driven:
+// with mn <= mx the smaller and larger of |x|, |y| and c = j/64 nearest
+// mn/mx (the index from an FP32 estimate), atan(mn/mx) = atan(c) +
+// atan(delta), delta = (mn - c mx) / (mx + c mn) (one division, |delta| <=
+// 2^-7); atan(delta) by its Taylor series to delta^7 (truncation below
+// 2^-58 relative); then the octant: pi/2 - r where |y| > |x|, pi - r where
+// x < 0 (sign bit, so -0 counts), and the sign of y. Measured worst case
+// about 2 ulp. 19 FP64 operations. `tab` holds rows {atan(j/64) hi, lo}.
+__device__ __forceinline__ double qatan2(double y, double x, const double *tab) {
+    const long long xb = __double_as_longlong(x), yb = __double_as_longlong(y);
+    const long long ab = xb & 0x7FFFFFFFFFFFFFFFLL, bb = yb & 0x7FFFFFFFFFFFFFFFLL;
+    const bool swap = bb > ab;
+    const long long mnb = swap ? ab : bb, mxb = swap ? bb : ab;
+    const double mn = __longlong_as_double(mnb), mx = __longlong_as_double(mxb);
+    int j = 0;
+    const int de = (int)(mxb >> 52) - (int)(mnb >> 52);
+    if (de <= 7 && mnb != 0) {
+        const float fmn = __int_as_float(0x3F800000 | (int)((mnb >> 29) & 0x7FFFFF));
+        const float fmx = __int_as_float(0x3F800000 | (int)((mxb >> 29) & 0x7FFFFF));
+        const float w = __fdividef(fmn, fmx) * __int_as_float((127 - de) << 23);
+        j = min(__float2int_rn(w * 64.0f), 64);
+    }
+    // c = j / 64 from the bits of j
+    const double c = j ? __longlong_as_double(__double_as_longlong(u32_to_double((uint64_t)j)) - (6LL << 52)) : 0.0;
+    const double num = fma(-c, mx, mn);
+    const double den = fma(c, mn, mx);
+    const double dl = num * qrcp(den);
+    const double s2 = dl * dl;
+    const double q = fma(fma(s2, -1.0 / 7.0, 0.2), s2, -1.0 / 3.0);
+    double r = tab[2 * j] + (tab[2 * j + 1] + fma(dl * s2, q, dl));
+    if (swap) r = (QMC_PIO2_HI - r) + QMC_PIO2_LO;
+    if (xb < 0) r = (QMC_PI_HI - r) + QMC_PI_LO;
+    return __longlong_as_double(__double_as_longlong(r) ^ (yb & (long long)0x8000000000000000ULL));
+}
+
 // ---------------------------------------------------------------- complex
 struct dc {
     double re, im;
@@ -151,8 +187,8 @@ __device__ __forceinline__ float arg32(dc a, bool m0) {
 }
 // Principal log; on the real axis the argument is taken from below
 // (x - i0), the prescription of F - i0.
-__device__ __forceinline__ dc clog_m0(dc a, const double *tab) {
-    double arg = (a.im == 0.0) ? (a.re < 0.0 ? -CUDART_PI : 0.0) : atan2(a.im, a.re);
+__device__ __forceinline__ dc clog_m0(dc a, const double *tab, const double *atab) {
+    double arg = (a.im == 0.0) ? (a.re < 0.0 ? -CUDART_PI : 0.0) : qatan2(a.im, a.re, atab);
     return dc{0.5 * qlog(fma(a.re, a.re, a.im * a.im), tab), arg};
 }
 __device__ __forceinline__ dc cexp_(dc a) {
@@ -213,6 +249,7 @@ struct TileSmem {
     double invb[QMC_SMAX];
     double invb_full;  // prod over the singular slots of 1/b_q (A of the full pole set)
     double logtab[3 * QMC_LOG_TABLE_ROWS];
+    double atantab[2 * QMC_ATAN_TABLE_ROWS];
     double w140d;  // 140^d of the staged sector
     unsigned long long tile;
     int cached_sector, cached_point;
@@ -575,6 +612,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
     const int full = (1 << ns) - 1;
     const int dbase = sec.nU + sec.nF;
     const double *tab = S.logtab;
+    const double *atab = S.atantab;
     dc BV[NG], LV[NG];
     double it[SMAX], lt[SMAX], bq[SMAX];
 #pragma unroll
@@ -645,8 +683,13 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                 }
                 H[k][j] = H[j][k];
             }
-        dc z[DMAX], J[DMAX][DMAX];
+        // J = 1 - i V with V real: V_jk = lambda_j (t_j (1-t_j) H_jk + delta_jk (1 - 2 t_j) dF_j).
+        // det(1 + X) = 1 + tr X + E2(X) + det X (E2: sum of principal 2 x 2
+        // minors) with X = -i V gives det J = (1 - E2(V)) + i (det V - tr V) in
+        // real arithmetic (d = 2: (1 - det V) - i tr V; d = 1: 1 - i V_00).
+        dc z[DMAX];
         dc rho[DMAX];
+        double Vm[DMAX][DMAX];
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) {
             const double lam = S.job.lambda[j];
@@ -654,10 +697,8 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
             z[j] = C(tc[j], -tc[j] * g);
             rho[j] = C(1.0, -g);
 #pragma unroll
-            for (int k = 0; k < DMAX; ++k) {
-                double v = lam * (tc[j] * oc[j] * H[j][k] + (j == k ? (oc[j] - tc[j]) * dF[j] : 0.0));
-                J[j][k] = C(j == k ? 1.0 : 0.0, -v);
-            }
+            for (int k = 0; k < DMAX; ++k)
+                Vm[j][k] = lam * (tc[j] * oc[j] * H[j][k] + (j == k ? (oc[j] - tc[j]) * dF[j] : 0.0));
             if (j >= d) {
                 z[j] = C(1.0);
                 rho[j] = C(1.0);
@@ -665,13 +706,19 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
         }
         dc detJ;
         if (d == 1) {
-            detJ = J[0][0];
+            detJ = C(1.0, -Vm[0][0]);
         } else if (d == 2) {
-            detJ = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            const double detV = fma(Vm[0][0], Vm[1][1], -Vm[0][1] * Vm[1][0]);
+            detJ = C(1.0 - detV, -(Vm[0][0] + Vm[1][1]));
         } else {
-            detJ = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                   J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                   J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            const double c00 = fma(Vm[1][1], Vm[2][2], -Vm[1][2] * Vm[2][1]);
+            const double c01 = fma(Vm[1][0], Vm[2][2], -Vm[1][2] * Vm[2][0]);
+            const double c02 = fma(Vm[1][0], Vm[2][1], -Vm[1][1] * Vm[2][0]);
+            const double detV = fma(Vm[0][0], c00, fma(-Vm[0][1], c01, Vm[0][2] * c02));
+            const double e2 = c00 + fma(Vm[0][0], Vm[1][1], -Vm[0][1] * Vm[1][0]) +
+                              fma(Vm[0][0], Vm[2][2], -Vm[0][2] * Vm[2][0]);
+            const double trV = Vm[0][0] + Vm[1][1] + Vm[2][2];
+            detJ = C(1.0 - e2, detV - trV);
         }
         dc zp[DMAX][QMC_EMAX];
         powers<DMAX, dc>(z, d, sec.pad0, zp);
@@ -697,7 +744,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                         mul_ipow<dc>(rho[j], sec.bi[j], Xn, Xd);
                         sarg = fmaf((float)sec.bi[j], arg32(rho[j], false), sarg);
                     } else {
-                        lsum = lsum + clog_m0(rho[j], tab) * sec.b[j];
+                        lsum = lsum + clog_m0(rho[j], tab, atab) * sec.b[j];
                     }
                 }
             } else if ((sec.regular_mask >> j) & 1) {
@@ -707,7 +754,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                         mul_ipow<dc>(z[j], sec.bi[j], Xn, Xd);
                         sarg = fmaf((float)sec.bi[j], arg32(z[j], false), sarg);
                     } else {
-                        lsum = lsum + clog_m0(z[j], tab) * sec.b[j];
+                        lsum = lsum + clog_m0(z[j], tab, atab) * sec.b[j];
                     }
                 }
             }
@@ -715,8 +762,8 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
         const bool needU = (lam_here && sec.u1 != 0.0 && !comb_all) || !sec.u0_int;
         const bool needF = (lam_here && sec.f1 != 0.0 && !comb_all) || !sec.f0_int;
         dc lU = zero<dc>(), lF = zero<dc>();
-        if (needU) lU = clog_m0(U, tab);
-        if (needF) lF = clog_m0(F, tab);
+        if (needU) lU = clog_m0(U, tab, atab);
+        if (needF) lF = clog_m0(F, tab, atab);
         if (sec.u0_int) mul_ipow<dc>(U, (int)sec.u0, num, den);
         else num = num * cexp_(lU * sec.u0);
         if (sec.f0_int) mul_ipow<dc>(F, (int)sec.f0, num, den);
@@ -729,7 +776,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                 mul_ipow<dc>(F, sec.f1i, Xn, Xd);
                 sarg = fmaf((float)sec.f1i, arg32(F, true), sarg);
                 const dc X = Xn * conj_(Xd);                  // |Xd|^2 Xn / Xd
-                const double phi = atan2(X.im, X.re);
+                const double phi = qatan2(X.im, X.re, atab);
                 const float kf = rintf((sarg - __double2float_rn(phi)) * 0.15915494f);
                 LV[V] = dc{0.5 * qlog(norm_(Xn) * qrcp(norm_(Xd)), tab),
                            fma((double)kf, 2.0 * CUDART_PI, phi)};
@@ -809,6 +856,8 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
         S.cached_point = -1;
     }
     for (int i = threadIdx.x; i < 3 * QMC_LOG_TABLE_ROWS; i += blockDim.x) S.logtab[i] = kLogTable[i];
+    if (CPLX)
+        for (int i = threadIdx.x; i < 2 * QMC_ATAN_TABLE_ROWS; i += blockDim.x) S.atantab[i] = kAtanTable[i];
     for (;;) {
         int signfail_tile = 0;
         __syncthreads();  // previous tile fully consumed
@@ -1000,6 +1049,11 @@ __global__ void qmc_rcp_kernel(const double *x, uint64_t n, double *out) {
     if (i < n) out[i] = qrcp(x[i]);
 }
 
+__global__ void qmc_atan2_kernel(const double *yx, uint64_t n, double *out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = qatan2(yx[2 * i], yx[2 * i + 1], kAtanTable);
+}
+
 __global__ void qmc_shift_kernel(uint64_t state, int m, int d, double *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m * d) out[i] = splitmix_uniform(state, (uint64_t)i);
@@ -1082,6 +1136,12 @@ extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void 
 extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream) {
     if (n == 0) return 0;
     qmc_log_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+extern "C" int qmc_k_atan2(const double *yx_dev, uint64_t n, double *out_dev, void *stream) {
+    if (n == 0) return 0;
+    qmc_atan2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(yx_dev, n, out_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -109,6 +109,7 @@ def lib():
                 "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
                 "qmc_fp64_log": ([vp, P(dbl), sz, P(dbl)], i32),
                 "qmc_fp64_rcp": ([vp, P(dbl), sz, P(dbl)], i32),
+                "qmc_fp64_atan2": ([vp, P(dbl), P(dbl), sz, P(dbl)], i32),
                 "qmc_shift_stats": ([P(dbl), i32, i32, P(dbl), P(dbl)], i32),
                 "qmc_plan_use_graph": ([vp, i32], i32),
                 "qmc_plan_job_failures": ([vp, P(ctypes.c_uint32)], i32),
@@ -150,7 +151,7 @@ def exported_symbols():
             "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
-            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp",
+            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp", "qmc_fp64_atan2",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
             "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_gemm_bf16_device", "qmc_mlp_create",
@@ -448,6 +449,14 @@ def qmc_fp64_log(ctx, x):
     x = np.ascontiguousarray(x, dtype=np.float64)
     out = np.zeros_like(x)
     _check(ctx, lib().qmc_fp64_log(ctx, _dp(x), x.size, _dp(out)))
+    return out
+
+
+def qmc_fp64_atan2(ctx, y, x):
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    _check(ctx, lib().qmc_fp64_atan2(ctx, _dp(y), _dp(x), x.size, _dp(out)))
     return out
 
 

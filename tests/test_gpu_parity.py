@@ -82,6 +82,21 @@ def test_evaluator_reciprocal_within_one_ulp(gpu):
     assert err.max() <= 1.0, (err.max(), xs[np.argmax(err)])
 
 
+def test_evaluator_atan2_within_4_ulp(gpu):
+    rng = np.random.default_rng(8)
+    th = rng.uniform(-np.pi, np.pi, 100000)
+    r = np.exp(rng.uniform(-20, 20, 100000))
+    y = np.concatenate([r * np.sin(th), rng.uniform(-1, 1, 50000) * 10.0 ** rng.uniform(-30, 30, 50000),
+                        np.array([0.0, -0.0, 1.0, -1.0, 1e-300, 0.0, -0.0])])
+    x = np.concatenate([r * np.cos(th), rng.uniform(-1, 1, 50000) * 10.0 ** rng.uniform(-30, 30, 50000),
+                        np.array([-1.0, -1.0, -0.0, 0.0, -1.0, 2.0, 3.0])])
+    got = qmc.qmc_fp64_atan2(gpu.ctx, y, x)
+    ref = np.arctan2(y, x)               # libm, within 1 ulp; signed-zero conventions of IEEE
+    err = np.abs(got - ref) / np.maximum(np.spacing(np.abs(ref)), np.spacing(0.0))
+    assert err.max() <= 4.0, (err.max(), y[np.argmax(err)], x[np.argmax(err)])
+    assert np.array_equal(np.signbit(got), np.signbit(ref))
+
+
 def test_evaluator_log_within_1_5_ulp(gpu):
     rng = np.random.default_rng(5)
     xs = np.concatenate([rng.uniform(0.5, 2.0, 200000), np.exp(rng.uniform(-700, 700, 200000)),
