@@ -95,10 +95,12 @@ typedef struct {
 #define QMC_TRANSFORM_BAKER 1
 #define QMC_TRANSFORM_NONE 2
 
-/* Arithmetic of the evaluator for undeformed sectors. FP64: everything in
- * FP64. MIXED: the monomial products of U and F and their group sums in
- * FP32; the korobov3 weight, logs and powers of U and F, the series
- * assembly and all reductions in FP64. Deformed sectors always run FP64. */
+/* Arithmetic of the evaluator. FP64: everything in FP64. MIXED: the
+ * monomial products of U and F and their group sums in FP32 (for deformed
+ * sectors also the first and second derivatives of F at the real point and
+ * U and F at the complex point z); the korobov3 weight, the deformation
+ * matrix and det J, logs and powers of U and F, the series assembly and all
+ * reductions in FP64. */
 #define QMC_PRECISION_FP64 0
 #define QMC_PRECISION_MIXED 1
 
@@ -116,11 +118,13 @@ typedef struct {
                               as (out >> 11) * 2^-53 */
     double lambda[6];      /* deformation parameter per variable (deformed sectors) */
     uint32_t z[6];         /* explicit generating vector, each z_j in U_n (z[0] = 0: the table's) */
-    int32_t flags;         /* QMC_JOB_UNSHIFTED: evaluate the unshifted rule (Delta = 0) */
+    int32_t flags;         /* QMC_JOB_UNSHIFTED: evaluate the unshifted rule (Delta = 0);
+                              QMC_JOB_FP64: FP64 arithmetic even in a mixed-precision context */
     int32_t pad;
 } qmc_job;
 
 #define QMC_JOB_UNSHIFTED 1
+#define QMC_JOB_FP64 2
 
 /* Create a context on CUDA device `device`. `opt` may be NULL (defaults).
  * On success *out owns all device memory the context allocates; free with
@@ -248,13 +252,14 @@ int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int nor
 /* Autotune the evaluator's launch shape per kernel class (0: real d <= 3,
  * 1: deformed d <= 3, 2: real d <= 6 with 3 or 4 singular variables, 3 and
  * 4: the mixed-precision variants of 0 and 2, 5: real d <= 6 with at most 2
- * singular variables, 6: its mixed-precision variant): on up to 32 of the
+ * singular variables, 6: its mixed-precision variant, 7: the mixed-precision
+ * variant of 1): on up to 32 of the
  * given jobs per class (at most 8 shifts each) every block size in
  * {128, 256} and points per thread in {4, 8, 16, 32} is timed with CUDA
  * events; the fastest is kept in the context and used by later plans whose
  * options leave block/ppt at 0. best_block/best_ppt (may be NULL) receive
  * QMC_NUM_CLASSES entries (0 = class absent). */
-#define QMC_NUM_CLASSES 7
+#define QMC_NUM_CLASSES 8
 int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
                  int *best_ppt);
 
@@ -331,6 +336,7 @@ typedef struct {
     int iterations;         /* evaluation passes */
     uint64_t max_lattice;   /* largest lattice any sector reached */
     double presample_evaluations;   /* lattice points x shifts of the lambda presampling */
+    int fp64_escalations;           /* sectors re-evaluated in FP64 in a mixed-precision context */
 } qmc_integrate_info;
 
 /* Adaptive integration of the sums (section "Adaptive weighted sum
@@ -343,7 +349,10 @@ typedef struct {
  * lattices with qmc_allocate (alpha = 2, w_i = var_i n_i^2, tau_i from the
  * measured kernel time split by a per-sector cost model), rounding up to
  * tabulated lattices (<= max_points; options.max_growth limits the growth
- * per pass). Deformed sectors use options.lambda, or, when it is 0, a lambda
+ * per pass; in a mixed-precision context a sector that would need more than
+ * max_points, or has reached it short of its target, is evaluated again in
+ * FP64, below the FP32 products' error floor). Deformed sectors use
+ * options.lambda, or, when it is 0, a lambda
  * per (point, sector) chosen once by presampling; a sector whose evaluation
  * fails the sign check (a point with Im F > 0) is presampled again with
  * candidates below its lambda and evaluated again (at most 8 such rounds,

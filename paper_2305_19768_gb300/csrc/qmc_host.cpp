@@ -526,7 +526,8 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
                 return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
             zvec = it->second;
         }
-        const int cls = ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(S.cls) : S.cls;
+        const bool mixed = ctx->opt.precision == QMC_PRECISION_MIXED && !(J.flags & QMC_JOB_FP64);
+        const int cls = mixed ? qmc_class_mixed(S.cls) : S.cls;
         if (norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
             return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d with %d poles exceed the evaluator's series length %d",
                         i, lo, hi, S.ns, qmc_class_lmax(cls));

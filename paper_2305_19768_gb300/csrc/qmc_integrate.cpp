@@ -173,6 +173,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
         int p, i, s;
         uint64_t n = 0;
         bool have = false, dirty = true;
+        bool fp64 = false;   // escalated to FP64 in a mixed-precision context
         double mean[2 * 8], var[2 * 8];
         double cost = 1.0;
         double lambda = 0.3;
@@ -274,6 +275,7 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
             J.n = sl.n;
             J.seed = ctx->opt.seed;
             J.stream = ((uint64_t)iter << 40) | q;
+            J.flags = sl.fp64 ? QMC_JOB_FP64 : 0;
             for (int j = 0; j < 6; ++j) J.lambda[j] = sl.lambda;
             jobs.push_back(J);
             jslot.push_back(q);
@@ -308,20 +310,19 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
                 cudaEventElapsedTime(&ms, plan->kev[2 * c], plan->kev[2 * c + 1]);
                 kernel_s += ms * 1e-3;
                 double ev = 0.0, cw = 0.0;
-                auto eff = [&](const QmcHostSector &S) {
-                    return ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(S.cls) : S.cls;
+                auto eff = [&](const qmc_job &J) {
+                    const QmcHostSector &S = ctx->integrals[J.integral_id].sectors[J.sector];
+                    return ctx->opt.precision == QMC_PRECISION_MIXED && !(J.flags & QMC_JOB_FP64)
+                               ? qmc_class_mixed(S.cls) : S.cls;
                 };
                 for (size_t j = 0; j < jobs.size(); ++j) {
-                    const QmcHostSector &S = ctx->integrals[jobs[j].integral_id].sectors[jobs[j].sector];
-                    if (eff(S) != plan->launches[c].cls) continue;
+                    if (eff(jobs[j]) != plan->launches[c].cls) continue;
                     ev += (double)jobs[j].n * m;
                     cw += (double)jobs[j].n * m * slots[jslot[j]].cost;
                 }
                 const double per_cost = cw > 0 ? ms * 1e-3 / cw : 1e-9;
-                for (size_t j = 0; j < jobs.size(); ++j) {
-                    const QmcHostSector &S = ctx->integrals[jobs[j].integral_id].sectors[jobs[j].sector];
-                    if (eff(S) == plan->launches[c].cls) tau[jslot[j]] = per_cost * slots[jslot[j]].cost;
-                }
+                for (size_t j = 0; j < jobs.size(); ++j)
+                    if (eff(jobs[j]) == plan->launches[c].cls) tau[jslot[j]] = per_cost * slots[jslot[j]].cost;
                 evals += ev;
             }
             qmc_plan_destroy(plan);
@@ -456,6 +457,14 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
                     qmc_allocate(W.data(), tv.data(), &V, 1, (int)members.size(), alpha, 0.0, nn.data());
                     for (size_t u = 0; u < members.size(); ++u) {
                         Slot &sl = slots[members[u]];
+                        if (ctx->opt.precision == QMC_PRECISION_MIXED && !sl.fp64 &&
+                            (nn[u] > (double)nmax_cap || sl.n >= nmax_cap)) {
+                            // beyond the lattice cap in mixed precision: the FP32 products'
+                            // error floor, not the lattice, limits this sector -- FP64 from here
+                            sl.fp64 = true;
+                            sl.dirty = true;
+                            grew = true;
+                        }
                         uint64_t want = round_up(nn[u]);
                         if (ctx->opt.max_growth > 1 && (double)want > (double)sl.n * ctx->opt.max_growth)
                             want = std::max(round_down((double)sl.n * ctx->opt.max_growth), round_up((double)sl.n + 1));
@@ -497,6 +506,9 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
         for (const Slot &sl : slots) mx = std::max(mx, sl.n);
         info->max_lattice = mx;
         info->presample_evaluations = ctx->presample_evals - presample_evals0;
+        int esc = 0;
+        for (const Slot &sl : slots) esc += sl.fp64 ? 1 : 0;
+        info->fp64_escalations = esc;
     }
     if (rc_final == QMC_E_TIMEOUT) return fail(ctx, QMC_E_TIMEOUT, "qmc_integrate: timeout after %d iterations", iter);
     if (rc_final == QMC_E_NOT_CONVERGED)

@@ -91,7 +91,8 @@ enum QmcClass {
     QMC_CLASS_REAL6M = 4,  // REAL6 with FP32 monomial products
     QMC_CLASS_REAL6S = 5,  // real integrand, d <= 6, <= 2 singular variables (4 corners)
     QMC_CLASS_REAL6SM = 6, // REAL6S with FP32 monomial products
-    QMC_NCLASS = 7
+    QMC_CLASS_CPLX3M = 7,  // CPLX3 with FP32 monomial products (derivatives of F, U and F at z)
+    QMC_NCLASS = 8
 };
 
 static inline bool qmc_class_big(int cls) {
@@ -101,12 +102,13 @@ static inline bool qmc_class_big(int cls) {
 static inline int qmc_class_lmax(int cls) { return qmc_class_big(cls) ? 6 : 4; }
 static inline int qmc_class_dmax(int cls) { return qmc_class_big(cls) ? 6 : 3; }
 static inline int qmc_class_smax(int cls) { return (cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M) ? 4 : 2; }
-// The mixed-precision variant of a real class (deformed sectors stay FP64).
+// The mixed-precision variant of a class.
 static inline int qmc_class_mixed(int cls) {
     switch (cls) {
         case QMC_CLASS_REAL3: return QMC_CLASS_REAL3M;
         case QMC_CLASS_REAL6: return QMC_CLASS_REAL6M;
         case QMC_CLASS_REAL6S: return QMC_CLASS_REAL6SM;
+        case QMC_CLASS_CPLX3: return QMC_CLASS_CPLX3M;
         default: return cls;
     }
 }

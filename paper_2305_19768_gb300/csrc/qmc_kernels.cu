@@ -198,18 +198,32 @@ __device__ __forceinline__ dc cexp_(dc a) {
     return dc{e * c, e * s};
 }
 
+// complex FP32 (mixed-precision monomial products of the deformed evaluator)
+struct fc {
+    float re, im;
+};
+__device__ __forceinline__ fc operator+(fc a, fc b) { return fc{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ fc operator*(fc a, fc b) {
+    return fc{fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ fc to_fc(dc a) { return fc{__double2float_rn(a.re), __double2float_rn(a.im)}; }
+__device__ __forceinline__ dc to_dc(fc a) { return dc{(double)a.re, (double)a.im}; }
+
 // scalar-generic helpers
 __device__ __forceinline__ float mulsc(float a, float s) { return a * s; }
+__device__ __forceinline__ fc mulsc(fc a, float s) { return fc{a.re * s, a.im * s}; }
 __device__ __forceinline__ double mulsc(double a, double s) { return a * s; }
 __device__ __forceinline__ dc mulsc(dc a, double s) { return a * s; }
 template <class T> __device__ __forceinline__ T zero();
 template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
 template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
 template <> __device__ __forceinline__ dc zero<dc>() { return dc{0.0, 0.0}; }
+template <> __device__ __forceinline__ fc zero<fc>() { return fc{0.0f, 0.0f}; }
 template <class T> __device__ __forceinline__ T from_real(double);
 template <> __device__ __forceinline__ float from_real<float>(double x) { return (float)x; }
 template <> __device__ __forceinline__ double from_real<double>(double x) { return x; }
 template <> __device__ __forceinline__ dc from_real<dc>(double x) { return dc{x, 0.0}; }
+template <> __device__ __forceinline__ fc from_real<fc>(double x) { return fc{(float)x, 0.0f}; }
 template <class T> __device__ __forceinline__ T one() { return from_real<T>(1.0); }
 __device__ __forceinline__ double re_of(double a) { return a; }
 __device__ __forceinline__ double re_of(dc a) { return a.re; }
@@ -601,7 +615,7 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
 // z_j = t_j - i lambda_j t_j (1 - t_j) dF/dt_j at the (corner) point, with
 // rho_j = z_j / t_j for singular variables and J = dz/dt; every quantity of
 // G is recomputed at each corner t' = t with t_V = 0.
-template <int DMAX, int SMAX, int LMAX>
+template <int DMAX, int SMAX, int LMAX, bool MIXED>
 __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const double (&t)[DMAX],
                                               const double (&omt)[DMAX], int lo, int hi, int nord,
                                               dc (&res)[LMAX], int &signfail) {
@@ -661,28 +675,56 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
                     }
             }
         }
-        double tp[DMAX][QMC_EMAX];
-        powers<DMAX, double>(tc, d, sec.pad0, tp);
+        // derivatives of F at the corner point (real); MIXED: FP32 monomial
+        // products and sums, converted to FP64 for V and det J
         double dF[DMAX], H[DMAX][DMAX];
+        if constexpr (MIXED) {
+            float tcf[DMAX], tpf[DMAX][QMC_EMAX];
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j) {
-            dF[j] = 0.0;
-            if (j < d)
-                dF[j] = poly_sum<DMAX, double>(S.exps, S.cval, dbase + sec.dFoff[j],
-                                               dbase + sec.dFoff[j] + sec.dFn[j], tp);
-        }
+            for (int j = 0; j < DMAX; ++j) tcf[j] = __double2float_rn(tc[j]);
+            powers<DMAX, float>(tcf, d, sec.pad0, tpf);
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j)
-#pragma unroll
-            for (int k = j; k < DMAX; ++k) {
-                H[j][k] = 0.0;
-                if (j < d && k < d) {
-                    const int h = j * QMC_DMAX - j * (j - 1) / 2 + (k - j);  // host packing order
-                    H[j][k] = poly_sum<DMAX, double>(S.exps, S.cval, dbase + sec.Hoff[h],
-                                                     dbase + sec.Hoff[h] + sec.Hn[h], tp);
-                }
-                H[k][j] = H[j][k];
+            for (int j = 0; j < DMAX; ++j) {
+                dF[j] = 0.0;
+                if (j < d)
+                    dF[j] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, dbase + sec.dFoff[j],
+                                                          dbase + sec.dFoff[j] + sec.dFn[j], tpf);
             }
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j)
+#pragma unroll
+                for (int k = j; k < DMAX; ++k) {
+                    H[j][k] = 0.0;
+                    if (j < d && k < d) {
+                        const int h = j * QMC_DMAX - j * (j - 1) / 2 + (k - j);  // host packing order
+                        H[j][k] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, dbase + sec.Hoff[h],
+                                                                dbase + sec.Hoff[h] + sec.Hn[h], tpf);
+                    }
+                    H[k][j] = H[j][k];
+                }
+        } else {
+            double tp[DMAX][QMC_EMAX];
+            powers<DMAX, double>(tc, d, sec.pad0, tp);
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j) {
+                dF[j] = 0.0;
+                if (j < d)
+                    dF[j] = poly_sum<DMAX, double>(S.exps, S.cval, dbase + sec.dFoff[j],
+                                                   dbase + sec.dFoff[j] + sec.dFn[j], tp);
+            }
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j)
+#pragma unroll
+                for (int k = j; k < DMAX; ++k) {
+                    H[j][k] = 0.0;
+                    if (j < d && k < d) {
+                        const int h = j * QMC_DMAX - j * (j - 1) / 2 + (k - j);  // host packing order
+                        H[j][k] = poly_sum<DMAX, double>(S.exps, S.cval, dbase + sec.Hoff[h],
+                                                         dbase + sec.Hoff[h] + sec.Hn[h], tp);
+                    }
+                    H[k][j] = H[j][k];
+                }
+        }
         // J = 1 - i V with V real: V_jk = lambda_j (t_j (1-t_j) H_jk + delta_jk (1 - 2 t_j) dF_j).
         // det(1 + X) = 1 + tr X + E2(X) + det X (E2: sum of principal 2 x 2
         // minors) with X = -i V gives det J = (1 - E2(V)) + i (det V - tr V) in
@@ -720,10 +762,22 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
             const double trV = Vm[0][0] + Vm[1][1] + Vm[2][2];
             detJ = C(1.0 - e2, detV - trV);
         }
-        dc zp[DMAX][QMC_EMAX];
-        powers<DMAX, dc>(z, d, sec.pad0, zp);
-        const dc U = poly_sum<DMAX, dc>(S.exps, S.cval, sec.gU[0], sec.nU, zp);
-        const dc F = poly_sum<DMAX, dc>(S.exps, S.cval, sec.nU, sec.nU + sec.nF, zp);
+        dc U, F;
+        if constexpr (MIXED) {
+            // U and F at z from FP32 complex monomial products; everything
+            // after (powers and logs of U and F, det J, the assembly) is FP64
+            fc zf[DMAX], zpf[DMAX][QMC_EMAX];
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j) zf[j] = to_fc(z[j]);
+            powers<DMAX, fc>(zf, d, sec.pad0, zpf);
+            U = to_dc(poly_sum<DMAX, fc>(S.exps, S.cvalf, sec.gU[0], sec.nU, zpf));
+            F = to_dc(poly_sum<DMAX, fc>(S.exps, S.cvalf, sec.nU, sec.nU + sec.nF, zpf));
+        } else {
+            dc zp[DMAX][QMC_EMAX];
+            powers<DMAX, dc>(z, d, sec.pad0, zp);
+            U = poly_sum<DMAX, dc>(S.exps, S.cval, sec.gU[0], sec.nU, zp);
+            F = poly_sum<DMAX, dc>(S.exps, S.cval, sec.nU, sec.nU + sec.nF, zp);
+        }
         if (F.im > 0.0) ++signfail;
         // all exponents integers: the corner's eps exponent is one complex log,
         // ln X with X = prod rho_j^b_j prod z_j^b_j U^u1 F^f1, whose imaginary
@@ -956,7 +1010,7 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
                 if (nonneg_is_zero(W) || zero_t) continue;
                 T res[LMAX];
                 if constexpr (CPLX) {
-                    eval_deformed<DMAX, SMAX, LMAX>(S, t, omt, lo, hi, nord, res, signfail_tile);
+                    eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
                 } else {
                     eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
                 }
@@ -1106,6 +1160,7 @@ extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt
         case QMC_CLASS_REAL6M: return launch_cls<6, 4, 6, false, true>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL6S: return launch_cls<6, 2, 6, false, false>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL6SM: return launch_cls<6, 2, 6, false, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_CPLX3M: return launch_cls<3, 2, 4, true, true>(L, block, ppt, grid, st);
         default: return -2;
     }
 }
@@ -1171,6 +1226,7 @@ extern "C" int qmc_k_occupancy(int cls, int block) {
         case QMC_CLASS_REAL6M: return occupancy_cls<6, 4, 6, false, true>(block);
         case QMC_CLASS_REAL6S: return occupancy_cls<6, 2, 6, false, false>(block);
         case QMC_CLASS_REAL6SM: return occupancy_cls<6, 2, 6, false, true>(block);
+        case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block);
         default: return 0;
     }
 }

@@ -30,7 +30,7 @@ ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIM
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
 
-QMC_NUM_CLASSES = 7   # evaluator classes (include/qmc.h)
+QMC_NUM_CLASSES = 8   # evaluator classes (include/qmc.h)
 
 
 class QmcError(RuntimeError):
@@ -57,7 +57,8 @@ class qmc_sum_spec(ctypes.Structure):
 class qmc_integrate_info(ctypes.Structure):
     _fields_ = [("evaluations", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("kernel_seconds", ctypes.c_double), ("iterations", ctypes.c_int),
-                ("max_lattice", ctypes.c_uint64), ("presample_evaluations", ctypes.c_double)]
+                ("max_lattice", ctypes.c_uint64), ("presample_evaluations", ctypes.c_double),
+                ("fp64_escalations", ctypes.c_int)]
 
 
 class qmc_job(ctypes.Structure):

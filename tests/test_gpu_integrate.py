@@ -127,3 +127,23 @@ def test_sign_check_failure_is_presampled_again():
     (a, ea), (b, eb) = vals
     sig = np.hypot(abs(ea), abs(eb))
     assert abs(a - b) <= 5 * sig
+
+
+def test_mixed_precision_escalates_to_fp64_at_the_lattice_cap():
+    # with the lattice capped at the pilot size and a request the pilot cannot
+    # meet, every mixed-precision sector is evaluated again in FP64; an FP64
+    # context never escalates
+    I = w.box_massless()
+    for precision, expect in ((qmc.QMC_PRECISION_MIXED, True), (qmc.QMC_PRECISION_FP64, False)):
+        ctx = _ctx(precision=precision, max_points=1009, min_points=1009)
+        try:
+            iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+            qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+            val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-10, lowest_order=-2, norders=3,
+                                                   check=False)
+            assert rc == -5
+            assert (info["fp64_escalations"] > 0) == expect, info
+            if expect:
+                assert info["fp64_escalations"] == len(I.sectors)
+        finally:
+            qmc.qmc_destroy(ctx)
