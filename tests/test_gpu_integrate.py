@@ -147,3 +147,28 @@ def test_mixed_precision_escalates_to_fp64_at_the_lattice_cap():
                 assert info["fp64_escalations"] == len(I.sectors)
         finally:
             qmc.qmc_destroy(ctx)
+
+
+def test_amplitude_with_coefficient_strings():
+    # the coefficient-series amplitude of test_amplitude_with_coefficient_series,
+    # given as strings: parsed, expanded exactly, handed to the same call
+    from paper_2305_19768_gb300.inputs.coefficients import coefficient_series
+
+    coef, coef_lo = coefficient_series([["(4 - eps^2)/(2 + eps)", "6/2"]], 2, [{"s": -3.0, "t": -2.0}], 1)
+    assert coef_lo == 0 and coef.shape == (1, 1, 2, 2)
+    assert np.array_equal(coef[0, 0], np.array([[2.0, -1.0], [3.0, 0.0]]))
+    ctx = _ctx()
+    try:
+        ib = qmc.qmc_load_sectors_mem(ctx, w.box_massless().to_text())
+        it = qmc.qmc_load_sectors_mem(ctx, w.triangle_massive().to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+        val, err, info, rc = qmc.qmc_integrate(ctx, [ib, it], coef=coef, coef_lo=coef_lo, epsrel=1e-7,
+                                               lowest_order=-2, norders=3)
+        assert rc == 0
+        b = closed_form("box1L_massless", "s=-3,t=-2")
+        t0 = closed_form("triangle_m1_pm1")[0]
+        exact = [2 * b[-2], 2 * b[-1] - b[-2], 2 * b[0] - b[-1] + 3 * t0]
+        for o in range(3):
+            _within(val[0, 0, o], err[0, 0, o], exact[o])
+    finally:
+        qmc.qmc_destroy(ctx)
