@@ -92,6 +92,9 @@ class SectorView:
 
     def __init__(self, integral, sector: int, inv, lam=None, transform: int = 0):
         s = integral.sectors[sector]
+        n2 = sum(1 for x in s.a if int(x) <= -2)
+        if any(int(x) < -2 for x in s.a) or n2 > 1 or (n2 and s.deform and lam is not None):
+            raise ValueError("subtraction of degree 1 covers one a_j = -2 per undeformed sector")
         self.d = s.d
         self.Ue, self.Uc = integral.coefficients_at(sector, "U", inv)
         self.Fe, self.Fc = integral.coefficients_at(sector, "F", inv)

@@ -247,7 +247,10 @@ static cplx det_leibniz(int d, const cplx *A) {
     return det;
 }
 
-static int is_singular(const orc_sector *S, int j) { return S->a[j] == -1; }
+/* singular: t_j^{a_j + b_j eps} with a_j = -1 (logarithmic) or -2 (one
+ * variable per sector, undeformed sectors only: subtraction of the Taylor
+ * polynomial of degree 1) */
+static int is_singular(const orc_sector *S, int j) { return S->a[j] <= -1; }
 
 /* G(t', eps): everything in the sector integrand except prod_{j in S}
  * t_j^{-1 + b_j eps}, at the real point tp (omtp = 1 - tp), as a series up
@@ -295,7 +298,7 @@ static series G_series(const orc_sector *S, const double *tp, const double *omtp
     for (int j = 0; j < d; ++j) {
         cplx base;
         double a, b;
-        if (is_singular(S, j)) { base = rho[j]; a = -1.0; b = S->b[j]; }
+        if (is_singular(S, j)) { base = rho[j]; a = (double)S->a[j]; b = S->b[j]; }
         else { base = z[j]; a = S->a[j]; b = S->b[j]; }
         if (a == 0.0 && b == 0.0) continue;
         cplx lg = clog(base);
@@ -318,11 +321,39 @@ static series G_series(const orc_sector *S, const double *tp, const double *omtp
     return G;
 }
 
+/* dG/dt_q at the real point tp for an undeformed sector: t_q enters G only
+ * through U and F, so dG/dt_q = G ((u0 + u1 eps) U_q / U + (f0 + f1 eps) F_q / F). */
+static series dG_series(const orc_sector *S, const double *tp, int q, int hi, int *signfail) {
+    int d = S->d;
+    cplx t[ORC_DMAX];
+    for (int j = 0; j < d; ++j) t[j] = tp[j];
+    int D[ORC_DMAX];
+    memset(D, 0, sizeof D);
+    D[q] = 1;
+    cplx U = poly_deriv(S->nU, d, S->Ue, S->Uc, t, NULL);
+    cplx F = poly_deriv(S->nF, d, S->Fe, S->Fc, t, NULL);
+    cplx Uq = poly_deriv(S->nU, d, S->Ue, S->Uc, t, D);
+    cplx Fq = poly_deriv(S->nF, d, S->Fe, S->Fc, t, D);
+    series G = G_series(S, tp, tp, hi, signfail);
+    series L;
+    memset(&L, 0, sizeof L);
+    L.lo = 0; L.n = 2;
+    L.c[0] = S->u0 * Uq / U + S->f0 * Fq / F;
+    L.c[1] = S->u1 * Uq / U + S->f1 * Fq / F;
+    return s_mul(&G, &L, hi);
+}
+
 /* The eps-expanded integrand at the transformed point t (omt = 1 - t):
  *   f = sum_{V subset of S} G(t with t_V = 0)
  *         prod_{j in V} (1/(b_j eps) - t_j^{-1+b_j eps}) prod_{j in S\V} t_j^{-1+b_j eps},
  * which integrates over [0,1]^d to the Laurent expansion of the sector
  * integral (each j in S: int t^{-1+b eps} g = g(0)/(b eps) + int t^{-1+b eps}(g - g(0))).
+ * A variable with a_j = -p, p = 2, takes the Taylor subtraction of degree 1:
+ *   int t^{-p+b eps} g = sum_{k<p} g^(k)(0)/k! / (k - p + 1 + b eps)
+ *                        + int t^{-p+b eps} (g - sum_{k<p} g^(k)(0) t^k / k!),
+ * so per singular variable the states are "t kept" (factor t^{-p+b eps})
+ * and k = 0..p-1 (t = 0, the k-th derivative of G, factor
+ * 1/(k - p + 1 + b eps) - t^{k-p+b eps}); f sums over all state choices.
  * Returns coefficients of eps^lo .. eps^hi in out[(o - lo)]. */
 static void integrand_series(const orc_sector *S, const double *t, const double *omt, int lo,
                              int hi, cplx *out, double *cond, int *signfail) {
@@ -337,24 +368,44 @@ static void integrand_series(const orc_sector *S, const double *t, const double 
     series total;
     memset(&total, 0, sizeof total);
     total.lo = lo; total.n = hi - lo + 1;
-    for (int V = 0; V < (1 << ns); ++V) {
+    /* state of slot q: 0 = t_q kept, k + 1 = (t_q = 0, k-th derivative), k < p_q */
+    int nstates = 1, radix[ORC_SMAX];
+    for (int q = 0; q < ns; ++q) {
+        radix[q] = 1 - S->a[sing[q]];          /* p_q + 1 */
+        nstates *= radix[q];
+    }
+    for (int st = 0; st < nstates; ++st) {
+        int state[ORC_SMAX], rem = st, dq = -1;
         double tp[ORC_DMAX], omtp[ORC_DMAX];
         for (int j = 0; j < d; ++j) { tp[j] = t[j]; omtp[j] = omt[j]; }
-        for (int q = 0; q < ns; ++q)
-            if (V & (1 << q)) { tp[sing[q]] = 0.0; omtp[sing[q]] = 1.0; }
-        series term = G_series(S, tp, omtp, H, signfail);
+        for (int q = 0; q < ns; ++q) {
+            state[q] = rem % radix[q];
+            rem /= radix[q];
+            if (state[q] > 0) { tp[sing[q]] = 0.0; omtp[sing[q]] = 1.0; }
+            if (state[q] == 2) dq = sing[q];
+        }
+        series term = dq >= 0 ? dG_series(S, tp, dq, H, signfail) : G_series(S, tp, omtp, H, signfail);
         for (int q = 0; q < ns; ++q) {
             int j = sing[q];
+            int p = -S->a[j];
             double b = S->b[j];
+            int k = state[q] - 1;
             series tpow = s_exp_eps(b * log(t[j]), H);
-            tpow = s_scale(&tpow, 1.0 / t[j]);          /* t^{-1 + b eps} */
+            tpow = s_scale(&tpow, pow(t[j], state[q] == 0 ? -p : k - p));   /* t^{c + b eps} */
             series fac;
-            if (V & (1 << q)) {
-                series pole;
-                memset(&pole, 0, sizeof pole);
-                pole.lo = -1; pole.n = 1; pole.c[0] = 1.0 / b;
+            if (state[q] > 0) {
+                int m = k - p + 1;                    /* 1/(m + b eps) */
+                series inv;
+                memset(&inv, 0, sizeof inv);
+                if (m == 0) {
+                    inv.lo = -1; inv.n = 1; inv.c[0] = 1.0 / b;
+                } else {
+                    inv.lo = 0; inv.n = H + 1;
+                    cplx c = 1.0 / m;
+                    for (int i = 0; i <= H; ++i) { inv.c[i] = c; c *= -b / m; }
+                }
                 series neg = s_scale(&tpow, -1.0);
-                fac = s_add(&pole, &neg, H);
+                fac = s_add(&inv, &neg, H);
             } else {
                 fac = tpow;
             }

@@ -46,7 +46,8 @@ class Sector:
 
     @property
     def singular(self) -> List[int]:
-        return [j for j in range(self.d) if self.a[j] == -1]
+        """Variables with a_j <= -1 (subtracted endpoint singularities)."""
+        return [j for j in range(self.d) if self.a[j] <= -1]
 
 
 def _normalize(U: LinPoly, F: LinPoly, a, b, u0, u1, f0, f1):
@@ -84,10 +85,10 @@ def decompose(U: LinPoly, F: LinPoly, u0, u1, f0, f1, *, deform=False, max_depth
                 if Fraction(x).denominator != 1:
                     raise DecompositionError("non-integer monomial exponent")
                 aa.append(int(x))
-                if aa[-1] < -1:
-                    raise DecompositionError(f"sector {origin}: exponent a_{j}={aa[-1]} < -1 "
-                                             "needs higher-order subtraction")
-                if aa[-1] == -1 and b[j] == 0:
+                if aa[-1] < -2:
+                    raise DecompositionError(f"sector {origin}: exponent a_{j}={aa[-1]} < -2 "
+                                             "needs subtraction beyond degree 1")
+                if aa[-1] <= -1 and b[j] == 0:
                     raise DecompositionError(f"sector {origin}: unregulated singularity in t_{j}")
             out.append(Sector(Us.nvars, aa, [Fraction(x) for x in b], Us, Fs,
                               Fraction(u0), Fraction(u1), Fraction(f0), Fraction(f1),

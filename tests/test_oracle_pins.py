@@ -352,3 +352,62 @@ def test_baker_transform_moments_and_triangle():
     acc *= I.prefactor[0].real
     err = acc.std(ddof=1) / np.sqrt(m)
     assert abs(acc.mean() - closed_form("triangle_m1_pm1")[0].real) <= 4 * err + 1e-12
+
+
+# ---------------------------------------------------------------- a_j = -2: subtraction of degree 1
+def test_subtraction_degree1_1d_exact_series():
+    # int_0^1 t^{-2 + b eps} G(t) dt, G = 1 + 2 t + 3 t^2 - t^3: sum_k c_k / (k - 1 + b eps)
+    b = 1.25
+    G = {(0,): 1.0, (1,): 2.0, (2,): 3.0, (3,): -1.0}
+    I = _toy_integral(1, [-2], [b], G)
+    lo, no = -1, 4
+    exact = sum(c * _series_of_inverse_linear(e[0] - 1, b, lo, no) for e, c in G.items())
+    mean, var = rqmc_integral(I, [], next_prime(8000), 8, lo, no)
+    assert_within(mean, var, exact, rel=1e-10)
+
+
+def test_subtraction_degree1_2d_nonseparable_exact_series():
+    # a = (-2, -1): sum c_ij / ((i - 1 + b1 eps)(j + b2 eps))
+    b1, b2 = -1.5, 0.75
+    coefs = {(0, 0): 1.0, (1, 0): -2.0, (0, 1): 0.5, (1, 1): 3.0, (2, 1): -2.0, (3, 0): 1.5}
+    I = _toy_integral(2, [-2, -1], [b1, b2], coefs)
+    lo, no = -2, 4
+    exact = np.zeros(no, dtype=complex)
+    for (i, j), c in coefs.items():
+        li, lj = (-1 if i == 1 else 0), (-1 if j == 0 else 0)
+        exact += c * combine.laurent_product(li, _series_of_inverse_linear(i - 1, b1, li, no + 2),
+                                             lj, _series_of_inverse_linear(j, b2, lj, no + 2), lo, no)
+    mean, var = rqmc_integral(I, [], next_prime(40000), 8, lo, no)
+    assert_within(mean, var, exact, rel=1e-9)
+
+
+def test_subtraction_degree1_with_eps_exponent():
+    # int_0^1 t^{-2 + b eps} (1 + t)^{1 + c eps} dt: boundary terms g(0)/(-1 + b eps) and
+    # g'(0)/(b eps) = (1 + c eps)/(b eps) exactly, plus the subtracted remainder whose
+    # eps coefficients are integrals of t^-2 (b ln t)^i/i! [(1+t)(c ln(1+t))^j/j! - delta_j0
+    # - t (delta_j0 + c delta_j1)], i + j = k, by adaptive quadrature (QUADPACK)
+    from scipy.integrate import quad
+    b, c = 0.5, -1.5
+    I = _toy_integral(1, [-2], [b], {(0,): 1, (1,): 1}, u0=1, u1=c)
+    lo, no = -1, 4
+    exact = np.zeros(no)
+    exact += _series_of_inverse_linear(-1, b, lo, no).real            # 1/(-1 + b eps)
+    exact[-1 - lo] += 1 / b                                             # (1 + c eps)/(b eps)
+    exact[0 - lo] += c / b
+
+    def bracket(t, j):
+        v = (1 + t) * (c * math.log1p(t)) ** j / math.factorial(j)
+        if j == 0:
+            v -= 1 + t
+        if j == 1:
+            v -= c * t
+        return v
+
+    for k in range(0, lo + no):
+        tot = 0.0
+        for i in range(k + 1):
+            f = (lambda t, i=i, j=k - i: (b * math.log(t)) ** i / math.factorial(i) * bracket(t, j) / t ** 2)
+            tot += quad(f, 0, 1, epsabs=1e-15, epsrel=1e-13, limit=400)[0]
+        exact[k - lo] += tot
+    mean, var = rqmc_integral(I, [], next_prime(20000), 8, lo, no)
+    assert_within(mean, var, exact, rel=1e-9)
