@@ -150,16 +150,27 @@ uint32_t pack_exps(const int *e, int d) {
 
 int classify(qmc_ctx *ctx, HostSector &S, int si) {
     S.ns = 0;
+    int n2 = 0;
     for (int j = 0; j < S.d; ++j) {
-        if (S.a[j] < -1) return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d < -1 needs higher-order subtraction", si, j, S.a[j]);
-        if (S.a[j] == -1) {
+        if (S.a[j] < -2)
+            return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d < -2 needs subtraction beyond degree 1", si, j, S.a[j]);
+        if (S.a[j] <= -1) {
             if (S.b[j] == 0.0) return fail(ctx, QMC_E_INVAL, "sector %d: unregulated 1/t_%d", si, j);
             ++S.ns;
+            if (S.a[j] == -2) ++n2;
         } else if (S.a[j] > QMC_EMAX) {
             return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d above %d", si, j, S.a[j], QMC_EMAX);
         }
     }
     if (S.ns > QMC_SMAX) return fail(ctx, QMC_E_INVAL, "sector %d: %d singular variables > %d", si, S.ns, QMC_SMAX);
+    if (n2) {
+        if (n2 > 1 || S.deform || S.d > 3 || S.ns > 2)
+            return fail(ctx, QMC_E_INVAL,
+                        "sector %d: a_j = -2 is supported for one variable of an undeformed sector with d <= 3 "
+                        "and at most 2 singular variables", si);
+        S.cls = QMC_CLASS_REAL3H;
+        return QMC_OK;
+    }
     if (S.deform) {
         if (S.d > 3 || S.ns > 2)
             return fail(ctx, QMC_E_INVAL, "sector %d: deformed sectors need d <= 3 and <= 2 singular variables", si);
@@ -199,11 +210,13 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
         H.f1i = (int32_t)S.f1;
     }
     int q = 0;
+    H.p2slot = -1;
     for (int j = 0; j < S.d; ++j) {
         H.a[j] = S.a[j];
         H.b[j] = S.b[j];
         if (bint) H.bi[j] = (int32_t)S.b[j];
-        if (S.a[j] == -1) H.sing[q++] = j;
+        if (S.a[j] == -2) H.p2slot = q;
+        if (S.a[j] <= -1) H.sing[q++] = j;
         else if (S.a[j] != 0 || S.b[j] != 0.0) H.regular_mask |= 1 << j;
     }
     int emax = 0;
@@ -244,26 +257,45 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
         if (which == 0) H.nU = count;
         else H.nF = count;
     }
+    // dP/dt_j as a monomial table, merged by exponent
+    auto deriv = [&](const std::vector<Term> &P, int j) {
+        std::vector<Term> out;
+        for (const Term &T : P) {
+            if (T.e[j] == 0) continue;
+            Term D = T;
+            for (int i = 0; i < QMC_NCOEF; ++i) D.c[i] *= T.e[j];
+            D.e[j] -= 1;
+            bool merged = false;
+            for (Term &O : out)
+                if (memcmp(O.e, D.e, sizeof D.e) == 0) {
+                    for (int i = 0; i < QMC_NCOEF; ++i) O.c[i] += D.c[i];
+                    merged = true;
+                    break;
+                }
+            if (!merged) out.push_back(D);
+        }
+        return out;
+    };
+    if (H.p2slot >= 0) {
+        // dU/dt_q and dF/dt_q of the a = -2 variable (subtraction of degree 1)
+        const int j2 = H.sing[H.p2slot];
+        const int base = (int)local.size();
+        std::vector<Term> du = deriv(S.U, j2), df = deriv(S.F, j2);
+        H.dqUoff = (int)local.size() - base;
+        H.dqUn = (int)du.size();
+        for (const Term &T : du) {
+            int rc = push(T);
+            if (rc) return rc;
+        }
+        H.dqFoff = (int)local.size() - base;
+        H.dqFn = (int)df.size();
+        for (const Term &T : df) {
+            int rc = push(T);
+            if (rc) return rc;
+        }
+    }
     if (S.deform) {
         // dF/dt_j and d2F/dt_j dt_k (j <= k) as monomial tables, merged by exponent
-        auto deriv = [&](const std::vector<Term> &P, int j) {
-            std::vector<Term> out;
-            for (const Term &T : P) {
-                if (T.e[j] == 0) continue;
-                Term D = T;
-                for (int i = 0; i < QMC_NCOEF; ++i) D.c[i] *= T.e[j];
-                D.e[j] -= 1;
-                bool merged = false;
-                for (Term &O : out)
-                    if (memcmp(O.e, D.e, sizeof D.e) == 0) {
-                        for (int i = 0; i < QMC_NCOEF; ++i) O.c[i] += D.c[i];
-                        merged = true;
-                        break;
-                    }
-                if (!merged) out.push_back(D);
-            }
-            return out;
-        };
         int base = (int)local.size();
         for (int j = 0; j < S.d; ++j) {
             std::vector<Term> dj = deriv(S.F, j);

@@ -34,6 +34,8 @@ struct QmcSectorDev {
                                             // corner); bit 1: every b_j too (one complex log per corner)
     int32_t bi[QMC_DMAX];                   // b_j, u1, f1 as integers where bit 1 / bit 0 of pad1 is set
     int32_t u1i, f1i;
+    int32_t p2slot;                         // singular slot with a = -2 (subtraction of degree 1), or -1
+    int32_t dqUoff, dqUn, dqFoff, dqFn;     // dU/dt, dF/dt of that variable (relative to monoF + nF)
     int32_t gU[QMC_NGROUP + 1];
     int32_t gF[QMC_NGROUP + 1];
     int32_t dFoff[QMC_DMAX], dFn[QMC_DMAX];   // relative to monoF + nF
@@ -92,7 +94,8 @@ enum QmcClass {
     QMC_CLASS_REAL6S = 5,  // real integrand, d <= 6, <= 2 singular variables (4 corners)
     QMC_CLASS_REAL6SM = 6, // REAL6S with FP32 monomial products
     QMC_CLASS_CPLX3M = 7,  // CPLX3 with FP32 monomial products (derivatives of F, U and F at z)
-    QMC_NCLASS = 8
+    QMC_CLASS_REAL3H = 8,  // real, d <= 3, <= 2 singular variables, one with a = -2 (degree-1 subtraction)
+    QMC_NCLASS = 9
 };
 
 static inline bool qmc_class_big(int cls) {

@@ -611,6 +611,142 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     assemble<SMAX, LMAX, double>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, A_empty, S.invb_full, res);
 }
 
+// ---------------------------------------------------------------- degree-1 subtraction
+// One singular variable q with a_q = -2 (the others a = -1): its endpoint
+// singularity is removed with the Taylor polynomial of degree 1,
+//   int t^{-2+b eps} g = g(0)/(-1 + b eps) + g'(0)/(b eps)
+//                        + int t^{-2+b eps} (g - g(0) - t g'(0)),
+// and the a = -1 variables as in eval_real. Per singular variable the states
+// are 0 (t kept, factor t^{-p+b eps}) and k + 1 for k < p (t = 0, the k-th
+// t-derivative of G, factor 1/(k - p + 1 + b eps) - t^{k-p+b eps}); the
+// integrand sums over all state choices. G = C U^{u0+u1 eps} F^{f0+f1 eps}
+// (times the regular factors) depends on t_q only through U and F, so
+// dG/dt_q = G ((u0 + u1 eps) U_q / U + (f0 + f1 eps) F_q / F). Series run
+// over the orders -2..5 in fixed arrays; plain, not tuned: sectors with
+// a = -2 are rare.
+template <int LMAX>
+__device__ void eval_real_h(const TileSmem<LMAX> &S, const double (&t)[3], int lo, int hi, int nord,
+                            double (&res)[LMAX]) {
+    constexpr int NT = 8, OFF = 2;   // index i holds the order i - OFF
+    const QmcSectorDev &sec = S.sec;
+    const int d = sec.d, ns = sec.ns;
+    const double *tab = S.logtab;
+    const int Hm = hi + ns;          // orders every factor must carry
+    double Cc = 1.0, Lc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if (j < d && ((sec.regular_mask >> j) & 1)) {
+            if (sec.a[j] > 0) Cc *= ipow_signed<double>(t[j], 1.0, sec.a[j]);
+            if (sec.b[j] != 0.0) Lc = fma(sec.b[j], qlog(t[j], tab), Lc);
+        }
+    double ts[2] = {1.0, 1.0}, lts[2] = {0.0, 0.0}, bs[2] = {0.0, 0.0};
+    int ps[2] = {1, 1}, js[2] = {0, 0};
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        if (q < ns) {
+            const int j = sec.sing[q];
+            js[q] = j;
+            ts[q] = j == 0 ? t[0] : (j == 1 ? t[1] : t[2]);
+            lts[q] = qlog(ts[q], tab);
+            bs[q] = sec.b[j];
+            ps[q] = -sec.a[j];
+        }
+    double acc[NT];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) acc[i] = 0.0;
+    const int r0 = ns > 0 ? ps[0] + 1 : 1, r1 = ns > 1 ? ps[1] + 1 : 1;
+    for (int s0 = 0; s0 < r0; ++s0)
+        for (int s1 = 0; s1 < r1; ++s1) {
+            const int st[2] = {s0, s1};
+            double tc[3] = {t[0], t[1], t[2]};
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (q < ns && st[q] > 0) {
+                    if (js[q] == 0) tc[0] = 0.0;
+                    if (js[q] == 1) tc[1] = 0.0;
+                    if (js[q] == 2) tc[2] = 0.0;
+                }
+            double tp[3][QMC_EMAX];
+            powers<3, double>(tc, d, sec.pad0, tp);
+            const double U = poly_sum<3, double>(S.exps, S.cval, 0, sec.nU, tp);
+            const double F = poly_sum<3, double>(S.exps, S.cval, sec.nU, sec.nU + sec.nF, tp);
+            double B = Cc;
+            B *= sec.u0_int ? ipow_signed<double>(U, qrcp(U), (int)sec.u0) : exp(sec.u0 * qlog(U, tab));
+            B *= sec.f0_int ? ipow_signed<double>(F, qrcp(F), (int)sec.f0) : exp(sec.f0 * qlog(F, tab));
+            const double Lam = Lc + sec.u1 * qlog(U, tab) + sec.f1 * qlog(F, tab);
+            double g[NT];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) g[i] = 0.0;
+            double term = B;
+#pragma unroll
+            for (int i = 0; i + OFF < NT; ++i) {
+                if (i <= Hm) g[OFF + i] = term;
+                term = term * Lam * (1.0 / (i + 1));
+            }
+            const int p2 = sec.p2slot;
+            if (p2 >= 0 && st[p2] == 2) {
+                const int db = sec.nU + sec.nF;
+                const double Uq = poly_sum<3, double>(S.exps, S.cval, db + sec.dqUoff, db + sec.dqUoff + sec.dqUn, tp);
+                const double Fq = poly_sum<3, double>(S.exps, S.cval, db + sec.dqFoff, db + sec.dqFoff + sec.dqFn, tp);
+                const double rU = Uq / U, rF = Fq / F;
+                const double al = fma(sec.u0, rU, sec.f0 * rF), be = fma(sec.u1, rU, sec.f1 * rF);
+#pragma unroll
+                for (int i = NT - 1; i >= 0; --i) g[i] = al * g[i] + (i > 0 ? be * g[i - 1] : 0.0);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q >= ns) continue;
+                const int p = ps[q], sq = st[q];
+                const int c = sq == 0 ? -p : (sq - 1) - p;       // power of t in the factor
+                double fac[NT];
+                double e = ipow_signed<double>(ts[q], qrcp(ts[q]), c);
+                const double bl = bs[q] * lts[q];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    fac[i] = 0.0;
+                    if (i >= OFF && i - OFF <= Hm) {
+                        fac[i] = sq == 0 ? e : -e;
+                        e = e * bl * (1.0 / (i - OFF + 1));
+                    }
+                }
+                if (sq > 0) {
+                    const int m = sq - p;                          // 1/(m + b eps)
+                    if (m == 0) {
+                        fac[OFF - 1] += 1.0 / bs[q];
+                    } else {
+                        double v = 1.0 / m;
+#pragma unroll
+                        for (int i = OFF; i < NT; ++i) {
+                            if (i - OFF <= Hm) fac[i] += v;
+                            v *= -bs[q] / m;
+                        }
+                    }
+                }
+                double pr[NT];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    pr[i] = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NT; ++k) {
+                        const int j = i + OFF - k;   // order(i) = order(k) + order(j)
+                        if (j >= 0 && j < NT) pr[i] = fma(g[k], fac[j], pr[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NT; ++i) g[i] = pr[i];
+            }
+#pragma unroll
+            for (int i = 0; i < NT; ++i) acc[i] += g[i];
+        }
+#pragma unroll
+    for (int o = 0; o < LMAX; ++o) {
+        res[o] = 0.0;
+#pragma unroll
+        for (int i = 0; i < NT; ++i)
+            if (o < nord && i == lo + o + OFF) res[o] = acc[i];
+    }
+}
+
 // ---------------------------------------------------------------- deformed integrand
 // z_j = t_j - i lambda_j t_j (1 - t_j) dF/dt_j at the (corner) point, with
 // rho_j = z_j / t_j for singular variables and J = dz/dt; every quantity of
@@ -900,8 +1036,8 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
 #define QMC_MINB 3   // resident 128-thread blocks per SM the real evaluator's registers must allow
 #endif
 
-template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false>
+__global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
     using T = typename std::conditional<CPLX, dc, double>::type;
     const int lo = Lc.lo, nord = Lc.norders;
@@ -1012,7 +1148,8 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3) ? 1 : QMC_MINB) qmc_
                 if constexpr (CPLX) {
                     eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
                 } else {
-                    eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
+                    if constexpr (HS) eval_real_h<LMAX>(S, t, lo, hi, nord, res);
+                    else eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
                 }
 #pragma unroll
                 for (int o = 0; o < LMAX; ++o)
@@ -1130,21 +1267,21 @@ __global__ void qmc_fp64_probe_kernel(double *out, int iters) {
     if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
 }
 
-template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED>
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
 int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
     if (block == 256)
-        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256><<<grid, 256, 0, st>>>(*L, ppt);
+        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS><<<grid, 256, 0, st>>>(*L, ppt);
     else
-        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128><<<grid, 128, 0, st>>>(*L, ppt);
+        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS><<<grid, 128, 0, st>>>(*L, ppt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED>
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
 int occupancy_cls(int block) {
     int v = 0;
     cudaError_t e = block == 256
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256>, 256, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128>, 128, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS>, 256, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS>, 128, 0);
     return e == cudaSuccess ? v : 0;
 }
 
@@ -1161,6 +1298,7 @@ extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt
         case QMC_CLASS_REAL6S: return launch_cls<6, 2, 6, false, false>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL6SM: return launch_cls<6, 2, 6, false, true>(L, block, ppt, grid, st);
         case QMC_CLASS_CPLX3M: return launch_cls<3, 2, 4, true, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL3H: return launch_cls<3, 2, 4, false, false, true>(L, block, ppt, grid, st);
         default: return -2;
     }
 }
@@ -1227,6 +1365,7 @@ extern "C" int qmc_k_occupancy(int cls, int block) {
         case QMC_CLASS_REAL6S: return occupancy_cls<6, 2, 6, false, false>(block);
         case QMC_CLASS_REAL6SM: return occupancy_cls<6, 2, 6, false, true>(block);
         case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block);
+        case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block);
         default: return 0;
     }
 }

@@ -307,3 +307,20 @@ def test_invalid_inputs_rejected(gpu):
     with pytest.raises(qmc.QmcError) as e:
         qmc.qmc_set_lattices(gpu.ctx, np.array([10], dtype=np.uint64), np.array([[2, 1, 1, 1, 1, 1]]))
     assert e.value.code == -1
+
+
+def test_degree1_subtraction_sectors(gpu):
+    # sectors with one a_j = -2 variable (class REAL3H) against the oracle: the
+    # pinned 1-D and 2-D polynomial cases and a 3-D sector with eps-dependent
+    # exponents of U and F and a second (a = -1) singular variable
+    from test_oracle_pins import _toy_integral
+
+    I1 = _toy_integral(1, [-2], [1.25], {(0,): 1.0, (1,): 2.0, (2,): 3.0, (3,): -1.0})
+    _compare_integral(gpu, I1, [[]], 4001, 4, -1, 4)
+    I2 = _toy_integral(2, [-2, -1], [-1.5, 0.75],
+                       {(0, 0): 1.0, (1, 0): -2.0, (0, 1): 0.5, (1, 1): 3.0, (2, 1): -2.0, (3, 0): 1.5})
+    _compare_integral(gpu, I2, [[]], 4001, 4, -2, 4)
+    I3 = _toy_integral(3, [-2, 0, -1], [1.0, 0.5, -2.0],
+                       {(0, 0, 0): 1.0, (1, 0, 0): 1.0, (0, 1, 0): 2.0, (1, 1, 1): 0.5},
+                       u0=-1, u1=2, Fterms={(0, 0, 0): 2.0, (1, 0, 1): 1.0, (0, 2, 0): 0.5}, f0=-2, f1=-1)
+    _compare_integral(gpu, I3, [[]], 2003, 4, -2, 4)
