@@ -300,7 +300,7 @@ def test_invalid_inputs_rejected(gpu):
     with pytest.raises(qmc.QmcError) as e:
         qmc.qmc_load_sectors_mem(gpu.ctx, "qmc-sectors 1 name broken")
     assert e.value.code == -2
-    bad = I.to_text().replace("a -1 -1 0", "a -2 -1 0", 1)
+    bad = I.to_text().replace("a -1 -1 0", "a -3 -1 0", 1)   # below a = -2: not subtracted
     with pytest.raises(qmc.QmcError) as e:
         qmc.qmc_load_sectors_mem(gpu.ctx, bad)
     assert e.value.code == -1
