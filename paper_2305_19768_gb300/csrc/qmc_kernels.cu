@@ -431,12 +431,14 @@ __device__ __forceinline__ T ipow_signed(T x, T xinv, int e) {
 // rounded to FP32), converted to FP64 before the subset sums; everything
 // else (korobov3 weight, logs and powers of U and F, the series assembly and
 // the reductions) stays FP64.
-template <int DMAX, int SMAX, int LMAX, bool MIXED>
+template <int DMAX, int SMAX, int LMAX, bool MIXED, int NS = -1>
 __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double (&t)[DMAX], int lo,
                                           int hi, int nord, double (&res)[LMAX]) {
     constexpr int NG = 1 << SMAX;
     const QmcSectorDev &sec = S.sec;
-    const int d = sec.d, ns = sec.ns;
+    // NS >= 0: the number of singular variables fixed at compile time (the
+    // caller dispatches per tile), so the corner and pole-set loops are exact
+    const int d = sec.d, ns = NS >= 0 ? NS : sec.ns;
     const double *tab = S.logtab;
     double tp[DMAX][QMC_EMAX];
     powers<DMAX, double>(t, d, sec.pad0, tp);
@@ -1148,8 +1150,16 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
                 if constexpr (CPLX) {
                     eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
                 } else {
-                    if constexpr (HS) eval_real_h<LMAX>(S, t, lo, hi, nord, res);
-                    else eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
+                    if constexpr (HS) {
+                        eval_real_h<LMAX>(S, t, lo, hi, nord, res);
+                    } else if constexpr (DMAX <= 3) {
+                        // one instantiation per number of singular variables (uniform per tile)
+                        if (S.sec.ns == 2) eval_real<DMAX, SMAX, LMAX, MIXED, 2>(S, t, lo, hi, nord, res);
+                        else if (S.sec.ns == 1) eval_real<DMAX, SMAX, LMAX, MIXED, 1>(S, t, lo, hi, nord, res);
+                        else eval_real<DMAX, SMAX, LMAX, MIXED, 0>(S, t, lo, hi, nord, res);
+                    } else {
+                        eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
+                    }
                 }
 #pragma unroll
                 for (int o = 0; o < LMAX; ++o)
