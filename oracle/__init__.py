@@ -37,7 +37,7 @@ class OrcSector(ctypes.Structure):
                 ("Ue", ctypes.POINTER(ctypes.c_int)), ("Uc", ctypes.POINTER(ctypes.c_double)),
                 ("Fe", ctypes.POINTER(ctypes.c_int)), ("Fc", ctypes.POINTER(ctypes.c_double)),
                 ("deform", ctypes.c_int), ("lam", ctypes.c_double * DMAX),
-                ("transform", ctypes.c_int)]
+                ("transform", ctypes.c_int), ("weight", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -117,6 +117,7 @@ class SectorView:
             for j in range(s.d):
                 st.lam[j] = float(lam[j])
         st.transform = transform
+        st.weight = float(getattr(s, "weight", 1))
         self.st = st
         self.nsing = len(s.singular)
 

@@ -56,6 +56,7 @@ typedef struct {
     int deform;
     double lambda[ORC_DMAX];
     int transform;       /* 0 korobov3, 1 baker, 2 none */
+    double weight;       /* constant factor of the sector (0 is read as 1) */
 } orc_sector;
 
 /* ---------------- splitmix64 (Steele, Lea & Flood 2014) ---------------- */
@@ -438,6 +439,7 @@ static int point_value_cond(const orc_sector *S, const double *u, int lo, int no
     if (W == 0.0) return 0;
     for (int j = 0; j < d; ++j)
         if (t[j] == 0.0) return 0;
+    if (S->weight != 0.0) W *= S->weight;
     cplx vals[ORC_LMAX];
     double cnd[ORC_LMAX] = {0};
     integrand_series(S, t, omt, lo, lo + norders - 1, vals, cnd, signfail);
@@ -462,9 +464,10 @@ void orc_integrand_at(const orc_sector *S, const double *t, int lo, int norders,
     cplx vals[ORC_LMAX];
     for (int j = 0; j < S->d; ++j) omt[j] = 1.0 - t[j];
     integrand_series(S, t, omt, lo, lo + norders - 1, vals, NULL, signfail);
+    const double wt = S->weight != 0.0 ? S->weight : 1.0;
     for (int o = 0; o < norders; ++o) {
-        out[2 * o] = creal(vals[o]);
-        out[2 * o + 1] = cimag(vals[o]);
+        out[2 * o] = wt * creal(vals[o]);
+        out[2 * o + 1] = wt * cimag(vals[o]);
     }
 }
 

@@ -51,6 +51,14 @@ struct Tok {
         return w;
     }
     bool expect(const char *w) { return word() == w && ok; }
+    std::string peek() {
+        const auto pos = is.tellg();
+        std::string w;
+        is >> w;
+        is.clear();
+        is.seekg(pos);
+        return w;
+    }
     long long integer() {
         std::string w = word();
         if (!ok) return 0;
@@ -108,6 +116,12 @@ int parse_integral(qmc_ctx *ctx, const std::string &text, HostIntegral &I) {
             return fail(ctx, QMC_E_INVAL, "sector %lld: d=%d outside 1..%d", si, S.d, QMC_DMAX);
         if (!t.expect("deform")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'deform'", si);
         S.deform = t.integer() != 0;
+        if (t.peek() == "weight") {   // optional constant factor of the sector
+            t.word();
+            S.weight = t.real();
+            if (!(S.weight > 0) || !std::isfinite(S.weight))
+                return fail(ctx, QMC_E_PARSE, "sector %lld: weight must be positive", si);
+        }
         if (!t.expect("a")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'a'", si);
         for (int j = 0; j < S.d; ++j) S.a[j] = (int)t.integer();
         if (!t.expect("b")) return fail(ctx, QMC_E_PARSE, "sector %lld: expected 'b'", si);
@@ -192,6 +206,7 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
     H.d = S.d;
     H.ns = S.ns;
     H.deform = S.deform ? 1 : 0;
+    H.weight = S.weight;
     H.ninv = ninv;
     H.u0 = S.u0;
     H.u1 = S.u1;

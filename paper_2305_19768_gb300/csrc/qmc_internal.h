@@ -42,6 +42,7 @@ struct QmcSectorDev {
     int32_t Hoff[QMC_NHESS], Hn[QMC_NHESS];   // j <= k packed row-major
     double b[QMC_DMAX];
     double u0, u1, f0, f1;
+    double weight;                          // constant factor of the sector
 };
 
 // One evaluation job: (sector, kinematic point) with its lattice and shifts.

@@ -264,7 +264,7 @@ struct TileSmem {
     double invb_full;  // prod over the singular slots of 1/b_q (A of the full pole set)
     double logtab[3 * QMC_LOG_TABLE_ROWS];
     double atantab[2 * QMC_ATAN_TABLE_ROWS];
-    double w140d;  // 140^d of the staged sector
+    double w140d;  // constant factor of the staged sector: its weight, times 140^d for korobov3
     unsigned long long tile;
     int cached_sector, cached_point;
     int job_index;
@@ -1026,8 +1026,9 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
             double af = 1.0;
             for (int q = 0; q < S.sec.ns; ++q) af *= 1.0 / S.sec.b[S.sec.sing[q]];
             S.invb_full = af;
-            double w = 1.0;
-            for (int j = 0; j < S.sec.d; ++j) w *= 140.0;
+            double w = S.sec.weight;   // the sector's constant factor, times 140^d for korobov3
+            if (Lc.transform == 0)
+                for (int j = 0; j < S.sec.d; ++j) w *= 140.0;
             S.w140d = w;
         }
     }
@@ -1195,7 +1196,7 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
         if (threadIdx.x < 2 * nord) {
             double sum = 0.0;
             for (int w = 0; w < BLOCK / 32; ++w) sum += S.red[w][threadIdx.x];
-            if (Lc.transform == 0) sum *= S.w140d;   // the korobov3 weight's constant 140^d
+            sum *= S.w140d;   // the sector's constant factor and the korobov3 weight's 140^d
             Lc.partials[tile * (uint64_t)(2 * nord) + threadIdx.x] = sum;
             if (!isfinite(sum)) atomicAdd(Lc.status + 1, 1ULL);
         }

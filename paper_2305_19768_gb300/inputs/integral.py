@@ -10,7 +10,7 @@ it plays the role of the paper's per-integral library description (the
     invariants <k> <name_1> ... <name_k>
     prefactor <lowest order> <count> <re_0> <im_0> <re_1> <im_1> ...
     nsectors <S>
-    sector <index> d <d> deform <0|1>
+    sector <index> d <d> deform <0|1> [weight <w>]
     a <a_1> ... <a_d>
     b <b_1> ... <b_d>
     U <u0> <u1> <nterms>
@@ -76,7 +76,10 @@ class Integral:
         out.append(" ".join(pf))
         out.append(f"nsectors {len(self.sectors)}")
         for i, s in enumerate(self.sectors):
-            out.append(f"sector {i} d {s.d} deform {1 if s.deform else 0}")
+            head = f"sector {i} d {s.d} deform {1 if s.deform else 0}"
+            if getattr(s, "weight", 1) != 1:
+                head += f" weight {int(s.weight)}"
+            out.append(head)
             out.append(" ".join(["a"] + [str(int(x)) for x in s.a]))
             out.append(" ".join(["b"] + [_num(x) for x in s.b]))
             for tag, P, e0, e1 in (("U", s.U, s.u0, s.u1), ("F", s.F, s.f0, s.f1)):
@@ -122,6 +125,10 @@ class Integral:
             d = int(nxt())
             assert nxt() == "deform"
             deform = bool(int(nxt()))
+            weight = 1
+            if tok[pos] == "weight":
+                nxt()
+                weight = int(nxt())
             assert nxt() == "a"
             a = [int(nxt()) for _ in range(d)]
             assert nxt() == "b"
@@ -139,7 +146,7 @@ class Integral:
                     P._acc(e, c)
                 polys.append((P, e0, e1))
             (U, u0, u1), (F, f0, f1) = polys
-            secs.append(Sector(d, a, b, U, F, u0, u1, f0, f1, deform))
+            secs.append(Sector(d, a, b, U, F, u0, u1, f0, f1, deform, weight=weight))
         assert nxt() == "end"
         return cls(name, L, N, D0, invs, lo, pref, secs)
 

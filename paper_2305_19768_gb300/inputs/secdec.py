@@ -43,6 +43,7 @@ class Sector:
     f1: Fraction
     deform: bool = False
     origin: str = ""
+    weight: int = 1          # constant factor of the sector (|det N| of a geometric sector)
 
     @property
     def singular(self) -> List[int]:

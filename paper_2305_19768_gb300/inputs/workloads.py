@@ -13,6 +13,8 @@ and without contour deformation, combined with coefficients into sums).
   physical region (s > 4 m^2) needs contour deformation; four sectors, d = 3.
 * ``double_box_massless``: two-loop planar double box, seven massless
   propagators, poles up to 1/eps^4, d = 6.
+Builders take method="iterative" (primary sectors, then iterative
+decomposition) or "geometric" (inputs.geometric).
 * ``bubble``/``triangle`` families used in the 10-integral amplitude.
 
 Kinematic points are drawn with splitmix64 (Steele, Lea & Flood 2014) from a
@@ -52,26 +54,34 @@ def uniform_stream(seed: int, count: int) -> np.ndarray:
     return out
 
 
-def _integral_from_graph(g: Graph, D0: int, *, deform: bool, pref_order: int = 6) -> Integral:
+def _integral_from_graph(g: Graph, D0: int, *, deform: bool, pref_order: int = 6,
+                         method: str = "iterative") -> Integral:
     U, F = symanzik(g)
     N = len(g.edges)
     L = g.nloops
     u0, u1, f0, f1 = exponents(N, L, D0)
-    secs = decompose(U, F, u0, u1, f0, f1, deform=deform)
+    if method == "geometric":
+        from .geometric import decompose_geometric
+
+        secs = decompose_geometric(U, F, u0, u1, f0, f1, deform=deform)
+    elif method == "iterative":
+        secs = decompose(U, F, u0, u1, f0, f1, deform=deform)
+    else:
+        raise ValueError(f"unknown decomposition method {method!r}")
     lo, pc = prefactor_series(N, L, D0, pref_order)
     return Integral(g.name, L, N, D0, list(g.kin.invariants), lo, [complex(c) for c in pc], secs)
 
 
-def triangle_massive(msq=1, psq=-1) -> Integral:
+def triangle_massive(msq=1, psq=-1, method: str = "iterative") -> Integral:
     g = Graph(edges=[(0, 1), (1, 2), (2, 0)], masses_sq=[Fraction(msq)] * 3, legs=[0, 1, 2],
               kin=kin_numeric_3pt(psq, psq, psq), name="triangle_m1_pm1")
-    return _integral_from_graph(g, 4, deform=False)
+    return _integral_from_graph(g, 4, deform=False, method=method)
 
 
-def box_massless(deform: bool = False) -> Integral:
+def box_massless(deform: bool = False, method: str = "iterative") -> Integral:
     g = Graph(edges=[(0, 1), (1, 2), (2, 3), (3, 0)], masses_sq=[Fraction(0)] * 4,
               legs=[0, 1, 2, 3], kin=kin_massless_4pt(), name="box1L_massless")
-    return _integral_from_graph(g, 4, deform=deform)
+    return _integral_from_graph(g, 4, deform=deform, method=method)
 
 
 def box_massive(msq=1, deform: bool = True) -> Integral:
@@ -80,13 +90,13 @@ def box_massive(msq=1, deform: bool = True) -> Integral:
     return _integral_from_graph(g, 4, deform=deform)
 
 
-def double_box_massless() -> Integral:
+def double_box_massless(method: str = "iterative") -> Integral:
     # vertices: 0-1-2 top row, 3-4-5 bottom row; rung 1-4
     # legs: p0 at 3 (bottom left), p1 at 0 (top left), p2 at 2 (top right), p3 at 5
     g = Graph(edges=[(0, 1), (1, 2), (2, 5), (5, 4), (4, 3), (3, 0), (1, 4)],
               masses_sq=[Fraction(0)] * 7, legs=[3, 0, 2, 5], kin=kin_massless_4pt(),
               name="box2L_planar_massless")
-    return _integral_from_graph(g, 4, deform=False)
+    return _integral_from_graph(g, 4, deform=False, method=method)
 
 
 def bubble(msq=0, inv="s", deform: bool = True, names=None) -> Integral:

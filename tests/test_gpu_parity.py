@@ -324,3 +324,19 @@ def test_degree1_subtraction_sectors(gpu):
                        {(0, 0, 0): 1.0, (1, 0, 0): 1.0, (0, 1, 0): 2.0, (1, 1, 1): 0.5},
                        u0=-1, u1=2, Fterms={(0, 0, 0): 2.0, (1, 0, 1): 1.0, (0, 2, 0): 0.5}, f0=-2, f1=-1)
     _compare_integral(gpu, I3, [[]], 2003, 4, -2, 4)
+
+
+def test_geometric_sectors_and_weights(gpu):
+    # sectors from the geometric decomposition through the evaluator: the massless
+    # box (all sectors), double-box sectors of every singular-variable count, and a
+    # sector with a weight other than 1 (applied per tile on the device)
+    I = w.box_massless(method="geometric")
+    _compare_integral(gpu, I, [[-3.0, -2.0]], 10007, 4, -2, 3)
+    D = w.double_box_massless(method="geometric")
+    by_ns = {}
+    for i, s in enumerate(D.sectors):
+        by_ns.setdefault(len(s.singular), i)
+    _compare_integral(gpu, D, [[-3.0, -1.0]], 2003, 2, -4, 5, sectors=sorted(by_ns.values()))
+    T = w.triangle_massive(method="geometric")
+    T.sectors[1].weight = 3
+    _compare_integral(gpu, T, [[]], 4001, 4, 0, 1)
