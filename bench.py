@@ -51,11 +51,11 @@ def _workloads():
     return {
         # the default: one-loop massless box, Euclidean point
         "box1L_massless": dict(
-            make=w.box_massless, kin=[[-3.0, -2.0]], lo=-2, nord=3, n=1000003, m=32, deform=False,
+            make=lambda method="iterative": w.box_massless(method=method), kin=[[-3.0, -2.0]], lo=-2, nord=3, n=1000003, m=32, deform=False,
             desc="box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n={n} CBC, m={m} shifts"),
         # finite massive triangle, p_i^2 = -1, m^2 = 1
         "triangle_massive": dict(
-            make=w.triangle_massive, kin=[[]], lo=0, nord=1, n=100003, m=16, deform=False,
+            make=lambda method="iterative": w.triangle_massive(method=method), kin=[[]], lo=0, nord=1, n=100003, m=16, deform=False,
             desc="triangle m^2=1 p_i^2=-1, 3 sectors d=2, eps^0, n={n} CBC, m={m} shifts"),
         # massive box in the physical region: 1024 seeded (s, t), contour deformation
         # with lambda presampled per (point, sector), all jobs in one persistent launch
@@ -73,7 +73,7 @@ def _workloads():
                  "eps^-2..eps^0, n={n} CBC, m={m} shifts"),
         # two-loop planar massless double box, Euclidean point
         "box2L_planar_massless": dict(
-            make=w.double_box_massless, kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
+            make=lambda method="iterative": w.double_box_massless(method=method), kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
             desc="box2L_planar_massless s=-3 t=-1, 282 sectors d=6, eps^-4..eps^0, n={n} CBC, m={m} shifts"),
     }
 
@@ -211,6 +211,8 @@ def main():
                     choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box1L_massless_physical",
                              "box2L_planar_massless"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--decomposition", default="iterative", choices=["iterative", "geometric"],
+                    help="sector decomposition of the box and double-box workloads")
     ap.add_argument("--n", type=int, default=0, help="lattice size (default: the workload's)")
     ap.add_argument("--shifts", type=int, default=0, help="random shifts (default: the workload's)")
     ap.add_argument("--block", type=int, default=0)
@@ -237,10 +239,10 @@ def main():
     from paper_2305_19768_gb300.inputs import workloads as w
 
     W = _workloads()[args.workload]
-    I = W["make"]()
+    I = W["make"](method=args.decomposition) if args.decomposition != "iterative" else W["make"]()
     args.n, args.shifts = args.n or W["n"], args.shifts or W["m"]
     LO, NORD = W["lo"], W["nord"]
-    default = args.workload == "box1L_massless" and args.precision == "fp64"
+    default = args.workload == "box1L_massless" and args.precision == "fp64" and args.decomposition == "iterative"
     opts = {}
     if args.block:
         opts["block"] = args.block
@@ -396,7 +398,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": W["desc"].format(n=args.n, m=args.shifts), "evals_per_step": evals_per_step,
-                       "precision": args.precision,
+                       "precision": args.precision, "decomposition": args.decomposition, "sectors": nsec,
                        "l2": "flushed between timed steps (256 MB write)", "wall_s": wall},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
