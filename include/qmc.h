@@ -253,13 +253,15 @@ int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int nor
  * 1: deformed d <= 3, 2: real d <= 6 with 3 or 4 singular variables, 3 and
  * 4: the mixed-precision variants of 0 and 2, 5: real d <= 6 with at most 2
  * singular variables, 6: its mixed-precision variant, 7: the mixed-precision
- * variant of 1, 8: real d <= 3 with one a_j = -2 variable): on up to 32 of the
+ * variant of 1, 8: real d <= 3 with one a_j = -2 variable, 9: real d <= 6
+ * with 3 singular variables, 10: its mixed-precision variant; class 2 then
+ * holds the d <= 6 sectors with 4): on up to 32 of the
  * given jobs per class (at most 8 shifts each) every block size in
  * {128, 256} and points per thread in {4, 8, 16, 32} is timed with CUDA
  * events; the fastest is kept in the context and used by later plans whose
  * options leave block/ppt at 0. best_block/best_ppt (may be NULL) receive
  * QMC_NUM_CLASSES entries (0 = class absent). */
-#define QMC_NUM_CLASSES 9
+#define QMC_NUM_CLASSES 11
 int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
                  int *best_ppt);
 

@@ -193,6 +193,8 @@ int classify(qmc_ctx *ctx, HostSector &S, int si) {
         S.cls = QMC_CLASS_REAL3;
     } else if (S.ns <= 2) {
         S.cls = QMC_CLASS_REAL6S;
+    } else if (S.ns == 3) {
+        S.cls = QMC_CLASS_REAL6T;
     } else {
         S.cls = QMC_CLASS_REAL6;
     }
@@ -624,6 +626,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         c.cls = cls;
         c.orig = per_orig[cls];
         c.block = ctx->opt.block == 256 ? 256 : (ctx->opt.block == 128 ? 128 : (ctx->tuned_block[cls] ? ctx->tuned_block[cls] : 128));
+        if (qmc_class_dmax(cls) > 3) c.block = 128;   // the d <= 6 classes exist with 128-thread blocks only
         c.ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : (ctx->tuned_ppt[cls] ? ctx->tuned_ppt[cls] : 16);
         if (ctx->opt.ppt <= 0 && !ctx->tuned_ppt[cls]) {
             // small lattices: tiles of 512 points instead of 2048, so that a

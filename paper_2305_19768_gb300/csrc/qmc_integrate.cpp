@@ -617,6 +617,7 @@ extern "C" int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo
         int bb = 128, bp = 16;
         for (int b : blocks)
             for (int p : ppts) {
+                if (b == 256 && qmc_class_dmax(cls) > 3) continue;   // 128-thread blocks only
                 ctx->opt.block = b;
                 ctx->opt.ppt = p;
                 qmc_plan *plan = nullptr;

@@ -89,23 +89,30 @@ struct QmcLaunch {
 enum QmcClass {
     QMC_CLASS_REAL3 = 0,   // real integrand, d <= 3, <= 2 singular variables
     QMC_CLASS_CPLX3 = 1,   // contour-deformed, d <= 3, <= 2 singular variables
-    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6, 3 or 4 singular variables
+    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6, 4 singular variables (16 corners)
     QMC_CLASS_REAL3M = 3,  // REAL3 with FP32 monomial products
     QMC_CLASS_REAL6M = 4,  // REAL6 with FP32 monomial products
     QMC_CLASS_REAL6S = 5,  // real integrand, d <= 6, <= 2 singular variables (4 corners)
     QMC_CLASS_REAL6SM = 6, // REAL6S with FP32 monomial products
     QMC_CLASS_CPLX3M = 7,  // CPLX3 with FP32 monomial products (derivatives of F, U and F at z)
     QMC_CLASS_REAL3H = 8,  // real, d <= 3, <= 2 singular variables, one with a = -2 (degree-1 subtraction)
-    QMC_NCLASS = 9
+    QMC_CLASS_REAL6T = 9,  // real integrand, d <= 6, 3 singular variables (8 corners)
+    QMC_CLASS_REAL6TM = 10,// REAL6T with FP32 monomial products
+    QMC_NCLASS = 11
 };
 
 static inline bool qmc_class_big(int cls) {
-    return cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M || cls == QMC_CLASS_REAL6S || cls == QMC_CLASS_REAL6SM;
+    return cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M || cls == QMC_CLASS_REAL6S || cls == QMC_CLASS_REAL6SM ||
+           cls == QMC_CLASS_REAL6T || cls == QMC_CLASS_REAL6TM;
 }
 // Series length (orders) each class supports: K + ns + 1 <= class_lmax.
 static inline int qmc_class_lmax(int cls) { return qmc_class_big(cls) ? 6 : 4; }
 static inline int qmc_class_dmax(int cls) { return qmc_class_big(cls) ? 6 : 3; }
-static inline int qmc_class_smax(int cls) { return (cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M) ? 4 : 2; }
+static inline int qmc_class_smax(int cls) {
+    if (cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M) return 4;
+    if (cls == QMC_CLASS_REAL6T || cls == QMC_CLASS_REAL6TM) return 3;
+    return 2;
+}
 // The mixed-precision variant of a class.
 static inline int qmc_class_mixed(int cls) {
     switch (cls) {
@@ -113,6 +120,7 @@ static inline int qmc_class_mixed(int cls) {
         case QMC_CLASS_REAL6: return QMC_CLASS_REAL6M;
         case QMC_CLASS_REAL6S: return QMC_CLASS_REAL6SM;
         case QMC_CLASS_CPLX3: return QMC_CLASS_CPLX3M;
+        case QMC_CLASS_REAL6T: return QMC_CLASS_REAL6TM;
         default: return cls;
     }
 }

@@ -1278,21 +1278,33 @@ __global__ void qmc_fp64_probe_kernel(double *out, int iters) {
     if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
 }
 
+// Blocks of 256 threads exist for the d <= 3 classes only: the d <= 6 classes
+// run near the register limit, where a second warp set per block buys nothing
+// (and their instantiations dominate the build).
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
 int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
-    if (block == 256)
-        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS><<<grid, 256, 0, st>>>(*L, ppt);
-    else
-        qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS><<<grid, 128, 0, st>>>(*L, ppt);
+    if constexpr (DMAX <= 3) {
+        if (block == 256) {
+            qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS><<<grid, 256, 0, st>>>(*L, ppt);
+            return cudaGetLastError() == cudaSuccess ? 0 : -1;
+        }
+    }
+    qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS><<<grid, 128, 0, st>>>(*L, ppt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
 int occupancy_cls(int block) {
     int v = 0;
-    cudaError_t e = block == 256
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS>, 256, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS>, 128, 0);
+    cudaError_t e;
+    if constexpr (DMAX <= 3)
+        e = block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS>, 256, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS>, 128, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS>,
+                                                          128, 0);
     return e == cudaSuccess ? v : 0;
 }
 
@@ -1310,6 +1322,8 @@ extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt
         case QMC_CLASS_REAL6SM: return launch_cls<6, 2, 6, false, true>(L, block, ppt, grid, st);
         case QMC_CLASS_CPLX3M: return launch_cls<3, 2, 4, true, true>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL3H: return launch_cls<3, 2, 4, false, false, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6T: return launch_cls<6, 3, 6, false, false>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6TM: return launch_cls<6, 3, 6, false, true>(L, block, ppt, grid, st);
         default: return -2;
     }
 }
@@ -1377,6 +1391,8 @@ extern "C" int qmc_k_occupancy(int cls, int block) {
         case QMC_CLASS_REAL6SM: return occupancy_cls<6, 2, 6, false, true>(block);
         case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block);
         case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block);
+        case QMC_CLASS_REAL6T: return occupancy_cls<6, 3, 6, false, false>(block);
+        case QMC_CLASS_REAL6TM: return occupancy_cls<6, 3, 6, false, true>(block);
         default: return 0;
     }
 }
