@@ -411,17 +411,18 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
 int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
                           double *out_dev, void *stream);
 
-/* The evaluator's own FP64 natural logarithm applied on the device to n
- * positive normal doubles (host arrays x[n] -> out[n]), for verification:
- * Tang's table-driven method (ACM TOMS 16, 1990) with a 1025-entry table
- * and a degree-5 log1p, within 1.5 ulp (without Tang's separate procedure
- * near x = 1). Errors: QMC_E_INVAL for a non-positive, subnormal or
- * non-finite x. */
+/* The evaluator's own natural logarithm applied on the device to n doubles
+ * (host arrays x[n] -> out[n]), for verification: Tang's table-driven
+ * reduction (ACM TOMS 16, 1990) with a 1025-entry table, evaluated in
+ * integer fixed point (a 128-bit sum) and rounded once: within 0.51 ulp of
+ * the exact logarithm. Zero gives -inf, +inf gives +inf, a negative x or NaN
+ * gives NaN, subnormals are accepted. Errors: QMC_E_INVAL for null arrays. */
 int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out);
 
 /* The evaluator's own FP64 reciprocal (two Newton-Raphson steps from the
  * hardware approximation), applied like qmc_fp64_log, for verification:
- * within 1 ulp of the correctly rounded 1/x. Same arguments and errors. */
+ * within 1 ulp of the correctly rounded 1/x. Same arguments; QMC_E_INVAL
+ * also for a non-positive, subnormal or non-finite x. */
 int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out);
 
 /* The evaluator's own two-argument arctangent (table-driven reduction by

@@ -1,15 +1,10 @@
-"""Write qmc_log_table.h: the table of the evaluator's table-driven FP64
-logarithm (Tang, "Table-driven implementation of the logarithm function in
+"""Write qmc_log_table.h: the table of the evaluator's fixed-point logarithm
+(qmc_ilog.h; Tang, "Table-driven implementation of the logarithm function in
 IEEE floating-point arithmetic", ACM TOMS 16 (1990)).
 
-For j = 0..1024, F_j = 1 + j/1024 and
-    INVF[j]          = RN(1/F_j)
-    LOGF_HI[j]       = ln(F_j) rounded to a multiple of 2^-42
-    LOGF_LO[j]       = RN(ln(F_j) - LOGF_HI[j])
-and LN2_HI = ln 2 rounded to a multiple of 2^-42, LN2_LO = RN(ln 2 - LN2_HI).
-Rounding the leading parts to the 2^-42 grid makes e * LN2_HI + LOGF_HI[j]
-exact for every binary exponent |e| < 2^10. Values come from mpmath at 60
-digits and are written as C99 hexadecimal floating constants.
+For j = 0..1024, F_j = 1 + j/1024, row j holds three 64-bit words:
+    RN(2^63 / F_j),  RN(2^116 ln F_j) mod 2^64,  RN(2^116 ln F_j) div 2^64.
+Values come from mpmath at 80 digits.
 
 The same header carries the table of the evaluator's two-argument arctangent:
 for j = 0..64, ATAN_HI[j] = RN(atan(j/64)), ATAN_LO[j] = RN(atan(j/64) -
@@ -21,7 +16,7 @@ import os
 
 import mpmath as mp
 
-mp.mp.dps = 60
+mp.mp.dps = 80
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "qmc_log_table.h")
 
 
@@ -30,21 +25,15 @@ def rn(x) -> float:
     return float(mp.mpf(x))
 
 
-def grid42(x) -> float:
-    return float(mp.nint(mp.mpf(x) * 2 ** 42) / 2 ** 42)
-
-
 def main():
     rows = []
     for j in range(1025):
         F = mp.mpf(1) + mp.mpf(j) / 1024
-        L = mp.log(F)
-        hi = grid42(L)
-        lo = rn(L - mp.mpf(hi))
-        rows.append((rn(1 / F), hi, lo))
-    ln2 = mp.log(2)
-    ln2_hi = grid42(ln2)
-    ln2_lo = rn(ln2 - mp.mpf(ln2_hi))
+        inv = int(mp.nint(mp.mpf(2) ** 63 / F))
+        L = int(mp.nint(mp.log(F) * mp.mpf(2) ** 116))
+        rows.append((inv, L & (2 ** 64 - 1), L >> 64))
+    ln2 = int(mp.nint(mp.log(2) * mp.mpf(2) ** 116))
+    assert ln2 & (2 ** 64 - 1) == 0x9ABC9E3B39803F2F and ln2 >> 64 == 0xB17217F7D1CF7   # qmc_ilog.h
     atan_rows = []
     for j in range(65):
         a = mp.atan(mp.mpf(j) / 64)
@@ -56,14 +45,13 @@ def main():
     pi_hi = rn(mp.pi)
     pi_lo = rn(mp.pi - mp.mpf(pi_hi))
     with open(OUT, "w") as fh:
-        fh.write("// Table of the evaluator's FP64 logarithm (written by make_log_table.py).\n")
-        fh.write("// Row j: RN(1/F_j), ln(F_j) on the 2^-42 grid, RN(remainder); F_j = 1 + j/1024.\n")
+        fh.write("// Table of the evaluator's fixed-point logarithm (written by make_log_table.py).\n")
+        fh.write("// Row j: RN(2^63/F_j), RN(2^116 ln F_j) low and high words; F_j = 1 + j/1024.\n")
         fh.write("#pragma once\n")
-        fh.write(f"#define QMC_LN2_HI {ln2_hi.hex()}\n#define QMC_LN2_LO {ln2_lo.hex()}\n")
         fh.write("#define QMC_LOG_TABLE_ROWS 1025\n")
         fh.write("#define QMC_LOG_TABLE_INIT { \\\n")
-        for inv, hi, lo in rows:
-            fh.write(f"    {inv.hex()}, {hi.hex()}, {lo.hex()}, \\\n")
+        for inv, lo, hi in rows:
+            fh.write(f"    {inv:#x}ULL, {lo:#x}ULL, {hi:#x}ULL, \\\n")
         fh.write("}\n")
         fh.write("// Row j: RN(atan(j/64)), RN(remainder).\n")
         fh.write(f"#define QMC_PIO2_HI {pio2_hi.hex()}\n#define QMC_PIO2_LO {pio2_lo.hex()}\n")

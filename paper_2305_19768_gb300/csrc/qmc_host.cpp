@@ -883,10 +883,12 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
 }
 
 // one device function applied elementwise to host data (verification entry points)
+// positive_normal: the function's domain is the positive normal doubles
+// (others are rejected); otherwise every double is accepted
 static int fp64_apply(qmc_ctx *ctx, const double *x, size_t n, double *out, const char *name,
-                      int (*launch)(const double *, uint64_t, double *, void *)) {
+                      int (*launch)(const double *, uint64_t, double *, void *), bool positive_normal) {
     if (!ctx || (n && (!x || !out))) return fail(ctx, QMC_E_INVAL, "%s: bad arguments", name);
-    for (size_t i = 0; i < n; ++i)
+    for (size_t i = 0; positive_normal && i < n; ++i)
         if (!(x[i] >= 2.2250738585072014e-308) || !std::isfinite(x[i]))
             return fail(ctx, QMC_E_INVAL, "%s: x[%zu] is not a positive normal number", name, i);
     if (n == 0) return QMC_OK;
@@ -908,11 +910,11 @@ static int fp64_apply(qmc_ctx *ctx, const double *x, size_t n, double *out, cons
 }
 
 int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out) {
-    return fp64_apply(ctx, x, n, out, "qmc_fp64_log", qmc_k_log);
+    return fp64_apply(ctx, x, n, out, "qmc_fp64_log", qmc_k_log, false);
 }
 
 int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out) {
-    return fp64_apply(ctx, x, n, out, "qmc_fp64_rcp", qmc_k_rcp);
+    return fp64_apply(ctx, x, n, out, "qmc_fp64_rcp", qmc_k_rcp, true);
 }
 
 int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, double *out) {

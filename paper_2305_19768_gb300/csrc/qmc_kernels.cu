@@ -23,12 +23,13 @@
 
 #include <type_traits>
 
+#include "qmc_ilog.h"
 #include "qmc_internal.h"
 #include "qmc_log_table.h"
 
 namespace {
 
-__device__ const double kLogTable[3 * QMC_LOG_TABLE_ROWS] = QMC_LOG_TABLE_INIT;
+__device__ const uint64_t kLogTable[3 * QMC_LOG_TABLE_ROWS] = QMC_LOG_TABLE_INIT;
 __device__ const double kAtanTable[2 * QMC_ATAN_TABLE_ROWS] = QMC_ATAN_TABLE_INIT;
 
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
@@ -85,33 +86,10 @@ __device__ __forceinline__ double lattice_coord(uint64_t r, double nd, double in
     return nonneg_ge_one(x) ? frac_of_one_two(x) : x;   // x - 1 is exact for x in [1, 2)
 }
 
-// Natural logarithm of a positive normal double, table-driven after Tang
-// (ACM TOMS 16, 1990): x = 2^e m, m in [1,2); F = 1 + j/1024 nearest to m
-// (integer operations on the bits); r = m - F exact; f = r RN(1/F),
-// |f| <= 2^-11; ln x = e ln2 + ln F + log1p(f), log1p by its Taylor series
-// to f^5 (truncation below 2^-57 relative). e*LN2_HI + LOGF_HI is exact (both
-// on the 2^-42 grid). Without Tang's separate procedure near x = 1, the two
-// roundings in f show where ln F and f nearly cancel: measured worst case
-// 1.05 ulp. 12 FP64 operations. `tab` holds rows {RN(1/F), ln F hi, lo}.
-__device__ __forceinline__ double qlog(double x, const double *tab) {
-    const long long bits = __double_as_longlong(x);
-    const long long mb = bits & 0x000FFFFFFFFFFFFFLL;
-    const int j = (int)((mb + (1LL << 41)) >> 42);               // 0..1024
-    const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);
-    const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 42));
-    // exponent as a double without a conversion instruction: (2^52 + 2^51 + e) - (2^52 + 2^51)
-    const long long e = (bits >> 52) - 1023;
-    const double ed = __longlong_as_double(0x4338000000000000LL + e) - 6755399441055744.0;
-    const double r = m - F;
-    const double f = r * tab[3 * j];
-    double q = fma(f, 0.2, -0.25);
-    q = fma(q, f, 1.0 / 3.0);
-    q = fma(q, f, -0.5);
-    const double lo = fma(ed, QMC_LN2_LO, tab[3 * j + 2]);
-    const double s = fma(f * f, q, lo);                            // tail + lo
-    const double hi = fma(ed, QMC_LN2_HI, tab[3 * j + 1]);
-    return hi + (f + s);
-}
+// Natural logarithm: the fixed-point evaluation of qmc_ilog.h on the integer
+// pipe (Tang's reduction with a 1025-row table; within 0.501 ulp). `tab` is
+// the table of that header, staged in shared memory.
+__device__ __forceinline__ double qlog(double x, const uint64_t *tab) { return qmc_ilog(x, tab); }
 
 // Reciprocal by Newton-Raphson (y <- y + y (1 - x y), quadratic convergence)
 // from the hardware approximation rcp.approx.ftz.f64, two steps: not
@@ -187,7 +165,7 @@ __device__ __forceinline__ float arg32(dc a, bool m0) {
 }
 // Principal log; on the real axis the argument is taken from below
 // (x - i0), the prescription of F - i0.
-__device__ __forceinline__ dc clog_m0(dc a, const double *tab, const double *atab) {
+__device__ __forceinline__ dc clog_m0(dc a, const uint64_t *tab, const double *atab) {
     double arg = (a.im == 0.0) ? (a.re < 0.0 ? -CUDART_PI : 0.0) : qatan2(a.im, a.re, atab);
     return dc{0.5 * qlog(fma(a.re, a.re, a.im * a.im), tab), arg};
 }
@@ -262,7 +240,7 @@ struct TileSmem {
     double delta[QMC_DMAX];
     double invb[QMC_SMAX];
     double invb_full;  // prod over the singular slots of 1/b_q (A of the full pole set)
-    double logtab[3 * QMC_LOG_TABLE_ROWS];
+    uint64_t logtab[3 * QMC_LOG_TABLE_ROWS];
     double atantab[2 * QMC_ATAN_TABLE_ROWS];
     double w140d;  // constant factor of the staged sector: its weight, times 140^d for korobov3
     unsigned long long tile;
@@ -439,7 +417,7 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     // NS >= 0: the number of singular variables fixed at compile time (the
     // caller dispatches per tile), so the corner and pole-set loops are exact
     const int d = sec.d, ns = NS >= 0 ? NS : sec.ns;
-    const double *tab = S.logtab;
+    const uint64_t *tab = S.logtab;
     double tp[DMAX][QMC_EMAX];
     powers<DMAX, double>(t, d, sec.pad0, tp);
 
@@ -632,7 +610,7 @@ __device__ void eval_real_h(const TileSmem<LMAX> &S, const double (&t)[3], int l
     constexpr int NT = 8, OFF = 2;   // index i holds the order i - OFF
     const QmcSectorDev &sec = S.sec;
     const int d = sec.d, ns = sec.ns;
-    const double *tab = S.logtab;
+    const uint64_t *tab = S.logtab;
     const int Hm = hi + ns;          // orders every factor must carry
     double Cc = 1.0, Lc = 0.0;
 #pragma unroll
@@ -763,7 +741,7 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
     const int d = sec.d, ns = sec.ns;
     const int full = (1 << ns) - 1;
     const int dbase = sec.nU + sec.nF;
-    const double *tab = S.logtab;
+    const uint64_t *tab = S.logtab;
     const double *atab = S.atantab;
     dc BV[NG], LV[NG];
     double it[SMAX], lt[SMAX], bq[SMAX];
