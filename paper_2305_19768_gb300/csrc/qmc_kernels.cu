@@ -86,6 +86,119 @@ __device__ __forceinline__ double lattice_coord(uint64_t r, double nd, double in
     return nonneg_ge_one(x) ? frac_of_one_two(x) : x;   // x - 1 is exact for x in [1, 2)
 }
 
+// The same coordinate on the integer pipe. One lattice coordinate is walked
+// as r = k z mod n together with the exact binary expansion of r/n to 64
+// places: Q = floor(r 2^64 / n), R = r 2^64 mod n (n < 2^32). Stepping k by
+// one adds (Qz, Rz), the expansion of z/n, with a carry from R into Q;
+// modulo 2^64 the wrap of r needs no correction. When r/n >= 2^-12
+// (Q >= 2^52) the 53-bit rounding of r/n is read off Q with R as the sticky
+// part (r/n is never a rounding midpoint, see above), RN(r/n) is then a
+// multiple of 2^-64, and so is delta (the shifts are multiples of 2^-53):
+// their sum is exact in 64 bits plus a carry, and its IEEE rounding and the
+// fold are integer operations. The rare coordinates with r/n < 2^-12 take
+// the FP64 steps. Both give the bits of lattice_coord.
+struct LatticeWalk {
+    uint64_t Q;
+    uint32_t r, R;
+};
+
+// floor(a 2^64 / n) and a 2^64 mod n for a < n < 2^32: two long-division
+// steps of 32 bits each
+__host__ __device__ __forceinline__ void fixdiv64(uint64_t a, uint64_t n, uint64_t &q, uint64_t &rem) {
+    const uint64_t h = a << 32;
+    const uint64_t q1 = h / n, r1 = h - q1 * n;
+    const uint64_t l = r1 << 32;
+    const uint64_t q0 = l / n;
+    q = (q1 << 32) | q0;
+    rem = l - q0 * n;
+}
+
+__device__ __forceinline__ void walk_init(LatticeWalk &w, uint64_t r0, uint64_t n) {
+    uint64_t R;
+    w.r = (uint32_t)r0;
+    fixdiv64(r0, n, w.Q, R);
+    w.R = (uint32_t)R;
+}
+
+// One step k -> k + 1 with z, rz < n < 2^32. A 32-bit sum of two residues
+// may wrap; a wrapped sum exceeds n as well, and subtracting n modulo 2^32
+// gives the residue either way.
+__device__ __forceinline__ void walk_step(LatticeWalk &w, uint32_t z, uint64_t qz, uint32_t rz, uint32_t n) {
+    const uint32_t rn = w.r + z;
+    w.r = (rn >= n || rn < w.r) ? rn - n : rn;
+    const uint32_t R = w.R + rz;
+    const bool c = R >= n || R < w.R;
+    w.R = c ? R - n : R;
+    w.Q += qz + (c ? 1ULL : 0ULL);
+}
+
+// RN(s 2^-64) for s < 2^64 (integer operations on the bits)
+__device__ __forceinline__ double fix64_to_double_rn(uint64_t s) {
+    if (s < (1ULL << 53)) {                     // at most 53 significant bits: exact
+        if (s == 0) return 0.0;
+        const int p = 63 - __clzll((long long)s);
+        const uint64_t mant = (s << (52 - p)) & 0x000FFFFFFFFFFFFFULL;
+        return __longlong_as_double((long long)(((uint64_t)(1023 + p - 64) << 52) | mant));
+    }
+    const int sh = 11 - __clzll((long long)s);   // 1..11 dropped bits
+    uint64_t m = s >> sh;
+    const uint64_t dropped = s & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+    m += (dropped > half || (dropped == half && (m & 1))) ? 1 : 0;
+    // s 2^-64 = m 2^(sh - 64), m in [2^52, 2^53]: a carry moves into the exponent
+    return __longlong_as_double((long long)(((uint64_t)(1023 + 52 + sh - 64 - 1) << 52) + m));
+}
+
+// delta as a multiple of 2^-64, if it is one (delta in [0, 1))
+__device__ __forceinline__ bool delta_fix(double delta, uint64_t &D) {
+    const uint64_t b = (uint64_t)__double_as_longlong(delta);
+    D = 0;
+    if (b == 0) return true;
+    const int e = (int)(b >> 52) - 1023;        // delta = 1.f 2^e, e <= -1
+    if (e >= 0 || e < -1022) return false;
+    const uint64_t mant = (b & 0x000FFFFFFFFFFFFFULL) | (1ULL << 52);
+    const int sh = 64 + e - 52;                 // delta 2^64 = mant 2^sh
+    if (sh >= 0) {
+        D = mant << sh;
+        return true;
+    }
+    if (sh < -52 || (mant & ((1ULL << -sh) - 1))) return false;
+    D = mant >> -sh;
+    return true;
+}
+
+// The coordinate of the walk with shift delta (D = delta 2^64 when dfix_ok)
+__device__ __forceinline__ double walk_coord(const LatticeWalk &w, uint32_t n, double nd, double inv_n, double delta,
+                                             uint64_t D, bool dfix_ok) {
+    const uint64_t Q = w.Q;
+    if (!dfix_ok || Q < (1ULL << 52)) return lattice_coord(w.r, nd, inv_n, delta);
+    // RN(r/n) 2^64: keep 53 bits of Q, round with the dropped bits and R/n
+    const int sh = 11 - __clzll((long long)Q);   // 0..11
+    uint64_t m = Q >> sh;
+    bool up;
+    if (sh == 0) {
+        up = 2 * (uint64_t)w.R > n || (2 * (uint64_t)w.R == n && (m & 1));
+    } else {
+        const uint64_t dropped = Q & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+        up = dropped > half || (dropped == half && (w.R != 0 || (m & 1)));
+    }
+    const uint64_t q = (m + (up ? 1 : 0)) << sh;   // < 2^64: r/n <= 1 - 1/n
+    const uint64_t sum = q + D;
+    if (sum >= q) {                                 // q + delta < 1; a sum rounded to 1 folds to 0
+        const double x = fix64_to_double_rn(sum);
+        return nonneg_ge_one(x) ? 0.0 : x;
+    }
+    // q + delta in [1, 2): round to the 2^-52 grid (ties to even on bit 12),
+    // then subtract 1; a sum rounded up to 2 folds to 0
+    uint64_t y = sum >> 12;
+    const uint64_t low = sum & 0xFFF;
+    y += (low > 0x800 || (low == 0x800 && (y & 1))) ? 1 : 0;
+    if (y >= (1ULL << 52)) return 0.0;
+    if (y == 0) return 0.0;
+    const int p = 63 - __clzll((long long)y);
+    const uint64_t mant = (y << (52 - p)) & 0x000FFFFFFFFFFFFFULL;
+    return __longlong_as_double((long long)(((uint64_t)(1023 + p - 52) << 52) | mant));
+}
+
 // Natural logarithm: the fixed-point evaluation of qmc_ilog.h on the integer
 // pipe (Tang's reduction with a 1025-row table; within 0.501 ulp). `tab` is
 // the table of that header, staged in shared memory.
@@ -238,6 +351,10 @@ struct TileSmem {
     double cval[QMC_MAXMONO];
     float cvalf[QMC_MAXMONO];
     double delta[QMC_DMAX];
+    uint64_t dfix[QMC_DMAX];   // delta 2^64
+    uint64_t qz[QMC_DMAX];     // floor(z 2^64 / n)
+    uint32_t rz[QMC_DMAX];     // z 2^64 mod n
+    uint32_t zmod[QMC_DMAX];   // z mod n
     double invb[QMC_SMAX];
     double invb_full;  // prod over the singular slots of 1/b_q (A of the full pole set)
     uint64_t logtab[3 * QMC_LOG_TABLE_ROWS];
@@ -1066,6 +1183,12 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
             int j = threadIdx.x;
             S.delta[j] = (j < S.sec.d && !(S.job.flags & 1))
                              ? splitmix_uniform(S.job.seed_state, (uint64_t)s * S.sec.d + j) : 0.0;
+            S.dfix[j] = (uint64_t)(S.delta[j] * 18446744073709551616.0);   // exact: delta is a multiple of 2^-53
+            uint64_t qz = 0, rz = 0, zm = (uint64_t)S.job.z[j] % S.job.n;
+            if (j < S.sec.d) fixdiv64(zm, S.job.n, qz, rz);
+            S.qz[j] = qz;
+            S.rz[j] = (uint32_t)rz;
+            S.zmod[j] = (uint32_t)zm;
         }
         __syncthreads();
 
@@ -1081,15 +1204,12 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
         const uint64_t kt1 = min(n, kt0 + (uint64_t)Lc.tile_k);
         const uint64_t k0 = kt0 + (uint64_t)threadIdx.x * (uint64_t)ppt;
         if (k0 < kt1) {
-            uint64_t r[DMAX];
-            uint64_t zz[DMAX];
-            double dl[DMAX];
+            // per coordinate only the walk lives in registers; z, the
+            // expansion of z/n and the shift are read from shared memory
+            LatticeWalk wk[DMAX];
+            const uint32_t n32 = (uint32_t)n;
 #pragma unroll
-            for (int j = 0; j < DMAX; ++j) {
-                zz[j] = S.job.z[j];
-                r[j] = (j < d) ? (k0 * zz[j]) % n : 0;
-                dl[j] = S.delta[j];
-            }
+            for (int j = 0; j < DMAX; ++j) walk_init(wk[j], (j < d) ? (k0 * (uint64_t)S.zmod[j]) % n : 0, n);
             const uint64_t kend = min(kt1, k0 + (uint64_t)ppt);
 #pragma unroll 1
             for (uint64_t k = k0; k < kend; ++k) {
@@ -1101,7 +1221,7 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
                     t[j] = 1.0;
                     omt[j] = 0.0;
                     if (j < d) {
-                        const double u = lattice_coord(r[j], nd, inv_n, dl[j]);
+                        const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
                         if (Lc.transform == 0) {          // korobov3
                             const double u2 = u * u;
                             t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
@@ -1119,8 +1239,7 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
                             omt[j] = 1.0 - u;
                         }
                         zero_t |= nonneg_is_zero(t[j]);
-                        uint64_t rn = r[j] + zz[j];
-                        r[j] = (rn >= n) ? rn - n : rn;
+                        walk_step(wk[j], S.zmod[j], S.qz[j], S.rz[j], n32);
                     }
                 }
                 const double W = Lc.transform == 0 ? Ws * Ws * Ws : 1.0;   // 140^d: per tile
@@ -1205,17 +1324,29 @@ __global__ void qmc_finish_kernel(QmcLaunch Lc) {
     if (j == 0 && threadIdx.x == 0) *Lc.queue = 0ULL;
 }
 
+// Each thread walks kQmcLatticeRun consecutive indices with the evaluator's
+// integer walk (the first one set up by division, the rest by steps).
+constexpr int kQmcLatticeRun = 8;
 __global__ void qmc_lattice_kernel(uint64_t n, double inv_n, const uint32_t *z, int d,
                                    const double *delta, uint64_t k0, uint64_t count, double *x,
                                    uint64_t *rout) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const uint64_t k = k0 + i;
+    const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kQmcLatticeRun;
+    if (i0 >= count) return;
+    const uint64_t i1 = min(count, i0 + (uint64_t)kQmcLatticeRun);
     for (int j = 0; j < d; ++j) {
-        // (k mod n) * z < 2^64 for n < 2^32
-        const uint64_t r = ((k % n) * (uint64_t)z[j]) % n;
-        x[i * d + j] = lattice_coord(r, (double)n, inv_n, delta[j]);
-        if (rout) rout[i * d + j] = r;
+        const uint64_t zj = (uint64_t)z[j] % n;
+        uint64_t qz, rz, D;
+        fixdiv64(zj, n, qz, rz);
+        const uint32_t n32 = (uint32_t)n;
+        const bool dok = delta_fix(delta[j], D);
+        LatticeWalk w;
+        // ((k0 + i0) mod n) z < 2^64 for n < 2^32
+        walk_init(w, (((k0 + i0) % n) * zj) % n, n);
+        for (uint64_t i = i0; i < i1; ++i) {
+            x[i * d + j] = walk_coord(w, n32, (double)n, inv_n, delta[j], D, dok);
+            if (rout) rout[i * d + j] = w.r;
+            walk_step(w, (uint32_t)zj, qz, (uint32_t)rz, n32);
+        }
     }
 }
 
@@ -1316,7 +1447,8 @@ extern "C" int qmc_k_lattice_points(uint64_t n, const uint32_t *z_dev, int d, co
                                     uint64_t k0, uint64_t count, double *x_dev, uint64_t *r_dev,
                                     void *stream) {
     if (count == 0) return 0;
-    const unsigned grid = (unsigned)((count + 255) / 256);
+    const uint64_t threads = (count + kQmcLatticeRun - 1) / kQmcLatticeRun;
+    const unsigned grid = (unsigned)((threads + 255) / 256);
     qmc_lattice_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, 1.0 / (double)n, z_dev, d, delta_dev, k0,
                                                                count, x_dev, r_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

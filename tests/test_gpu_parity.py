@@ -56,6 +56,33 @@ def test_lattice_points_bit_exact(gpu, n, d):
         assert np.array_equal(xg.view(np.uint64), xo.view(np.uint64))
 
 
+def test_lattice_points_bit_exact_whole_lattice(gpu):
+    """Every point of shifted lattices, walked in runs the way the evaluator
+    walks them: the integer path (rounding of r/n read off its 64-place
+    binary expansion, exact sum with the shift, the fold above 1), the FP64
+    path of the coordinates with r/n < 2^-12, and shifts that are not
+    multiples of 2^-64 (FP64 path throughout)."""
+    n = 1000003
+    z = np.array(lattice_for(n, 3)[1], dtype=np.uint32)
+    for s in range(2):
+        delta = oracle.shifts(9, s, 1, 3)[0]
+        xg, rg = qmc.qmc_lattice_points(gpu.ctx, n, z, delta, 0, n)
+        xo, ro = oracle.lattice_points(n, z, delta, 0, n)
+        assert np.array_equal(rg, ro)
+        assert np.array_equal(xg.view(np.uint64), xo.view(np.uint64))
+    rng = np.random.default_rng(12)
+    for n in (4294967291, 2147483648, 99991):
+        z = np.array([int(rng.integers(1, n)) | 1 for _ in range(3)], dtype=np.uint32)
+        for delta in (oracle.shifts(3, 1, 1, 3)[0], np.array([0.5, 2.0 ** -60, 1.0 - 2.0 ** -53]),
+                      np.array([3e-20, 0.7 + 2.0 ** -40, 1e-300])):
+            k0 = int(rng.integers(0, max(1, n - 300000)))
+            cnt = min(300000, n - k0)
+            xg, rg = qmc.qmc_lattice_points(gpu.ctx, n, z, delta, k0, cnt)
+            xo, ro = oracle.lattice_points(n, z, delta, k0, cnt)
+            assert np.array_equal(rg, ro)
+            assert np.array_equal(xg.view(np.uint64), xo.view(np.uint64)), (n, delta)
+
+
 def test_lattice_division_exhaustive(gpu):
     # every r of one lattice, and random r near 2^32: the corrected division is RN(r/n)
     n = 1000003
