@@ -21,6 +21,7 @@
 extern "C" int qmc_k_shifts(uint64_t state, int m, int d, double *out_dev, void *stream);
 extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_rcp(const double *x_dev, uint64_t n, double *out_dev, void *stream);
+extern "C" int qmc_k_korobov(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_atan2(const double *yx_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_occupancy(int cls, int block);
 
@@ -886,7 +887,8 @@ int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, doubl
 // positive_normal: the function's domain is the positive normal doubles
 // (others are rejected); otherwise every double is accepted
 static int fp64_apply(qmc_ctx *ctx, const double *x, size_t n, double *out, const char *name,
-                      int (*launch)(const double *, uint64_t, double *, void *), bool positive_normal) {
+                      int (*launch)(const double *, uint64_t, double *, void *), bool positive_normal,
+                      size_t out_per = 1) {
     if (!ctx || (n && (!x || !out))) return fail(ctx, QMC_E_INVAL, "%s: bad arguments", name);
     for (size_t i = 0; positive_normal && i < n; ++i)
         if (!(x[i] >= 2.2250738585072014e-308) || !std::isfinite(x[i]))
@@ -895,12 +897,13 @@ static int fp64_apply(qmc_ctx *ctx, const double *x, size_t n, double *out, cons
     cudaSetDevice(ctx->device);
     double *dx = nullptr, *dy = nullptr;
     int rc = QMC_OK;
-    if (cudaMalloc(&dx, n * sizeof(double)) != cudaSuccess || cudaMalloc(&dy, n * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&dx, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dy, n * out_per * sizeof(double)) != cudaSuccess) {
         rc = fail(ctx, QMC_E_CUDA, "%s: allocation failed", name);
     } else {
         cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
         if (launch(dx, n, dy, ctx->stream)) rc = fail(ctx, QMC_E_CUDA, "%s: kernel launch failed", name);
-        cudaMemcpyAsync(out, dy, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(out, dy, n * out_per * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (!rc && e != cudaSuccess) rc = fail(ctx, QMC_E_CUDA, "%s: %s", name, cudaGetErrorString(e));
     }
@@ -915,6 +918,14 @@ int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out) {
 
 int qmc_fp64_rcp(qmc_ctx *ctx, const double *x, size_t n, double *out) {
     return fp64_apply(ctx, x, n, out, "qmc_fp64_rcp", qmc_k_rcp, true);
+}
+
+int qmc_korobov3(qmc_ctx *ctx, const double *u, size_t n, double *out) {
+    if (ctx)
+        for (size_t i = 0; u && i < n; ++i)
+            if (!(u[i] >= 0.0 && u[i] < 1.0) || (u[i] > 0.0 && u[i] < 2.2250738585072014e-308))
+                return fail(ctx, QMC_E_INVAL, "qmc_korobov3: u[%zu] is not 0 or a normal number in (0, 1)", i);
+    return fp64_apply(ctx, u, n, out, "qmc_korobov3", qmc_k_korobov, false, 2);
 }
 
 int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, double *out) {

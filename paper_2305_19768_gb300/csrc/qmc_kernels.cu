@@ -199,6 +199,57 @@ __device__ __forceinline__ double walk_coord(const LatticeWalk &w, uint32_t n, d
     return __longlong_as_double((long long)(((uint64_t)(1023 + p - 52) << 52) | mant));
 }
 
+// korobov3 on the integer pipe for u in (0, 1): t = u^4 P(u), P(u) = 35 -
+// 84u + 70u^2 - 20u^3, and ws = u (1 - u) (the weight is 140^d prod ws^3).
+// u = mu 2^(e-52) with its 53-bit mantissa; u^2 and u^4 are mantissa
+// products kept to 64 bits (truncated). P runs by Horner on U = floor(u 2^64)
+// with nonnegative intermediate values: for u < 1/2 as 35 - u(84 - u(70 -
+// 20u)) in Q57 (P >= 8 there), for u >= 1/2 in v = 1 - u as 1 + v(4 + v(10 +
+// 20v)) in Q59 (P >= 1); v = (2^64 - U) 2^-64 is exact for u >= 2^-11 (else
+// within 2^-64). Each result is one 128-bit product rounded once to nearest:
+// within about 0.53 ulp of the exact values for this u.
+// RN((a b) 2^x) for a b > 0; 0 where the result would not be normal
+__device__ __forceinline__ double round_pack(uint64_t a, uint64_t b, int x) {
+    const qmc_u128 r = (qmc_u128)a * b;
+    const uint64_t hi = (uint64_t)(r >> 64), lo = (uint64_t)r;
+    if ((hi | lo) == 0) return 0.0;
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+    const int E = 127 - lz + x;                       // leading bit 2^E
+    if (E < -1022) return 0.0;
+    const qmc_u128 N = r << lz;
+    const uint64_t nh = (uint64_t)(N >> 64), nl = (uint64_t)N;
+    uint64_t mant = nh >> 11;
+    const bool round_bit = ((nh >> 10) & 1) != 0, sticky = (nh & 0x3FF) != 0 || nl != 0;
+    mant += (round_bit && (sticky || (mant & 1))) ? 1 : 0;
+    return __longlong_as_double((long long)(((uint64_t)(1023 + E - 1) << 52) + mant));
+}
+
+__device__ __forceinline__ void korobov3_int(double u, double &t, double &ws) {
+    const uint64_t b = (uint64_t)__double_as_longlong(u);
+    const int e = (int)(b >> 52) - 1023;              // -1022 <= e <= -1 for a normal u < 1
+    const uint64_t mu = (b & 0x000FFFFFFFFFFFFFULL) | (1ULL << 52);
+    const int s = e + 12;                             // u 2^64 = mu 2^s
+    const uint64_t U = s >= 0 ? mu << s : (s > -53 ? mu >> -s : 0);
+    const uint64_t V = U ? 0 - U : ~0ULL;             // (1 - u) 2^64 (u < 2^-64: 2^64 - 1)
+    uint64_t P;
+    int pq;
+    if (U < (1ULL << 63)) {
+        const uint64_t a1 = (70ULL << 57) - __umul64hi(U, 20ULL << 57);
+        const uint64_t a2 = (84ULL << 57) - __umul64hi(U, a1);
+        P = (35ULL << 57) - __umul64hi(U, a2);
+        pq = 57;
+    } else {
+        const uint64_t a1 = (10ULL << 59) + __umul64hi(V, 20ULL << 59);
+        const uint64_t a2 = (4ULL << 59) + __umul64hi(V, a1);
+        P = (1ULL << 59) + __umul64hi(V, a2);
+        pq = 59;
+    }
+    const uint64_t p2 = (uint64_t)(((qmc_u128)mu * mu) >> 42);   // u^2 = p2 2^(2e - 62)
+    const uint64_t p4 = __umul64hi(p2, p2);                       // u^4 = p4 2^(4e - 60)
+    t = round_pack(p4, P, 4 * e - 60 - pq);
+    ws = round_pack(mu, V, e - 52 - 64);
+}
+
 // Natural logarithm: the fixed-point evaluation of qmc_ilog.h on the integer
 // pipe (Tang's reduction with a 1025-row table; within 0.501 ulp). `tab` is
 // the table of that header, staged in shared memory.
@@ -1131,7 +1182,11 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
 
 // ---------------------------------------------------------------- the evaluator
 #ifndef QMC_MINB
-#define QMC_MINB 3   // resident 128-thread blocks per SM the real evaluator's registers must allow
+// resident 128-thread blocks per SM the real d <= 3 evaluator's registers
+// must allow: with the logarithm, lattice and transform on the integer pipe
+// the kernel is latency-bound, and 16 warps per SM (128 registers, some
+// spilled to L1) beat 12 without spills
+#define QMC_MINB 4
 #endif
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false>
@@ -1223,14 +1278,24 @@ __global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB
                     if (j < d) {
                         const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
                         if (Lc.transform == 0) {          // korobov3
-                            const double u2 = u * u;
-                            t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
-                            if (CPLX) {
+                            // integer pipe for the real d <= 3 classes; the
+                            // deformed ones also need 1 - t, and the d <= 6
+                            // ones run two blocks per SM at the register limit,
+                            // where the longer integer chain costs more than
+                            // its FP64 operations
+                            if constexpr (CPLX || DMAX > 3) {
+                                const double u2 = u * u;
+                                t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
                                 const double v = 1.0 - u;
                                 const double v2 = v * v;
-                                omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
+                                if (CPLX) omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
+                                Ws *= fma(-u, u, u);
+                            } else {
+                                double ws = 0.0;
+                                t[j] = 0.0;
+                                if (!nonneg_is_zero(u)) korobov3_int(u, t[j], ws);
+                                Ws = j == 0 ? ws : Ws * ws;
                             }
-                            Ws *= fma(-u, u, u);
                         } else if (Lc.transform == 1) {   // baker: t = 1 - |2u - 1|, weight 1
                             t[j] = u < 0.5 ? 2.0 * u : 2.0 * (1.0 - u);
                             omt[j] = u < 0.5 ? 1.0 - 2.0 * u : 2.0 * u - 1.0;
@@ -1355,6 +1420,15 @@ __global__ void qmc_log_kernel(const double *x, uint64_t n, double *out) {
     if (i < n) out[i] = qlog(x[i], kLogTable);
 }
 
+__global__ void qmc_korobov_kernel(const double *x, uint64_t n, double *out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double t = 0.0, ws = 0.0;
+    if (!nonneg_is_zero(x[i])) korobov3_int(x[i], t, ws);
+    out[2 * i] = t;
+    out[2 * i + 1] = ws;
+}
+
 __global__ void qmc_rcp_kernel(const double *x, uint64_t n, double *out) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = qrcp(x[i]);
@@ -1470,6 +1544,12 @@ extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void 
 extern "C" int qmc_k_atan2(const double *yx_dev, uint64_t n, double *out_dev, void *stream) {
     if (n == 0) return 0;
     qmc_atan2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(yx_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+extern "C" int qmc_k_korobov(const double *x_dev, uint64_t n, double *out_dev, void *stream) {
+    if (n == 0) return 0;
+    qmc_korobov_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -110,6 +110,7 @@ def lib():
                 "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
                 "qmc_fp64_log": ([vp, P(dbl), sz, P(dbl)], i32),
                 "qmc_fp64_rcp": ([vp, P(dbl), sz, P(dbl)], i32),
+                "qmc_korobov3": ([vp, P(dbl), sz, P(dbl)], i32),
                 "qmc_fp64_atan2": ([vp, P(dbl), P(dbl), sz, P(dbl)], i32),
                 "qmc_shift_stats": ([P(dbl), i32, i32, P(dbl), P(dbl)], i32),
                 "qmc_plan_use_graph": ([vp, i32], i32),
@@ -152,7 +153,7 @@ def exported_symbols():
             "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
-            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp", "qmc_fp64_atan2",
+            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp", "qmc_korobov3", "qmc_fp64_atan2",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
             "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_gemm_bf16_device", "qmc_mlp_create",
@@ -459,6 +460,14 @@ def qmc_fp64_atan2(ctx, y, x):
     out = np.zeros_like(x)
     _check(ctx, lib().qmc_fp64_atan2(ctx, _dp(y), _dp(x), x.size, _dp(out)))
     return out
+
+
+def qmc_korobov3(ctx, u):
+    """(t, u (1 - u)) of the evaluator's korobov3 transform at each u."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros((u.size, 2))
+    _check(ctx, lib().qmc_korobov3(ctx, _dp(u), u.size, _dp(out)))
+    return out[:, 0].copy(), out[:, 1].copy()
 
 
 def qmc_fp64_rcp(ctx, x):
