@@ -1182,15 +1182,15 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
 
 // ---------------------------------------------------------------- the evaluator
 #ifndef QMC_MINB
-// resident 128-thread blocks per SM the real d <= 3 evaluator's registers
-// must allow: with the logarithm, lattice and transform on the integer pipe
+// resident 128-thread blocks per SM (or half as many of 256 threads) the
+// real d <= 3 evaluator's registers must allow: with the logarithm, lattice and transform on the integer pipe
 // the kernel is latency-bound, and 16 warps per SM (128 registers, some
 // spilled to L1) beat 12 without spills
 #define QMC_MINB 4
 #endif
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false>
-__global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
+__global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB * 128 / BLOCK) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
     using T = typename std::conditional<CPLX, dc, double>::type;
     const int lo = Lc.lo, nord = Lc.norders;
