@@ -1182,15 +1182,33 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
 
 // ---------------------------------------------------------------- the evaluator
 #ifndef QMC_MINB
-// resident 128-thread blocks per SM (or half as many of 256 threads) the
-// real d <= 3 evaluator's registers must allow: with the logarithm, lattice and transform on the integer pipe
-// the kernel is latency-bound, and 16 warps per SM (128 registers, some
-// spilled to L1) beat 12 without spills
+// Resident 128-thread blocks per SM (or half as many of 256 threads) the
+// real d <= 3 evaluator's registers must allow. With the logarithm, lattice
+// and transform on the integer pipe the kernel is latency-bound, and 16
+// warps per SM (128 registers, some spilled to L1) beat 12 without spills.
 #define QMC_MINB 4
 #endif
 
+// The same for the deformed and the d <= 6 classes, which need up to 255
+// registers without a bound: 3 blocks (170 registers, spills to L1) beat 2
+// blocks by 12 to 24 %; the mixed-precision deformed class, with fewer live
+// FP64 values, goes best at 4 (128 registers)
+#ifndef QMC_MINB_WIDE
+#define QMC_MINB_WIDE 3
+#endif
+#ifndef QMC_MINB_WIDE_MIXED
+#define QMC_MINB_WIDE_MIXED 4
+#endif
+
+template <int BLOCK, bool WIDE, bool CPLX_MIXED, bool HS>
+constexpr int qmc_min_blocks() {
+    return HS ? 1
+              : WIDE ? ((CPLX_MIXED ? QMC_MINB_WIDE_MIXED : QMC_MINB_WIDE) * 128 + BLOCK - 1) / BLOCK
+                     : QMC_MINB * 128 / BLOCK;
+}
+
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false>
-__global__ void __launch_bounds__(BLOCK, (CPLX || DMAX > 3 || HS) ? 1 : QMC_MINB * 128 / BLOCK) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
+__global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3), (CPLX && MIXED), HS>()) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
     using T = typename std::conditional<CPLX, dc, double>::type;
     const int lo = Lc.lo, nord = Lc.norders;
