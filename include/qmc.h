@@ -419,12 +419,13 @@ int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, 
  * gives NaN, subnormals are accepted. Errors: QMC_E_INVAL for null arrays. */
 int qmc_fp64_log(qmc_ctx *ctx, const double *x, size_t n, double *out);
 
-/* The evaluator's korobov3 transform of the real integrands (timings
+/* The evaluator's korobov3 transform of the d <= 3 integrands (timings
  * section of the paper: the korobov3 periodizing transform) applied on the
- * device to n points u (host arrays u[n] -> out[n][2]): out[i][0] = t =
- * u^4 (35 - 84u + 70u^2 - 20u^3), out[i][1] = u (1 - u) (the weight is
+ * device to n points u (host arrays u[n] -> out[n][3]): out[i][0] = t =
+ * phi(u) = u^4 (35 - 84u + 70u^2 - 20u^3), out[i][1] = 1 - t = phi(1 - u)
+ * (with the exact 1 - u), out[i][2] = u (1 - u) (the weight is
  * 140 (u (1 - u))^3 per coordinate). Integer fixed-point products, rounded
- * once: within about 0.5 ulp of the exact values. u = 0 gives (0, 0).
+ * once: within about 0.53 ulp of the exact values. u = 0 gives (0, 1, 0).
  * Errors: QMC_E_INVAL for null arrays or a u outside {0} and the normal
  * numbers of (0, 1). */
 int qmc_korobov3(qmc_ctx *ctx, const double *u, size_t n, double *out);

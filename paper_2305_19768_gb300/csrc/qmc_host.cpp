@@ -925,7 +925,7 @@ int qmc_korobov3(qmc_ctx *ctx, const double *u, size_t n, double *out) {
         for (size_t i = 0; u && i < n; ++i)
             if (!(u[i] >= 0.0 && u[i] < 1.0) || (u[i] > 0.0 && u[i] < 2.2250738585072014e-308))
                 return fail(ctx, QMC_E_INVAL, "qmc_korobov3: u[%zu] is not 0 or a normal number in (0, 1)", i);
-    return fp64_apply(ctx, u, n, out, "qmc_korobov3", qmc_k_korobov, false, 2);
+    return fp64_apply(ctx, u, n, out, "qmc_korobov3", qmc_k_korobov, false, 3);
 }
 
 int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, double *out) {

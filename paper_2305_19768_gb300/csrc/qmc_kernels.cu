@@ -199,15 +199,18 @@ __device__ __forceinline__ double walk_coord(const LatticeWalk &w, uint32_t n, d
     return __longlong_as_double((long long)(((uint64_t)(1023 + p - 52) << 52) | mant));
 }
 
-// korobov3 on the integer pipe for u in (0, 1): t = u^4 P(u), P(u) = 35 -
-// 84u + 70u^2 - 20u^3, and ws = u (1 - u) (the weight is 140^d prod ws^3).
-// u = mu 2^(e-52) with its 53-bit mantissa; u^2 and u^4 are mantissa
-// products kept to 64 bits (truncated). P runs by Horner on U = floor(u 2^64)
-// with nonnegative intermediate values: for u < 1/2 as 35 - u(84 - u(70 -
-// 20u)) in Q57 (P >= 8 there), for u >= 1/2 in v = 1 - u as 1 + v(4 + v(10 +
-// 20v)) in Q59 (P >= 1); v = (2^64 - U) 2^-64 is exact for u >= 2^-11 (else
-// within 2^-64). Each result is one 128-bit product rounded once to nearest:
-// within about 0.53 ulp of the exact values for this u.
+// korobov3 on the integer pipe for u in (0, 1): t = phi(u) = u^4 P(u),
+// P(u) = 35 - 84u + 70u^2 - 20u^3; 1 - t = phi(1 - u); and ws = u (1 - u)
+// (the weight is 140^d prod ws^3).
+// phi(x) for x = M 2^(e-63) (M a normalised 64-bit mantissa) with
+// X = floor(x 2^64): x^2 and x^4 are mantissa products kept to 64 bits
+// (truncated); P runs by Horner on X with nonnegative intermediate values,
+// for x < 1/2 as 35 - x(84 - x(70 - 20x)) in Q57 (P >= 8 there), for
+// x >= 1/2 in y = 1 - x as 1 + y(4 + y(10 + 20y)) in Q59 (P >= 1), with
+// y 2^64 = 2^64 - X. t takes x = u from the mantissa of u; 1 - t takes
+// x = 1 - u from V = 2^64 - U, which is exact for u >= 2^-11 (else within
+// 2^-64 relative). Each result is one 128-bit product rounded once to
+// nearest: within about 0.53 ulp of the exact values for this u.
 // RN((a b) 2^x) for a b > 0; 0 where the result would not be normal
 __device__ __forceinline__ double round_pack(uint64_t a, uint64_t b, int x) {
     const qmc_u128 r = (qmc_u128)a * b;
@@ -224,29 +227,39 @@ __device__ __forceinline__ double round_pack(uint64_t a, uint64_t b, int x) {
     return __longlong_as_double((long long)(((uint64_t)(1023 + E - 1) << 52) + mant));
 }
 
-__device__ __forceinline__ void korobov3_int(double u, double &t, double &ws) {
+__device__ __forceinline__ double korobov_phi_fix(uint64_t M, int e, uint64_t X) {
+    uint64_t P;
+    int pq;
+    if (X < (1ULL << 63)) {
+        const uint64_t a1 = (70ULL << 57) - __umul64hi(X, 20ULL << 57);
+        const uint64_t a2 = (84ULL << 57) - __umul64hi(X, a1);
+        P = (35ULL << 57) - __umul64hi(X, a2);
+        pq = 57;
+    } else {
+        const uint64_t Y = 0 - X;
+        const uint64_t a1 = (10ULL << 59) + __umul64hi(Y, 20ULL << 59);
+        const uint64_t a2 = (4ULL << 59) + __umul64hi(Y, a1);
+        P = (1ULL << 59) + __umul64hi(Y, a2);
+        pq = 59;
+    }
+    const uint64_t p2 = __umul64hi(M, M);             // x^2 = p2 2^(2e - 62)
+    const uint64_t p4 = __umul64hi(p2, p2);           // x^4 = p4 2^(4e - 60)
+    return round_pack(p4, P, 4 * e - 60 - pq);
+}
+
+template <bool OMT>
+__device__ __forceinline__ void korobov3_int(double u, double &t, double &omt, double &ws) {
     const uint64_t b = (uint64_t)__double_as_longlong(u);
     const int e = (int)(b >> 52) - 1023;              // -1022 <= e <= -1 for a normal u < 1
     const uint64_t mu = (b & 0x000FFFFFFFFFFFFFULL) | (1ULL << 52);
     const int s = e + 12;                             // u 2^64 = mu 2^s
     const uint64_t U = s >= 0 ? mu << s : (s > -53 ? mu >> -s : 0);
     const uint64_t V = U ? 0 - U : ~0ULL;             // (1 - u) 2^64 (u < 2^-64: 2^64 - 1)
-    uint64_t P;
-    int pq;
-    if (U < (1ULL << 63)) {
-        const uint64_t a1 = (70ULL << 57) - __umul64hi(U, 20ULL << 57);
-        const uint64_t a2 = (84ULL << 57) - __umul64hi(U, a1);
-        P = (35ULL << 57) - __umul64hi(U, a2);
-        pq = 57;
-    } else {
-        const uint64_t a1 = (10ULL << 59) + __umul64hi(V, 20ULL << 59);
-        const uint64_t a2 = (4ULL << 59) + __umul64hi(V, a1);
-        P = (1ULL << 59) + __umul64hi(V, a2);
-        pq = 59;
+    t = korobov_phi_fix(mu << 11, e, U);
+    if (OMT) {
+        const int lz = __clzll((long long)V);         // V >= 2^11
+        omt = korobov_phi_fix(V << lz, -1 - lz, V);
     }
-    const uint64_t p2 = (uint64_t)(((qmc_u128)mu * mu) >> 42);   // u^2 = p2 2^(2e - 62)
-    const uint64_t p4 = __umul64hi(p2, p2);                       // u^4 = p4 2^(4e - 60)
-    t = round_pack(p4, P, 4 * e - 60 - pq);
     ws = round_pack(mu, V, e - 52 - 64);
 }
 
@@ -1296,22 +1309,20 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
                     if (j < d) {
                         const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
                         if (Lc.transform == 0) {          // korobov3
-                            // integer pipe for the real d <= 3 classes; the
-                            // deformed ones also need 1 - t, and the d <= 6
-                            // ones run two blocks per SM at the register limit,
-                            // where the longer integer chain costs more than
-                            // its FP64 operations
-                            if constexpr (CPLX || DMAX > 3) {
+                            // integer pipe for the d <= 3 classes (with
+                            // 1 - t for the deformed ones); the d <= 6
+                            // classes run at the register limit, where the
+                            // longer integer chain costs more than its FP64
+                            // operations
+                            if constexpr (!CPLX && DMAX > 3) {
                                 const double u2 = u * u;
                                 t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
-                                const double v = 1.0 - u;
-                                const double v2 = v * v;
-                                if (CPLX) omt[j] = v2 * v2 * fma(v, fma(v, fma(v, -20.0, 70.0), -84.0), 35.0);
                                 Ws *= fma(-u, u, u);
                             } else {
-                                double ws = 0.0;
+                                double ws = 0.0, om = 1.0;
                                 t[j] = 0.0;
-                                if (!nonneg_is_zero(u)) korobov3_int(u, t[j], ws);
+                                if (!nonneg_is_zero(u)) korobov3_int<CPLX>(u, t[j], om, ws);
+                                if (CPLX) omt[j] = om;
                                 Ws = j == 0 ? ws : Ws * ws;
                             }
                         } else if (Lc.transform == 1) {   // baker: t = 1 - |2u - 1|, weight 1
@@ -1441,10 +1452,11 @@ __global__ void qmc_log_kernel(const double *x, uint64_t n, double *out) {
 __global__ void qmc_korobov_kernel(const double *x, uint64_t n, double *out) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double t = 0.0, ws = 0.0;
-    if (!nonneg_is_zero(x[i])) korobov3_int(x[i], t, ws);
-    out[2 * i] = t;
-    out[2 * i + 1] = ws;
+    double t = 0.0, omt = 1.0, ws = 0.0;
+    if (!nonneg_is_zero(x[i])) korobov3_int<true>(x[i], t, omt, ws);
+    out[3 * i] = t;
+    out[3 * i + 1] = omt;
+    out[3 * i + 2] = ws;
 }
 
 __global__ void qmc_rcp_kernel(const double *x, uint64_t n, double *out) {

@@ -463,11 +463,11 @@ def qmc_fp64_atan2(ctx, y, x):
 
 
 def qmc_korobov3(ctx, u):
-    """(t, u (1 - u)) of the evaluator's korobov3 transform at each u."""
+    """(t, 1 - t, u (1 - u)) of the evaluator's korobov3 transform at each u."""
     u = np.ascontiguousarray(u, dtype=np.float64)
-    out = np.zeros((u.size, 2))
+    out = np.zeros((u.size, 3))
     _check(ctx, lib().qmc_korobov3(ctx, _dp(u), u.size, _dp(out)))
-    return out[:, 0].copy(), out[:, 1].copy()
+    return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy()
 
 
 def qmc_fp64_rcp(ctx, x):

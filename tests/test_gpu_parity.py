@@ -99,10 +99,9 @@ def test_lattice_division_exhaustive(gpu):
 
 
 def test_korobov3_against_exact_rationals(gpu):
-    """The integer-pipe korobov3 (t and u (1 - u)) against the exact rational
-    values of the polynomial at each double u, correctly rounded by Python's
-    Fraction -> float: within 0.55 ulp, on both halves of (0, 1), at the ends,
-    at tiny u and at 1/2."""
+    """The integer-pipe korobov3 (t = phi(u), 1 - t = phi(1 - u) and
+    u (1 - u)) against the exact rational values at each double u: within
+    0.55 ulp, on both halves of (0, 1), at the ends, at tiny u and at 1/2."""
     from fractions import Fraction
     rng = np.random.default_rng(17)
     us = np.concatenate([rng.uniform(0.0, 1.0, 20000), np.exp(rng.uniform(-55, 0, 5000)),
@@ -110,17 +109,21 @@ def test_korobov3_against_exact_rationals(gpu):
                          np.array([0.5, np.nextafter(0.5, 0.0), np.nextafter(0.5, 1.0), 2.0 ** -60, 1e-25,
                                    np.nextafter(1.0, 0.0), 2.0 ** -11, 0.25, 0.75])])
     us = us[(us > 0) & (us < 1)]
-    t, ws = qmc.qmc_korobov3(gpu.ctx, us)
-    worst_t = worst_w = 0.0
-    for u, gt, gw in zip(us, t, ws):
+    t, omt, ws = qmc.qmc_korobov3(gpu.ctx, us)
+
+    def ulps(got, exact):
+        return float(abs(Fraction(float(got)) - exact) / Fraction(float(np.spacing(float(exact)))))
+
+    worst = [0.0, 0.0, 0.0]
+    for u, gt, go, gw in zip(us, t, omt, ws):
         U = Fraction(float(u))
-        et = U ** 4 * (35 - 84 * U + 70 * U ** 2 - 20 * U ** 3)
-        ew = U * (1 - U)
-        worst_t = max(worst_t, float(abs(Fraction(float(gt)) - et) / Fraction(float(np.spacing(float(et))))))
-        worst_w = max(worst_w, float(abs(Fraction(float(gw)) - ew) / Fraction(float(np.spacing(float(ew))))))
-    assert worst_t <= 0.55 and worst_w <= 0.55, (worst_t, worst_w)
-    t0, w0 = qmc.qmc_korobov3(gpu.ctx, np.zeros(1))
-    assert t0[0] == 0.0 and w0[0] == 0.0
+        V = 1 - U
+        worst[0] = max(worst[0], ulps(gt, U ** 4 * (35 - 84 * U + 70 * U ** 2 - 20 * U ** 3)))
+        worst[1] = max(worst[1], ulps(go, V ** 4 * (35 - 84 * V + 70 * V ** 2 - 20 * V ** 3)))
+        worst[2] = max(worst[2], ulps(gw, U * V))
+    assert max(worst) <= 0.55, worst
+    t0, o0, w0 = qmc.qmc_korobov3(gpu.ctx, np.zeros(1))
+    assert t0[0] == 0.0 and o0[0] == 1.0 and w0[0] == 0.0
 
 
 def test_evaluator_reciprocal_within_one_ulp(gpu):
