@@ -77,3 +77,27 @@ def test_integer_log_against_libm_and_special_values(ilog):
     assert spec[0] == 0.0 and not np.signbit(spec[0])
     assert spec[1] == -np.inf and spec[2] == -np.inf and spec[3] == np.inf
     assert np.isnan(spec[4:]).all()
+
+
+def test_log_table_rows_are_exact_roundings():
+    """Rows of qmc_log_table.h: RN(2^63 / F_j) checked with exact rationals,
+    RN(2^116 ln F_j) with 60-digit decimal logarithms, on every 16th row and
+    the ends (F = 1 and F = 2 must be exact: ln F cancels e ln 2 there)."""
+    import re
+    from fractions import Fraction
+
+    text = open(os.path.join(CSRC, "qmc_log_table.h")).read()
+    body = text[text.index("QMC_LOG_TABLE_INIT"):text.index("}", text.index("QMC_LOG_TABLE_INIT"))]
+    words = [int(w, 16) for w in re.findall(r"0x[0-9a-f]+(?=ULL)", body)]
+    assert len(words) == 3 * 1025
+    getcontext().prec = 60
+    for j in list(range(0, 1025, 16)) + [1, 1023, 1024]:
+        F = Fraction(1024 + j, 1024)
+        inv, lo, hi = words[3 * j:3 * j + 3]
+        q = Fraction(2 ** 63) / F
+        assert inv == round(q)                                   # round() on Fraction: nearest
+        L = (Decimal(1024 + j) / Decimal(1024)).ln() * (Decimal(2) ** 116)
+        assert (hi << 64) | lo == int(L.to_integral_value())     # ROUND_HALF_EVEN, no ties here
+    assert words[0:3] == [2 ** 63, 0, 0]
+    ln2 = int(((Decimal(2)).ln() * (Decimal(2) ** 116)).to_integral_value())
+    assert (words[3 * 1024 + 2] << 64) | words[3 * 1024 + 1] == ln2 and words[3 * 1024] == 2 ** 62
