@@ -58,3 +58,27 @@ def test_median_candidates_match_the_input_generator():
         assert np.array_equal(z[:, :d], median_candidates(n, d, r, seed))
         assert np.all(z[:, d:] == 1)
         assert all(gcd(int(c), n) == 1 and 1 <= c < n for c in z[:, :d].ravel())
+
+
+def test_host_arithmetic_edge_cases():
+    """Documented edge behaviour of the host entry points: no shifts is an
+    error; empty series and orders outside the window give zeros; a sum with
+    no positive weight or no positive variance target leaves the lattices at
+    n_min; tau <= 0 and alpha <= 0 are errors."""
+    with pytest.raises(qmc.QmcError):
+        qmc.qmc_shift_stats(np.zeros((0, 2, 2)))
+    a = np.array([1.0 + 2.0j, 3.0 - 1.0j])
+    assert qmc.qmc_series_mul(a, -1, a, -1, -2, 0).size == 0
+    assert np.all(qmc.qmc_series_mul(a, -1, np.zeros(0, complex), 0, -2, 3) == 0)
+    assert np.all(qmc.qmc_series_mul(a, -1, a, -1, 5, 3) == 0)          # window above the product
+    assert np.all(qmc.qmc_series_var(a, 0, np.zeros(0), 0, 0, 2) == 0)
+    W = np.array([[0.0, 0.0], [1.0, 4.0], [2.0, 1.0]])
+    V = np.array([1e-6, -1.0, 1e-6])                                    # the second target is not > 0
+    n = qmc.qmc_allocate(W, np.ones(2), V, 2.0, 1000.0)
+    n_third = qmc.qmc_allocate(W[2:], np.ones(2), V[2:], 2.0, 1000.0)
+    assert np.array_equal(n, n_third)
+    assert np.array_equal(qmc.qmc_allocate(W[:1], np.ones(2), V[:1], 2.0, 1000.0), [1000.0, 1000.0])
+    with pytest.raises(qmc.QmcError):
+        qmc.qmc_allocate(W, np.array([1.0, 0.0]), V)
+    with pytest.raises(qmc.QmcError):
+        qmc.qmc_allocate(W, np.ones(2), V, alpha=0.0)
