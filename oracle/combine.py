@@ -27,7 +27,7 @@ def shift_stats(Q: np.ndarray):
     m = Q.shape[0]
     mean = Q.mean(axis=0)
     if m < 2:
-        return mean, np.full(Q.shape[1], np.inf + 1j * np.inf)
+        return mean, np.full(Q.shape[1], complex(np.inf, np.inf))   # no spread estimate from one shift
     vr = ((Q.real - mean.real) ** 2).sum(axis=0) / (m - 1)
     vi = ((Q.imag - mean.imag) ** 2).sum(axis=0) / (m - 1)
     return mean, vr / m + 1j * vi / m

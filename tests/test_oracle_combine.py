@@ -28,6 +28,33 @@ def test_shift_stats_unbiased_variance_of_mean():
     assert np.allclose(var.imag, np.var(Q.imag, axis=0, ddof=1) / 32)
 
 
+def test_shift_stats_hand_computed_cases():
+    # two shifts Q = 1 + 2i and 3 - 2i: mean 2 + 0i; the unbiased variances
+    # are ((1-2)^2 + (3-2)^2)/1 = 2 and ((2-0)^2 + (-2-0)^2)/1 = 8, so the
+    # variances of the mean are 2/2 = 1 and 8/2 = 4
+    mean, var = combine.shift_stats(np.array([[1 + 2j], [3 - 2j]]))
+    assert mean[0] == 2 + 0j and var[0] == 1 + 4j
+    # three shifts 0, 3, 6 (real): mean 3, unbiased variance (9 + 0 + 9)/2 = 9,
+    # variance of the mean 9/3 = 3; the imaginary part has zero spread
+    mean, var = combine.shift_stats(np.array([[0.0 + 5j], [3.0 + 5j], [6.0 + 5j]]))
+    assert mean[0] == 3 + 5j and var[0] == 3 + 0j
+    # orders are independent columns
+    mean, var = combine.shift_stats(np.array([[1.0, 10.0], [3.0, 10.0]], dtype=complex))
+    assert np.array_equal(mean, [2.0, 10.0]) and np.array_equal(var.real, [1.0, 0.0])
+    # one shift: no variance estimate
+    _, var = combine.shift_stats(np.array([[1.0 + 1j]]))
+    assert np.isinf(var[0].real) and np.isinf(var[0].imag)
+
+
+def test_relative_error_definition():
+    # sqrt(dR^2 + dI^2) / sqrt(R^2 + I^2) with variance = dR^2 + dI^2:
+    # value 3 + 4i (modulus 5), dR = 0.3, dI = 0.4 -> 0.5 / 5 = 0.1
+    assert abs(combine.relative_error(3 + 4j, 0.3 ** 2 + 0.4 ** 2) - 0.1) < 1e-15
+    assert combine.relative_error(-2.0, 1e-8) == pytest.approx(5e-5, rel=1e-14)
+    assert combine.relative_error(0.0, 1.0) == float("inf")
+    assert combine.relative_error(1j, 0.0) == 0.0
+
+
 def test_variance_propagation_through_coefficients():
     # var(c * I) for a deterministic Laurent c: sum_p |c_p|^2 var(I^(o-p))
     c = np.array([2.0, -1.0 + 1j])
