@@ -77,15 +77,12 @@ def _workloads():
             desc="box2L_planar_massless s=-3 t=-1, 282 sectors d=6, eps^-4..eps^0, n={n} CBC, m={m} shifts"),
     }
 
-# DRAM traffic per evaluator launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) for the kernel source with this SHA-1; any other
-# kernel source reports null.
-PROFILED_TRAFFIC = {
-    # full-size launch (n = 1000003, m = 32), ncu 1 pass: 681.22 KB read,
-    # 8.27 MB written (register spills leaving L2)
-    "010aa0807e75c5f190f94e7caa00d38a22a9d7b5": 8951296,
-}
-
+# Figures of one ncu capture of the evaluator for the kernel source with this
+# SHA-1 and this workload (any other source or workload reports null):
+# traffic = dram__bytes_read.sum + dram__bytes_write.sum per launch;
+# fp64_executed_flops_per_eval = (2 DFMA + DMUL + DADD thread instructions)
+# per evaluation; fp64_pipe_busy = sm__pipe_fp64_cycles_active of peak.
+PROFILED = {}
 
 def kernel_sha1():
     import hashlib
@@ -202,6 +199,42 @@ def run_reference(args):
     return 0
 
 
+def run_gemm(args):
+    """The learned model's BF16 GEMM C = A B^T on device buffers: milliseconds
+    per call (CUDA events on the launching stream after the warm-up calls) and
+    TFLOP/s = 2 M N K / time. One JSON line."""
+    import torch
+
+    from paper_2305_19768_gb300 import qmc
+
+    M, N, K = (int(v) for v in args.gemm.split(","))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda", dtype=torch.float32)
+    err = torch.zeros(1, device="cuda", dtype=torch.int32)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        qmc.qmc_gemm_bf16_device(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, err.data_ptr(),
+                                 stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"metric": "bf16 GEMM throughput", "value": 2.0 * M * N * K / (ms * 1e-3) / 1e12,
+                      "unit": "TFLOP/s", "ms_per_call": ms, "shape": [M, N, K], "steps": args.steps,
+                      "wait_errors": int(err.item())}), flush=True)
+    return 0 if int(err.item()) == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,9 +254,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-scan", action="store_true", help="skip the amplitude-scan comparison")
+    ap.add_argument("--gemm", default="", metavar="M,N,K",
+                    help="time only the learned model's tensor-core BF16 GEMM at this shape")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.gemm:
+        return run_gemm(args)
 
     import torch
 
@@ -327,15 +364,28 @@ def main():
         t_e2e += time.perf_counter() - t0
     e2e_val = evals_per_step * max(1, args.steps // 2) * world / t_e2e
 
-    # roofline of the evaluator kernel: algorithmic FP64 flops / event time
-    fl_per_eval = flopmod.workload_flops(I, LO, NORD, deform=W["deform"])
+    # roofline of the evaluator kernels: FP64 flops of the formulation (no
+    # credit for the steps on the integer pipe) / their event time, against
+    # the DFMA peak measured in this run; FP32 work of the mixed classes
+    # against the FFMA peak; transcendentals per evaluation beside them
+    work = flopmod.workload_work(I, LO, NORD, mixed=args.precision == "mixed")
     avg_eval_ms = float(np.mean(eval_ms))
-    achieved = fl_per_eval * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
+    achieved = work.fp64 * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
     sha = kernel_sha1()
+    prof = PROFILED.get((sha, args.workload, args.precision, args.decomposition, args.n), {})
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s (fp64)",
-            "frac": achieved / peak_gflops, "traffic": PROFILED_TRAFFIC.get(sha) if default else None,
-            "flops_per_eval": fl_per_eval, "peak_source": "DFMA probe in this run",
+            "frac": achieved / peak_gflops, "traffic": prof.get("traffic"),
+            "flops_per_eval": work.fp64, "peak_source": "DFMA probe in this run (of measured)",
+            "transcendentals_per_eval": {k: getattr(work, k) for k in ("log", "atan2", "rcp", "exp")},
+            "fp64_executed_flops_per_eval": prof.get("fp64_executed_flops_per_eval"),
+            "fp64_pipe_busy": prof.get("fp64_pipe_busy"),
+            "evals_per_launch": evals_per_step, "eval_ms_per_step": avg_eval_ms,
             "kernel_sha1": sha}
+    if work.fp32 > 0:
+        peak32 = qmc.qmc_fp32_peak(ctx)
+        a32 = work.fp32 * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
+        roof["fp32"] = {"flops_per_eval": work.fp32, "achieved": a32, "peak": peak32,
+                        "frac": a32 / peak32, "peak_source": "FFMA probe in this run (of measured)"}
 
     # secondary: time to 1e-4 relative error per eps-coefficient through
     # qmc_integrate (pilot lattice 1e4, adaptive), FP64 and mixed precision,

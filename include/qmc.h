@@ -384,30 +384,37 @@ int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, doub
 
 /* Evaluation that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the
- * time they evaluate -- code running while a CUDA stream is being captured
- * into a graph, hard real-time loops that must not hit cudaMalloc's implicit
- * device synchronisation, or hosts whose device memory is owned by another
- * allocator with a fixed budget. It computes what qmc_eval_jobs computes for
- * the same jobs (per-shift sums, layout [job][shift][order][re, im]) but
- * writes them to the caller's device buffer `out_dev`
- * (qmc_plan_output_size doubles for the same jobs) and keeps its job table,
- * tile counter, status words and tile partial sums in one fixed 4 MiB array
- * in device memory that every GPU loading this library holds until the
- * process exits. Limits: at most 256 jobs per call, all of one evaluator
- * class (all deformed or all undeformed, d <= 3), and at most 520160
- * doubles of tile partials ((4 MiB - 33024 bytes) / 8), counted as the sum
- * over jobs of shifts * ceil(n / (block * ppt)) * 2 * norders; larger
- * requests are rejected with QMC_E_INVAL and a message, before any GPU work.
- * It never calls cudaMalloc, cudaFree or any allocating library routine.
- * The context (qmc_create, qmc_set_lattices, qmc_load_sectors_mem,
- * qmc_set_kinematics) must be set up beforehand; that set-up does allocate.
- * The first call on a device looks up the array's device address (a
- * one-time set-up with that device current), so make that first call
- * before any stream capture. Every call reuses the same array and clears
- * the counter and status words it needs at zero; calls that overlap on the
- * GPU (other threads, other streams) race on it and give wrong results.
- * Runs on `stream` (NULL = the context's stream) and returns after the work
- * has finished, with QMC_E_NONFINITE / QMC_E_SIGN_CHECK as qmc_plan_results. */
+ * time they evaluate -- hard real-time loops that must not hit cudaMalloc's
+ * implicit device synchronisation, or hosts whose device memory is owned by
+ * another allocator with a fixed budget. It computes what qmc_eval_jobs
+ * computes for the same jobs (per-shift sums, layout
+ * [job][shift][order][re, im]) but writes them to the caller's device buffer
+ * `out_dev` (qmc_plan_output_size doubles for the same jobs) and keeps its
+ * job table, tile counter, status words and tile partial sums in one fixed
+ * 4 MiB array in device memory that every GPU loading this library holds
+ * until the process exits. Limits: at most 256 jobs per call, all of one
+ * evaluator class (all deformed or all undeformed, d <= 3; the context's
+ * precision setting picks the FP64 or the mixed-precision class, as in
+ * qmc_plan_create), and at most 520160 doubles of tile partials
+ * ((4 MiB - 33024 bytes) / 8), counted as the sum over jobs of
+ * shifts * ceil(n / (block * ppt)) * 2 * norders with the launch shape fixed
+ * by the options (block 128 unless 256 is set, ppt 16 unless set; the
+ * autotuned and small-lattice shapes of qmc_plan_create are not used, so the
+ * sums agree with qmc_eval_jobs to rounding, not bit for bit); larger requests
+ * are rejected with QMC_E_INVAL and a message, before any GPU work. It never
+ * calls cudaMalloc, cudaFree or any allocating library routine. The context
+ * (qmc_create, qmc_set_lattices, qmc_load_sectors_mem, qmc_set_kinematics)
+ * must be set up beforehand; that set-up does allocate. The first call on a
+ * device looks up the array's device address (a one-time set-up with that
+ * device current). The call copies its job table from host memory, then
+ * blocks until the work on `stream` (NULL = the context's stream) has
+ * finished; it must not be captured into a CUDA graph, and a stream that is
+ * being captured is refused with QMC_E_INVAL. Every call reuses the same
+ * array and clears the counter and status words it needs at zero; calls that
+ * overlap on the GPU (other threads, other streams) race on it and give wrong
+ * results. Returns QMC_E_NONFINITE / QMC_E_SIGN_CHECK as qmc_plan_results,
+ * QMC_E_INVAL also when an integral's invariant count differs from the
+ * loaded kinematics. */
 int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders,
                           double *out_dev, void *stream);
 
@@ -448,6 +455,10 @@ int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, dou
  * dependent-chain-free loop timed with CUDA events. */
 int qmc_fp64_peak(qmc_ctx *ctx, double *gflops);
 
+/* The same for FP32 (8 independent FFMA chains per thread): the roofline
+ * denominator of the mixed-precision classes' FP32 monomial products. */
+int qmc_fp32_peak(qmc_ctx *ctx, double *gflops);
+
 /* ------------------------------------------------------------------------
  * Learned part: tensor-core MLP kernels
  * ------------------------------------------------------------------------ */
@@ -468,6 +479,16 @@ int qmc_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int M, int N, 
  * alignment, NULL pointers), QMC_E_CUDA (launch). */
 int qmc_gemm_bf16_device(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
                          void *stream);
+
+/* qmc_gemm_bf16_device with an explicit limit on the polls of each pipeline
+ * wait (TMA stage filled, stage freed by the MMAs, all MMAs complete).
+ * qmc_gemm_bf16_device uses 2^26 polls (seconds). A CTA whose wait runs out
+ * increments *err_dev, waits with the full limit for the copies and MMAs it
+ * has in flight, frees its tensor memory and returns without writing its
+ * tile; with wait_limit = 0 every CTA takes that path. This exists to test
+ * the timeout path without a hung GPU. Errors as qmc_gemm_bf16_device. */
+int qmc_gemm_bf16_device_limit(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
+                               void *stream, unsigned wait_limit);
 
 /* A multilayer perceptron trained and evaluated on the GPU (the learned
  * sizing/surrogate model): x (nin) -> tanh(W0 x + b0) -> (depth - 1) layers

@@ -1,7 +1,7 @@
 """Build libqmc.so (the C-ABI library with the sm_103a kernels) in-tree.
 
-nvcc compiles the kernels and the host library as two translation units in
-parallel for exactly one target, sm_103a; the result lands in
+nvcc compiles the kernels and the host library as separate translation units
+in parallel for exactly one target, sm_103a; the result lands in
 ``paper_2305_19768_gb300/_build/libqmc.so``.
 """
 from __future__ import annotations
@@ -17,7 +17,10 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_mlp.cu", "qmc_host.cpp", "qmc_integrate.cpp"]
+# the evaluator's instantiations are split over four translation units
+# (qmc_kernels.cu and the three part files that include it) compiled in parallel
+SOURCES = ["qmc_kernels_wide.cu", "qmc_kernels_cplx.cu", "qmc_kernels.cu", "qmc_kernels_h.cu", "qmc_mlp.cu",
+           "qmc_host.cpp", "qmc_integrate.cpp"]
 
 
 def _nvcc() -> str:

@@ -192,11 +192,9 @@ int classify(qmc_ctx *ctx, HostSector &S, int si) {
         S.cls = QMC_CLASS_CPLX3;
     } else if (S.d <= 3 && S.ns <= 2) {
         S.cls = QMC_CLASS_REAL3;
-    } else if (S.ns <= 2) {
-        S.cls = QMC_CLASS_REAL6S;
-    } else if (S.ns == 3) {
-        S.cls = QMC_CLASS_REAL6T;
     } else {
+        // one d <= 6 evaluator for 0 to 4 singular variables: it dispatches per
+        // tile, so all such sectors share one launch
         S.cls = QMC_CLASS_REAL6;
     }
     return QMC_OK;
@@ -980,6 +978,31 @@ int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {
     return QMC_OK;
 }
 
+int qmc_fp32_peak(qmc_ctx *ctx, double *gflops) {
+    if (!ctx || !gflops) return QMC_E_INVAL;
+    cudaSetDevice(ctx->device);
+    float *d = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&d, 2 * sizeof(float)));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int block = 256, grid = ctx->sm_count * 8, iters = 16384;
+    qmc_k_fp32_probe(d, 256, grid, block, ctx->stream);  // warm-up
+    cudaEventRecord(a, ctx->stream);
+    qmc_k_fp32_probe(d, iters, grid, block, ctx->stream);
+    cudaEventRecord(b, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ctx, QMC_E_CUDA, "fp32 probe: %s", cudaGetErrorString(e));
+    const double flops = 2.0 * 8.0 * iters * (double)grid * block;
+    *gflops = flops / (ms * 1e-3) / 1e9;
+    return QMC_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- no-allocation entry point
@@ -991,6 +1014,15 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
         return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: %d jobs exceed the fixed limit of %d", njobs,
                     QMC_NOALLOC_MAX_JOBS);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, QMC_E_CUDA, "cudaSetDevice failed");
+    {
+        // the call copies from host stack memory and waits for the stream: neither
+        // belongs in a graph, so a capturing stream is refused before any work
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStream_t cst = stream ? (cudaStream_t)stream : ctx->stream;
+        if (cudaStreamIsCapturing(cst, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: the stream is being captured; this call blocks "
+                                          "until its work has finished and cannot be captured");
+    }
     QmcJobDev recs[QMC_NOALLOC_MAX_JOBS];
     const int block = ctx->opt.block == 256 ? 256 : 128;
     const int ppt = ctx->opt.ppt > 0 ? ctx->opt.ppt : 16;
@@ -1006,6 +1038,9 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
         if (J.sector < 0 || J.sector >= (int)I.sectors.size())
             return fail(ctx, QMC_E_INVAL, "job %d: bad sector %d", i, J.sector);
         const HostSector &S = I.sectors[J.sector];
+        if (!I.invariants.empty() && (int)I.invariants.size() != ctx->ninv)
+            return fail(ctx, QMC_E_INVAL, "job %d: integral has %zu invariants, kinematics %d", i,
+                        I.invariants.size(), ctx->ninv);
         if (J.point < 0 || (J.point >= ctx->npoints && !(I.invariants.empty() && J.point == 0)))
             return fail(ctx, QMC_E_INVAL, "job %d: bad kinematic point %d", i, J.point);
         if (J.shifts < 1) return fail(ctx, QMC_E_INVAL, "job %d: shifts < 1", i);
@@ -1014,8 +1049,10 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
         auto it = ctx->lattices.find(J.n);
         if (it == ctx->lattices.end())
             return fail(ctx, QMC_E_INVAL, "job %d: lattice n=%llu not in the table", i, (unsigned long long)J.n);
-        if (cls < 0) cls = S.cls;
-        if (S.cls != cls)
+        // the context's precision picks the class, as in qmc_plan_create
+        const int scls = ctx->opt.precision == QMC_PRECISION_MIXED ? qmc_class_mixed(S.cls) : S.cls;
+        if (cls < 0) cls = scls;
+        if (scls != cls)
             return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: all jobs must use one evaluator class");
         if (qmc_class_big(cls) || norders > qmc_class_lmax(cls) || hi + S.ns + 1 > qmc_class_lmax(cls))
             return fail(ctx, QMC_E_INVAL, "job %d: orders %d..%d not supported by the evaluator", i, lo, hi);

@@ -89,15 +89,15 @@ struct QmcLaunch {
 enum QmcClass {
     QMC_CLASS_REAL3 = 0,   // real integrand, d <= 3, <= 2 singular variables
     QMC_CLASS_CPLX3 = 1,   // contour-deformed, d <= 3, <= 2 singular variables
-    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6, 4 singular variables (16 corners)
+    QMC_CLASS_REAL6 = 2,   // real integrand, d <= 6 or > 2 singular variables (up to 4: 16 corners)
     QMC_CLASS_REAL3M = 3,  // REAL3 with FP32 monomial products
     QMC_CLASS_REAL6M = 4,  // REAL6 with FP32 monomial products
-    QMC_CLASS_REAL6S = 5,  // real integrand, d <= 6, <= 2 singular variables (4 corners)
-    QMC_CLASS_REAL6SM = 6, // REAL6S with FP32 monomial products
+    QMC_CLASS_REAL6S = 5,  // former split of REAL6 (<= 2 singular variables); now the REAL6 kernel
+    QMC_CLASS_REAL6SM = 6, // its mixed-precision variant (the REAL6M kernel)
     QMC_CLASS_CPLX3M = 7,  // CPLX3 with FP32 monomial products (derivatives of F, U and F at z)
     QMC_CLASS_REAL3H = 8,  // real, d <= 3, <= 2 singular variables, one with a = -2 (degree-1 subtraction)
-    QMC_CLASS_REAL6T = 9,  // real integrand, d <= 6, 3 singular variables (8 corners)
-    QMC_CLASS_REAL6TM = 10,// REAL6T with FP32 monomial products
+    QMC_CLASS_REAL6T = 9,  // former split of REAL6 (3 singular variables); now the REAL6 kernel
+    QMC_CLASS_REAL6TM = 10,// its mixed-precision variant (the REAL6M kernel)
     QMC_NCLASS = 11
 };
 
@@ -108,11 +108,7 @@ static inline bool qmc_class_big(int cls) {
 // Series length (orders) each class supports: K + ns + 1 <= class_lmax.
 static inline int qmc_class_lmax(int cls) { return qmc_class_big(cls) ? 6 : 4; }
 static inline int qmc_class_dmax(int cls) { return qmc_class_big(cls) ? 6 : 3; }
-static inline int qmc_class_smax(int cls) {
-    if (cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M) return 4;
-    if (cls == QMC_CLASS_REAL6T || cls == QMC_CLASS_REAL6TM) return 3;
-    return 2;
-}
+static inline int qmc_class_smax(int cls) { return qmc_class_big(cls) ? 4 : 2; }
 // The mixed-precision variant of a class.
 static inline int qmc_class_mixed(int cls) {
     switch (cls) {
@@ -132,6 +128,7 @@ int qmc_k_launch_finish(const QmcLaunch *L, void *stream);
 int qmc_k_lattice_points(uint64_t n, const uint32_t *z_dev, int d, const double *delta_dev,
                          uint64_t k0, uint64_t count, double *x_dev, uint64_t *r_dev, void *stream);
 int qmc_k_fp64_probe(double *out_dev, int iters, int grid, int block, void *stream);
+int qmc_k_fp32_probe(float *out_dev, int iters, int grid, int block, void *stream);
 int qmc_k_sm_count(int device);
 int qmc_k_occupancy(int cls, int block);
 size_t qmc_k_noalloc_partial_capacity(void);

@@ -27,6 +27,10 @@
 #include "qmc_internal.h"
 #include "qmc_log_table.h"
 
+#ifndef QMC_PART
+#define QMC_PART 0
+#endif
+
 namespace {
 
 __device__ const uint64_t kLogTable[3 * QMC_LOG_TABLE_ROWS] = QMC_LOG_TABLE_INIT;
@@ -772,6 +776,266 @@ __device__ __forceinline__ void eval_real(const TileSmem<LMAX> &S, const double 
     assemble<SMAX, LMAX, double>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, A_empty, S.invb_full, res);
 }
 
+// ---------------------------------------------------------------- fixed orders
+// The assembly and the real integrand with the number of singular variables
+// NS and the highest requested order HI fixed at compile time (the evaluator
+// dispatches on them per tile): every series has its exact length, so no
+// term beyond the requested orders is formed and no order is selected at run
+// time. resN[i] receives the coefficient of eps^(i - NS), i = 0 .. NS + HI
+// (the sector's leading pole eps^-NS up to eps^HI).
+template <int NS> struct SlotArr {
+    static constexpr int N = NS > 0 ? NS : 1;
+};
+
+template <int NS, int HI, class T>
+__device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (&LV)[1 << NS],
+                                               const double (&it)[SlotArr<NS>::N],
+                                               const double (&lt)[SlotArr<NS>::N],
+                                               const double (&bq)[SlotArr<NS>::N],
+                                               const double (&invb)[SlotArr<NS>::N], double A_empty,
+                                               double A_full, T (&resN)[NS + HI + 1]) {
+    constexpr int NG = 1 << NS;
+    constexpr int LM = HI + NS + 1;   // series length of the full corner
+    T g[NG][LM];
+    // corner series B_V Lambda_V^i / i!, i < HI + |V| + 1
+#pragma unroll
+    for (int V = 0; V < NG; ++V) {
+        const int nV = HI + __popc(V) + 1;
+        g[V][0] = BV[V];
+#pragma unroll
+        for (int i = 1; i < LM; ++i)
+            if (i < nV) g[V][i] = i == 1 ? g[V][0] * LV[V] : mulsc(g[V][i - 1] * LV[V], 1.0 / i);
+    }
+    // superset Moebius transform: D_P = sum_{V >= P} (-1)^|V\P| G_V
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int P = 0; P < NG; ++P) {
+            if (P & (1 << q)) continue;
+            const int nP = HI + __popc(P) + 1;
+#pragma unroll
+            for (int i = 0; i < LM; ++i)
+                if (i < nP) g[P][i] = g[P][i] - g[P | (1 << q)][i];
+        }
+#pragma unroll
+    for (int i = 0; i < LM; ++i) resN[i] = zero<T>();
+#pragma unroll
+    for (int P = 0; P < NG; ++P) {
+        const int np = __popc(P);
+        const int nP = HI + np + 1;
+        // A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q
+        double A = 1.0;
+        if (P == 0) {
+            A = A_empty;
+        } else if (P == NG - 1) {
+            A = A_full;
+        } else {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const double f = (P & (1 << q)) ? invb[q] : it[q];
+                A = q == 0 ? f : A * f;
+            }
+        }
+        T PE[LM];
+        if (P == NG - 1) {
+            // every singular variable in the pole set: no exp(eps E_P) factor
+#pragma unroll
+            for (int k = 0; k < LM; ++k)
+                if (k < nP) PE[k] = g[P][k];
+        } else {
+            // E_P = sum_{q not in P} b_q ln t_q and its exponential series
+            double E = 0.0;
+            bool first = true;
+#pragma unroll
+            for (int q = 0; q < NS; ++q)
+                if (!(P & (1 << q)) && nP > 1) {
+                    E = first ? bq[q] * lt[q] : fma(bq[q], lt[q], E);
+                    first = false;
+                }
+            double e[LM];
+            e[0] = 1.0;
+#pragma unroll
+            for (int l = 1; l < LM; ++l)
+                if (l < nP) e[l] = l == 1 ? E : e[l - 1] * (E * (1.0 / l));
+#pragma unroll
+            for (int k = 0; k < LM; ++k) {
+                if (k >= nP) continue;
+                PE[k] = g[P][k];
+#pragma unroll
+                for (int i = 0; i < LM; ++i)
+                    if (i < k) PE[k] = PE[k] + mulsc(g[P][i], e[k - i]);
+            }
+        }
+        // term k of pole set P is the order k - |P|
+#pragma unroll
+        for (int k = 0; k < LM; ++k)
+            if (k < nP) resN[k - np + NS] = resN[k - np + NS] + mulsc(PE[k], A);
+    }
+}
+
+template <int DMAX, int NS, int HI, bool MIXED, int LMAX>
+__device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const double (&t)[DMAX],
+                                             double (&resN)[NS + HI + 1]) {
+    constexpr int NG = 1 << NS;
+    constexpr int NSA = SlotArr<NS>::N;
+    const QmcSectorDev &sec = S.sec;
+    const int d = sec.d;
+    const uint64_t *tab = S.logtab;
+    double tp[DMAX][QMC_EMAX];
+    powers<DMAX, double>(t, d, sec.pad0, tp);
+    // group sums by singular mask, then subset sums h[X] = sum_{M subset X} g[M];
+    // the polynomial at corner V (t_V = 0) is h[(NG-1) ^ V]
+    double hU[NG], hF[NG];
+    if constexpr (MIXED) {
+        float tf[DMAX], tpf[DMAX][QMC_EMAX];
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) tf[j] = __double2float_rn(t[j]);
+        powers<DMAX, float>(tf, d, sec.pad0, tpf);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            hU[g] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, sec.gU[g], sec.gU[g + 1], tpf);
+            hF[g] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tpf);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            hU[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.gU[g], sec.gU[g + 1], tp);
+            hF[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tp);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+            if (g & (1 << q)) {
+                hU[g] += hU[g ^ (1 << q)];
+                hF[g] += hF[g ^ (1 << q)];
+            }
+    constexpr bool need_lam = HI + NS >= 1;   // some corner needs its eps exponent
+    // factors of the regular variables: prod t^{a_j} and sum b_j ln t_j
+    double Cc = 1.0, Lc = 0.0;
+    bool hasCc = false, hasLc = false;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d && ((sec.regular_mask >> j) & 1)) {
+            const int a = sec.a[j];
+            if (a > 0) {
+                Cc = hasCc ? Cc * pow_sel<double>(tp[j], (uint32_t)a) : pow_sel<double>(tp[j], (uint32_t)a);
+                hasCc = true;
+            }
+            if (need_lam && sec.b[j] != 0.0) {
+                const double l = qlog(t[j], tab);
+                Lc = hasLc ? fma(sec.b[j], l, Lc) : sec.b[j] * l;
+                hasLc = true;
+            }
+        }
+    }
+    // singular slots: t, ln t (needed when a pole set without q has a term of
+    // order >= 1 below HI), b
+    constexpr bool need_lt = HI + NS - 1 >= 1;
+    double it[NSA], lt[NSA], bq[NSA];
+#pragma unroll
+    for (int q = 0; q < NSA; ++q) {
+        it[q] = 1.0;
+        lt[q] = 0.0;
+        bq[q] = 0.0;
+        if (q < NS) {
+            double tq = 1.0, bb = 0.0;
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j)
+                if (j == sec.sing[q]) {
+                    tq = t[j];
+                    bb = sec.b[j];
+                }
+            it[q] = tq;
+            bq[q] = bb;
+            if (need_lt) lt[q] = qlog(tq, tab);
+        }
+    }
+    // 1/t_q in pairs: 1/a = b / (a b) with one reciprocal per pair, whose value
+    // is also the pair's share of A of the empty pole set prod 1/t_q
+    double A_empty = 1.0;
+#pragma unroll
+    for (int q = 0; q + 1 < NS; q += 2) {
+        const double r = qrcp(it[q] * it[q + 1]);
+        const double t0 = it[q];
+        it[q] = it[q + 1] * r;
+        it[q + 1] = t0 * r;
+        A_empty = q == 0 ? r : A_empty * r;
+    }
+    if constexpr (NS & 1) {
+        it[NS - 1] = qrcp(it[NS - 1]);
+        A_empty = NS == 1 ? it[0] : A_empty * it[NS - 1];
+    }
+    // corners: B_V = Cc U^u0 F^f0, Lambda_V = Lc + ln(U^u1 F^f1) (one log when
+    // u1, f1 are small integers, else u1 ln U + f1 ln F)
+    const int u0 = (int)sec.u0, f0 = (int)sec.f0, u1 = (int)sec.u1, f1 = (int)sec.f1;
+    const bool comb = (sec.pad1 & 1) != 0;
+    double BV[NG], LV[NG];
+    // 1/F at the corners that need it, in pairs of corners (V, V + 1)
+    double FiV[NG];
+#pragma unroll
+    for (int V = 0; V < NG; V += 2) {
+        const bool lamA = HI + __popc(V) >= 1;
+        const double Fa = hF[(NG - 1) ^ V];
+        const bool na = (sec.f0_int && f0 < 0) || (lamA && comb && f1 < 0);
+        FiV[V] = 0.0;
+        if (V + 1 < NG) {
+            const bool lamB = HI + __popc(V + 1) >= 1;
+            const double Fb = hF[(NG - 1) ^ (V + 1)];
+            const bool nb = (sec.f0_int && f0 < 0) || (lamB && comb && f1 < 0);
+            FiV[V + 1] = 0.0;
+            if (na && nb) {
+                const double r = qrcp(Fa * Fb);
+                FiV[V] = Fb * r;
+                FiV[V + 1] = Fa * r;
+            } else if (na) {
+                FiV[V] = qrcp(Fa);
+            } else if (nb) {
+                FiV[V + 1] = qrcp(Fb);
+            }
+        } else if (na) {
+            FiV[V] = qrcp(Fa);
+        }
+    }
+#pragma unroll
+    for (int V = 0; V < NG; ++V) {
+        const bool lam_here = HI + __popc(V) >= 1;
+        const double U = hU[(NG - 1) ^ V];
+        const double F = hF[(NG - 1) ^ V];
+        const bool needUinv = (sec.u0_int && u0 < 0) || (lam_here && comb && u1 < 0);
+        const double Ui = needUinv ? qrcp(U) : 0.0;
+        const double Fi = FiV[V];
+        double B = 1.0;
+        bool unit = true;
+        if (hasCc) {
+            B = Cc;
+            unit = false;
+        }
+        if (!sec.u0_int || u0 != 0) {
+            const double pu = sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog(U, tab));
+            B = unit ? pu : B * pu;
+            unit = false;
+        }
+        if (!sec.f0_int || f0 != 0) {
+            const double pf = sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog(F, tab));
+            B = unit ? pf : B * pf;
+        }
+        BV[V] = B;
+        LV[V] = 0.0;
+        if (lam_here) {
+            double l;
+            if (comb) l = qlog(ipow_signed<double>(U, Ui, u1) * ipow_signed<double>(F, Fi, f1), tab);
+            else l = fma(sec.u1, qlog(U, tab), sec.f1 * qlog(F, tab));
+            LV[V] = hasLc ? Lc + l : l;
+        }
+    }
+    double ib[NSA];
+#pragma unroll
+    for (int q = 0; q < NSA; ++q) ib[q] = q < NS ? S.invb[q] : 0.0;
+    assemble_fixed<NS, HI, double>(BV, LV, it, lt, bq, ib, A_empty, S.invb_full, resN);
+}
+
 // ---------------------------------------------------------------- degree-1 subtraction
 // One singular variable q with a_q = -2 (the others a = -1): its endpoint
 // singularity is removed with the Taylor polynomial of degree 1,
@@ -1220,6 +1484,110 @@ constexpr int qmc_min_blocks() {
                      : QMC_MINB * 128 / BLOCK;
 }
 
+// The thread's points [k0, kend) of the current tile: lattice walk, shifted
+// point and transform, integrand, and acc[o] += W f_o for the output orders
+// eps^(lo+o), o < nord. NSC, HIC >= 0: the tile's number of singular
+// variables and highest order fixed at compile time (real sectors), the
+// series summed per order eps^-NSC .. eps^HIC and mapped to the output orders
+// once at the end; NSC = HIC = -1: the run-time general path.
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, int NSC, int HIC, class T>
+__device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const QmcLaunch &Lc, uint64_t k0,
+                                              uint64_t kend, int lo, int hi, int nord, T (&acc)[LMAX],
+                                              int &signfail_tile) {
+    constexpr bool FIXED = NSC >= 0 && HIC >= 0;
+    constexpr int NO = FIXED ? NSC + HIC + 1 : 1;
+    double accN[NO];
+#pragma unroll
+    for (int i = 0; i < NO; ++i) accN[i] = 0.0;
+    const int d = S.sec.d;
+    const uint64_t n = S.job.n;
+    const double nd = (double)n, inv_n = S.job.inv_n;
+    // per coordinate only the walk lives in registers; z, the expansion of
+    // z/n and the shift are read from shared memory
+    LatticeWalk wk[DMAX];
+    const uint32_t n32 = (uint32_t)n;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) walk_init(wk[j], (j < d) ? (k0 * (uint64_t)S.zmod[j]) % n : 0, n);
+#pragma unroll 1
+    for (uint64_t k = k0; k < kend; ++k) {
+        double t[DMAX], omt[DMAX];
+        double Ws = 1.0;  // prod u(1-u); the korobov3 weight is 140^d Ws^3
+        bool zero_t = false;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            t[j] = 1.0;
+            omt[j] = 0.0;
+            if (j < d) {
+                const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
+                if (Lc.transform == 0) {          // korobov3
+                    // integer pipe for the d <= 3 classes (with 1 - t for the
+                    // deformed ones); the d <= 6 classes run at the register
+                    // limit, where the longer integer chain costs more than
+                    // its FP64 operations
+                    if constexpr (!CPLX && DMAX > 3) {
+                        const double u2 = u * u;
+                        t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
+                        Ws *= fma(-u, u, u);
+                    } else {
+                        double ws = 0.0, om = 1.0;
+                        t[j] = 0.0;
+                        if (!nonneg_is_zero(u)) korobov3_int<CPLX>(u, t[j], om, ws);
+                        if (CPLX) omt[j] = om;
+                        Ws = j == 0 ? ws : Ws * ws;
+                    }
+                } else if (Lc.transform == 1) {   // baker: t = 1 - |2u - 1|, weight 1
+                    t[j] = u < 0.5 ? 2.0 * u : 2.0 * (1.0 - u);
+                    omt[j] = u < 0.5 ? 1.0 - 2.0 * u : 2.0 * u - 1.0;
+                } else {                          // no transform
+                    t[j] = u;
+                    omt[j] = 1.0 - u;
+                }
+                zero_t |= nonneg_is_zero(t[j]);
+                walk_step(wk[j], S.zmod[j], S.qz[j], S.rz[j], n32);
+            }
+        }
+        const double W = Lc.transform == 0 ? Ws * Ws * Ws : 1.0;   // 140^d: per tile
+        if (nonneg_is_zero(W) || zero_t) continue;
+        if constexpr (FIXED) {
+            double resN[NO];
+            eval_real_fx<DMAX, NSC, HIC, MIXED, LMAX>(S, t, resN);
+#pragma unroll
+            for (int i = 0; i < NO; ++i) accN[i] = fma(resN[i], W, accN[i]);
+        } else {
+            T res[LMAX];
+            if constexpr (CPLX) {
+                eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
+            } else {
+                if constexpr (HS) {
+                    eval_real_h<LMAX>(S, t, lo, hi, nord, res);
+                } else if constexpr (DMAX <= 3) {
+                    // one instantiation per number of singular variables (uniform per tile)
+                    if (S.sec.ns == 2) eval_real<DMAX, SMAX, LMAX, MIXED, 2>(S, t, lo, hi, nord, res);
+                    else if (S.sec.ns == 1) eval_real<DMAX, SMAX, LMAX, MIXED, 1>(S, t, lo, hi, nord, res);
+                    else eval_real<DMAX, SMAX, LMAX, MIXED, 0>(S, t, lo, hi, nord, res);
+                } else {
+                    eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < LMAX; ++o)
+                if (o < nord) acc[o] = acc[o] + mulsc(res[o], W);
+        }
+    }
+    if constexpr (FIXED) {
+        // output order o is eps^(lo+o), i.e. index lo + o + NSC of accN; orders
+        // below the sector's leading pole are 0 (selected without local memory)
+#pragma unroll
+        for (int o = 0; o < LMAX; ++o) {
+            double v = 0.0;
+#pragma unroll
+            for (int i = 0; i < NO; ++i)
+                if (i == lo + o + NSC) v = accN[i];
+            if (o < nord) acc[o] = from_real<T>(v);
+        }
+    }
+}
+
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false>
 __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3), (CPLX && MIXED), HS>()) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
@@ -1278,9 +1646,7 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
         }
         __syncthreads();
 
-        const int d = S.sec.d;
         const uint64_t n = S.job.n;
-        const double nd = (double)n, inv_n = S.job.inv_n;
         const int hi = lo + nord - 1;
         T acc[LMAX];
 #pragma unroll
@@ -1290,73 +1656,25 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
         const uint64_t kt1 = min(n, kt0 + (uint64_t)Lc.tile_k);
         const uint64_t k0 = kt0 + (uint64_t)threadIdx.x * (uint64_t)ppt;
         if (k0 < kt1) {
-            // per coordinate only the walk lives in registers; z, the
-            // expansion of z/n and the shift are read from shared memory
-            LatticeWalk wk[DMAX];
-            const uint32_t n32 = (uint32_t)n;
-#pragma unroll
-            for (int j = 0; j < DMAX; ++j) walk_init(wk[j], (j < d) ? (k0 * (uint64_t)S.zmod[j]) % n : 0, n);
             const uint64_t kend = min(kt1, k0 + (uint64_t)ppt);
-#pragma unroll 1
-            for (uint64_t k = k0; k < kend; ++k) {
-                double t[DMAX], omt[DMAX];
-                double Ws = 1.0;  // prod u(1-u); the korobov3 weight is 140^d Ws^3
-                bool zero_t = false;
-#pragma unroll
-                for (int j = 0; j < DMAX; ++j) {
-                    t[j] = 1.0;
-                    omt[j] = 0.0;
-                    if (j < d) {
-                        const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
-                        if (Lc.transform == 0) {          // korobov3
-                            // integer pipe for the d <= 3 classes (with
-                            // 1 - t for the deformed ones); the d <= 6
-                            // classes run at the register limit, where the
-                            // longer integer chain costs more than its FP64
-                            // operations
-                            if constexpr (!CPLX && DMAX > 3) {
-                                const double u2 = u * u;
-                                t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
-                                Ws *= fma(-u, u, u);
-                            } else {
-                                double ws = 0.0, om = 1.0;
-                                t[j] = 0.0;
-                                if (!nonneg_is_zero(u)) korobov3_int<CPLX>(u, t[j], om, ws);
-                                if (CPLX) omt[j] = om;
-                                Ws = j == 0 ? ws : Ws * ws;
-                            }
-                        } else if (Lc.transform == 1) {   // baker: t = 1 - |2u - 1|, weight 1
-                            t[j] = u < 0.5 ? 2.0 * u : 2.0 * (1.0 - u);
-                            omt[j] = u < 0.5 ? 1.0 - 2.0 * u : 2.0 * u - 1.0;
-                        } else {                          // no transform
-                            t[j] = u;
-                            omt[j] = 1.0 - u;
-                        }
-                        zero_t |= nonneg_is_zero(t[j]);
-                        walk_step(wk[j], S.zmod[j], S.qz[j], S.rz[j], n32);
+            bool done = false;
+            if constexpr (!CPLX && !HS) {
+                // real sectors up to eps^0 (every sum the integrator forms):
+                // the compile-time path for the tile's number of singular variables
+                if (hi == 0) {
+                    const int ns = S.sec.ns;
+                    done = true;
+                    if (ns == 0) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 0, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                    else if (ns == 1) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 1, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                    else if (ns == 2 || SMAX < 3) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 2 ? 2 : 1), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                    else if constexpr (SMAX >= 3) {
+                        if (ns == 3 || SMAX < 4) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 3, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                        else thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 4 ? 4 : 3), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
                     }
                 }
-                const double W = Lc.transform == 0 ? Ws * Ws * Ws : 1.0;   // 140^d: per tile
-                if (nonneg_is_zero(W) || zero_t) continue;
-                T res[LMAX];
-                if constexpr (CPLX) {
-                    eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
-                } else {
-                    if constexpr (HS) {
-                        eval_real_h<LMAX>(S, t, lo, hi, nord, res);
-                    } else if constexpr (DMAX <= 3) {
-                        // one instantiation per number of singular variables (uniform per tile)
-                        if (S.sec.ns == 2) eval_real<DMAX, SMAX, LMAX, MIXED, 2>(S, t, lo, hi, nord, res);
-                        else if (S.sec.ns == 1) eval_real<DMAX, SMAX, LMAX, MIXED, 1>(S, t, lo, hi, nord, res);
-                        else eval_real<DMAX, SMAX, LMAX, MIXED, 0>(S, t, lo, hi, nord, res);
-                    } else {
-                        eval_real<DMAX, SMAX, LMAX, MIXED>(S, t, lo, hi, nord, res);
-                    }
-                }
-#pragma unroll
-                for (int o = 0; o < LMAX; ++o)
-                    if (o < nord) acc[o] = acc[o] + mulsc(res[o], W);
             }
+            if (!done)
+                thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, -1, -1>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
         }
         // sign-check failures of this tile: per job (if counted) and in total
         if (CPLX && __ballot_sync(0xffffffffu, signfail_tile != 0)) {
@@ -1394,6 +1712,7 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
     }
 }
 
+#if QMC_PART == 0
 // Sum each (job, shift, component) over its tiles in tile order (Neumaier),
 // divide by n, write the per-shift estimate; then re-arm the tile queue.
 __global__ void qmc_finish_kernel(QmcLaunch Lc) {
@@ -1491,6 +1810,25 @@ __global__ void qmc_fp64_probe_kernel(double *out, int iters) {
     if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
 }
 
+// FP32 throughput probe: 8 independent FFMA chains per thread.
+__global__ void qmc_fp32_probe_kernel(float *out, int iters) {
+    float a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = 1.0f + 1e-6f * (float)(threadIdx.x + c);
+    const float m1 = 0.9999999f, m2 = 1e-7f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = fmaf(a[c], m1, m2);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == 12345.678f) out[0] = s;  // never true; keeps the loop alive
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
+}
+
+#endif  // QMC_PART == 0
+
 // Blocks of 256 threads exist for the d <= 3 classes only: the d <= 6 classes
 // run near the register limit, where a second warp set per block buys nothing
 // (and their instantiations dominate the build).
@@ -1523,22 +1861,78 @@ int occupancy_cls(int block) {
 
 }  // namespace
 
-extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt, int grid, void *stream) {
+// Per translation unit: the launcher and occupancy query of the classes it
+// instantiates (-2 / 0 for the others). The evaluator classes are compiled in
+// four translation units in parallel: part 0 the real d <= 3 classes (and
+// everything that is not an evaluator), part 1 the deformed classes, part 2
+// the d <= 6 classes, part 3 the degree-1 subtraction class.
+#define QMC_PART_FN2(name, part) name##_part##part
+#define QMC_PART_FN(name, part) QMC_PART_FN2(name, part)
+
+extern "C" int QMC_PART_FN(qmc_k_launch_eval, QMC_PART)(int cls, const QmcLaunch *L, int block, int ppt, int grid,
+                                                         void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (cls) {
+#if QMC_PART == 0
         case QMC_CLASS_REAL3: return launch_cls<3, 2, 4, false, false>(L, block, ppt, grid, st);
-        case QMC_CLASS_CPLX3: return launch_cls<3, 2, 4, true, false>(L, block, ppt, grid, st);
-        case QMC_CLASS_REAL6: return launch_cls<6, 4, 6, false, false>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL3M: return launch_cls<3, 2, 4, false, true>(L, block, ppt, grid, st);
-        case QMC_CLASS_REAL6M: return launch_cls<6, 4, 6, false, true>(L, block, ppt, grid, st);
-        case QMC_CLASS_REAL6S: return launch_cls<6, 2, 6, false, false>(L, block, ppt, grid, st);
-        case QMC_CLASS_REAL6SM: return launch_cls<6, 2, 6, false, true>(L, block, ppt, grid, st);
+#elif QMC_PART == 1
+        case QMC_CLASS_CPLX3: return launch_cls<3, 2, 4, true, false>(L, block, ppt, grid, st);
         case QMC_CLASS_CPLX3M: return launch_cls<3, 2, 4, true, true>(L, block, ppt, grid, st);
+#elif QMC_PART == 2
+        // one d <= 6 kernel for 0..4 singular variables (the former REAL6S and
+        // REAL6T classes included)
+        case QMC_CLASS_REAL6:
+        case QMC_CLASS_REAL6S:
+        case QMC_CLASS_REAL6T: return launch_cls<6, 4, 6, false, false>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6M:
+        case QMC_CLASS_REAL6SM:
+        case QMC_CLASS_REAL6TM: return launch_cls<6, 4, 6, false, true>(L, block, ppt, grid, st);
+#elif QMC_PART == 3
         case QMC_CLASS_REAL3H: return launch_cls<3, 2, 4, false, false, true>(L, block, ppt, grid, st);
-        case QMC_CLASS_REAL6T: return launch_cls<6, 3, 6, false, false>(L, block, ppt, grid, st);
-        case QMC_CLASS_REAL6TM: return launch_cls<6, 3, 6, false, true>(L, block, ppt, grid, st);
+#endif
         default: return -2;
     }
+}
+
+extern "C" int QMC_PART_FN(qmc_k_occupancy, QMC_PART)(int cls, int block) {
+    switch (cls) {
+#if QMC_PART == 0
+        case QMC_CLASS_REAL3: return occupancy_cls<3, 2, 4, false, false>(block);
+        case QMC_CLASS_REAL3M: return occupancy_cls<3, 2, 4, false, true>(block);
+#elif QMC_PART == 1
+        case QMC_CLASS_CPLX3: return occupancy_cls<3, 2, 4, true, false>(block);
+        case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block);
+#elif QMC_PART == 2
+        case QMC_CLASS_REAL6:
+        case QMC_CLASS_REAL6S:
+        case QMC_CLASS_REAL6T: return occupancy_cls<6, 4, 6, false, false>(block);
+        case QMC_CLASS_REAL6M:
+        case QMC_CLASS_REAL6SM:
+        case QMC_CLASS_REAL6TM: return occupancy_cls<6, 4, 6, false, true>(block);
+#elif QMC_PART == 3
+        case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block);
+#endif
+        default: return 0;
+    }
+}
+
+#if QMC_PART == 0
+extern "C" int qmc_k_launch_eval_part1(int, const QmcLaunch *, int, int, int, void *);
+extern "C" int qmc_k_launch_eval_part2(int, const QmcLaunch *, int, int, int, void *);
+extern "C" int qmc_k_launch_eval_part3(int, const QmcLaunch *, int, int, int, void *);
+extern "C" int qmc_k_occupancy_part1(int, int);
+extern "C" int qmc_k_occupancy_part2(int, int);
+extern "C" int qmc_k_occupancy_part3(int, int);
+
+extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt, int grid, void *stream) {
+    int (*const parts[4])(int, const QmcLaunch *, int, int, int, void *) = {
+        qmc_k_launch_eval_part0, qmc_k_launch_eval_part1, qmc_k_launch_eval_part2, qmc_k_launch_eval_part3};
+    for (auto f : parts) {
+        const int rc = f(cls, L, block, ppt, grid, stream);
+        if (rc != -2) return rc;
+    }
+    return -2;
 }
 
 extern "C" int qmc_k_launch_finish(const QmcLaunch *L, void *stream) {
@@ -1594,6 +1988,11 @@ extern "C" int qmc_k_fp64_probe(double *out_dev, int iters, int grid, int block,
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+extern "C" int qmc_k_fp32_probe(float *out_dev, int iters, int grid, int block, void *stream) {
+    qmc_fp32_probe_kernel<<<grid, block, 0, (cudaStream_t)stream>>>(out_dev, iters);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 extern "C" int qmc_k_sm_count(int device) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
@@ -1601,20 +2000,13 @@ extern "C" int qmc_k_sm_count(int device) {
 }
 
 extern "C" int qmc_k_occupancy(int cls, int block) {
-    switch (cls) {
-        case QMC_CLASS_REAL3: return occupancy_cls<3, 2, 4, false, false>(block);
-        case QMC_CLASS_CPLX3: return occupancy_cls<3, 2, 4, true, false>(block);
-        case QMC_CLASS_REAL6: return occupancy_cls<6, 4, 6, false, false>(block);
-        case QMC_CLASS_REAL3M: return occupancy_cls<3, 2, 4, false, true>(block);
-        case QMC_CLASS_REAL6M: return occupancy_cls<6, 4, 6, false, true>(block);
-        case QMC_CLASS_REAL6S: return occupancy_cls<6, 2, 6, false, false>(block);
-        case QMC_CLASS_REAL6SM: return occupancy_cls<6, 2, 6, false, true>(block);
-        case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block);
-        case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block);
-        case QMC_CLASS_REAL6T: return occupancy_cls<6, 3, 6, false, false>(block);
-        case QMC_CLASS_REAL6TM: return occupancy_cls<6, 3, 6, false, true>(block);
-        default: return 0;
+    int (*const parts[4])(int, int) = {qmc_k_occupancy_part0, qmc_k_occupancy_part1, qmc_k_occupancy_part2,
+                                       qmc_k_occupancy_part3};
+    for (auto f : parts) {
+        const int v = f(cls, block);
+        if (v) return v;
     }
+    return 0;
 }
 
 // ---------------------------------------------------------------- no-allocation variant
@@ -1683,3 +2075,4 @@ extern "C" int qmc_k_noalloc_eval(int device, int cls, const QmcJobDev *jobs_hos
         return -1;
     return 0;
 }
+#endif  // QMC_PART == 0

@@ -1,0 +1,4 @@
+// Evaluator classes of part 1 of the kernels (see qmc_kernels.cu): compiled
+// as their own translation unit so that the build runs in parallel.
+#define QMC_PART 1
+#include "qmc_kernels.cu"

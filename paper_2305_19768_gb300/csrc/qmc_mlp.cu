@@ -46,6 +46,11 @@ constexpr int kAStageBytes = kTileM * kBK * 2;           // 16 KB
 constexpr int kBStageBytes = kMaxN * kBK * 2;            // 32 KB
 constexpr int kStageBytes = kAStageBytes + kBStageBytes;
 constexpr int kGemmSmem = kStages * kStageBytes + 1024;  // + slack to align the ring to 1024 B
+// Polls of one mbarrier wait before it gives up (with 64 ns sleeps: a few
+// seconds). The pipeline's waits take their limit from the launch (this value
+// unless a caller asks for fewer); the clean-up after a timeout always waits
+// with this one, so that copies and MMAs in flight land before the CTA frees
+// its tensor memory and exits.
 constexpr unsigned kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -72,8 +77,8 @@ __host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (unsigned it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -98,7 +103,7 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
 qmc_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float *C,
-                 int N, int K, int chunks_per_split, size_t split_stride, unsigned *err) {
+                 int N, int K, int chunks_per_split, size_t split_stride, unsigned *err, unsigned wait_limit) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base;
@@ -138,7 +143,7 @@ qmc_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         // producer: TMA into the ring, each stage reused once the MMAs reading it committed
         for (int i = 0; i < nc; ++i) {
             const int s = i % kStages;
-            if (i >= kStages && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / kStages - 1) & 1))) {
+            if (i >= kStages && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / kStages - 1) & 1), wait_limit)) {
                 ok = false;
                 break;
             }
@@ -155,7 +160,7 @@ qmc_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const uint32_t idesc = instr_desc_bf16(kTileM, N);
         for (int i = 0; i < nc; ++i) {
             const int s = i % kStages;
-            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / kStages) & 1))) {
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / kStages) & 1), wait_limit)) {
                 ok = false;
                 break;
             }
@@ -182,7 +187,7 @@ qmc_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                          smem_u32(&done))
                      : "memory");
     }
-    if (!mbar_wait(smem_u32(&done), 0)) ok = false;
+    if (!mbar_wait(smem_u32(&done), 0, wait_limit)) ok = false;
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
     if (ok) {
@@ -206,9 +211,12 @@ qmc_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     } else {
         if (tid == 0) {
             atomicAdd(err, 1u);
-            // copies still in flight land before the CTA's shared memory goes away
+            // copies still in flight land before the CTA's shared memory goes
+            // away, and the MMAs issued so far finish before the accumulator's
+            // tensor memory is freed (the MMA thread always commits `done`)
             for (int i = consumed; i < issued; ++i)
-                mbar_wait(smem_u32(&full[i % kStages]), (uint32_t)((i / kStages) & 1));
+                mbar_wait(smem_u32(&full[i % kStages]), (uint32_t)((i / kStages) & 1), kWaitLimit);
+            mbar_wait(smem_u32(&done), 0, kWaitLimit);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::);
@@ -273,8 +281,8 @@ SplitWorkspace &workspace() {
 // C[M][N] = A[M][K] B[N][K]^T, device pointers; M % 128 == 0, K % 16 == 0,
 // N % 16 == 0 and 16 <= N <= 256; A, B 16-byte aligned; C rows contiguous
 // (ldc = N). Split-K when the M tiles leave most SMs idle.
-extern "C" int qmc_k_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
-                               void *stream) {
+extern "C" int qmc_k_gemm_bf16_limit(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
+                                     void *stream, unsigned wait_limit) {
     if (M <= 0 || M % 128 || K <= 0 || K % 16 || N < 16 || N > 256 || N % 16) return -2;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return -2;
     static bool attr_set = false;
@@ -310,7 +318,8 @@ extern "C" int qmc_k_gemm_bf16(const void *A, const void *B, float *C, int M, in
         out = w.ptr;
     }
     qmc_gemm_bf16_tc<<<dim3(mt, splits), kGemmThreads, kGemmSmem, (cudaStream_t)stream>>>(mapA, mapB, out, N, K,
-                                                                                           per, mn, err_dev);
+                                                                                           per, mn, err_dev,
+                                                                                           wait_limit);
     if (splits > 1) {
         const unsigned blocks = (unsigned)std::min<size_t>((mn + 255) / 256, 4096);
         qmc_gemm_splitk_sum<<<blocks, 256, 0, (cudaStream_t)stream>>>(out, splits, mn, C, mn);
@@ -318,10 +327,22 @@ extern "C" int qmc_k_gemm_bf16(const void *A, const void *B, float *C, int M, in
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+extern "C" int qmc_k_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
+                               void *stream) {
+    return qmc_k_gemm_bf16_limit(A, B, C, M, N, K, err_dev, stream, kWaitLimit);
+}
+
 extern "C" int qmc_gemm_bf16_device(const void *A, const void *B, float *C, int M, int N, int K, unsigned *err_dev,
                                     void *stream) {
     if (!A || !B || !C || !err_dev) return QMC_E_INVAL_LOCAL;
     const int rc = qmc_k_gemm_bf16(A, B, C, M, N, K, err_dev, stream);
+    return rc == -2 ? QMC_E_INVAL_LOCAL : (rc ? QMC_E_CUDA_LOCAL : 0);
+}
+
+extern "C" int qmc_gemm_bf16_device_limit(const void *A, const void *B, float *C, int M, int N, int K,
+                                          unsigned *err_dev, void *stream, unsigned wait_limit) {
+    if (!A || !B || !C || !err_dev) return QMC_E_INVAL_LOCAL;
+    const int rc = qmc_k_gemm_bf16_limit(A, B, C, M, N, K, err_dev, stream, wait_limit);
     return rc == -2 ? QMC_E_INVAL_LOCAL : (rc ? QMC_E_CUDA_LOCAL : 0);
 }
 

@@ -1,152 +1,317 @@
-"""Algorithmic FP64 work per integrand evaluation (roofline numerator).
+"""FP64 and FP32 work per integrand evaluation (the roofline numerator).
 
 One evaluation = one lattice point of one sector for one shift, all eps
-orders, all subtraction corners. The count follows the evaluator's
-formulation of the method (Section "Kernels" of the design notes):
+orders, all subtraction corners. The count follows the evaluator's own
+formulation of the method, operation by operation:
 
-* +, -, x, division and reciprocal count 1 flop, a fused multiply-add 2;
-* each transcendental counts a fixed algorithmic cost: log and exp 20
-  flops, atan2 20, sincos 30 (a minimax polynomial of degree ~10 plus range
-  reduction), independent of how a math library implements them;
-* only the terms the requested orders need are counted: corner V carries
-  its eps exponent (one log of U^u1 F^f1) only if hi + |V| >= 1, the ln t of
-  a singular variable only if hi + ns - 1 >= 1, and so on.
+* FP64 flops: add, subtract and multiply count 1, a fused multiply-add 2.
+  Steps that the evaluator computes on the integer pipe count 0 FP64 flops:
+  the lattice coordinate (exact fixed-point walk), the korobov3 transform of
+  the d <= 3 classes, and every logarithm (fixed-point table reduction).
+  Multiplications by the constant 1 that the compiler folds away (first
+  factors of products started at 1, the 1/1 of series recursions) are not
+  counted.
+* FP32 flops: the same rule for the monomial products of the
+  mixed-precision classes.
+* Transcendentals are counted separately, never as flops: logarithms
+  (integer pipe), arctangents (table plus a series on the FP64 pipe; its
+  FP64 operations are in the flop count), hardware reciprocal seeds
+  (rcp.approx, followed by two Newton steps = 4 FMA counted as flops),
+  exponentials and sine/cosine pairs (library).
+* Only terms the requested orders need are counted: corner V carries its eps
+  exponent only if hi + |V| >= 1, the ln t of a singular variable only if
+  hi + ns - 1 >= 1, pole set P forms its series terms below hi + |P| + 1.
 
-The figure is per sector; workloads average it over their sectors.
+Workloads average the per-sector figures over their sectors (equal lattices).
 """
 from __future__ import annotations
 
-LOG = EXP = ATAN2 = 20
-SINCOS = 30
+from dataclasses import dataclass, field
+
+RCP_FLOPS = 8   # two Newton steps from the hardware seed: 4 FMA
 
 
-def _monomial_flops(P) -> int:
+@dataclass
+class Work:
+    fp64: float = 0.0
+    fp32: float = 0.0
+    log: float = 0.0
+    atan2: float = 0.0
+    rcp: float = 0.0
+    exp: float = 0.0
+    sincos: float = 0.0
+
+    def add(self, other: "Work", scale: float = 1.0) -> "Work":
+        for k in self.__dataclass_fields__:
+            setattr(self, k, getattr(self, k) + scale * getattr(other, k))
+        return self
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in self.__dataclass_fields__}
+
+    def recip(self, count=1):
+        self.fp64 += RCP_FLOPS * count
+        self.rcp += count
+
+
+def _popc(v: int) -> int:
+    return bin(v).count("1")
+
+
+def _sector_shape(sector):
+    d = sector.d
+    sing = [j for j in range(d) if sector.a[j] <= -1]
+    ns = len(sing)
+    emax = max(sector.U.max_var_exponent(), sector.F.max_var_exponent(), 1)
+    for j in range(d):
+        if sector.a[j] > 0:
+            emax = max(emax, sector.a[j])
+    return d, sing, ns, emax
+
+
+def _is_small_int(x) -> bool:
+    return float(x) == int(float(x)) and abs(float(x)) <= 4
+
+
+def _grouped_poly(P, sing, ns):
+    """Flops of the grouped monomial sums of one polynomial: per monomial its
+    (nv - 1) power products and one FMA with the coefficient; the first
+    monomial of each singular-mask group takes a multiply (or nothing, if
+    constant) instead."""
+    groups = {}
+    for e in P.terms:
+        mask = sum(1 << q for q, j in enumerate(sing) if e[j] > 0)
+        groups.setdefault(mask, []).append(e)
     f = 0
-    for e, _ in P.terms.items():
-        nv = sum(1 for x in e if x)
-        f += (nv - 1) + 2 if nv else 1
+    for mons in groups.values():
+        for i, e in enumerate(mons):
+            nv = sum(1 for x in e if x)
+            if nv == 0:
+                f += 0 if i == 0 else 1
+            else:
+                f += (nv - 1) + (1 if i == 0 else 2)
     return f
 
 
-def sector_flops(sector, lo: int, norders: int) -> int:
-    d = sector.d
-    ns = len(sector.singular)
-    hi = lo + norders - 1
-    f = 0
-    f += 2 * d                          # r / n and + delta
-    f += 9 * d                          # korobov3 t
-    f += 3 * d + 3                      # weight: u(1-u), product, cube, 140^d
-    emax = max(sector.U.max_var_exponent(), sector.F.max_var_exponent(), 1)
-    f += d * (emax - 1)                 # power table
-    f += _monomial_flops(sector.U) + _monomial_flops(sector.F)
-    f += 2 * ns * (1 << max(ns - 1, 0))  # subset sums of both polynomials
-    u0, f0, u1, f1 = int(sector.u0), int(sector.f0), int(sector.u1), int(sector.f1)
-    for V in range(1 << ns):
-        nV = hi + bin(V).count("1") + 1
-        f += (1 if f0 < 0 else 0) + (1 if u0 < 0 else 0) + max(abs(u0) + abs(f0) - 1, 0) + 1
-        if nV > 1:
-            f += max(abs(u1) + abs(f1) - 1, 0) + LOG + 1
-            f += 2 * (nV - 1)           # corner series B Lambda^i / i!
-    f += ns                              # 1/t of singular variables
-    if hi + ns - 1 >= 1:
-        f += ns * LOG
-    need_lam = hi + ns >= 1
-    for j in range(d):
-        if sector.a[j] != -1 and sector.b[j] != 0 and need_lam:
-            f += LOG + 2
-    for q in range(ns):                  # superset Moebius transform
-        for P in range(1 << ns):
-            if not P & (1 << q):
-                f += max(hi + bin(P).count("1") + 1, 0)
-    for P in range(1 << ns):
-        np_ = bin(P).count("1")
+def _powers(d, emax):
+    return d * ((emax >= 2) + (emax >= 3) + (emax >= 4))
+
+
+def _assemble(ns, lo, hi, nord, cplx: bool) -> float:
+    """The pole-set assembly (corner series, superset Moebius transform,
+    A_P, E_P and its exponential series, the convolution and res += A PE)."""
+    mul = 6 if cplx else 1          # value x value: complex product (2 FMA + 2 MUL) or one multiply
+    fmul = 2 if cplx else 1         # value x real scalar
+    f = 0.0
+    full = (1 << ns) - 1
+    for V in range(full + 1):
+        nV = hi + _popc(V) + 1
+        for i in range(1, nV):
+            # g_i = g_{i-1} Lambda / i: complex x complex (cplx) or real x real, then x (1/i) unless i = 1
+            f += mul + (0 if i == 1 else fmul)
+    for q in range(ns):
+        for P in range(full + 1):
+            if P & (1 << q):
+                continue
+            nP = hi + _popc(P) + 1
+            f += max(nP, 0) * (2 if cplx else 1)
+    for P in range(full + 1):
+        np_ = _popc(P)
         nP = hi + np_ + 1
         if nP < 1:
             continue
-        f += ns                          # A_P
-        if nP > 1:
-            f += 2 * (ns - np_) + 2 * (nP - 1)   # E_P and its series
+        if P not in (0, full):
+            f += ns                          # A_P from its factors (runtime-selected start)
+        if nP > 1 and P != full:
+            f += 2 * (ns - np_)              # E_P = sum b_q ln t_q
+            f += 2 * max(nP - 2, 0)          # e_l = e_{l-1} E / l, l >= 2
         for k in range(max(0, lo + np_), nP):
-            f += 2 * k                   # convolution term k
-        f += 2 * min(norders, nP)        # res += A PE
-    f += 2 * norders                     # weight x value into the accumulator
+            if P != full:
+                f += 2 * k * (2 if cplx else 1)   # PE_k += g_i e_{k-i}
+        f += 2 * max(nord - max(0, -(lo + np_)), 0) * (2 if cplx else 1)   # res += A PE, every order in range
     return f
 
 
-CMUL = 6        # complex product: 2 FMA + 2 MUL (or 4 MUL + 2 ADD)
-CFMA_REAL = 4   # real coefficient times complex value added in: 2 FMA
+def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
+    """Work of one evaluation in the real (undeformed) evaluator classes."""
+    d, sing, ns, emax = _sector_shape(sector)
+    hi = lo + norders - 1
+    wide = d > 3 or ns > 2
+    w = Work()
+    # transform: d <= 3 classes on the integer pipe (only the product of the
+    # per-coordinate weights u(1-u) is FP64); d <= 6 classes in FP64
+    if wide:
+        w.fp64 += 9 * d                  # t = u^2 u^2 (35 + u(-84 + u(70 - 20u)))
+        w.fp64 += 3 * d - 1              # Ws *= u - u^2
+    else:
+        w.fp64 += d - 1
+    w.fp64 += 2                          # W = Ws^3
+    # power tables and grouped monomial sums (FP32 in the mixed classes)
+    pw = _powers(d, emax)
+    polys = _grouped_poly(sector.U, sing, ns) + _grouped_poly(sector.F, sing, ns)
+    if mixed:
+        w.fp32 += pw + polys
+        w.fp64 += pw                     # FP64 powers still feed the regular prefactor
+    else:
+        w.fp64 += pw + polys
+    w.fp64 += 2 * ns * (1 << max(ns - 1, 0))   # subset sums of U and F
+    need_lam = hi + ns >= 1
+    nb_reg = sum(1 for j in range(d) if sector.a[j] > -1 and float(sector.b[j]) != 0.0)
+    na_reg = sum(1 for j in range(d) if sector.a[j] > 0)
+    if need_lam:
+        w.log += nb_reg
+        w.fp64 += 2 * nb_reg             # Lc += b_j ln t_j
+    w.fp64 += max(na_reg - 1, 0)         # Cc = prod t^a
+    if hi + ns - 1 >= 1:
+        w.log += ns                      # ln t of the singular variables
+    # reciprocals of the singular t's
+    if ns == 2:
+        w.fp64 += 3
+        w.recip()
+    elif ns == 1:
+        w.recip()
+    elif ns > 2:
+        w.recip(ns)
+        w.fp64 += ns - 1
+    u0, f0, u1, f1 = (float(x) for x in (sector.u0, sector.f0, sector.u1, sector.f1))
+    u0i, f0i = _is_small_int(u0), _is_small_int(f0)
+    comb = _is_small_int(u1) and _is_small_int(f1)
+    full = (1 << ns) - 1
+    # 1/F at the corners that need it, in pairs
+    needF = [V <= full and ((f0i and f0 < 0) or (hi + _popc(V) >= 1 and comb and f1 < 0))
+             for V in range(1 << max(ns, 1))]
+    for V in range(0, len(needF), 2):
+        a, b = needF[V], (needF[V + 1] if V + 1 < len(needF) else False)
+        if a and b:
+            w.fp64 += 3
+            w.recip()
+        elif a or b:
+            w.recip()
+    for V in range(full + 1):
+        lam_here = hi + _popc(V) >= 1
+        if (u0i and u0 < 0) or (lam_here and comb and u1 < 0):
+            w.recip()
+        factors = 1 if na_reg else 0
+        for e0, isint in ((u0, u0i), (f0, f0i)):
+            if isint and e0 != 0:
+                w.fp64 += abs(int(e0)) - 1
+                factors += 1
+            elif not isint:
+                w.log += 1
+                w.exp += 1
+                w.fp64 += 1
+                factors += 1
+        w.fp64 += max(factors - 1, 0)    # B = Cc U^u0 F^f0
+        if lam_here:
+            if comb:
+                # U^u1 F^f1 (each power 1 when its exponent is 0), then one log
+                w.fp64 += max(abs(int(u1)) - 1, 0) + max(abs(int(f1)) - 1, 0) + 1
+                w.log += 1
+            else:
+                w.log += 2
+                w.fp64 += 3
+            w.fp64 += 1                  # Lambda_V = Lc + log
+    w.fp64 += _assemble(ns, lo, hi, norders, cplx=False)
+    w.fp64 += 2 * norders                # acc += res W
+    return w
 
 
 def _derivative_flops(P, d: int):
     """Real flops of all first and second derivatives of P at a real point
-    (each derivative monomial: its products and one FMA with the coefficient)."""
+    (the host's derivative tables: per derivative monomial its products and
+    one FMA with the coefficient)."""
     f = 0
     for e in P.terms:
         vars_ = [j for j in range(d) if e[j]]
         nv = len(vars_)
-        f += nv * (max(nv - 2, 0) + 2)                       # dP/dt_j
-        f += (nv * (nv + 1) // 2) * (max(nv - 3, 0) + 2)     # d2P/dt_j dt_k
+        f += nv * (max(nv - 2, 0) + 2)
+        f += (nv * (nv + 1) // 2) * (max(nv - 3, 0) + 2)
     return f
 
 
 def _complex_poly_flops(P) -> int:
+    # per monomial: (nv - 1) complex products (2 FMA + 2 MUL = 6) and the real
+    # coefficient times the complex value added in (2 FMA = 4)
     f = 0
     for e in P.terms:
         nv = sum(1 for x in e if x)
-        f += max(nv - 1, 0) * CMUL + CFMA_REAL
+        f += max(nv - 1, 0) * 6 + 4
     return f
 
 
-def deformed_sector_flops(sector, lo: int, norders: int) -> int:
-    """The deformed evaluator's formulation: korobov3 of u and of 1 - u; at
-    each corner V the derivatives of F, the real matrix V_jk and det J in
-    closed form, z and rho, U and F at z in complex arithmetic, the prefactor
-    num/den with one complex reciprocal and, where the corner needs its eps
-    exponent, one complex log of the product of its factors (a real log of
-    the squared modulus and an atan2); then the assembly in complex
-    arithmetic."""
-    d = sector.d
-    ns = len(sector.singular)
+def deformed_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
+    """Work of one evaluation in the deformed classes: korobov3 of u and 1 - u
+    on the integer pipe; at each corner V the derivatives of F, the real
+    matrix V_jk and det J in closed form, z and rho, U and F at z in complex
+    arithmetic, the prefactor num/den with one complex reciprocal and, where
+    the corner needs its eps exponent, one complex log of the product of its
+    factors (a real log of the squared modulus and an atan2); then the
+    assembly in complex arithmetic."""
+    d, sing, ns, emax = _sector_shape(sector)
     hi = lo + norders - 1
-    u0, f0, u1, f1 = int(sector.u0), int(sector.f0), int(sector.u1), int(sector.f1)
-    f = 2 * d + 18 * d + 3 * d + 3       # lattice, korobov3 of u and 1 - u, weight
-    f += ns + (ns * LOG if hi + ns - 1 >= 1 else 0)   # 1/t, ln t of singular variables
-    per_corner = _derivative_flops(sector.F, d)
-    per_corner += 4 * d * d + 3 * d      # V_jk, z, rho
-    per_corner += {1: 0, 2: 5, 3: 26}.get(d, 26)      # det J (closed form)
-    per_corner += _complex_poly_flops(sector.U) + _complex_poly_flops(sector.F)
-    per_corner += 1                      # sign check
-    nreg_a = sum(1 for j in range(d) if sector.a[j] > 0)
-    per_corner += CMUL * (ns + abs(u0) + abs(f0) + nreg_a) + 6 + CMUL   # num/den, 1/den, num x (1/den)
-    nb = sum(1 for j in range(d) if sector.b[j] != 0)
-    lam_corner = CMUL * (nb + abs(u1) + abs(f1)) + CMUL + 6 + 2 + LOG + ATAN2 + 3
+    w = Work()
+    w.fp64 += (d - 1) + 2                        # Ws products, W = Ws^3
+    if ns:
+        w.recip(ns)                              # 1/t of the singular variables
+    if hi + ns - 1 >= 1:
+        w.log += ns
+    u0, f0, u1, f1 = (float(x) for x in (sector.u0, sector.f0, sector.u1, sector.f1))
+    comb_all = (_is_small_int(u1) and _is_small_int(f1)
+                and all(_is_small_int(b) for b in sector.b))
+    nb = sum(1 for j in range(d) if float(sector.b[j]) != 0.0)
+    na_reg = sum(1 for j in range(d) if sector.a[j] > 0)
     for V in range(1 << ns):
-        f += per_corner
-        if hi + bin(V).count("1") >= 1:
-            f += lam_corner
-            f += 2 * CMUL * (hi + bin(V).count("1"))     # corner series B Lambda^i / i!
-    # Moebius transform and pole-set assembly on complex values
-    for q in range(ns):
-        for P in range(1 << ns):
-            if not P & (1 << q):
-                f += 2 * max(hi + bin(P).count("1") + 1, 0)
-    for P in range(1 << ns):
-        np_ = bin(P).count("1")
-        nP = hi + np_ + 1
-        if nP < 1:
-            continue
-        f += ns
-        if nP > 1:
-            f += 2 * (ns - np_) + 2 * (nP - 1)
-        for k in range(max(0, lo + np_), nP):
-            f += 2 * k * 2
-        f += 4 * min(norders, nP)
-    f += 4 * norders
-    return f
+        per = Work()
+        deriv = _derivative_flops(sector.F, d) + d * _powers(1, emax)
+        if mixed:
+            per.fp32 += deriv
+        else:
+            per.fp64 += deriv
+        per.fp64 += 3 * d * d + 3 * d + 3 * d    # V_jk, rho = 1 - i g, z
+        per.fp64 += {1: 0, 2: 5, 3: 26}.get(d, 26)   # det J in closed form
+        cpoly = _complex_poly_flops(sector.U) + _complex_poly_flops(sector.F) + d * 6 * (emax - 1)
+        if mixed:
+            per.fp32 += cpoly
+        else:
+            per.fp64 += cpoly
+        # num / den: complex products of the prefactor factors, 1/den, num x (1/den)
+        nfac = ns + abs(int(u0)) + abs(int(f0)) + na_reg
+        per.fp64 += 6 * nfac + 3 + 3 + 6
+        per.recip()
+        if hi + _popc(V) >= 1:
+            if comb_all:
+                per.fp64 += 6 * (nb + abs(int(u1)) + abs(int(f1))) + 6   # X = Xn conj(Xd)
+                per.fp64 += 27                   # atan2: reduction, division, degree-7 series, octant
+                per.atan2 += 1
+                per.recip(2)                     # inside atan2 and 1/|Xd|^2
+                per.fp64 += 3 + 3 + 1 + 1 + 2    # |Xn|^2, |Xd|^2, ratio, 0.5 x log, arg
+                per.log += 1
+            else:
+                per.fp64 += 12 * (nb + 2)
+                per.atan2 += nb + 2
+                per.log += nb + 2
+            per.fp64 += 12 * (hi + _popc(V))     # corner series B Lambda^i / i! (complex)
+        w.add(per)
+    w.fp64 += _assemble(ns, lo, hi, norders, cplx=True)
+    w.fp64 += 4 * norders                        # acc += res W
+    return w
+
+
+def sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
+    if getattr(sector, "deform", False):
+        return deformed_sector_work(sector, lo, norders, mixed)
+    return real_sector_work(sector, lo, norders, mixed)
+
+
+def workload_work(integral, lo: int, norders: int, mixed: bool = False) -> Work:
+    """Mean work per evaluation over the integral's sectors (equal lattices)."""
+    tot = Work()
+    for s in integral.sectors:
+        tot.add(sector_work(s, lo, norders, mixed))
+    n = max(1, len(integral.sectors))
+    return Work(**{k: v / n for k, v in tot.as_dict().items()})
 
 
 def workload_flops(integral, lo: int, norders: int, deform: bool = False) -> float:
-    """Mean FP64 flops per evaluation over the integral's sectors (equal lattices)."""
-    fs = [deformed_sector_flops(s, lo, norders) if deform else sector_flops(s, lo, norders)
-          for s in integral.sectors]
-    return sum(fs) / len(fs)
+    """Mean FP64 flops per evaluation (no credit for integer-pipe steps)."""
+    return workload_work(integral, lo, norders).fp64

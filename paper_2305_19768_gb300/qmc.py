@@ -107,6 +107,7 @@ def lib():
                                         P(u64)], i32),
                 "qmc_shifts": ([vp, u64, u64, i32, i32, P(dbl)], i32),
                 "qmc_fp64_peak": ([vp, P(dbl)], i32),
+                "qmc_fp32_peak": ([vp, P(dbl)], i32),
                 "qmc_eval_jobs_noalloc": ([vp, P(qmc_job), i32, i32, i32, vp, vp], i32),
                 "qmc_fp64_log": ([vp, P(dbl), sz, P(dbl)], i32),
                 "qmc_fp64_rcp": ([vp, P(dbl), sz, P(dbl)], i32),
@@ -120,6 +121,7 @@ def lib():
                 "qmc_median_candidates": ([u64, i32, i32, u64, P(ctypes.c_uint32)], i32),
                 "qmc_gemm_bf16": ([P(ctypes.c_uint16), P(ctypes.c_uint16), P(ctypes.c_float), i32, i32, i32], i32),
                 "qmc_gemm_bf16_device": ([vp, vp, vp, i32, i32, i32, vp, vp], i32),
+                "qmc_gemm_bf16_device_limit": ([vp, vp, vp, i32, i32, i32, vp, vp, ctypes.c_uint32], i32),
                 "qmc_mlp_create": ([P(vp), i32, i32, i32, i32, i32, u64], i32),
                 "qmc_mlp_destroy": ([vp], None),
                 "qmc_mlp_num_params": ([vp, P(sz)], i32),
@@ -153,10 +155,11 @@ def exported_symbols():
             "qmc_load_sectors_mem", "qmc_load_sectors", "qmc_integral_info", "qmc_set_kinematics",
             "qmc_plan_create", "qmc_plan_output_size", "qmc_plan_run", "qmc_plan_results",
             "qmc_plan_last_time", "qmc_plan_destroy", "qmc_eval_jobs", "qmc_lattice_points",
-            "qmc_shifts", "qmc_fp64_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp", "qmc_korobov3", "qmc_fp64_atan2",
+            "qmc_shifts", "qmc_fp64_peak", "qmc_fp32_peak", "qmc_eval_jobs_noalloc", "qmc_fp64_log", "qmc_fp64_rcp", "qmc_korobov3", "qmc_fp64_atan2",
             "qmc_shift_stats", "qmc_series_mul", "qmc_series_var", "qmc_allocate", "qmc_integrate",
             "qmc_plan_use_graph", "qmc_plan_job_failures", "qmc_presample_lambda", "qmc_autotune",
-            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_gemm_bf16_device", "qmc_mlp_create",
+            "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_gemm_bf16_device",
+            "qmc_gemm_bf16_device_limit", "qmc_mlp_create",
             "qmc_mlp_destroy", "qmc_mlp_num_params", "qmc_mlp_get_params", "qmc_mlp_set_params",
             "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train", "qmc_integrate_ex"]
 
@@ -354,6 +357,14 @@ def qmc_gemm_bf16_device(A_ptr, B_ptr, C_ptr, M, N, K, err_ptr, stream_ptr=0):
     _check(None, lib().qmc_gemm_bf16_device(ctypes.c_void_p(A_ptr), ctypes.c_void_p(B_ptr), ctypes.c_void_p(C_ptr),
                                             M, N, K, ctypes.c_void_p(err_ptr),
                                             ctypes.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def qmc_gemm_bf16_device_limit(A_ptr, B_ptr, C_ptr, M, N, K, err_ptr, wait_limit, stream_ptr=0):
+    """qmc_gemm_bf16_device with `wait_limit` polls per pipeline wait."""
+    _check(None, lib().qmc_gemm_bf16_device_limit(ctypes.c_void_p(A_ptr), ctypes.c_void_p(B_ptr),
+                                                  ctypes.c_void_p(C_ptr), M, N, K, ctypes.c_void_p(err_ptr),
+                                                  ctypes.c_void_p(stream_ptr) if stream_ptr else None,
+                                                  int(wait_limit)))
 
 
 def _fp(a):
@@ -568,6 +579,12 @@ def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, eps
 def qmc_fp64_peak(ctx) -> float:
     g = ctypes.c_double()
     _check(ctx, lib().qmc_fp64_peak(ctx, ctypes.byref(g)))
+    return g.value
+
+
+def qmc_fp32_peak(ctx) -> float:
+    g = ctypes.c_double()
+    _check(ctx, lib().qmc_fp32_peak(ctx, ctypes.byref(g)))
     return g.value
 
 

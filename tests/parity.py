@@ -19,6 +19,9 @@ conditioned in FP64.
 """
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 import oracle
@@ -66,13 +69,42 @@ def oracle_sums(integral, sector, inv, n, m, seed, stream, lo, norders, lam=None
     return out, absm, cond
 
 
-def assert_close(gpu, orc, absm, cond=None, rtol=RTOL, what=""):
+def achieved(gpu, orc, absm, cond=None):
+    """Per eps order (axis -2 of [shifts][orders][2]): the worst |gpu - oracle|
+    relative to |Q| (the complex modulus of the oracle's per-shift sum), to
+    the absolute mass A, and to the corner mass C."""
+    gpu = np.asarray(gpu).reshape(orc.shape)
+    err = np.abs(gpu - orc).max(axis=-1)                      # [shifts][orders]
+    q = np.hypot(orc[..., 0], orc[..., 1])
+    out = {"err_over_Q": (err / np.maximum(q, 1e-300)).max(axis=0).tolist(),
+           "err_over_A": (err / np.maximum(absm, 1e-300)).max(axis=0).tolist()}
+    if cond is not None:
+        out["err_over_C"] = (err / np.maximum(cond, 1e-300)).max(axis=0).tolist()
+        out["C_over_Q"] = (cond / np.maximum(q, 1e-300)).max(axis=0).tolist()
+    return out
+
+
+def record(what, lo, stats, bound="fp64"):
+    """Append one parity measurement to the JSON-lines file named by the
+    QMC_PARITY_LOG environment variable (nothing if unset)."""
+    path = os.environ.get("QMC_PARITY_LOG")
+    if not path:
+        return
+    with open(path, "a") as fh:
+        fh.write(json.dumps({"what": what, "lo": lo, "bound": bound, **stats}) + "\n")
+
+
+def assert_close(gpu, orc, absm, cond=None, rtol=RTOL, what="", lo=None, ctol=None):
     gpu = np.asarray(gpu).reshape(orc.shape)
     scale = np.maximum(np.abs(orc), absm[..., None])
     err = np.abs(gpu - orc)
     allow = rtol * scale + 1e-300
     if cond is not None:
-        allow = allow + CTOL * cond[..., None]
+        allow = allow + (CTOL if ctol is None else ctol) * cond[..., None]
+    if orc.ndim == 3:
+        stats = achieved(gpu, orc, absm, cond)
+        stats["worst_over_bound"] = float((err / allow).max())
+        record(what, lo, stats, "fp64" if rtol == RTOL else f"rtol={rtol:g}")
     bad = err > allow
     if bad.any():
         idx = np.argwhere(bad)[:5]

@@ -105,3 +105,39 @@ def test_gemm_bf16_device_buffers_and_split_k(M, N, K):
     bound = (K / 16 + 2) * 2.0 ** -24 * (a.abs() @ b.abs().T) + 1e-30
     worst = float(((C.double() - ref).abs() / bound).max())
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("M,N,K", [(512, 256, 1024), (19456, 256, 1024)])
+def test_gemm_wait_timeout_sets_the_error_word_and_frees_tensor_memory(M, N, K):
+    # every pipeline wait given zero polls: each CTA must give up, count
+    # itself in the error word, drain its copies and MMAs, free its tensor
+    # memory and return; a normal GEMM right after must then allocate tensor
+    # memory again and be exact. (512: split-K, one K chunk per CTA, only the
+    # MMA-side waits run out; 19456: 16 chunks per CTA, the producer's
+    # stage-free waits run out too.)
+    torch = pytest.importorskip("torch")
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda", dtype=torch.float32)
+    err = torch.zeros(1, device="cuda", dtype=torch.int32)
+    qmc.qmc_gemm_bf16_device_limit(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, err.data_ptr(), 0)
+    torch.cuda.synchronize()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mt, nchunks = M // 128, (K + 63) // 64
+    splits = max(1, min(nchunks, sms // mt))
+    per = (nchunks + splits - 1) // splits
+    splits = (nchunks + per - 1) // per
+    assert int(err.item()) == mt * splits
+    err.zero_()
+    for limit in (None, 1 << 26):
+        C.zero_()
+        if limit is None:
+            qmc.qmc_gemm_bf16_device(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, err.data_ptr())
+        else:
+            qmc.qmc_gemm_bf16_device_limit(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, err.data_ptr(), limit)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        a, b = A.double(), B.double()
+        bound = (K / 16 + 2) * 2.0 ** -24 * (a.abs() @ b.abs().T) + 1e-30
+        assert float(((C.double() - a @ b.T).abs() / bound).max()) <= 1.0

@@ -207,7 +207,8 @@ def _compare_integral(gpu, I, inv_points, n, m, lo, norders, lam=None, sectors=N
     for i, sp in enumerate(specs):
         o, a, c = oracle_sums(I, sp["sector"], list(inv_points[sp["point"]]), n, m, seed,
                               sp["stream"], lo, norders, lam)
-        worst = max(worst, assert_close(out[i], o, a, c, what=f"sector {sp['sector']} point {sp['point']}"))
+        worst = max(worst, assert_close(out[i], o, a, c, lo=lo,
+                                        what=f"{I.name} n={n} sector {sp['sector']} point {sp['point']}"))
     return worst
 
 
@@ -326,7 +327,8 @@ def test_full_size_sampled_outputs():
         out = out.reshape(12, m, 3, 2)
         for sector, shift in ((0, 0), (5, 17), (11, 31)):
             o, a, c = oracle_sums(I, sector, [-3.0, -2.0], n, m, 1, sector, -2, 3, shift_rows=[shift])
-            assert_close(out[sector, shift][None], o, a, c, what=f"full-size sector {sector} shift {shift}")
+            assert_close(out[sector, shift][None], o, a, c, lo=-2,
+                         what=f"box1L_massless n={n} full-size sector {sector} shift {shift}")
         # property at any size: the mean over shifts reproduces the closed form
         from golden_values import closed_form
         ex = closed_form("box1L_massless", "s=-3,t=-2")
