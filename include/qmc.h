@@ -76,8 +76,30 @@ typedef struct {
     int max_growth;        /* largest factor by which one pass of qmc_integrate may enlarge a
                               sector's lattice (the next pass re-measures before growing
                               further); 0 = no limit, the allocation rule alone [0] */
-    int reserved[2];
+    int lattice;           /* QMC_LATTICE_CBC [default]: the installed table of generating
+                              vectors; QMC_LATTICE_MEDIAN: median QMC rules in qmc_integrate */
+    int lattice_candidates;/* r of the median rule (odd); r > 0 selects median rules as in the
+                              paper's lattice_candidates option [0 = CBC; 11 with QMC_LATTICE_MEDIAN] */
+    int batched;           /* qmc_integrate: -1 = one kinematic point at a time (the unbatched
+                              method); 0 or 1 = all points in one adaptive run [default] */
+    int keep_shift_sums;   /* qmc_integrate keeps every slot's last per-shift sums for
+                              qmc_per_shift_sums [0 = no] */
+    int reserved[4];
 } qmc_options;
+
+/* Generating vectors of qmc_integrate (section "Median Quasi-Monte Carlo
+ * rules"). CBC: the installed table, lattice sizes rounded up to tabulated
+ * sizes. MEDIAN: lattice sizes are any prime (rounded up to the next prime),
+ * and for every (kinematic point, sector) and size the generating vector is
+ * the median of r candidates drawn from U_n (Eq. (median); qmc_median_lattice),
+ * which costs r extra unshifted evaluations of the sector on that lattice. */
+#define QMC_LATTICE_CBC 0
+#define QMC_LATTICE_MEDIAN 1
+
+/* Device argument of qmc_create for a host-only context: no GPU is used and
+ * every call that would need one returns QMC_E_CUDA; qmc_integrate then
+ * evaluates through an evaluator installed with qmc_set_evaluator. */
+#define QMC_DEVICE_NONE (-1)
 
 /* What epsrel refers to in qmc_integrate. COEFFICIENT: each eps coefficient
  * A^(o) separately, sqrt(dR^2 + dI^2) <= epsrel |A^(o)| (the paper's
@@ -126,9 +148,10 @@ typedef struct {
 #define QMC_JOB_UNSHIFTED 1
 #define QMC_JOB_FP64 2
 
-/* Create a context on CUDA device `device`. `opt` may be NULL (defaults).
- * On success *out owns all device memory the context allocates; free with
- * qmc_destroy. Errors: QMC_E_CUDA (no device), QMC_E_NOMEM. */
+/* Create a context on CUDA device `device` (or a host-only context with
+ * QMC_DEVICE_NONE). `opt` may be NULL (defaults). On success *out owns all
+ * device memory the context allocates; free with qmc_destroy.
+ * Errors: QMC_E_CUDA (no device), QMC_E_NOMEM, QMC_E_INVAL (options). */
 int qmc_create(qmc_ctx **out, int device, const qmc_options *opt);
 
 /* Destroy a context and everything it owns (plans included). NULL is a no-op. */
@@ -320,8 +343,9 @@ int qmc_allocate(const double *W, const double *tau, const double *V, int nsums,
 /* What qmc_integrate sums: amplitudes A_k = sum_i C_ki I_i over the
  * integrals integral_ids[0..nint-1], with complex Laurent coefficients
  * coef[npoints][namp][nint][ncoef] of orders coef_lo.. (host). coef = NULL
- * means every C_ki = 1. A NULL spec integrates the sum of all loaded
- * integrals (namp = 1). */
+ * means every C_ki = 1. A NULL spec sums all loaded integrals with the
+ * coefficients of qmc_set_coefficients, or with C = 1 (namp = 1) if none
+ * are set. */
 typedef struct {
     const int *integral_ids;
     int nint;
@@ -332,13 +356,14 @@ typedef struct {
 } qmc_sum_spec;
 
 typedef struct {
-    double evaluations;     /* lattice points x shifts evaluated */
+    double evaluations;     /* lattice points x shifts evaluated (all ranks) */
     double seconds;         /* wall time of the call */
     double kernel_seconds;  /* device time of the evaluator kernels */
     int iterations;         /* evaluation passes */
     uint64_t max_lattice;   /* largest lattice any sector reached */
     double presample_evaluations;   /* lattice points x shifts of the lambda presampling */
     int fp64_escalations;           /* sectors re-evaluated in FP64 in a mixed-precision context */
+    double median_evaluations;      /* lattice points of the median-rule candidate evaluations */
 } qmc_integrate_info;
 
 /* Adaptive integration of the sums (section "Adaptive weighted sum
@@ -381,6 +406,73 @@ int qmc_integrate(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double 
 int qmc_integrate_ex(qmc_ctx *ctx, const qmc_sum_spec *spec, double epsrel, double epsabs, double timeout_s,
                      int lowest_order, int norders, qmc_c64 *value, qmc_c64 *error, qmc_integrate_info *info,
                      const uint64_t *n_init, int shifts, double *w_out, uint64_t *n_out, double *lambda_io);
+
+/* Coefficients of the weighted sums A_k = sum_i C_ki I_i that qmc_integrate
+ * forms when it is given no qmc_sum_spec (the paper's problem statement:
+ * sums of integrals with coefficient series, section "Adaptive weighted sum
+ * evaluation"): C is a host array [npoints][namp][nint][ncoef_orders] of
+ * complex Laurent coefficients, orders lowest_coef_order.., over the nint
+ * integrals loaded so far, in load order, at the npoints kinematic points of
+ * qmc_set_kinematics (copied). namp = 0 clears them (qmc_integrate then sums
+ * all loaded integrals with C = 1). Errors: QMC_E_INVAL. */
+int qmc_set_coefficients(qmc_ctx *ctx, int namp, const qmc_c64 *C, int npoints, int nint, int lowest_coef_order,
+                         int ncoef_orders);
+
+/* Value and error per eps order of one integral from the last qmc_integrate
+ * call on this context, prefactor included: host arrays value[npoints][norders]
+ * and error[npoints][norders] (re = sigma of Re, im = sigma of Im) for that
+ * call's orders lowest_order.. and kinematic points. Errors: QMC_E_INVAL if the
+ * integral took no part in the last call. */
+int qmc_integral_results(qmc_ctx *ctx, int integral_id, qmc_c64 *value, qmc_c64 *error);
+
+/* Layout of qmc_per_shift_sums. */
+typedef struct {
+    int npoints, nsectors, shifts;
+    int sector_lo, sector_orders;   /* sector eps orders sector_lo .. sector_lo + sector_orders - 1 */
+    size_t count;                   /* doubles in the full array */
+} qmc_shift_layout;
+
+/* Per-shift sums of one integral's sectors from their last evaluation in the
+ * last qmc_integrate call (options.keep_shift_sums must have been set): host
+ * array out[npoints][nsectors][shifts][sector_orders][re, im] with cap doubles
+ * of room (out may be NULL to query the layout only). `layout` (may be NULL)
+ * receives the shape, and each slot's lattice size goes to n_out[npoints][nsectors]
+ * (may be NULL). Errors: QMC_E_INVAL (not kept, not integrated, cap too small). */
+int qmc_per_shift_sums(qmc_ctx *ctx, int integral_id, double *out, size_t cap, qmc_shift_layout *layout,
+                       uint64_t *n_out);
+
+/* Cumulative work of the context: lattice points x shifts evaluated by every
+ * plan, one-shot evaluation and integration on it (all ranks' evaluations for
+ * rank-partitioned integrations), and the wall-clock seconds spent inside
+ * qmc_integrate calls. Either output may be NULL. */
+int qmc_stats(qmc_ctx *ctx, double *evaluations, double *seconds);
+
+/* Ranks of a distributed qmc_integrate (section on distributed evaluation:
+ * independent integrand evaluations spread over workers). Every rank runs the
+ * same qmc_integrate call on its own context with the same tables,
+ * kinematics, options and seed. Each pass, the (kinematic point, sector) slots
+ * to evaluate are split over the ranks by cost (largest first, each to the
+ * least-loaded rank); each rank evaluates its share, then `allreduce` sums a
+ * buffer of n doubles in place over all ranks (the per-shift sums, sign-check
+ * flags and timings of the pass, zeros where another rank evaluated), so that
+ * every rank holds the same statistics and takes the same allocation
+ * decisions: the results equal a one-rank call bit for bit. The callback
+ * returns 0 on success; it is called the same number of times on every rank.
+ * world = 1 (or allreduce = NULL) restores single-rank integration. */
+typedef int (*qmc_allreduce_fn)(void *user, double *buf, size_t n);
+int qmc_set_ranks(qmc_ctx *ctx, int rank, int world, qmc_allreduce_fn allreduce, void *user);
+
+/* Evaluator of qmc_integrate supplied by the caller: fills out[job][shift]
+ * [order][re, im] (the layout of qmc_eval_jobs) for the host job array, and
+ * returns 0 (QMC_E_SIGN_CHECK with job_fail[njobs] set nonzero for the jobs
+ * with sign-check failures). The library has no CPU
+ * evaluator of its own; this exists so that the driver's host logic
+ * (allocation, combination, rank partition) runs in a host-only context
+ * (QMC_DEVICE_NONE) for tests on machines without a GPU. NULL restores the
+ * GPU evaluator. */
+typedef int (*qmc_eval_fn)(void *user, const qmc_job *jobs, int njobs, int lo, int norders, double *out,
+                           uint32_t *job_fail);
+int qmc_set_evaluator(qmc_ctx *ctx, qmc_eval_fn eval, void *user);
 
 /* Evaluation that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the

@@ -43,6 +43,16 @@ struct QmcHostIntegral {
 
 struct qmc_plan;
 
+// What the last qmc_integrate call left for one integral.
+struct QmcLastIntegral {
+    int lowest_order = 0, norders = 0, npoints = 0;
+    std::vector<qmc_c64> value, error;   // [npoints][norders], prefactor included
+    int nsectors = 0, shifts = 0, sector_lo = 0, sector_orders = 0;
+    bool have_sums = false;
+    std::vector<double> sums;            // [npoints][nsectors][shifts][sector_orders][2]
+    std::vector<uint64_t> n;             // [npoints][nsectors] final lattice sizes
+};
+
 struct qmc_ctx {
     int device = 0;
     qmc_options opt{};
@@ -61,6 +71,18 @@ struct qmc_ctx {
     int tuned_block[QMC_NCLASS] = {};   // autotuned launch shape per kernel class (0 = default)
     int tuned_ppt[QMC_NCLASS] = {};
     double presample_evals = 0.0;       // lattice points x shifts spent in qmc_presample_lambda
+    bool host_only = false;             // QMC_DEVICE_NONE: no GPU, caller-supplied evaluator only
+    std::vector<double> h_kin;          // host copy of the kinematics [npoints][ninv]
+    // coefficients of qmc_set_coefficients: [npoints][namp][nint][ncoef]
+    int coef_namp = 0, coef_npoints = 0, coef_nint = 0, coef_lo = 0, coef_n = 0;
+    std::vector<qmc_c64> coef;
+    std::map<int, QmcLastIntegral> last;   // by integral id, from the last qmc_integrate
+    double stat_evals = 0.0, stat_seconds = 0.0;
+    int rank = 0, world = 1;            // qmc_set_ranks
+    qmc_allreduce_fn allreduce = nullptr;
+    void *allreduce_user = nullptr;
+    qmc_eval_fn eval_hook = nullptr;    // qmc_set_evaluator
+    void *eval_user = nullptr;
 };
 
 struct ClassLaunch {
@@ -77,6 +99,7 @@ struct ClassLaunch {
 struct qmc_plan {
     qmc_ctx *ctx = nullptr;
     int lo = 0, norders = 0, njobs = 0;
+    double evals = 0.0;                  // lattice points x shifts of one run
     size_t out_size = 0;
     double *d_out = nullptr;
     unsigned long long *d_status = nullptr;

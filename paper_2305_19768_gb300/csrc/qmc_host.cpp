@@ -361,6 +361,8 @@ int upload_tables(qmc_ctx *ctx) {
             secs.push_back(H);
         }
     }
+    ctx->nsectors_dev = (int)secs.size();
+    if (ctx->host_only) return QMC_OK;   // tables checked and indexed, nothing to upload
     cudaFree(ctx->d_sectors);
     cudaFree(ctx->d_monos);
     ctx->d_sectors = nullptr;
@@ -413,20 +415,31 @@ extern "C" {
 int qmc_create(qmc_ctx **out, int device, const qmc_options *opt) {
     if (!out) return QMC_E_INVAL;
     *out = nullptr;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return QMC_E_CUDA;
-    if (device < 0 || device >= ndev) return QMC_E_INVAL;
+    const bool host_only = device == QMC_DEVICE_NONE;
+    if (!host_only) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return QMC_E_CUDA;
+        if (device < 0 || device >= ndev) return QMC_E_INVAL;
+    }
     qmc_ctx *ctx = new (std::nothrow) qmc_ctx();
     if (!ctx) return QMC_E_NOMEM;
-    ctx->device = device;
+    ctx->device = host_only ? 0 : device;
+    ctx->host_only = host_only;
     if (opt) ctx->opt = *opt;
     if (ctx->opt.shifts <= 0) ctx->opt.shifts = 32;
     if (ctx->opt.seed == 0) ctx->opt.seed = 1;
     if (ctx->opt.min_points == 0) ctx->opt.min_points = 10000;
     if (ctx->opt.presamples <= 0) ctx->opt.presamples = 10000;
-    if (ctx->opt.transform < 0 || ctx->opt.transform > 2) {
+    if (ctx->opt.transform < 0 || ctx->opt.transform > 2 || ctx->opt.lattice < 0 || ctx->opt.lattice > 1 ||
+        ctx->opt.lattice_candidates < 0 || (ctx->opt.lattice_candidates > 0 && !(ctx->opt.lattice_candidates & 1)) ||
+        ctx->opt.batched < -1 || ctx->opt.batched > 1) {
         delete ctx;
         return QMC_E_INVAL;
+    }
+    if (ctx->opt.lattice == QMC_LATTICE_MEDIAN && ctx->opt.lattice_candidates == 0) ctx->opt.lattice_candidates = 11;
+    if (host_only) {
+        *out = ctx;
+        return QMC_OK;
     }
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -440,6 +453,10 @@ int qmc_create(qmc_ctx **out, int device, const qmc_options *opt) {
 
 void qmc_destroy(qmc_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->host_only) {
+        delete ctx;
+        return;
+    }
     cudaSetDevice(ctx->device);
     for (qmc_plan *p : ctx->plans) {
         free_plan_buffers(p);
@@ -473,7 +490,7 @@ int qmc_set_lattices(qmc_ctx *ctx, const uint64_t *n, const uint32_t *z, int cou
 
 int qmc_load_sectors_mem(qmc_ctx *ctx, const char *text, size_t len, int *integral_id) {
     if (!ctx || !text) return fail(ctx, QMC_E_INVAL, "qmc_load_sectors_mem: null argument");
-    cudaSetDevice(ctx->device);
+    if (!ctx->host_only) cudaSetDevice(ctx->device);
     HostIntegral I;
     int rc = parse_integral(ctx, std::string(text, len), I);
     if (rc) return rc;
@@ -519,9 +536,15 @@ int qmc_integral_info(qmc_ctx *ctx, int integral_id, int *nsectors, int *max_pol
 int qmc_set_kinematics(qmc_ctx *ctx, const double *inv, int npoints, int ninv) {
     if (!ctx || npoints < 0 || ninv < 0 || ninv > QMC_NCOEF - 1 || (npoints > 0 && ninv > 0 && !inv))
         return fail(ctx, QMC_E_INVAL, "qmc_set_kinematics: bad arguments");
-    cudaSetDevice(ctx->device);
     for (size_t i = 0; i < (size_t)npoints * ninv; ++i)
         if (!std::isfinite(inv[i])) return fail(ctx, QMC_E_INVAL, "non-finite invariant at %zu", i);
+    ctx->h_kin.assign(inv, inv + (size_t)npoints * ninv);
+    if (ctx->host_only) {
+        ctx->npoints = npoints;
+        ctx->ninv = ninv;
+        return QMC_OK;
+    }
+    cudaSetDevice(ctx->device);
     cudaFree(ctx->d_kin);
     ctx->d_kin = nullptr;
     size_t bytes = std::max<size_t>(1, (size_t)npoints * ninv) * sizeof(double);
@@ -539,11 +562,13 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
     if (!ctx || !out || (njobs > 0 && !jobs) || njobs < 0 || norders < 1)
         return fail(ctx, QMC_E_INVAL, "qmc_plan_create: bad arguments");
     *out = nullptr;
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_plan_create: host-only context (no GPU)");
     cudaSetDevice(ctx->device);
     const int hi = lo + norders - 1;
     std::vector<std::vector<QmcJobDev>> per(QMC_NCLASS);
     std::vector<std::vector<int>> per_orig(QMC_NCLASS);
     uint64_t out_off = 0;
+    double evals = 0.0;
     for (int i = 0; i < njobs; ++i) {
         const qmc_job &J = jobs[i];
         if (J.integral_id < 0 || J.integral_id >= (int)ctx->integrals.size())
@@ -593,6 +618,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         }
         D.flags = J.flags & QMC_JOB_UNSHIFTED;
         out_off += (uint64_t)J.shifts * norders * 2;
+        evals += (double)J.n * J.shifts;
         per[cls].push_back(D);
         per_orig[cls].push_back(i);
     }
@@ -602,6 +628,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
     p->norders = norders;
     p->njobs = njobs;
     p->out_size = (size_t)out_off;
+    p->evals = evals;
     auto bail = [&](int rc) {
         free_plan_buffers(p);
         delete p;
@@ -751,6 +778,7 @@ int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream) {
     }
     plan->last_stream = st;
     plan->last_out = out;
+    ctx->stat_evals += plan->evals;
     return QMC_OK;
 }
 
@@ -835,6 +863,7 @@ int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d, const
                        uint64_t k0, uint64_t count, double *x, uint64_t *r) {
     if (!ctx || !z || !delta || !x || d < 1 || d > QMC_DMAX || n < 2 || n >= (1ULL << 32))
         return fail(ctx, QMC_E_INVAL, "qmc_lattice_points: bad arguments");
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_lattice_points: host-only context (no GPU)");
     cudaSetDevice(ctx->device);
     uint32_t *dz = nullptr;
     double *dd = nullptr, *dx = nullptr;
@@ -867,6 +896,7 @@ int qmc_lattice_points(qmc_ctx *ctx, uint64_t n, const uint32_t *z, int d, const
 
 int qmc_shifts(qmc_ctx *ctx, uint64_t seed, uint64_t stream, int m, int d, double *delta) {
     if (!ctx || !delta || m < 1 || d < 1) return fail(ctx, QMC_E_INVAL, "qmc_shifts: bad arguments");
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_shifts: host-only context (no GPU)");
     cudaSetDevice(ctx->device);
     double *dd = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&dd, (size_t)m * d * sizeof(double)));
@@ -892,6 +922,7 @@ static int fp64_apply(qmc_ctx *ctx, const double *x, size_t n, double *out, cons
         if (!(x[i] >= 2.2250738585072014e-308) || !std::isfinite(x[i]))
             return fail(ctx, QMC_E_INVAL, "%s: x[%zu] is not a positive normal number", name, i);
     if (n == 0) return QMC_OK;
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "%s: host-only context (no GPU)", name);
     cudaSetDevice(ctx->device);
     double *dx = nullptr, *dy = nullptr;
     int rc = QMC_OK;
@@ -936,6 +967,7 @@ int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, dou
         yx[2 * i + 1] = x[i];
     }
     if (n == 0) return QMC_OK;
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_fp64_atan2: host-only context (no GPU)");
     cudaSetDevice(ctx->device);
     double *dyx = nullptr, *dout = nullptr;
     int rc = QMC_OK;
@@ -955,6 +987,7 @@ int qmc_fp64_atan2(qmc_ctx *ctx, const double *y, const double *x, size_t n, dou
 
 int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {
     if (!ctx || !gflops) return QMC_E_INVAL;
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_fp64_peak: host-only context (no GPU)");
     cudaSetDevice(ctx->device);
     double *d = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&d, 2 * sizeof(double)));
@@ -980,6 +1013,7 @@ int qmc_fp64_peak(qmc_ctx *ctx, double *gflops) {
 
 int qmc_fp32_peak(qmc_ctx *ctx, double *gflops) {
     if (!ctx || !gflops) return QMC_E_INVAL;
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_fp32_peak: host-only context (no GPU)");
     cudaSetDevice(ctx->device);
     float *d = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&d, 2 * sizeof(float)));
@@ -1013,6 +1047,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
     if (njobs > QMC_NOALLOC_MAX_JOBS)
         return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: %d jobs exceed the fixed limit of %d", njobs,
                     QMC_NOALLOC_MAX_JOBS);
+    if (ctx->host_only) return fail(ctx, QMC_E_CUDA, "qmc_eval_jobs_noalloc: host-only context (no GPU)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, QMC_E_CUDA, "cudaSetDevice failed");
     {
         // the call copies from host stack memory and waits for the stream: neither
@@ -1098,6 +1133,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
     if (rc == -2) return fail(ctx, QMC_E_INVAL, "qmc_eval_jobs_noalloc: size beyond the fixed scratch");
     if (rc) return fail(ctx, QMC_E_CUDA, "qmc_eval_jobs_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    for (int i = 0; i < njobs; ++i) ctx->stat_evals += (double)jobs[i].n * jobs[i].shifts;
     if (status[1]) return fail(ctx, QMC_E_NONFINITE, "%llu tile partial sums were not finite", status[1]);
     if (status[0]) return fail(ctx, QMC_E_SIGN_CHECK, "%llu deformed points had Im F > 0", status[0]);
     return QMC_OK;

@@ -26,6 +26,8 @@ QMC_PRECISION_MIXED = 1
 QMC_TRANSFORM_KOROBOV3, QMC_TRANSFORM_BAKER, QMC_TRANSFORM_NONE = 0, 1, 2
 QMC_JOB_UNSHIFTED = 1
 QMC_TARGET_COEFFICIENT, QMC_TARGET_AMPLITUDE = 0, 1
+QMC_LATTICE_CBC, QMC_LATTICE_MEDIAN = 0, 1
+QMC_DEVICE_NONE = -1
 ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIMEOUT",
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
@@ -45,7 +47,8 @@ class qmc_options(ctypes.Structure):
                 ("max_points", ctypes.c_uint64), ("presamples", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("precision", ctypes.c_int),
                 ("transform", ctypes.c_int), ("target_mode", ctypes.c_int),
-                ("max_growth", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("max_growth", ctypes.c_int), ("lattice", ctypes.c_int), ("lattice_candidates", ctypes.c_int),
+                ("batched", ctypes.c_int), ("keep_shift_sums", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class qmc_sum_spec(ctypes.Structure):
@@ -58,7 +61,12 @@ class qmc_integrate_info(ctypes.Structure):
     _fields_ = [("evaluations", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("kernel_seconds", ctypes.c_double), ("iterations", ctypes.c_int),
                 ("max_lattice", ctypes.c_uint64), ("presample_evaluations", ctypes.c_double),
-                ("fp64_escalations", ctypes.c_int)]
+                ("fp64_escalations", ctypes.c_int), ("median_evaluations", ctypes.c_double)]
+
+
+class qmc_shift_layout(ctypes.Structure):
+    _fields_ = [("npoints", ctypes.c_int), ("nsectors", ctypes.c_int), ("shifts", ctypes.c_int),
+                ("sector_lo", ctypes.c_int), ("sector_orders", ctypes.c_int), ("count", ctypes.c_size_t)]
 
 
 class qmc_job(ctypes.Structure):
@@ -71,6 +79,13 @@ class qmc_job(ctypes.Structure):
 
 class qmc_c64(ctypes.Structure):
     _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+# callback types of qmc_set_ranks and qmc_set_evaluator
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t)
+EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(qmc_job), ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint32))
+_callbacks = {}   # keeps the ctypes callback objects alive per context
 
 
 def library_path() -> str:
@@ -140,6 +155,12 @@ def lib():
                                    P(qmc_integrate_info)], i32),
                 "qmc_integrate_ex": ([vp, P(qmc_sum_spec), dbl, dbl, dbl, i32, i32, P(qmc_c64), P(qmc_c64),
                                       P(qmc_integrate_info), P(u64), i32, P(dbl), P(u64), P(dbl)], i32),
+                "qmc_set_coefficients": ([vp, i32, P(qmc_c64), i32, i32, i32, i32], i32),
+                "qmc_integral_results": ([vp, i32, P(qmc_c64), P(qmc_c64)], i32),
+                "qmc_per_shift_sums": ([vp, i32, P(dbl), sz, P(qmc_shift_layout), P(u64)], i32),
+                "qmc_stats": ([vp, P(dbl), P(dbl)], i32),
+                "qmc_set_ranks": ([vp, i32, i32, ALLREDUCE_FN, vp], i32),
+                "qmc_set_evaluator": ([vp, EVAL_FN, vp], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -161,7 +182,8 @@ def exported_symbols():
             "qmc_median_candidates", "qmc_median_lattice", "qmc_gemm_bf16", "qmc_gemm_bf16_device",
             "qmc_gemm_bf16_device_limit", "qmc_mlp_create",
             "qmc_mlp_destroy", "qmc_mlp_num_params", "qmc_mlp_get_params", "qmc_mlp_set_params",
-            "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train", "qmc_integrate_ex"]
+            "qmc_mlp_forward", "qmc_mlp_grad", "qmc_mlp_train", "qmc_integrate_ex", "qmc_set_coefficients",
+            "qmc_integral_results", "qmc_per_shift_sums", "qmc_stats", "qmc_set_ranks", "qmc_set_evaluator"]
 
 
 def _dp(a):
@@ -182,12 +204,13 @@ def qmc_create(device: int = 0, **opts):
     h = ctypes.c_void_p()
     rc = lib().qmc_create(ctypes.byref(h), device, ctypes.byref(o))
     if rc != QMC_OK:
-        raise QmcError(rc, "qmc_create failed (no usable CUDA device?)")
+        raise QmcError(rc, "qmc_create failed (no usable CUDA device?)" if rc == -3 else "qmc_create failed")
     return h
 
 
 def qmc_destroy(ctx):
     lib().qmc_destroy(ctx)
+    _callbacks.pop(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx, None)
 
 
 def qmc_last_error(ctx) -> str:
@@ -574,6 +597,105 @@ def qmc_integrate(ctx, integral_ids=None, coef=None, coef_lo=0, epsrel=1e-4, eps
     if nslots:
         return value, error, d, rc, w_out[:nslots], n_out[:nslots]
     return value, error, d, rc
+
+
+def qmc_set_coefficients(ctx, coef, coef_lo=0):
+    """coef: complex [npoints][namp][nint][ncoef] over all loaded integrals
+    (None clears them)."""
+    if coef is None:
+        _check(ctx, lib().qmc_set_coefficients(ctx, 0, None, 0, 0, 0, 0))
+        return
+    c, pc = _c64(coef)
+    npts, namp, nint, nc = c.shape
+    _check(ctx, lib().qmc_set_coefficients(ctx, namp, pc, npts, nint, coef_lo, nc))
+
+
+def qmc_integral_results(ctx, integral_id, npoints, norders):
+    """(value, error) complex [npoints][norders] of one integral from the last qmc_integrate."""
+    v = np.zeros((npoints, norders), dtype=np.complex128)
+    e = np.zeros((npoints, norders), dtype=np.complex128)
+    _check(ctx, lib().qmc_integral_results(ctx, integral_id, v.ctypes.data_as(P(qmc_c64)),
+                                           e.ctypes.data_as(P(qmc_c64))))
+    return v, e
+
+
+def qmc_per_shift_sums(ctx, integral_id):
+    """(sums [npoints][nsectors][shifts][sector_orders][2], sector_lo, n [npoints][nsectors])."""
+    lay = qmc_shift_layout()
+    _check(ctx, lib().qmc_per_shift_sums(ctx, integral_id, None, 0, ctypes.byref(lay), None))
+    out = np.zeros(lay.count)
+    n = np.zeros(lay.npoints * lay.nsectors, dtype=np.uint64)
+    _check(ctx, lib().qmc_per_shift_sums(ctx, integral_id, _dp(out), out.size, None,
+                                         n.ctypes.data_as(P(ctypes.c_uint64))))
+    return (out.reshape(lay.npoints, lay.nsectors, lay.shifts, lay.sector_orders, 2), lay.sector_lo,
+            n.reshape(lay.npoints, lay.nsectors))
+
+
+def qmc_stats(ctx):
+    e, sec = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().qmc_stats(ctx, ctypes.byref(e), ctypes.byref(sec)))
+    return e.value, sec.value
+
+
+def _key(ctx):
+    return ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx
+
+
+def qmc_set_ranks(ctx, rank, world, allreduce):
+    """allreduce(buf: numpy float64 array view) sums buf over the ranks in place."""
+    if allreduce is None or world == 1:
+        _check(ctx, lib().qmc_set_ranks(ctx, 0, 1, ALLREDUCE_FN(), None))
+        _callbacks.get(_key(ctx), {}).pop("allreduce", None)
+        return
+
+    def cb(user, buf, n):
+        try:
+            arr = np.ctypeslib.as_array(buf, shape=(n,))
+            allreduce(arr)
+            return 0
+        except Exception:   # noqa: BLE001 -- reported to the library as a failed exchange
+            return -1
+
+    f = ALLREDUCE_FN(cb)
+    _callbacks.setdefault(_key(ctx), {})["allreduce"] = f
+    _check(ctx, lib().qmc_set_ranks(ctx, rank, world, f, None))
+
+
+def qmc_set_evaluator(ctx, evaluate):
+    """evaluate(jobs: list of dicts, lo, norders) -> (out [njobs][shifts][norders][2], fails [njobs] or None)
+    replaces the GPU evaluator of qmc_integrate (None restores it)."""
+    if evaluate is None:
+        _check(ctx, lib().qmc_set_evaluator(ctx, EVAL_FN(), None))
+        _callbacks.get(_key(ctx), {}).pop("eval", None)
+        return
+
+    def cb(user, jobs, njobs, lo, norders, out, fails):
+        try:
+            specs = []
+            for i in range(njobs):
+                J = jobs[i]
+                specs.append(dict(integral_id=J.integral_id, sector=J.sector, point=J.point, shifts=J.shifts,
+                                  n=J.n, seed=J.seed, stream=J.stream, flags=J.flags,
+                                  z=[J.z[j] for j in range(6)], **{"lambda": [J.lambda_[j] for j in range(6)]}))
+            vals, fl = evaluate(specs, lo, norders)
+            flat = np.concatenate([np.asarray(v, dtype=np.float64).ravel() for v in vals]) if vals else np.zeros(0)
+            dst = np.ctypeslib.as_array(out, shape=(flat.size,)) if flat.size else None
+            if dst is not None:
+                dst[:] = flat
+            if fl is not None and any(fl):
+                fdst = np.ctypeslib.as_array(fails, shape=(njobs,))
+                fdst[:] = np.asarray(fl, dtype=np.uint32)
+                return -6
+            return 0
+        except Exception:   # noqa: BLE001 -- reported to the library as a failed evaluation
+            import traceback
+
+            traceback.print_exc()
+            return -1
+
+    f = EVAL_FN(cb)
+    _callbacks.setdefault(_key(ctx), {})["eval"] = f
+    _check(ctx, lib().qmc_set_evaluator(ctx, f, None))
 
 
 def qmc_fp64_peak(ctx) -> float:

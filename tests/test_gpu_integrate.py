@@ -172,3 +172,103 @@ def test_amplitude_with_coefficient_strings():
             _within(val[0, 0, o], err[0, 0, o], exact[o])
     finally:
         qmc.qmc_destroy(ctx)
+
+
+def test_median_rules_inside_integrate_match_the_closed_form():
+    # lattice_candidates = 11: per (point, sector) and lattice size the median
+    # of 11 unshifted candidate rules (Eq. (median)), lattices of any prime size
+    ctx = _ctx(lattice_candidates=11, min_points=30000)
+    try:
+        I = w.box_massless()
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0]]))
+        val, err, info, rc, _, nq = qmc.qmc_integrate(ctx, [iid], epsrel=1e-8, lowest_order=-2, norders=3,
+                                                      nslots=12)
+        assert rc == 0
+        ex = closed_form("box1L_massless", "s=-3,t=-2")
+        for o, order in enumerate((-2, -1, 0)):
+            _within(val[0, 0, o], err[0, 0, o], ex[order], nsig=5.0)
+            assert np.hypot(err[0, 0, o].real, err[0, 0, o].imag) <= 1e-8 * abs(val[0, 0, o]) * 1.0000001
+        assert info["median_evaluations"] >= 11 * 12 * 30011
+        assert all(int(n) >= 30011 for n in nq)
+    finally:
+        qmc.qmc_destroy(ctx)
+
+
+def test_weighted_sums_of_set_coefficients_and_per_integral_results():
+    ctx = _ctx(keep_shift_sums=1, shifts=16)
+    try:
+        box = w.box_massless()
+        geo = w.box_massless(method="geometric")
+        ib = qmc.qmc_load_sectors_mem(ctx, box.to_text())
+        ig = qmc.qmc_load_sectors_mem(ctx, geo.to_text())
+        kin = np.array([[-3.0, -2.0], [-5.0, -1.0]])
+        qmc.qmc_set_kinematics(ctx, kin)
+        C = np.zeros((2, 1, 2, 1), dtype=complex)
+        C[:, 0, 0, 0], C[:, 0, 1, 0] = 1.0, -1.0          # box minus the same box decomposed differently
+        qmc.qmc_set_coefficients(ctx, C)
+        val, err, info, rc = qmc.qmc_integrate(ctx, None, epsrel=0.0, epsabs=1e-7, lowest_order=-2, norders=3,
+                                               npoints=2)
+        assert rc == 0
+        for p, pt in enumerate(("s=-3,t=-2", "s=-5,t=-1")):
+            ex = closed_form("box1L_massless", pt)
+            for o in range(3):
+                _within(val[p, 0, o], err[p, 0, o], 0.0, nsig=5.0)     # the difference vanishes
+            for iid in (ib, ig):
+                v, e = qmc.qmc_integral_results(ctx, iid, 2, 3)
+                for o, order in enumerate((-2, -1, 0)):
+                    _within(v[p, o], e[p, o], ex[order], nsig=5.0)
+        sums, slo, n = qmc.qmc_per_shift_sums(ctx, ib)
+        assert sums.shape == (2, 12, 16, 3, 2) and slo == -2
+        ev, secs = qmc.qmc_stats(ctx)
+        assert ev >= info["evaluations"] and secs >= info["seconds"]
+    finally:
+        qmc.qmc_destroy(ctx)
+
+
+def _gpu_rank_worker(rank, port, world, result_dir):
+    import os
+
+    import torch.distributed as dist
+
+    from paper_2305_19768_gb300 import dist as qdist
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    ctx = _ctx(keep_shift_sums=1, shifts=8, max_points=200003)
+    try:
+        I = w.box_massless()
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0], [-5.0, -1.0], [-2.0, -7.0]]))
+        if world > 1:
+            qdist.set_ranks(ctx)
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-10, lowest_order=-2, norders=3, npoints=3,
+                                               check=False)
+        sums, _, n = qmc.qmc_per_shift_sums(ctx, iid)
+        if rank == 0:
+            np.savez(os.path.join(result_dir, f"g{world}.npz"), val=val, err=err, sums=sums, n=n, rc=rc,
+                     evals=info["evaluations"], iters=info["iterations"])
+    finally:
+        qmc.qmc_destroy(ctx)
+        dist.destroy_process_group()
+
+
+def test_two_ranks_partition_the_integration_and_equal_one_rank(tmp_path):
+    """Two processes (gloo exchange on the host), each evaluating its share of
+    the (point, sector) slots on the GPU: the result equals one process bit
+    for bit. The ranks' kernels never wait on each other; the exchange runs on
+    the host between passes."""
+    import socket
+
+    import torch.multiprocessing as mp
+
+    res = {}
+    for world in (1, 2):
+        with socket.socket() as s:
+            s.bind(("127.0.0.1", 0))
+            port = s.getsockname()[1]
+        mp.start_processes(_gpu_rank_worker, args=(port, world, str(tmp_path)), nprocs=world, start_method="spawn")
+        res[world] = np.load(tmp_path / f"g{world}.npz")
+    a, b = res[1], res[2]
+    assert int(a["iters"]) >= 2
+    for k in ("val", "err", "sums", "n", "rc", "evals", "iters"):
+        assert np.array_equal(a[k], b[k]), k
