@@ -1,7 +1,8 @@
-"""Benchmark: randomized rank-1 lattice QMC over the sector-decomposed one-loop
-massless box (s = -3, t = -2, D = 4 - 2 eps, orders eps^-2 .. eps^0; twelve
-sectors in three Feynman parameters), lattice n = 1000003 with a CBC vector,
-32 random shifts per sector: 3.84e8 integrand evaluations per step.
+"""Benchmark: randomized rank-1 lattice QMC over the sector-decomposed
+two-loop planar massless double box (s = -3, t = -1, D = 4 - 2 eps, orders
+eps^-4 .. eps^0; 282 sectors from iterated decomposition in six Feynman
+parameters, up to four singular variables), lattice n = 1000003 with a CBC
+vector, 32 random shifts per sector: 9.02e9 integrand evaluations per step.
 
 A step is one full evaluation pass: every sector on its lattice with every
 shift (lattice point, shift, korobov3, eps-expanded integrand with
@@ -9,14 +10,19 @@ subtraction, per-shift reduction), computed by the CUDA kernels behind the
 C-ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload box1L_massless|triangle_massive|box1L_massive_batch|
-                                box1L_massless_physical|box2L_planar_massless]
-                    [--precision fp64|mixed]
+                    [--workload box2L_planar_massless|box1L_massless|triangle_massive|
+                                box1L_massive_batch|box1L_massless_physical]
+                    [--precision fp64|mixed] [--decomposition iterative|geometric]
+                    [--gemm M,N,K]
 
-The default workload and precision are the ones above; the others measure
-the same metric on the finite massive triangle, the 1024-point deformed
-massive-box batch and the two-loop double box (FP64 or FP32 monomial
-products), and report no traffic, no extras and no scan.
+The default line is the double box in FP64; its `extra` holds the one-loop
+massless box (s = -3, t = -2, n = 1000003, m = 32) with its time to 1e-4
+through qmc_integrate, the mixed-precision (FP32 monomial products) pass of
+the double box with its error per eps order against the FP64 oracle, and
+the amplitude scan of the learned, batched, mixed-precision form against the
+plain FP64 method. The other workloads measure the same metric on the
+massless box, the finite massive triangle and the 1024-point deformed
+massive-box batches, without extras.
 
 Prints one JSON line (rank 0). Under torchrun each rank evaluates its own
 independent batch (its own shift streams): weak scaling, no data-path
@@ -41,6 +47,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "integrand evals/s"
+DEFAULT_WORKLOAD = "box2L_planar_massless"
 UNIT = "evals/s"
 JOB_RECORD_BYTES = 136   # device job record (QmcJobDev) copied per job
 
@@ -49,7 +56,7 @@ def _workloads():
     from paper_2305_19768_gb300.inputs import workloads as w
 
     return {
-        # the default: one-loop massless box, Euclidean point
+        # one-loop massless box, Euclidean point
         "box1L_massless": dict(
             make=lambda method="iterative": w.box_massless(method=method), kin=[[-3.0, -2.0]], lo=-2, nord=3, n=1000003, m=32, deform=False,
             desc="box1L_massless s=-3 t=-2, 12 sectors d=3, eps^-2..eps^0, n={n} CBC, m={m} shifts"),
@@ -71,7 +78,7 @@ def _workloads():
             nord=3, n=10007, m=32, deform=True,
             desc="box1L_massless deformed, 1024 (s,t) s~U[5,20] t~U[-8,-1] seed 3, 12 sectors d=3, "
                  "eps^-2..eps^0, n={n} CBC, m={m} shifts"),
-        # two-loop planar massless double box, Euclidean point
+        # the default: two-loop planar massless double box, Euclidean point
         "box2L_planar_massless": dict(
             make=lambda method="iterative": w.double_box_massless(method=method), kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
             desc="box2L_planar_massless s=-3 t=-1, 282 sectors d=6, eps^-4..eps^0, n={n} CBC, m={m} shifts"),
@@ -199,6 +206,124 @@ def run_reference(args):
     return 0
 
 
+def timed_plan(qmc, ctx, plan, out_ptr, sptr, flush, steps, warmup=3):
+    """CUDA-event times of the evaluator kernels (ms) over `steps` runs of a
+    plan after `warmup` runs, L2 flushed before each timed run."""
+    import torch
+
+    for _ in range(warmup):
+        qmc.qmc_plan_run(ctx, plan, out_ptr, sptr)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        qmc.qmc_plan_run(ctx, plan, out_ptr, sptr)
+        ms.append(qmc.qmc_plan_last_time(ctx, plan)[1])
+    return ms
+
+
+def box_extra(device, opts, sptr, flush, peak_gflops, seed):
+    """The one-loop massless box (s = -3, t = -2, 12 sectors, n = 1000003,
+    m = 32): throughput with its FP64 roofline, and the time to 1e-4 relative
+    error per eps coefficient through qmc_integrate (FP64 and mixed)."""
+    import torch
+
+    from paper_2305_19768_gb300 import flops as flopmod
+    from paper_2305_19768_gb300 import qmc
+
+    W = _workloads()["box1L_massless"]
+    I = W["make"]()
+    ctx = qmc.qmc_create(device, **opts)
+    out = {}
+    try:
+        qmc.load_lattice_table(ctx)
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, np.array(W["kin"]))
+        jobs, nj = qmc.make_jobs(qmc.jobs_for_integral(iid, len(I.sectors), 1, W["n"], W["m"], seed=seed))
+        plan = qmc.qmc_plan_create(ctx, jobs, nj, W["lo"], W["nord"])
+        o = torch.empty(qmc.qmc_plan_output_size(plan), dtype=torch.float64, device="cuda")
+        ms = timed_plan(qmc, ctx, plan, o.data_ptr(), sptr, flush, 10)
+        qmc.qmc_plan_destroy(plan)
+        evals = nj * W["m"] * W["n"]
+        fl = flopmod.workload_work(I, W["lo"], W["nord"]).fp64
+        rate = evals / (float(np.mean(ms)) * 1e-3)
+        out["box1L_massless"] = {
+            "workload": W["desc"].format(n=W["n"], m=W["m"]), "evals_per_s": rate, "eval_ms": float(np.mean(ms)),
+            "roofline": {"achieved": fl * rate / 1e9, "peak": peak_gflops, "frac": fl * rate / 1e9 / peak_gflops,
+                         "flops_per_eval": fl, "unit": "GFLOP/s (fp64)"}}
+        for prec, key in ((qmc.QMC_PRECISION_FP64, "fp64"), (qmc.QMC_PRECISION_MIXED, "mixed")):
+            c2 = qmc.qmc_create(device, precision=prec, **opts)
+            try:
+                qmc.load_lattice_table(c2)
+                i2 = qmc.qmc_load_sectors_mem(c2, I.to_text())
+                qmc.qmc_set_kinematics(c2, np.array(W["kin"]))
+                t0 = time.perf_counter()
+                _, _, info, rc = qmc.qmc_integrate(c2, [i2], epsrel=1e-4, lowest_order=W["lo"], norders=W["nord"],
+                                                   check=False)
+                out["box1L_massless"][f"time_to_1e-4_{key}_s"] = time.perf_counter() - t0
+                out["box1L_massless"][f"time_to_1e-4_{key}_rc"] = rc
+            finally:
+                qmc.qmc_destroy(c2)
+    finally:
+        qmc.qmc_destroy(ctx)
+    return out
+
+
+def mixed_extra(device, opts, I, W, kin, jobs, nj, evals_per_step, out_dev, sptr, seed, skip_oracle):
+    """The double box's mixed-precision pass (FP32 monomial products): its
+    throughput, its largest difference from the FP64 GPU pass, and its error
+    per eps order against the FP64 oracle on sampled (sector, shift) outputs,
+    one sector per number of singular variables."""
+    from paper_2305_19768_gb300 import qmc
+
+    ctx = qmc.qmc_create(device, precision=qmc.QMC_PRECISION_MIXED, **opts)
+    out = {}
+    try:
+        qmc.load_lattice_table(ctx)
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        qmc.qmc_set_kinematics(ctx, kin)
+        jm, njm = qmc.make_jobs(qmc.jobs_for_integral(iid, len(I.sectors), 1, W["n"], W["m"], seed=seed))
+        plan = qmc.qmc_plan_create(ctx, jm, njm, W["lo"], W["nord"])
+        ms = []
+        for i in range(3):
+            qmc.qmc_plan_run(ctx, plan, None, sptr)
+            _, me, _ = qmc.qmc_plan_last_time(ctx, plan)
+            if i:
+                ms.append(me)
+        res, _, _ = qmc.qmc_plan_results(ctx, plan, check=False)
+        qmc.qmc_plan_destroy(plan)
+    finally:
+        qmc.qmc_destroy(ctx)
+    ref = out_dev.cpu().numpy()
+    d = {"evals_per_s": evals_per_step / (float(np.mean(ms)) * 1e-3),
+         "max_abs_diff_vs_fp64_gpu": float(np.max(np.abs(res - ref)))}
+    if not skip_oracle:
+        import oracle
+        from paper_2305_19768_gb300.inputs.lattice import lattice_for
+
+        m, nord = W["m"], W["nord"]
+        res = res.reshape(nj, m, nord, 2)
+        by_ns = {}
+        for i, sec in enumerate(I.sectors):
+            by_ns.setdefault(len(sec.singular), i)
+        err_q = np.zeros(nord)
+        err_a = np.zeros(nord)
+        for k, (ns, sector) in enumerate(sorted(by_ns.items())):
+            shift = (11 * k + 5) % m
+            sec = I.sectors[sector]
+            _, z = lattice_for(W["n"], sec.d)
+            dl = oracle.shifts(seed, sector, m, sec.d)[[shift]]
+            o, a, _ = oracle.shift_sums(oracle.SectorView(I, sector, W["kin"][0]), W["n"], z, dl, W["lo"], nord)
+            e = np.abs(res[sector, shift] - o[0]).max(axis=-1)
+            err_q = np.maximum(err_q, e / np.maximum(np.hypot(o[0, :, 0], o[0, :, 1]), 1e-300))
+            err_a = np.maximum(err_a, e / np.maximum(a[0], 1e-300))
+        d["error_vs_fp64_oracle"] = {
+            "orders": list(range(W["lo"], W["lo"] + nord)), "max_err_over_abs_value": err_q.tolist(),
+            "max_err_over_abs_mass": err_a.tolist(),
+            "sample": f"one sector per number of singular variables ({sorted(by_ns.values())}), one shift each"}
+    return {"box2L_planar_massless_mixed": d}
+
+
 def run_gemm(args):
     """The learned model's BF16 GEMM C = A B^T on device buffers: milliseconds
     per call (CUDA events on the launching stream after the warm-up calls) and
@@ -241,7 +366,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="box1L_massless",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box1L_massless_physical",
                              "box2L_planar_massless"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
@@ -280,7 +405,8 @@ def main():
     I = W["make"](method=args.decomposition) if args.decomposition != "iterative" else W["make"]()
     args.n, args.shifts = args.n or W["n"], args.shifts or W["m"]
     LO, NORD = W["lo"], W["nord"]
-    default = args.workload == "box1L_massless" and args.precision == "fp64" and args.decomposition == "iterative"
+    default = (args.workload == DEFAULT_WORKLOAD and args.precision == "fp64" and args.decomposition == "iterative"
+               and args.n == W["n"] and args.shifts == W["m"])
     opts = {}
     if args.block:
         opts["block"] = args.block
@@ -357,12 +483,13 @@ def main():
     d2h = out_n * 8
     host_out = np.zeros(out_n)
     t_e2e = 0.0
-    for i in range(max(1, args.steps // 2)):
+    n_e2e = max(2, args.steps // 10)
+    for i in range(n_e2e):
         t0 = time.perf_counter()
         qmc.qmc_set_kinematics(ctx, kin)
         host_out = qmc.qmc_eval_jobs(ctx, jobs, nj, LO, NORD, out_n)
         t_e2e += time.perf_counter() - t0
-    e2e_val = evals_per_step * max(1, args.steps // 2) * world / t_e2e
+    e2e_val = evals_per_step * n_e2e * world / t_e2e
 
     # roofline of the evaluator kernels: FP64 flops of the formulation (no
     # credit for the steps on the integer pipe) / their event time, against
@@ -387,37 +514,11 @@ def main():
         roof["fp32"] = {"flops_per_eval": work.fp32, "achieved": a32, "peak": peak32,
                         "frac": a32 / peak32, "peak_source": "FFMA probe in this run (of measured)"}
 
-    # secondary: time to 1e-4 relative error per eps-coefficient through
-    # qmc_integrate (pilot lattice 1e4, adaptive), FP64 and mixed precision,
-    # and the mixed-precision throughput of the same evaluation pass
     extra = {}
     if not args.no_extra and default:
-        t0 = time.perf_counter()
-        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-4, lowest_order=LO, norders=NORD,
-                                               check=False)
-        extra["time_to_1e-4_s"] = time.perf_counter() - t0
-        extra["time_to_1e-4_rc"] = rc
-        ctxm = qmc.qmc_create(local, precision=qmc.QMC_PRECISION_MIXED, **opts)
-        qmc.load_lattice_table(ctxm)
-        iidm = qmc.qmc_load_sectors_mem(ctxm, I.to_text())
-        qmc.qmc_set_kinematics(ctxm, kin)
-        t0 = time.perf_counter()
-        qmc.qmc_integrate(ctxm, [iidm], epsrel=1e-4, lowest_order=LO, norders=NORD, check=False)
-        extra["time_to_1e-4_mixed_s"] = time.perf_counter() - t0
-        jobs_m, nj_m = qmc.make_jobs(qmc.jobs_for_integral(iidm, nsec, 1, args.n, args.shifts, seed=seed))
-        plan_m = qmc.qmc_plan_create(ctxm, jobs_m, nj_m, LO, NORD)
-        ms_m = []
-        for i in range(4):
-            qmc.qmc_plan_run(ctxm, plan_m, None, sptr)
-            _, me, _ = qmc.qmc_plan_last_time(ctxm, plan_m)
-            if i:
-                ms_m.append(me)
-        out_m, _, _ = qmc.qmc_plan_results(ctxm, plan_m, check=False)
-        ref = out_dev.cpu().numpy()
-        extra["mixed_evals_per_s"] = evals_per_step / (float(np.mean(ms_m)) * 1e-3)
-        extra["mixed_max_abs_diff_vs_fp64"] = float(np.max(np.abs(out_m - ref)))
-        qmc.qmc_plan_destroy(plan_m)
-        qmc.qmc_destroy(ctxm)
+        extra.update(box_extra(local, opts, sptr, flush, peak_gflops, seed))
+        extra.update(mixed_extra(local, opts, I, W, kin, jobs, nj, evals_per_step, out_dev, sptr, seed,
+                                 args.no_cpu_baseline or rank != 0))
 
     # the amplitude scan (time to 1e-4 relative amplitude error on the 10^4-point
     # (s, t) grid of a ten-integral amplitude): the learned, batched,

@@ -223,10 +223,12 @@ int qmc_plan_run(qmc_plan *plan, double *out_dev, void *stream);
  * `sign_failures` (may be NULL) receives the count of such points. */
 int qmc_plan_results(qmc_plan *plan, double *out, uint64_t *sign_failures);
 
-/* Device time of the plan's last run measured with CUDA events on the stream
- * it ran on: ms_total for the whole run, ms_eval for the evaluator kernels
- * alone (without the finishing reduction), and the number of kernel launches
- * it issued. Waits for the run to finish. Any output may be NULL. */
+/* Device time of the plan's last run measured with CUDA events: ms_total for
+ * the whole run, ms_eval for the evaluator kernels alone (the span from the
+ * first one's start to the last one's end: a plan with several evaluator
+ * classes runs them concurrently on side streams forked from and joined back
+ * into the run's stream), and the number of kernel launches it issued. Waits
+ * for the run to finish. Any output may be NULL. */
 int qmc_plan_last_time(qmc_plan *plan, float *ms_total, float *ms_eval, int *launches);
 
 /* Replay the plan's runs as one CUDA graph (enable != 0): the first run

@@ -106,6 +106,11 @@ struct qmc_plan {
     std::vector<ClassLaunch> launches;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> kev;   // [2 * class launch]: around each evaluator kernel
+    // class launches after the first run concurrently on side streams, forked
+    // from and joined back into the run's stream
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
     cudaStream_t last_stream = nullptr;
     double *last_out = nullptr;
     int last_launches = 0;

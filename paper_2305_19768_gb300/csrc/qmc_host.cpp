@@ -393,6 +393,12 @@ void free_plan_buffers(qmc_plan *p) {
     if (p->ev1) cudaEventDestroy(p->ev1);
     for (cudaEvent_t e : p->kev) cudaEventDestroy(e);
     p->kev.clear();
+    for (cudaStream_t st : p->side) cudaStreamDestroy(st);
+    p->side.clear();
+    for (cudaEvent_t e : p->join) cudaEventDestroy(e);
+    p->join.clear();
+    if (p->fork) cudaEventDestroy(p->fork);
+    p->fork = nullptr;
     p->d_out = nullptr;
     p->d_status = nullptr;
 }
@@ -648,6 +654,27 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
     for (int cls = 0; cls < QMC_NCLASS; ++cls) {
         std::vector<QmcJobDev> &v = per[cls];
         if (v.empty()) continue;
+        // the tile queue hands out tiles in job order: costly jobs first (more
+        // singular variables, larger lattices) shortens the tail of the launch,
+        // and jobs of one sector shape run side by side on the SMs
+        {
+            std::vector<int> ord(v.size());
+            for (size_t u = 0; u < ord.size(); ++u) ord[u] = (int)u;
+            auto key = [&](int u) {
+                const qmc_job &J = jobs[per_orig[cls][u]];
+                const int ns = ctx->integrals[J.integral_id].sectors[J.sector].ns;
+                return std::make_pair(ns, (double)v[u].n * v[u].shifts);
+            };
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return key(a) > key(b); });
+            std::vector<QmcJobDev> v2;
+            std::vector<int> o2;
+            for (int u : ord) {
+                v2.push_back(v[u]);
+                o2.push_back(per_orig[cls][u]);
+            }
+            v.swap(v2);
+            per_orig[cls].swap(o2);
+        }
         ClassLaunch c;
         c.cls = cls;
         c.orig = per_orig[cls];
@@ -698,10 +725,25 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         L.job_fail = c.d_jobfail;
         p->launches.push_back(c);
     }
+    // the largest class first: it sets the length of the run, the others fill its tail
+    std::stable_sort(p->launches.begin(), p->launches.end(), [](const ClassLaunch &a, const ClassLaunch &b) {
+        return a.L.ntiles * a.L.tile_k > b.L.ntiles * b.L.tile_k;
+    });
     for (size_t i = 0; i < 2 * p->launches.size(); ++i) {
         cudaEvent_t e;
         PLAN_TRY(cudaEventCreate(&e));
         p->kev.push_back(e);
+    }
+    if (p->launches.size() > 1) {
+        PLAN_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+        for (size_t i = 1; i < p->launches.size(); ++i) {
+            cudaStream_t st;
+            cudaEvent_t e;
+            PLAN_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            p->side.push_back(st);
+            PLAN_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            p->join.push_back(e);
+        }
     }
 #undef PLAN_TRY
     ctx->plans.push_back(p);
@@ -722,22 +764,29 @@ int plan_enqueue(qmc_plan *plan, double *out, cudaStream_t st, bool capturing) {
     const unsigned evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CUDA_TRY(ctx, cudaMemsetAsync(plan->d_status, 0, 2 * sizeof(unsigned long long), st));
     CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->ev0, st, evflags));
+    if (plan->fork) CUDA_TRY(ctx, cudaEventRecord(plan->fork, st));
     int launches = 0;
     for (size_t i = 0; i < plan->launches.size(); ++i) {
         ClassLaunch &c = plan->launches[i];
+        cudaStream_t cs = i == 0 ? st : plan->side[i - 1];
+        if (i > 0) CUDA_TRY(ctx, cudaStreamWaitEvent(cs, plan->fork, 0));
         c.L.out = out;
         c.L.kin = ctx->d_kin;
-        CUDA_TRY(ctx, cudaMemsetAsync(c.d_jobfail, 0, c.orig.size() * sizeof(unsigned int), st));
-        CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->kev[2 * i], st, evflags));
+        CUDA_TRY(ctx, cudaMemsetAsync(c.d_jobfail, 0, c.orig.size() * sizeof(unsigned int), cs));
+        CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->kev[2 * i], cs, evflags));
         if (c.L.ntiles > 0) {
-            if (qmc_k_launch_eval(c.cls, &c.L, c.block, c.ppt, c.grid, st))
+            if (qmc_k_launch_eval(c.cls, &c.L, c.block, c.ppt, c.grid, cs))
                 return fail(ctx, QMC_E_CUDA, "evaluator launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             ++launches;
         }
-        CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->kev[2 * i + 1], st, evflags));
-        if (qmc_k_launch_finish(&c.L, st))
+        CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->kev[2 * i + 1], cs, evflags));
+        if (qmc_k_launch_finish(&c.L, cs))
             return fail(ctx, QMC_E_CUDA, "finish launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ++launches;
+        if (i > 0) {
+            CUDA_TRY(ctx, cudaEventRecord(plan->join[i - 1], cs));
+            CUDA_TRY(ctx, cudaStreamWaitEvent(st, plan->join[i - 1], 0));
+        }
     }
     CUDA_TRY(ctx, cudaEventRecordWithFlags(plan->ev1, st, evflags));
     plan->last_launches = launches;
@@ -826,13 +875,18 @@ int qmc_plan_last_time(qmc_plan *plan, float *ms_total, float *ms_eval, int *lau
     if (!plan) return QMC_E_INVAL;
     qmc_ctx *ctx = plan->ctx;
     CUDA_TRY(ctx, cudaEventSynchronize(plan->ev1));
-    float t = 0.f, te = 0.f;
+    // the evaluator kernels run concurrently: their time is the span from the
+    // earliest start to the latest end
+    float t = 0.f, t0 = 1e30f, t1 = 0.f;
     CUDA_TRY(ctx, cudaEventElapsedTime(&t, plan->ev0, plan->ev1));
     for (size_t i = 0; i < plan->launches.size(); ++i) {
-        float x = 0.f;
-        CUDA_TRY(ctx, cudaEventElapsedTime(&x, plan->kev[2 * i], plan->kev[2 * i + 1]));
-        te += x;
+        float a = 0.f, b = 0.f;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&a, plan->ev0, plan->kev[2 * i]));
+        CUDA_TRY(ctx, cudaEventElapsedTime(&b, plan->ev0, plan->kev[2 * i + 1]));
+        t0 = std::min(t0, a);
+        t1 = std::max(t1, b);
     }
+    const float te = plan->launches.empty() ? 0.f : t1 - t0;
     if (ms_total) *ms_total = t;
     if (ms_eval) *ms_eval = te;
     if (launches) *launches = plan->last_launches;

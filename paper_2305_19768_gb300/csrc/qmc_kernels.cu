@@ -21,6 +21,7 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "qmc_ilog.h"
@@ -29,6 +30,12 @@
 
 #ifndef QMC_PART
 #define QMC_PART 0
+#endif
+// 1: the d <= 6 classes also take korobov3 on the integer pipe (as the d <= 3
+// classes do; measured 3 % faster on the double box than FP64 arithmetic
+// there); 0: FP64 arithmetic for them
+#ifndef QMC_KOROBOV_INT6
+#define QMC_KOROBOV_INT6 1
 #endif
 
 namespace {
@@ -789,10 +796,9 @@ template <int NS> struct SlotArr {
 
 template <int NS, int HI, class T>
 __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (&LV)[1 << NS],
-                                               const double (&it)[SlotArr<NS>::N],
+                                               const double (&tb)[SlotArr<NS>::N],
                                                const double (&lt)[SlotArr<NS>::N],
-                                               const double (&bq)[SlotArr<NS>::N],
-                                               const double (&invb)[SlotArr<NS>::N], double A_empty,
+                                               const double (&bq)[SlotArr<NS>::N], double A_empty,
                                                double A_full, T (&resN)[NS + HI + 1]) {
     constexpr int NG = 1 << NS;
     constexpr int LM = HI + NS + 1;   // series length of the full corner
@@ -817,25 +823,31 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
             for (int i = 0; i < LM; ++i)
                 if (i < nP) g[P][i] = g[P][i] - g[P | (1 << q)][i];
         }
+    // A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q by the subset
+    // recursion A_P = A_{P - q} t_q / b_q (q the lowest slot of P), and
+    // E_P = sum_{q not in P} b_q ln t_q by E_P = E_{P + q} + b_q ln t_q (q the
+    // lowest slot outside P), from E_full = 0
+    double AP[NG], EP[NG], bl[SlotArr<NS>::N];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) bl[q] = bq[q] * lt[q];
+    AP[0] = A_empty;
+#pragma unroll
+    for (int P = 1; P < NG; ++P) AP[P] = P == NG - 1 ? A_full : AP[P & (P - 1)] * tb[__ffs(P) - 1];
+    EP[NG - 1] = 0.0;
+#pragma unroll
+    for (int P = NG - 2; P >= 0; --P) {
+        const int q = __ffs(~P) - 1;           // lowest slot outside P
+        const int nP = HI + __popc(P) + 1;
+        EP[P] = 0.0;
+        if (nP > 1) EP[P] = (P | (1 << q)) == NG - 1 ? bl[q] : EP[P | (1 << q)] + bl[q];
+    }
 #pragma unroll
     for (int i = 0; i < LM; ++i) resN[i] = zero<T>();
 #pragma unroll
     for (int P = 0; P < NG; ++P) {
         const int np = __popc(P);
         const int nP = HI + np + 1;
-        // A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q
-        double A = 1.0;
-        if (P == 0) {
-            A = A_empty;
-        } else if (P == NG - 1) {
-            A = A_full;
-        } else {
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const double f = (P & (1 << q)) ? invb[q] : it[q];
-                A = q == 0 ? f : A * f;
-            }
-        }
+        const double A = AP[P];
         T PE[LM];
         if (P == NG - 1) {
             // every singular variable in the pole set: no exp(eps E_P) factor
@@ -843,15 +855,8 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
             for (int k = 0; k < LM; ++k)
                 if (k < nP) PE[k] = g[P][k];
         } else {
-            // E_P = sum_{q not in P} b_q ln t_q and its exponential series
-            double E = 0.0;
-            bool first = true;
-#pragma unroll
-            for (int q = 0; q < NS; ++q)
-                if (!(P & (1 << q)) && nP > 1) {
-                    E = first ? bq[q] * lt[q] : fma(bq[q], lt[q], E);
-                    first = false;
-                }
+            // the exponential series of E_P
+            const double E = EP[P];
             double e[LM];
             e[0] = 1.0;
 #pragma unroll
@@ -952,8 +957,12 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
             if (need_lt) lt[q] = qlog(tq, tab);
         }
     }
-    // 1/t_q in pairs: 1/a = b / (a b) with one reciprocal per pair, whose value
-    // is also the pair's share of A of the empty pole set prod 1/t_q
+    // t_q / b_q (the factors of the pole-set prefactors A_P), then 1/t_q in
+    // pairs: 1/a = b / (a b) with one reciprocal per pair, whose value is also
+    // the pair's share of A of the empty pole set prod 1/t_q
+    double tb[NSA];
+#pragma unroll
+    for (int q = 0; q < NSA; ++q) tb[q] = q < NS ? it[q] * S.invb[q] : 0.0;
     double A_empty = 1.0;
 #pragma unroll
     for (int q = 0; q + 1 < NS; q += 2) {
@@ -1030,10 +1039,7 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
             LV[V] = hasLc ? Lc + l : l;
         }
     }
-    double ib[NSA];
-#pragma unroll
-    for (int q = 0; q < NSA; ++q) ib[q] = q < NS ? S.invb[q] : 0.0;
-    assemble_fixed<NS, HI, double>(BV, LV, it, lt, bq, ib, A_empty, S.invb_full, resN);
+    assemble_fixed<NS, HI, double>(BV, LV, tb, lt, bq, A_empty, S.invb_full, resN);
 }
 
 // ---------------------------------------------------------------- degree-1 subtraction
@@ -1520,11 +1526,8 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
             if (j < d) {
                 const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
                 if (Lc.transform == 0) {          // korobov3
-                    // integer pipe for the d <= 3 classes (with 1 - t for the
-                    // deformed ones); the d <= 6 classes run at the register
-                    // limit, where the longer integer chain costs more than
-                    // its FP64 operations
-                    if constexpr (!CPLX && DMAX > 3) {
+                    // integer pipe (with 1 - t for the deformed classes)
+                    if constexpr (!CPLX && DMAX > 3 && !QMC_KOROBOV_INT6) {
                         const double u2 = u * u;
                         t[j] = u2 * u2 * fma(u, fma(u, fma(u, -20.0, 70.0), -84.0), 35.0);
                         Ws *= fma(-u, u, u);
@@ -1588,7 +1591,11 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
     }
 }
 
-template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false>
+// FIX: the real classes' kernel for sums up to eps^0 (highest order 0, every
+// sum the integrator forms), with only the compile-time paths; the general
+// kernel (FIX = false) serves every other order window. Two instantiations
+// keep each kernel's code, and its instruction-cache footprint, small.
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false, bool FIX = false>
 __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3), (CPLX && MIXED), HS>()) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
     using T = typename std::conditional<CPLX, dc, double>::type;
@@ -1657,24 +1664,21 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
         const uint64_t k0 = kt0 + (uint64_t)threadIdx.x * (uint64_t)ppt;
         if (k0 < kt1) {
             const uint64_t kend = min(kt1, k0 + (uint64_t)ppt);
-            bool done = false;
-            if constexpr (!CPLX && !HS) {
-                // real sectors up to eps^0 (every sum the integrator forms):
-                // the compile-time path for the tile's number of singular variables
-                if (hi == 0) {
-                    const int ns = S.sec.ns;
-                    done = true;
-                    if (ns == 0) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 0, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                    else if (ns == 1) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 1, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                    else if (ns == 2 || SMAX < 3) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 2 ? 2 : 1), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                    else if constexpr (SMAX >= 3) {
-                        if (ns == 3 || SMAX < 4) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 3, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                        else thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 4 ? 4 : 3), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                    }
+            if constexpr (!CPLX && !HS && FIX) {
+                // real sectors up to eps^0: the compile-time path for the tile's
+                // number of singular variables (the host launches this kernel
+                // only for hi = 0)
+                const int ns = S.sec.ns;
+                if (ns == 0) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 0, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                else if (ns == 1) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 1, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                else if (ns == 2 || SMAX < 3) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 2 ? 2 : 1), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                else if constexpr (SMAX >= 3) {
+                    if (ns == 3 || SMAX < 4) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 3, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                    else thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 4 ? 4 : 3), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
                 }
-            }
-            if (!done)
+            } else {
                 thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, -1, -1>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+            }
         }
         // sign-check failures of this tile: per job (if counted) and in total
         if (CPLX && __ballot_sync(0xffffffffu, signfail_tile != 0)) {
@@ -1832,31 +1836,49 @@ __global__ void qmc_fp32_probe_kernel(float *out, int iters) {
 // Blocks of 256 threads exist for the d <= 3 classes only: the d <= 6 classes
 // run near the register limit, where a second warp set per block buys nothing
 // (and their instantiations dominate the build).
-template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
-int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, bool FIX>
+int launch_shape(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
     if constexpr (DMAX <= 3) {
         if (block == 256) {
-            qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS><<<grid, 256, 0, st>>>(*L, ppt);
+            qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX><<<grid, 256, 0, st>>>(*L, ppt);
             return cudaGetLastError() == cudaSuccess ? 0 : -1;
         }
     }
-    qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS><<<grid, 128, 0, st>>>(*L, ppt);
+    qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX><<<grid, 128, 0, st>>>(*L, ppt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
-int occupancy_cls(int block) {
+int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
+    if constexpr (!CPLX && !HS) {
+        if (L->lo + L->norders - 1 == 0) return launch_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, true>(L, block, ppt, grid, st);
+    }
+    return launch_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, false>(L, block, ppt, grid, st);
+}
+
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, bool FIX>
+int occupancy_shape(int block) {
     int v = 0;
     cudaError_t e;
     if constexpr (DMAX <= 3)
         e = block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS>, 256, 0)
+                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX>, 256, 0)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS>, 128, 0);
+                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>, 128, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS>,
-                                                          128, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>, 128, 0);
     return e == cudaSuccess ? v : 0;
+}
+
+// Resident blocks per SM of the class's kernels (the larger of the fixed-order
+// and the general kernel: a persistent grid sized for it only over-subscribes
+// the other, whose surplus blocks find the tile queue empty)
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
+int occupancy_cls(int block) {
+    int v = occupancy_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, false>(block);
+    if constexpr (!CPLX && !HS) v = std::max(v, occupancy_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, true>(block));
+    return v;
 }
 
 }  // namespace

@@ -6,8 +6,8 @@ formulation of the method, operation by operation:
 
 * FP64 flops: add, subtract and multiply count 1, a fused multiply-add 2.
   Steps that the evaluator computes on the integer pipe count 0 FP64 flops:
-  the lattice coordinate (exact fixed-point walk), the korobov3 transform of
-  the d <= 3 classes, and every logarithm (fixed-point table reduction).
+  the lattice coordinate (exact fixed-point walk), the korobov3 transform
+  and every logarithm (fixed-point table reduction).
   Multiplications by the constant 1 that the compiler folds away (first
   factors of products started at 1, the 1/1 of series recursions) are not
   counted.
@@ -97,9 +97,43 @@ def _powers(d, emax):
     return d * ((emax >= 2) + (emax >= 3) + (emax >= 4))
 
 
+def _assemble_fixed(ns, hi) -> float:
+    """The real classes' assembly with the singular-variable count and the
+    highest order fixed at compile time: corner series, superset Moebius
+    transform, A_P and E_P by subset recursions, the exponential series of
+    E_P, the convolution, and every order from the leading pole eps^-ns up to
+    eps^hi into the accumulator."""
+    f = 0.0
+    full = (1 << ns) - 1
+    for V in range(full + 1):
+        nV = hi + _popc(V) + 1
+        for i in range(1, nV):
+            f += 1 + (0 if i == 1 else 1)        # g_i = g_{i-1} Lambda (/ i)
+    for q in range(ns):
+        for P in range(full + 1):
+            if not P & (1 << q):
+                f += max(hi + _popc(P) + 1, 0)   # Moebius subtractions
+    f += ns + max((1 << ns) - 2, 0)              # t_q / b_q, then A_P = A_{P-q} t_q / b_q
+    f += ns                                      # b_q ln t_q
+    for P in range(full):                        # E_P = E_{P+q} + b_q ln t_q
+        q = (~P & -~P).bit_length() - 1
+        if hi + _popc(P) + 1 > 1 and (P | (1 << q)) != full:
+            f += 1
+    for P in range(full + 1):
+        np_ = _popc(P)
+        nP = hi + np_ + 1
+        if P != full:
+            f += 2 * max(nP - 2, 0)              # e_l = e_{l-1} (E / l), l >= 2
+            f += sum(2 * k for k in range(nP))   # PE_k = g_k + sum_{i<k} g_i e_{k-i}
+        f += 2 * nP                              # res[k - |P|] += A_P PE_k
+    f += 2 * (ns + hi + 1)                       # acc += res W, every order -ns .. hi
+    return f
+
+
 def _assemble(ns, lo, hi, nord, cplx: bool) -> float:
-    """The pole-set assembly (corner series, superset Moebius transform,
-    A_P, E_P and its exponential series, the convolution and res += A PE)."""
+    """The general assembly (run-time orders; the deformed classes): corner
+    series, superset Moebius transform, A_P, E_P and its exponential series,
+    the convolution and res += A PE."""
     mul = 6 if cplx else 1          # value x value: complex product (2 FMA + 2 MUL) or one multiply
     fmul = 2 if cplx else 1         # value x real scalar
     f = 0.0
@@ -136,15 +170,10 @@ def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work
     """Work of one evaluation in the real (undeformed) evaluator classes."""
     d, sing, ns, emax = _sector_shape(sector)
     hi = lo + norders - 1
-    wide = d > 3 or ns > 2
     w = Work()
-    # transform: d <= 3 classes on the integer pipe (only the product of the
-    # per-coordinate weights u(1-u) is FP64); d <= 6 classes in FP64
-    if wide:
-        w.fp64 += 9 * d                  # t = u^2 u^2 (35 + u(-84 + u(70 - 20u)))
-        w.fp64 += 3 * d - 1              # Ws *= u - u^2
-    else:
-        w.fp64 += d - 1
+    # transform on the integer pipe: only the product of the per-coordinate
+    # weights u(1-u) is FP64
+    w.fp64 += d - 1
     w.fp64 += 2                          # W = Ws^3
     # power tables and grouped monomial sums (FP32 in the mixed classes)
     pw = _powers(d, emax)
@@ -164,15 +193,11 @@ def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work
     w.fp64 += max(na_reg - 1, 0)         # Cc = prod t^a
     if hi + ns - 1 >= 1:
         w.log += ns                      # ln t of the singular variables
-    # reciprocals of the singular t's
-    if ns == 2:
-        w.fp64 += 3
-        w.recip()
-    elif ns == 1:
-        w.recip()
-    elif ns > 2:
-        w.recip(ns)
-        w.fp64 += ns - 1
+    # A of the empty pole set, prod 1/t_q: one reciprocal per pair of singular
+    # variables (of the pair's product) and one for an odd one left
+    pairs, odd = ns // 2, ns % 2
+    w.fp64 += pairs + max(pairs + odd - 1, 0)
+    w.recip(pairs + odd)
     u0, f0, u1, f1 = (float(x) for x in (sector.u0, sector.f0, sector.u1, sector.f1))
     u0i, f0i = _is_small_int(u0), _is_small_int(f0)
     comb = _is_small_int(u1) and _is_small_int(f1)
@@ -211,8 +236,11 @@ def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work
                 w.log += 2
                 w.fp64 += 3
             w.fp64 += 1                  # Lambda_V = Lc + log
-    w.fp64 += _assemble(ns, lo, hi, norders, cplx=False)
-    w.fp64 += 2 * norders                # acc += res W
+    if hi == 0:
+        w.fp64 += _assemble_fixed(ns, hi)
+    else:
+        w.fp64 += _assemble(ns, lo, hi, norders, cplx=False)
+        w.fp64 += 2 * norders            # acc += res W
     return w
 
 

@@ -147,12 +147,33 @@ def _log(msg):
     print(f"[scan] {msg}", file=sys.stderr, flush=True)
 
 
+def allocate_from_variances(P: Problem, w_pred, amax_pred, epsrel, sel, alpha=2.0):
+    """Lattice sizes of Eq. (adaptive-solution) from predicted convergence
+    constants: at each point, the sum's variance target (epsrel times the
+    amplitude's largest coefficient)^2 is shared over its slots with weights
+    W_i = |C_i|^2 w_i and costs tau_i (the evaluator's FP64 work per
+    evaluation of the sector, from the flop model)."""
+    from . import flops as flopmod
+
+    tau = np.array([flopmod.sector_work(s, LO, NORD).fp64 + 20.0 * flopmod.sector_work(s, LO, NORD).log
+                     for I in P.integrals for s in I.sectors])
+    cidx = np.concatenate([np.full(n, i) for i, n in enumerate(P.nsec)])
+    W = (P.C[sel][:, cidx] ** 2) * w_pred                       # [points][slots]
+    V = (epsrel * amax_pred) ** 2                                 # [points]
+    q = 1.0 / (alpha + 1.0)
+    lam = (1.0 / alpha) * (((W * tau ** alpha) ** q).sum(axis=1) / V) ** ((alpha + 1.0) / alpha)
+    return (alpha * lam[:, None] * W / tau) ** q
+
+
 def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC_PRECISION_MIXED,
                 steps: int = 1500, spot_n: int = 1009, spot_shifts: int = 8, shifts: int = 16,
-                max_points: int = 1000003, max_growth: int = 4):
+                max_points: int = 1000003, max_growth: int = 4, sizing: str = "logn"):
     """Learned sizing + spot-checked surrogate + batched QMC (see module doc).
     Every QMC pass here grows a lattice by at most `max_growth` per pass and
-    caps it at `max_points`."""
+    caps it at `max_points`. `sizing`: how the network sizes the lattices of
+    the points it has not seen -- "logn" from the log-lattice-size head,
+    "variance" by the allocation of Eq. (adaptive-solution) from the
+    per-sector log-variance head, "both" the larger of the two."""
     t0 = time.perf_counter()
     train = np.arange(min(ntrain, len(P.points)))
     rest = np.arange(len(train), len(P.points))
@@ -168,13 +189,18 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     #    w = var n^2: w is far from constant over the lattices used here (the
     #    sector integrands converge much faster than n^-2 under korobov3), so a
     #    size extrapolated from w with alpha = 2 overshoots.
+    #    Beside them, the per-sector log-variance: log w with w = var n^2 at the
+    #    converged lattice (the convergence constant of Eq. (varscaling) that the
+    #    allocation of Eq. (adaptive-solution) takes).
     x = _features(P.points[train])
     logn = np.log(tr["n"].astype(np.float64))
     deformed = tr["lam"][0] > 0                     # slots with a contour deformation
     loglam = np.log(tr["lam"][:, deformed])
+    logw = np.log(np.maximum(tr["w"], 1e-300))
     amp = np.concatenate([tr["values"].real, tr["values"].imag], axis=1)
-    Y = np.concatenate([logn, loglam, amp], axis=1)
-    na = P.nslot + int(deformed.sum())              # first amplitude output
+    Y = np.concatenate([logn, loglam, logw, amp], axis=1)
+    nw = P.nslot + int(deformed.sum())              # first log-variance output
+    na = nw + P.nslot                               # first amplitude output
     mu, sd = Y.mean(axis=0), Y.std(axis=0) + 1e-12
     net = qmc.Mlp(2, 256, 4, Y.shape[1], seed=5)
     wt = np.ones(Y.shape[1], dtype=np.float32)
@@ -187,6 +213,8 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
         net.close()
     a_fit = fit[:, na:na + NORD] + 1j * fit[:, na + NORD:]
     fit_err = float(np.max(np.abs(a_fit - tr["values"]) / np.abs(tr["values"]).max(axis=1, keepdims=True)))
+    logn_fit_err = float(np.median(np.abs(fit[:, :P.nslot] - logn)))
+    logw_fit_err = float(np.median(np.abs(fit[:, nw:na] - logw)))
     t_model = time.perf_counter() - t0
     _log(f"model trained and evaluated: {t_model:.2f} s since start, final loss {losses[-1]:.4g}, "
          f"largest relative amplitude error on its training points {fit_err:.3g}")
@@ -194,16 +222,22 @@ def run_learned(P: Problem, epsrel: float, ntrain: int = 2000, precision=qmc.QMC
     res_errs = np.zeros((len(P.points), NORD), complex)
     res_vals[train], res_errs[train] = tr["values"], tr["errors"]
     base = dict(model_seconds=t_model, final_loss=float(losses[-1]), fit_rel_error=fit_err,
+                logn_fit_median_abs=logn_fit_err, logw_fit_median_abs=logw_fit_err, sizing=sizing,
                 train_seconds=tr["seconds"], train_evaluations=tr["evaluations"],
                 train_n_percentiles=np.percentile(tr["n"], [50, 90, 99, 100]).tolist())
     if len(rest) == 0:
         return dict(seconds=time.perf_counter() - t0, values=res_vals, errors=res_errs, accepted=0,
                     evaluations=tr["evaluations"], spot_seconds=0.0, sized_seconds=0.0, **base)
-    n_pred = np.exp(pred[:, :P.nslot])
+    n_logn = np.exp(pred[:, :P.nslot])
     a_pred = pred[:, na:na + NORD] + 1j * pred[:, na + NORD:]
+    if sizing == "logn":
+        n_pred = n_logn
+    else:
+        n_var = allocate_from_variances(P, np.exp(pred[:, nw:na]), np.abs(a_pred).max(axis=1), epsrel, rest)
+        n_pred = n_var if sizing == "variance" else np.maximum(n_var, n_logn)
     # deformation parameters: the prediction snapped to the presampling grid 0.7^c
     # (c = 0..15); the QMC's own sign check verifies it and presamples where it fails
-    c = np.clip(np.round(-pred[:, P.nslot:na] / np.log(1 / 0.7)), 0, 15)
+    c = np.clip(np.round(-pred[:, P.nslot:nw] / np.log(1 / 0.7)), 0, 15)
     lam_pred = np.zeros((len(rest), P.nslot))
     lam_pred[:, deformed] = 0.7 ** c
     # 3. spot check, one small-lattice pass for every remaining point -- run only

@@ -241,7 +241,7 @@ def _gpu_rank_worker(rank, port, world, result_dir):
         qmc.qmc_set_kinematics(ctx, np.array([[-3.0, -2.0], [-5.0, -1.0], [-2.0, -7.0]]))
         if world > 1:
             qdist.set_ranks(ctx)
-        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-10, lowest_order=-2, norders=3, npoints=3,
+        val, err, info, rc = qmc.qmc_integrate(ctx, [iid], epsrel=1e-14, lowest_order=-2, norders=3, npoints=3,
                                                check=False)
         sums, _, n = qmc.qmc_per_shift_sums(ctx, iid)
         if rank == 0:

@@ -38,13 +38,15 @@ def test_scan_modes_agree_on_a_small_grid():
 def test_network_gain_over_the_unsized_method():
     # on the points after the training set, the network's lattice sizes and
     # deformation parameters replace the pilot pass and the presampling: the
-    # sized QMC must spend fewer lattice points (presampling included) than the
-    # same QMC started from the pilot pass, and far fewer than the 10^4-point pilot
-    # of the plain method, at the same requested accuracy
+    # sized QMC must spend fewer lattice points (presampling included) and less
+    # wall time than the same QMC started from the pilot pass, and far fewer
+    # points than the 10^4-point pilot of the plain method, at the same
+    # requested accuracy
     P = scan.Problem(npoints=144, grid=(12, 12))
     eps = 1e-4
     learned = scan.run_learned(P, eps, ntrain=64, steps=600)
     rest = np.arange(64, 144)
+    scan.run_unsized(P, eps, sel=rest[:8])          # warm-up of the same launch shapes
     unsized = scan.run_unsized(P, eps, sel=rest)
     paper = scan.run_batched(P, eps, sel=rest)
     assert unsized["rc"] == 0 and paper["rc"] == 0
@@ -52,6 +54,20 @@ def test_network_gain_over_the_unsized_method():
     cost_u = unsized["evaluations"] + unsized["presample_evaluations"]
     cost_p = paper["evaluations"] + paper["presample_evaluations"]
     print("rest-point lattice points: network", cost_l, "pilot 1009", cost_u, "pilot 10^4", cost_p)
+    print("rest-point seconds: network", learned["sized_seconds"], "pilot 1009", unsized["seconds"])
     assert learned["sized_presample_evaluations"] == 0
     assert cost_l < cost_u < cost_p
+    assert learned["sized_seconds"] < unsized["seconds"]
+    assert scan.relative_errors(learned["values"], learned["errors"]).max() <= eps * 1.0000001
+
+
+@pytest.mark.parametrize("sizing", ["variance", "both"])
+def test_variance_head_sizing_meets_the_request(sizing):
+    # the per-sector log-variance head sizes the lattices through Eq.
+    # (adaptive-solution); the adaptive QMC then meets the request everywhere
+    P = scan.Problem(npoints=144, grid=(12, 12))
+    eps = 1e-4
+    learned = scan.run_learned(P, eps, ntrain=64, steps=600, sizing=sizing)
+    assert learned["sized_presample_evaluations"] == 0
+    assert np.isfinite(learned["logw_fit_median_abs"])
     assert scan.relative_errors(learned["values"], learned["errors"]).max() <= eps * 1.0000001
