@@ -48,6 +48,7 @@ if ROOT not in sys.path:
 
 METRIC = "integrand evals/s"
 DEFAULT_WORKLOAD = "box2L_planar_massless"
+SCAN_TRAIN_STEPS = 600   # Adam steps of the amplitude scan's network
 UNIT = "evals/s"
 JOB_RECORD_BYTES = 136   # device job record (QmcJobDev) copied per job
 
@@ -527,14 +528,17 @@ def main():
     if not args.no_extra and not args.no_scan and world == 1 and default:
         from paper_2305_19768_gb300 import scan
 
-        sc = scan.compare(10000, 1e-4, "plain,unsized,learned", 2000, plain_sample=50)
+        modes = ("plain", "unsized", "learned", "learned_variance")
+        sc = scan.compare(10000, 1e-4, ",".join(modes), 2000, plain_sample=50, steps=SCAN_TRAIN_STEPS)
         keep = ("seconds", "evaluations", "presample_evaluations", "max_rel_error", "rc", "iterations",
                 "sampled_points", "accepted", "train_seconds", "model_seconds", "sized_seconds",
-                "fit_rel_error", "vs_plain_max_rel_diff", "vs_plain_max_diff_over_combined_sigma")
+                "sized_evaluations", "fit_rel_error", "logn_fit_median_abs", "logw_fit_median_abs",
+                "vs_plain_max_rel_diff", "vs_plain_max_diff_over_combined_sigma")
         extra["amplitude_scan"] = {
             "grid": "100 x 100 (s, t), s in [5, 20], t in [-8, -1]; 10 one-loop integrals, 36 sectors",
+            "train_steps": SCAN_TRAIN_STEPS,
             **{k: v for k, v in sc.items() if k.startswith("speedup")},
-            **{m: {k: v for k, v in sc[m].items() if k in keep} for m in ("plain", "unsized", "learned")}}
+            **{m: {k: v for k, v in sc[m].items() if k in keep} for m in modes}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -423,6 +423,10 @@ struct TileSmem {
     QmcSectorDev sec;
     QmcJobDev job;
     uint32_t exps[QMC_MAXMONO];
+    // the monomial as a list of factors t_j^e, decoded once per tile: bits 0..2
+    // the factor count k (0..6), then k codes of 5 bits, code = 4 j + e - 1
+    // (the row of x_j^e in a thread's power table)
+    uint64_t mdesc[QMC_MAXMONO];
     double cval[QMC_MAXMONO];
     float cvalf[QMC_MAXMONO];
     double delta[QMC_DMAX];
@@ -468,6 +472,46 @@ __device__ __forceinline__ T poly_sum(const uint32_t *exps, const CT *cval, int 
         s = (m == m0) ? mulsc(v, c) : s + mulsc(v, c);   // contracted into an FMA
     }
     return s;
+}
+
+// Polynomial value over monomials [m0, m1) from the decoded factor lists and
+// the thread's power table in shared memory (row r of the thread at pt[r * S],
+// S the block size): per factor one shared load and one multiply.
+template <class T, class CT>
+__device__ __forceinline__ T poly_sum_tab(const uint64_t *desc, const CT *cval, int m0, int m1, const T *pt,
+                                          int stride) {
+    T s = zero<T>();
+    for (int m = m0; m < m1; ++m) {
+        const uint64_t dsc = desc[m];
+        const int k = (int)(dsc & 7u);
+        const CT c = cval[m];
+        if (k == 0) {                       // constant monomial
+            s = (m == m0) ? from_real<T>(c) : s + from_real<T>(c);
+            continue;
+        }
+        T v = pt[(int)((dsc >> 3) & 31u) * stride];
+        for (int i = 1; i < k; ++i) v = v * pt[(int)((dsc >> (3 + 5 * i)) & 31u) * stride];
+        s = (m == m0) ? mulsc(v, c) : s + mulsc(v, c);   // contracted into an FMA
+    }
+    return s;
+}
+
+// The thread's power table x_j^e (e = 1 .. emax) into rows 4 j + e - 1
+template <int DMAX, class T>
+__device__ __forceinline__ void powers_tab(const T (&x)[DMAX], int d, int emax, T *pt, int stride) {
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d) {
+            const T x1 = x[j];
+            pt[(4 * j) * stride] = x1;
+            if (emax >= 2) {
+                const T x2 = x1 * x1;
+                pt[(4 * j + 1) * stride] = x2;
+                if (emax >= 3) pt[(4 * j + 2) * stride] = x2 * x1;
+                if (emax >= 4) pt[(4 * j + 3) * stride] = x2 * x2;
+            }
+        }
+    }
 }
 
 template <int DMAX, class T>
@@ -878,34 +922,35 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
     }
 }
 
+// ptd / ptf: this thread's column of the power table in shared memory (FP64
+// and, for the mixed classes, FP32 view of the same storage), row stride `ps`
 template <int DMAX, int NS, int HI, bool MIXED, int LMAX>
 __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const double (&t)[DMAX],
-                                             double (&resN)[NS + HI + 1]) {
+                                             double (&resN)[NS + HI + 1], double *ptd, float *ptf, int ps) {
     constexpr int NG = 1 << NS;
     constexpr int NSA = SlotArr<NS>::N;
     const QmcSectorDev &sec = S.sec;
     const int d = sec.d;
     const uint64_t *tab = S.logtab;
-    double tp[DMAX][QMC_EMAX];
-    powers<DMAX, double>(t, d, sec.pad0, tp);
     // group sums by singular mask, then subset sums h[X] = sum_{M subset X} g[M];
     // the polynomial at corner V (t_V = 0) is h[(NG-1) ^ V]
     double hU[NG], hF[NG];
     if constexpr (MIXED) {
-        float tf[DMAX], tpf[DMAX][QMC_EMAX];
+        float tf[DMAX];
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) tf[j] = __double2float_rn(t[j]);
-        powers<DMAX, float>(tf, d, sec.pad0, tpf);
+        powers_tab<DMAX, float>(tf, d, sec.pad0, ptf, ps);
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
-            hU[g] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, sec.gU[g], sec.gU[g + 1], tpf);
-            hF[g] = (double)poly_sum<DMAX, float>(S.exps, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tpf);
+            hU[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.gU[g], sec.gU[g + 1], ptf, ps);
+            hF[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptf, ps);
         }
     } else {
+        powers_tab<DMAX, double>(t, d, sec.pad0, ptd, ps);
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
-            hU[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.gU[g], sec.gU[g + 1], tp);
-            hF[g] = poly_sum<DMAX, double>(S.exps, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], tp);
+            hU[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.gU[g], sec.gU[g + 1], ptd, ps);
+            hF[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptd, ps);
         }
     }
 #pragma unroll
@@ -925,7 +970,9 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
         if (j < d && ((sec.regular_mask >> j) & 1)) {
             const int a = sec.a[j];
             if (a > 0) {
-                Cc = hasCc ? Cc * pow_sel<double>(tp[j], (uint32_t)a) : pow_sel<double>(tp[j], (uint32_t)a);
+                // t_j^a: the FP64 power table, or (mixed classes, whose table is FP32) products
+                const double p = MIXED ? ipow_signed<double>(t[j], 1.0, a) : ptd[(4 * j + a - 1) * ps];
+                Cc = hasCc ? Cc * p : p;
                 hasCc = true;
             }
             if (need_lam && sec.b[j] != 0.0) {
@@ -1438,6 +1485,16 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
             S.cval[m] = v;
             S.cvalf[m] = (float)v;
             S.exps[m] = M.exps;
+            uint64_t dsc = 0;
+            int k = 0;
+            for (int j = 0; j < QMC_DMAX; ++j) {
+                const uint32_t ej = (M.exps >> (4 * j)) & 15u;
+                if (ej) {
+                    dsc |= (uint64_t)(4 * j + ej - 1) << (3 + 5 * k);
+                    ++k;
+                }
+            }
+            S.mdesc[m] = dsc | (uint64_t)k;
         }
         __syncthreads();
         if (threadIdx.x < QMC_SMAX) {
@@ -1499,7 +1556,7 @@ constexpr int qmc_min_blocks() {
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, int NSC, int HIC, class T>
 __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const QmcLaunch &Lc, uint64_t k0,
                                               uint64_t kend, int lo, int hi, int nord, T (&acc)[LMAX],
-                                              int &signfail_tile) {
+                                              int &signfail_tile, unsigned char *ptab) {
     constexpr bool FIXED = NSC >= 0 && HIC >= 0;
     constexpr int NO = FIXED ? NSC + HIC + 1 : 1;
     double accN[NO];
@@ -1553,7 +1610,8 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
         if (nonneg_is_zero(W) || zero_t) continue;
         if constexpr (FIXED) {
             double resN[NO];
-            eval_real_fx<DMAX, NSC, HIC, MIXED, LMAX>(S, t, resN);
+            eval_real_fx<DMAX, NSC, HIC, MIXED, LMAX>(S, t, resN, reinterpret_cast<double *>(ptab) + threadIdx.x,
+                                                      reinterpret_cast<float *>(ptab) + threadIdx.x, (int)blockDim.x);
 #pragma unroll
             for (int i = 0; i < NO; ++i) accN[i] = fma(resN[i], W, accN[i]);
         } else {
@@ -1598,6 +1656,9 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS = false, bool FIX = false>
 __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3), (CPLX && MIXED), HS>()) qmc_eval_kernel(QmcLaunch Lc, int ppt) {
     __shared__ TileSmem<LMAX> S;
+    // the fixed-order kernels' per-thread power tables (4 DMAX rows of BLOCK
+    // doubles, dynamic shared memory; empty for the other kernels)
+    extern __shared__ __align__(16) unsigned char qmc_ptab[];
     using T = typename std::conditional<CPLX, dc, double>::type;
     const int lo = Lc.lo, nord = Lc.norders;
     if (threadIdx.x == 0) {
@@ -1669,15 +1730,15 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
                 // number of singular variables (the host launches this kernel
                 // only for hi = 0)
                 const int ns = S.sec.ns;
-                if (ns == 0) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 0, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                else if (ns == 1) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 1, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                else if (ns == 2 || SMAX < 3) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 2 ? 2 : 1), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                if (ns == 0) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 0, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile, qmc_ptab);
+                else if (ns == 1) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 1, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile, qmc_ptab);
+                else if (ns == 2 || SMAX < 3) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 2 ? 2 : 1), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile, qmc_ptab);
                 else if constexpr (SMAX >= 3) {
-                    if (ns == 3 || SMAX < 4) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 3, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
-                    else thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 4 ? 4 : 3), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                    if (ns == 3 || SMAX < 4) thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, 3, 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile, qmc_ptab);
+                    else thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, (SMAX >= 4 ? 4 : 3), 0>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile, qmc_ptab);
                 }
             } else {
-                thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, -1, -1>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile);
+                thread_points<DMAX, SMAX, LMAX, CPLX, MIXED, HS, -1, -1>(S, Lc, k0, kend, lo, hi, nord, acc, signfail_tile, qmc_ptab);
             }
         }
         // sign-check failures of this tile: per job (if counted) and in total
@@ -1836,16 +1897,30 @@ __global__ void qmc_fp32_probe_kernel(float *out, int iters) {
 // Blocks of 256 threads exist for the d <= 3 classes only: the d <= 6 classes
 // run near the register limit, where a second warp set per block buys nothing
 // (and their instantiations dominate the build).
+// Dynamic shared memory of an evaluator kernel: the power tables of the
+// fixed-order real kernels
+template <int DMAX, bool CPLX, bool HS, bool FIX>
+constexpr int eval_dyn_smem(int block) {
+    return (!CPLX && !HS && FIX) ? 4 * DMAX * block * (int)sizeof(double) : 0;
+}
+
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS, bool FIX>
+int launch_block(const QmcLaunch *L, int ppt, int grid, cudaStream_t st) {
+    constexpr int dyn = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK);
+    static const bool attr_ok =
+        dyn == 0 || cudaFuncSetAttribute(qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
+    if (!attr_ok) return -1;
+    qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX><<<grid, BLOCK, dyn, st>>>(*L, ppt);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, bool FIX>
 int launch_shape(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st) {
     if constexpr (DMAX <= 3) {
-        if (block == 256) {
-            qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX><<<grid, 256, 0, st>>>(*L, ppt);
-            return cudaGetLastError() == cudaSuccess ? 0 : -1;
-        }
+        if (block == 256) return launch_block<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX>(L, ppt, grid, st);
     }
-    qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX><<<grid, 128, 0, st>>>(*L, ppt);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return launch_block<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>(L, ppt, grid, st);
 }
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
@@ -1856,19 +1931,24 @@ int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st
     return launch_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, false>(L, block, ppt, grid, st);
 }
 
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS, bool FIX>
+int occupancy_block() {
+    constexpr int dyn = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK);
+    if (dyn && cudaFuncSetAttribute(qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+        return 0;
+    int v = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>, BLOCK, dyn);
+    return e == cudaSuccess ? v : 0;
+}
+
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, bool FIX>
 int occupancy_shape(int block) {
-    int v = 0;
-    cudaError_t e;
-    if constexpr (DMAX <= 3)
-        e = block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX>, 256, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>, 128, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>, 128, 0);
-    return e == cudaSuccess ? v : 0;
+    if constexpr (DMAX <= 3) {
+        if (block == 256) return occupancy_block<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX>();
+    }
+    return occupancy_block<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>();
 }
 
 // Resident blocks per SM of the class's kernels (the larger of the fixed-order

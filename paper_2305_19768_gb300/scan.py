@@ -289,10 +289,13 @@ def relative_errors(values, errors):
 
 
 def compare(points: int = 10000, epsrel: float = 1e-4, modes="plain,unsized,learned", ntrain: int = 2000,
-            plain_sample: int = 0):
+            plain_sample: int = 0, steps: int = 1500):
     """Run the requested modes on the first `points` grid points and return the
     timings, evaluation counts and errors (plain may run on every
-    `plain_sample`-th point only; its time is then scaled to the whole grid)."""
+    `plain_sample`-th point only; its time is then scaled to the whole grid).
+    Modes: plain, batched, unsized, learned (lattices from the log-n head),
+    learned_variance (lattices from the log-variance head through Eq.
+    (adaptive-solution)); `steps` Adam steps train the network."""
     P = Problem(points)
     out = {"points": len(P.points), "epsrel": epsrel, "slots_per_point": P.nslot}
     ref = None
@@ -320,8 +323,8 @@ def compare(points: int = 10000, epsrel: float = 1e-4, modes="plain,unsized,lear
                                   presample_evaluations=r["presample_evaluations"],
                                   iterations=r["iterations"], kernel_seconds=r["kernel_seconds"],
                                   max_rel_error=float(relative_errors(r["values"], r["errors"]).max()))
-        elif mode == "learned":
-            r = run_learned(P, epsrel, ntrain)
+        elif mode in ("learned", "learned_variance"):
+            r = run_learned(P, epsrel, ntrain, steps=steps, sizing="logn" if mode == "learned" else "variance")
             d = {k: v for k, v in r.items() if k not in ("values", "errors")}
             d["max_rel_error"] = float(relative_errors(r["values"], r["errors"]).max())
             if ref is not None:
@@ -335,8 +338,8 @@ def compare(points: int = 10000, epsrel: float = 1e-4, modes="plain,unsized,lear
                 comb = np.hypot(np.abs(r["errors"][plain_sel]), np.abs(plain_errs))
                 d["vs_plain_max_rel_diff"] = float(np.max(diff / amax))
                 d["vs_plain_max_diff_over_combined_sigma"] = float(np.max(diff / np.maximum(comb, 1e-300)))
-            out["learned"] = d
-    for mode in ("learned", "unsized", "batched"):
+            out[mode] = d
+    for mode in ("learned", "learned_variance", "unsized", "batched"):
         if "plain" in out and mode in out:
             out[f"speedup_{mode}_vs_plain"] = out["plain"]["seconds"] / out[mode]["seconds"]
     return out
@@ -349,8 +352,9 @@ def main():
     ap.add_argument("--modes", default="plain,unsized,learned")
     ap.add_argument("--ntrain", type=int, default=2000)
     ap.add_argument("--plain-sample", type=int, default=0, help="time plain on every k-th point only")
+    ap.add_argument("--steps", type=int, default=1500, help="Adam steps of the network's training")
     args = ap.parse_args()
-    print(json.dumps(compare(args.points, args.epsrel, args.modes, args.ntrain, args.plain_sample)))
+    print(json.dumps(compare(args.points, args.epsrel, args.modes, args.ntrain, args.plain_sample, args.steps)))
 
 
 if __name__ == "__main__":

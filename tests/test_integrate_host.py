@@ -170,3 +170,30 @@ def test_two_rank_integration_equals_one_rank(tmp_path):
     assert int(a["iters"]) >= 2                      # at least one allocation pass ran
     for k in ("val", "err", "sums", "n", "rc", "evals", "iters"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_failed_exchange_or_evaluator_ends_the_integration_with_an_error():
+    # failure detection on the host: a rank exchange that reports failure (a
+    # peer that left) and an evaluator that fails both end qmc_integrate with
+    # an error status, nothing hangs
+    I = w.box_massless()
+    ctx, ids = _host_ctx([I], KIN[:1], shifts=4, min_points=1009, max_points=20011)
+    try:
+        def broken(buf):
+            raise RuntimeError("peer left")
+
+        qmc.qmc_set_ranks(ctx, 0, 2, broken)
+        with pytest.raises(qmc.QmcError) as e:
+            qmc.qmc_integrate(ctx, ids, epsrel=1e-9, lowest_order=-2, norders=3)
+        assert e.value.code == -1 and "exchange" in str(e.value)
+        qmc.qmc_set_ranks(ctx, 0, 1, None)
+
+        def failing(jobs, lo, norders):
+            raise RuntimeError("device lost")
+
+        qmc.qmc_set_evaluator(ctx, failing)
+        with pytest.raises(qmc.QmcError) as e:
+            qmc.qmc_integrate(ctx, ids, epsrel=1e-9, lowest_order=-2, norders=3)
+        assert "evaluator failed" in str(e.value)
+    finally:
+        qmc.qmc_destroy(ctx)
