@@ -270,6 +270,45 @@ def box_extra(device, opts, sptr, flush, peak_gflops, seed):
     return out
 
 
+def batch_extra(device, opts, sptr, flush, peak_gflops, seed, n=100003, m=32):
+    """The massive box in the physical region at 1024 seeded (s, t) points
+    (C3: contour deformation with lambda presampled per point and sector, all
+    4096 jobs in one persistent launch) at a lattice of n points: throughput
+    and FP64 roofline."""
+    import torch
+
+    from paper_2305_19768_gb300 import flops as flopmod
+    from paper_2305_19768_gb300 import qmc
+
+    W = _workloads()["box1L_massive_batch"]
+    I = W["make"]()
+    ctx = qmc.qmc_create(device, **opts)
+    try:
+        qmc.load_lattice_table(ctx)
+        iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
+        kin = np.array(W["kin"])
+        qmc.qmc_set_kinematics(ctx, kin)
+        specs = qmc.jobs_for_integral(iid, len(I.sectors), len(kin), n, m, seed=seed)
+        jobs, nj = qmc.make_jobs(specs)
+        lam, _ = qmc.qmc_presample_lambda(ctx, jobs, nj, W["lo"], W["nord"], lambda_max=1.0, ncand=16)
+        for sp, L in zip(specs, lam):
+            sp["lambda"] = float(L)
+        jobs, nj = qmc.make_jobs(specs)
+        plan = qmc.qmc_plan_create(ctx, jobs, nj, W["lo"], W["nord"])
+        o = torch.empty(qmc.qmc_plan_output_size(plan), dtype=torch.float64, device="cuda")
+        ms = timed_plan(qmc, ctx, plan, o.data_ptr(), sptr, flush, 2, warmup=1)
+        qmc.qmc_plan_destroy(plan)
+    finally:
+        qmc.qmc_destroy(ctx)
+    evals = nj * m * n
+    fl = flopmod.workload_work(I, W["lo"], W["nord"]).fp64
+    rate = evals / (float(np.mean(ms)) * 1e-3)
+    return {"box1L_massive_batch": {
+        "workload": W["desc"].format(n=n, m=m), "evals_per_s": rate, "eval_ms": float(np.mean(ms)),
+        "roofline": {"achieved": fl * rate / 1e9, "peak": peak_gflops, "frac": fl * rate / 1e9 / peak_gflops,
+                     "flops_per_eval": fl, "unit": "GFLOP/s (fp64)"}}}
+
+
 def mixed_extra(device, opts, I, W, kin, jobs, nj, evals_per_step, out_dev, sptr, seed, skip_oracle):
     """The double box's mixed-precision pass (FP32 monomial products): its
     throughput, its largest difference from the FP64 GPU pass, and its error
@@ -518,6 +557,7 @@ def main():
     extra = {}
     if not args.no_extra and default:
         extra.update(box_extra(local, opts, sptr, flush, peak_gflops, seed))
+        extra.update(batch_extra(local, opts, sptr, flush, peak_gflops, seed))
         extra.update(mixed_extra(local, opts, I, W, kin, jobs, nj, evals_per_step, out_dev, sptr, seed,
                                  args.no_cpu_baseline or rank != 0))
 

@@ -274,10 +274,49 @@ __device__ __forceinline__ void korobov3_int(double u, double &t, double &omt, d
     ws = round_pack(mu, V, e - 52 - 64);
 }
 
+__device__ __noinline__ double walk_coord_call(uint64_t Q, uint32_t r, uint32_t R, uint32_t n, double nd,
+                                               double inv_n, double delta, uint64_t D) {
+    LatticeWalk w;
+    w.Q = Q;
+    w.r = r;
+    w.R = R;
+    return walk_coord(w, n, nd, inv_n, delta, D, true);
+}
+
+struct K3 {
+    double t, omt, ws;
+};
+__device__ __noinline__ K3 korobov3_call(double u) {
+    K3 r{0.0, 1.0, 0.0};
+    korobov3_int<false>(u, r.t, r.omt, r.ws);
+    return r;
+}
+
 // Natural logarithm: the fixed-point evaluation of qmc_ilog.h on the integer
 // pipe (Tang's reduction with a 1025-row table; within 0.501 ulp). `tab` is
 // the table of that header, staged in shared memory.
 __device__ __forceinline__ double qlog(double x, const uint64_t *tab) { return qmc_ilog(x, tab); }
+
+// The same logarithm as one out-of-line function. The fixed-order d <= 6
+// kernel takes up to about twenty logarithms per evaluation; inlined, their
+// copies overflow the SM's instruction cache (warps then stall on
+// instruction fetch), so that kernel calls this single copy instead.
+// QMC_LOG_CALL: bit 0 for the d <= 6 kernel, bit 1 for the d <= 3 kernel.
+#ifndef QMC_LOG_CALL
+#define QMC_LOG_CALL 1
+#endif
+// korobov3 out of line in the d <= 6 fixed-order kernel (same reason;
+// measured: +7 % on the double box over the inlined form, after the
+// logarithm's +18 %; the d <= 3 kernel runs 2 % faster with its logarithm
+// inlined)
+#ifndef QMC_KOROBOV_CALL
+#define QMC_KOROBOV_CALL 1
+#endif
+// the lattice coordinate out of line as well (+1 % on the double box)
+#ifndef QMC_WALK_CALL
+#define QMC_WALK_CALL 1
+#endif
+__device__ __noinline__ double qlog_call(double x, const uint64_t *tab) { return qmc_ilog(x, tab); }
 
 // Reciprocal by Newton-Raphson (y <- y + y (1 - x y), quadratic convergence)
 // from the hardware approximation rcp.approx.ftz.f64, two steps: not
@@ -922,6 +961,13 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
     }
 }
 
+// The logarithm of the fixed-order kernels: out of line for d <= 6 (see qlog_call)
+template <int DMAX>
+__device__ __forceinline__ double qlog_fx(double x, const uint64_t *tab) {
+    if constexpr ((DMAX > 3 && (QMC_LOG_CALL & 1)) || (DMAX <= 3 && (QMC_LOG_CALL & 2))) return qlog_call(x, tab);
+    else return qmc_ilog(x, tab);
+}
+
 // ptd / ptf: this thread's column of the power table in shared memory (FP64
 // and, for the mixed classes, FP32 view of the same storage), row stride `ps`
 template <int DMAX, int NS, int HI, bool MIXED, int LMAX>
@@ -976,7 +1022,7 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
                 hasCc = true;
             }
             if (need_lam && sec.b[j] != 0.0) {
-                const double l = qlog(t[j], tab);
+                const double l = qlog_fx<DMAX>(t[j], tab);
                 Lc = hasLc ? fma(sec.b[j], l, Lc) : sec.b[j] * l;
                 hasLc = true;
             }
@@ -1001,7 +1047,7 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
                 }
             it[q] = tq;
             bq[q] = bb;
-            if (need_lt) lt[q] = qlog(tq, tab);
+            if (need_lt) lt[q] = qlog_fx<DMAX>(tq, tab);
         }
     }
     // t_q / b_q (the factors of the pole-set prefactors A_P), then 1/t_q in
@@ -1069,20 +1115,20 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
             unit = false;
         }
         if (!sec.u0_int || u0 != 0) {
-            const double pu = sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog(U, tab));
+            const double pu = sec.u0_int ? ipow_signed<double>(U, Ui, u0) : exp(sec.u0 * qlog_fx<DMAX>(U, tab));
             B = unit ? pu : B * pu;
             unit = false;
         }
         if (!sec.f0_int || f0 != 0) {
-            const double pf = sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog(F, tab));
+            const double pf = sec.f0_int ? ipow_signed<double>(F, Fi, f0) : exp(sec.f0 * qlog_fx<DMAX>(F, tab));
             B = unit ? pf : B * pf;
         }
         BV[V] = B;
         LV[V] = 0.0;
         if (lam_here) {
             double l;
-            if (comb) l = qlog(ipow_signed<double>(U, Ui, u1) * ipow_signed<double>(F, Fi, f1), tab);
-            else l = fma(sec.u1, qlog(U, tab), sec.f1 * qlog(F, tab));
+            if (comb) l = qlog_fx<DMAX>(ipow_signed<double>(U, Ui, u1) * ipow_signed<double>(F, Fi, f1), tab);
+            else l = fma(sec.u1, qlog_fx<DMAX>(U, tab), sec.f1 * qlog_fx<DMAX>(F, tab));
             LV[V] = hasLc ? Lc + l : l;
         }
     }
@@ -1581,7 +1627,11 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
             t[j] = 1.0;
             omt[j] = 0.0;
             if (j < d) {
-                const double u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
+                double u;
+                if constexpr (!CPLX && DMAX > 3 && FIXED && QMC_WALK_CALL)
+                    u = walk_coord_call(wk[j].Q, wk[j].r, wk[j].R, n32, nd, inv_n, S.delta[j], S.dfix[j]);
+                else
+                    u = walk_coord(wk[j], n32, nd, inv_n, S.delta[j], S.dfix[j], true);
                 if (Lc.transform == 0) {          // korobov3
                     // integer pipe (with 1 - t for the deformed classes)
                     if constexpr (!CPLX && DMAX > 3 && !QMC_KOROBOV_INT6) {
@@ -1591,7 +1641,15 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
                     } else {
                         double ws = 0.0, om = 1.0;
                         t[j] = 0.0;
-                        if (!nonneg_is_zero(u)) korobov3_int<CPLX>(u, t[j], om, ws);
+                        if constexpr (!CPLX && DMAX > 3 && FIXED && QMC_KOROBOV_CALL) {
+                            if (!nonneg_is_zero(u)) {
+                                const K3 k3 = korobov3_call(u);
+                                t[j] = k3.t;
+                                ws = k3.ws;
+                            }
+                        } else {
+                            if (!nonneg_is_zero(u)) korobov3_int<CPLX>(u, t[j], om, ws);
+                        }
                         if (CPLX) omt[j] = om;
                         Ws = j == 0 ? ws : Ws * ws;
                     }
@@ -1771,7 +1829,10 @@ __global__ void __launch_bounds__(BLOCK, qmc_min_blocks<BLOCK, (CPLX || DMAX > 3
             double sum = 0.0;
             for (int w = 0; w < BLOCK / 32; ++w) sum += S.red[w][threadIdx.x];
             sum *= S.w140d;   // the sector's constant factor and the korobov3 weight's 140^d
-            Lc.partials[tile * (uint64_t)(2 * nord) + threadIdx.x] = sum;
+            // streaming store (evict first): the partials are read once, by the
+            // finishing kernel, and at large lattices their stream would
+            // otherwise push the spilled thread stacks out of L2
+            __stcs(&Lc.partials[tile * (uint64_t)(2 * nord) + threadIdx.x], sum);
             if (!isfinite(sum)) atomicAdd(Lc.status + 1, 1ULL);
         }
     }
@@ -1792,7 +1853,7 @@ __global__ void qmc_finish_kernel(QmcLaunch Lc) {
         const uint64_t t0 = J.tile_begin + (uint64_t)s * J.tiles_per_shift;
         double sum = 0.0, comp = 0.0;
         for (uint64_t c = 0; c < (uint64_t)J.tiles_per_shift; ++c) {
-            const double x = Lc.partials[(t0 + c) * per + q];
+            const double x = __ldcs(&Lc.partials[(t0 + c) * per + q]);
             const double tt = sum + x;
             comp += (fabs(sum) >= fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
             sum = tt;
