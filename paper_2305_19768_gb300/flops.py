@@ -180,7 +180,8 @@ def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work
     polys = _grouped_poly(sector.U, sing, ns) + _grouped_poly(sector.F, sing, ns)
     if mixed:
         w.fp32 += pw + polys
-        w.fp64 += pw                     # FP64 powers still feed the regular prefactor
+        # the regular prefactor's powers t^a as FP64 products (the table is FP32)
+        w.fp64 += sum(max(int(sector.a[j]) - 1, 0) for j in range(d) if sector.a[j] > 0)
     else:
         w.fp64 += pw + polys
     w.fp64 += 2 * ns * (1 << max(ns - 1, 0))   # subset sums of U and F
