@@ -92,9 +92,14 @@ class SectorView:
 
     def __init__(self, integral, sector: int, inv, lam=None, transform: int = 0):
         s = integral.sectors[sector]
-        n2 = sum(1 for x in s.a if int(x) <= -2)
-        if any(int(x) < -2 for x in s.a) or n2 > 1 or (n2 and s.deform and lam is not None):
-            raise ValueError("subtraction of degree 1 covers one a_j = -2 per undeformed sector")
+        box = 1
+        for x in s.a:
+            if int(x) <= -1:
+                box *= -int(x)
+        if box > 1 and s.deform and lam is not None:
+            raise ValueError("Taylor subtraction beyond degree 0 (a_j <= -2) needs an undeformed sector")
+        if box > 64:
+            raise ValueError("the subtraction's Taylor box prod_j (-a_j) exceeds 64 coefficients")
         self.d = s.d
         self.Ue, self.Uc = integral.coefficients_at(sector, "U", inv)
         self.Fe, self.Fc = integral.coefficients_at(sector, "F", inv)

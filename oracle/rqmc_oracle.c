@@ -14,8 +14,9 @@
  *  - the korobov3 periodizing transform named in the timings section;
  *  - contour deformation z = t - i lambda t (1 - t) dF/dt with its Jacobian
  *    determinant (the paper only names the presampling that tunes lambda);
- *  - the eps-expanded sector integrand with plus-distribution subtraction of
- *    the logarithmic endpoint singularities t_j^{-1 + b_j eps}.
+ *  - the eps-expanded sector integrand with subtraction of the endpoint
+ *    singularities t_j^{-p + b_j eps}: plus distributions for p = 1, the
+ *    Taylor polynomial of degree p - 1 for p >= 2 (undeformed sectors).
  * The paper is silent on the lattice-point rounding, the transform formula,
  * the deformation formula and the subtraction; the readings used here are:
  *  x = (double)r / (double)n + Delta; if (x >= 1) x -= 1, with r = k z mod n
@@ -25,8 +26,10 @@
  *
  * Parity pins (checked by the CPU test suite, not by this file): closed forms
  * of the one-loop massive triangle, massless box and massive bubble,
- * lattice-sum invariants, Korobov moments, 1-D and 2-D subtraction integrals
- * with polynomial G, and tensor-product Gauss-Legendre quadrature.
+ * lattice-sum invariants, Korobov moments, subtraction integrals of degree
+ * 1 to 3 in one to four variables with polynomial G (exact sums) and with
+ * eps-dependent powers of U and F (adaptive quadrature of the remainder),
+ * and tensor-product Gauss-Legendre quadrature.
  */
 #include <complex.h>
 #include <math.h>
@@ -248,9 +251,9 @@ static cplx det_leibniz(int d, const cplx *A) {
     return det;
 }
 
-/* singular: t_j^{a_j + b_j eps} with a_j = -1 (logarithmic) or -2 (one
- * variable per sector, undeformed sectors only: subtraction of the Taylor
- * polynomial of degree 1) */
+/* singular: t_j^{a_j + b_j eps} with a_j <= -1. a_j = -1 is logarithmic;
+ * a_j = -p, p >= 2, takes the Taylor subtraction of degree p - 1 (undeformed
+ * sectors only) */
 static int is_singular(const orc_sector *S, int j) { return S->a[j] <= -1; }
 
 /* G(t', eps): everything in the sector integrand except prod_{j in S}
@@ -322,26 +325,155 @@ static series G_series(const orc_sector *S, const double *tp, const double *omtp
     return G;
 }
 
-/* dG/dt_q at the real point tp for an undeformed sector: t_q enters G only
- * through U and F, so dG/dt_q = G ((u0 + u1 eps) U_q / U + (f0 + f1 eps) F_q / F). */
-static series dG_series(const orc_sector *S, const double *tp, int q, int hi, int *signfail) {
+/* ---------------- Taylor coefficients of G in the zeroed variables ---------------- */
+/* Truncated multivariate power series ("jets") in the variables t_{V[0..nv-1]}
+ * over the box 0 <= k_q < rad[q]; flat index sum_q k_q prod_{r<q} rad[r]. */
+#define ORC_JMAX 64
+typedef struct {
+    int nv;
+    int rad[ORC_SMAX];
+    int size;
+} jbox;
+
+static void jbox_digits(const jbox *B, int idx, int *dig) {
+    for (int q = 0; q < B->nv; ++q) {
+        dig[q] = idx % B->rad[q];
+        idx /= B->rad[q];
+    }
+}
+
+/* c = a b, every product whose exponents leave the box dropped (c may alias a or b) */
+static void jet_mul(const jbox *B, const cplx *a, const cplx *b, cplx *c) {
+    cplx r[ORC_JMAX];
+    for (int k = 0; k < B->size; ++k) r[k] = 0.0;
+    for (int i = 0; i < B->size; ++i) {
+        int di[ORC_SMAX];
+        jbox_digits(B, i, di);
+        for (int j = 0; j < B->size; ++j) {
+            int dj[ORC_SMAX];
+            jbox_digits(B, j, dj);
+            int k = 0, stride = 1, inside = 1;
+            for (int q = 0; q < B->nv; ++q) {
+                int e = di[q] + dj[q];
+                if (e >= B->rad[q]) { inside = 0; break; }
+                k += e * stride;
+                stride *= B->rad[q];
+            }
+            if (inside) r[k] += a[i] * b[j];
+        }
+    }
+    for (int k = 0; k < B->size; ++k) c[k] = r[k];
+}
+
+/* Taylor coefficients of P^{e0 + e1 eps} (P = U or F) in the variables V at
+ * t_V = 0, the other variables at t: out[k] = coefficient of prod t_V^{k},
+ * as eps-series up to eps^hi, for every k in the box. P = P0 + delta with
+ * P0 = P(t_V = 0) and delta (no constant term) read off the monomial table;
+ * the generalized binomial theorem gives
+ *   P^alpha = sum_k binom(alpha, k) P0^{alpha - k} delta^k,
+ * binom(alpha, k) = prod_{i<k} (alpha - i) / k! a polynomial in eps, and
+ * P0^{alpha - k} = P0^{e0 - k} exp(e1 eps ln P0). delta^k vanishes in the box
+ * beyond k = sum_q (rad_q - 1). */
+static void jet_power(const orc_sector *S, int isF, const double *t, const int *V, const jbox *B,
+                      int hi, series *out) {
     int d = S->d;
-    cplx t[ORC_DMAX];
-    for (int j = 0; j < d; ++j) t[j] = tp[j];
-    int D[ORC_DMAX];
-    memset(D, 0, sizeof D);
-    D[q] = 1;
-    cplx U = poly_deriv(S->nU, d, S->Ue, S->Uc, t, NULL);
-    cplx F = poly_deriv(S->nF, d, S->Fe, S->Fc, t, NULL);
-    cplx Uq = poly_deriv(S->nU, d, S->Ue, S->Uc, t, D);
-    cplx Fq = poly_deriv(S->nF, d, S->Fe, S->Fc, t, D);
-    series G = G_series(S, tp, tp, hi, signfail);
-    series L;
-    memset(&L, 0, sizeof L);
-    L.lo = 0; L.n = 2;
-    L.c[0] = S->u0 * Uq / U + S->f0 * Fq / F;
-    L.c[1] = S->u1 * Uq / U + S->f1 * Fq / F;
-    return s_mul(&G, &L, hi);
+    int nP = isF ? S->nF : S->nU;
+    const int *ex = isF ? S->Fe : S->Ue;
+    const double *co = isF ? S->Fc : S->Uc;
+    double e0 = isF ? S->f0 : S->u0, e1 = isF ? S->f1 : S->u1;
+    int inV[ORC_DMAX] = {0};
+    for (int q = 0; q < B->nv; ++q) inV[V[q]] = 1;
+    cplx delta[ORC_JMAX];
+    for (int k = 0; k < B->size; ++k) delta[k] = 0.0;
+    for (int m = 0; m < nP; ++m) {
+        int idx = 0, stride = 1, inside = 1;
+        for (int q = 0; q < B->nv; ++q) {
+            int e = ex[m * d + V[q]];
+            if (e >= B->rad[q]) { inside = 0; break; }
+            idx += e * stride;
+            stride *= B->rad[q];
+        }
+        if (!inside) continue;
+        cplx v = co[m];
+        for (int j = 0; j < d; ++j)
+            if (!inV[j]) v *= cipow(t[j], ex[m * d + j]);
+        delta[idx] += v;
+    }
+    cplx P0 = delta[0];
+    if (cimag(P0) == 0.0) P0 = CMPLX(creal(P0), isF ? -0.0 : 0.0);   /* F - i0 */
+    delta[0] = 0.0;
+    cplx lg = clog(P0);
+    series pe = s_exp_eps(e1 * lg, hi);                /* P0^{e1 eps} */
+    int K = 0;
+    for (int q = 0; q < B->nv; ++q) K += B->rad[q] - 1;
+    for (int i = 0; i < B->size; ++i) {
+        memset(&out[i], 0, sizeof(series));
+        out[i].lo = 0;
+        out[i].n = hi + 1;
+    }
+    cplx dk[ORC_JMAX];                                  /* delta^k */
+    for (int i = 0; i < B->size; ++i) dk[i] = 0.0;
+    dk[0] = 1.0;
+    series binom = s_const(1.0);
+    for (int k = 0; k <= K; ++k) {
+        if (k > 0) {
+            jet_mul(B, dk, delta, dk);
+            series lin;                                  /* (e0 - (k - 1) + e1 eps) / k */
+            memset(&lin, 0, sizeof lin);
+            lin.lo = 0; lin.n = 2;
+            lin.c[0] = (e0 - (k - 1)) / (double)k;
+            lin.c[1] = e1 / (double)k;
+            binom = s_mul(&binom, &lin, hi);
+        }
+        series c = s_mul(&binom, &pe, hi);
+        c = s_scale(&c, cexp((e0 - k) * lg));
+        for (int i = 0; i < B->size; ++i)
+            if (dk[i] != 0.0) {
+                series term = s_scale(&c, dk[i]);
+                out[i] = s_add(&out[i], &term, hi);
+            }
+    }
+}
+
+/* Taylor coefficient of G (undeformed sector) of prod_{q} t_{V[q]}^{kap[q]}
+ * at t_V = 0, the other variables at t, as an eps-series up to eps^hi. There
+ * G = prod_{j regular} t_j^{a_j + b_j eps} U^{u0 + u1 eps} F^{f0 + f1 eps}, and
+ * only U and F depend on t_V: the coefficient is the regular factor times
+ * sum_{k' <= kap} [U^.]_{k'} [F^.]_{kap - k'}. */
+static series taylor_G(const orc_sector *S, const double *t, int nv, const int *V, const int *kap,
+                       int hi) {
+    jbox B;
+    B.nv = nv;
+    B.size = 1;
+    for (int q = 0; q < nv; ++q) {
+        B.rad[q] = kap[q] + 1;
+        B.size *= B.rad[q];
+    }
+    if (B.size > ORC_JMAX) abort();
+    series PU[ORC_JMAX], PF[ORC_JMAX];
+    jet_power(S, 0, t, V, &B, hi, PU);
+    jet_power(S, 1, t, V, &B, hi, PF);
+    series prod;
+    memset(&prod, 0, sizeof prod);
+    prod.lo = 0; prod.n = hi + 1;
+    for (int i = 0; i < B.size; ++i) {
+        int di[ORC_SMAX], j = 0, stride = 1;
+        jbox_digits(&B, i, di);
+        for (int q = 0; q < nv; ++q) {
+            j += (kap[q] - di[q]) * stride;
+            stride *= B.rad[q];
+        }
+        series term = s_mul(&PU[i], &PF[j], hi);
+        prod = s_add(&prod, &term, hi);
+    }
+    for (int j = 0; j < S->d; ++j) {
+        if (is_singular(S, j) || (S->a[j] == 0 && S->b[j] == 0.0)) continue;
+        cplx lg = clog((cplx)t[j]);
+        series f = s_exp_eps(S->b[j] * lg, hi);
+        f = s_scale(&f, cexp((double)S->a[j] * lg));
+        prod = s_mul(&prod, &f, hi);
+    }
+    return prod;
 }
 
 /* The eps-expanded integrand at the transformed point t (omt = 1 - t):
@@ -349,12 +481,15 @@ static series dG_series(const orc_sector *S, const double *tp, int q, int hi, in
  *         prod_{j in V} (1/(b_j eps) - t_j^{-1+b_j eps}) prod_{j in S\V} t_j^{-1+b_j eps},
  * which integrates over [0,1]^d to the Laurent expansion of the sector
  * integral (each j in S: int t^{-1+b eps} g = g(0)/(b eps) + int t^{-1+b eps}(g - g(0))).
- * A variable with a_j = -p, p = 2, takes the Taylor subtraction of degree 1:
- *   int t^{-p+b eps} g = sum_{k<p} g^(k)(0)/k! / (k - p + 1 + b eps)
- *                        + int t^{-p+b eps} (g - sum_{k<p} g^(k)(0) t^k / k!),
- * so per singular variable the states are "t kept" (factor t^{-p+b eps})
- * and k = 0..p-1 (t = 0, the k-th derivative of G, factor
- * 1/(k - p + 1 + b eps) - t^{k-p+b eps}); f sums over all state choices.
+ * A variable with a_j = -p, p >= 2, takes the Taylor subtraction of degree
+ * p - 1:
+ *   int t^{-p+b eps} g = sum_{k<p} g_k / (k - p + 1 + b eps)
+ *                        + int t^{-p+b eps} (g - sum_{k<p} g_k t^k),
+ * g_k the k-th Taylor coefficient of g at t = 0, so per singular variable the
+ * states are "t kept" (factor t^{-p+b eps}) and k = 0..p-1 (t = 0, Taylor
+ * coefficient k of G in that variable, factor 1/(k - p + 1 + b eps) -
+ * t^{k-p+b eps}); f sums over all state choices, with the mixed Taylor
+ * coefficient in the variables set to 0.
  * Returns coefficients of eps^lo .. eps^hi in out[(o - lo)]. */
 static void integrand_series(const orc_sector *S, const double *t, const double *omt, int lo,
                              int hi, cplx *out, double *cond, int *signfail) {
@@ -376,16 +511,24 @@ static void integrand_series(const orc_sector *S, const double *t, const double 
         nstates *= radix[q];
     }
     for (int st = 0; st < nstates; ++st) {
-        int state[ORC_SMAX], rem = st, dq = -1;
+        int state[ORC_SMAX], rem = st, nv = 0, V[ORC_SMAX], kap[ORC_SMAX], taylor = 0;
         double tp[ORC_DMAX], omtp[ORC_DMAX];
         for (int j = 0; j < d; ++j) { tp[j] = t[j]; omtp[j] = omt[j]; }
         for (int q = 0; q < ns; ++q) {
             state[q] = rem % radix[q];
             rem /= radix[q];
-            if (state[q] > 0) { tp[sing[q]] = 0.0; omtp[sing[q]] = 1.0; }
-            if (state[q] == 2) dq = sing[q];
+            if (state[q] > 0) {
+                tp[sing[q]] = 0.0;
+                omtp[sing[q]] = 1.0;
+                V[nv] = sing[q];
+                kap[nv++] = state[q] - 1;
+                if (state[q] > 1) taylor = 1;
+            }
         }
-        series term = dq >= 0 ? dG_series(S, tp, dq, H, signfail) : G_series(S, tp, omtp, H, signfail);
+        /* every Taylor order 0: G itself at t_V = 0; else the Taylor coefficient
+         * (undeformed sectors; the loader rejects the rest) */
+        if (taylor && S->deform) abort();
+        series term = taylor ? taylor_G(S, t, nv, V, kap, H) : G_series(S, tp, omtp, H, signfail);
         for (int q = 0; q < ns; ++q) {
             int j = sing[q];
             int p = -S->a[j];

@@ -86,9 +86,9 @@ def decompose(U: LinPoly, F: LinPoly, u0, u1, f0, f1, *, deform=False, max_depth
                 if Fraction(x).denominator != 1:
                     raise DecompositionError("non-integer monomial exponent")
                 aa.append(int(x))
-                if aa[-1] < -2:
-                    raise DecompositionError(f"sector {origin}: exponent a_{j}={aa[-1]} < -2 "
-                                             "needs subtraction beyond degree 1")
+                if aa[-1] < -4:
+                    raise DecompositionError(f"sector {origin}: exponent a_{j}={aa[-1]} < -4 "
+                                             "needs subtraction beyond degree 3")
                 if aa[-1] <= -1 and b[j] == 0:
                     raise DecompositionError(f"sector {origin}: unregulated singularity in t_{j}")
             out.append(Sector(Us.nvars, aa, [Fraction(x) for x in b], Us, Fs,

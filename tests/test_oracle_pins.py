@@ -24,7 +24,7 @@ from paper_2305_19768_gb300.inputs.secdec import Sector
 from golden_values import closed_form
 
 
-def rqmc_integral(I, inv, n, m, lo, norders, lam=None, seed=1):
+def rqmc_integral(I, inv, n, m, lo, norders, lam=None, seed=1, transform=0):
     """Oracle estimate of the full integral: prefactor x sum of sectors.
     Returns (mean [norders] complex at orders lo.., variance (re+im) per order)."""
     d = I.dmax
@@ -33,7 +33,7 @@ def rqmc_integral(I, inv, n, m, lo, norders, lam=None, seed=1):
     sno = lo + norders - 1 - I.prefactor_lo - slo + 1
     acc = np.zeros((m, sno), dtype=complex)
     for si in range(len(I.sectors)):
-        v = oracle.SectorView(I, si, inv, lam)
+        v = oracle.SectorView(I, si, inv, lam, transform=transform)
         dl = oracle.shifts(seed, si, m, I.sectors[si].d)
         out, _, _ = oracle.shift_sums(v, n, z[:I.sectors[si].d], dl, slo, sno)
         acc += out[..., 0] + 1j * out[..., 1]
@@ -355,6 +355,15 @@ def test_baker_transform_moments_and_triangle():
 
 
 # ---------------------------------------------------------------- a_j = -2: subtraction of degree 1
+# These run with the baker transform: under korobov3 the subtracted integrand's
+# border cancellation (about 2^-53 |g| t^-2 at t ~ 35 u^4, weight ~ u^3) leaves
+# the eps^0 and higher estimates off by O(10^2) with a shift spread just as
+# large at these lattice sizes, and a within-n-sigma check against the exact
+# value would pass whatever the integrand. assert_sharp() rules that out.
+def assert_sharp(var, exact, rel):
+    assert np.max(np.sqrt(var)) <= rel * np.max(np.abs(exact)), (np.sqrt(var), exact)
+
+
 def test_subtraction_degree1_1d_exact_series():
     # int_0^1 t^{-2 + b eps} G(t) dt, G = 1 + 2 t + 3 t^2 - t^3: sum_k c_k / (k - 1 + b eps)
     b = 1.25
@@ -362,8 +371,9 @@ def test_subtraction_degree1_1d_exact_series():
     I = _toy_integral(1, [-2], [b], G)
     lo, no = -1, 4
     exact = sum(c * _series_of_inverse_linear(e[0] - 1, b, lo, no) for e, c in G.items())
-    mean, var = rqmc_integral(I, [], next_prime(8000), 8, lo, no)
+    mean, var = rqmc_integral(I, [], next_prime(40000), 8, lo, no, transform=1)
     assert_within(mean, var, exact, rel=1e-10)
+    assert_sharp(var, exact, 2e-4)
 
 
 def test_subtraction_degree1_2d_nonseparable_exact_series():
@@ -377,8 +387,9 @@ def test_subtraction_degree1_2d_nonseparable_exact_series():
         li, lj = (-1 if i == 1 else 0), (-1 if j == 0 else 0)
         exact += c * combine.laurent_product(li, _series_of_inverse_linear(i - 1, b1, li, no + 2),
                                              lj, _series_of_inverse_linear(j, b2, lj, no + 2), lo, no)
-    mean, var = rqmc_integral(I, [], next_prime(40000), 8, lo, no)
+    mean, var = rqmc_integral(I, [], next_prime(40000), 8, lo, no, transform=1)
     assert_within(mean, var, exact, rel=1e-9)
+    assert_sharp(var, exact, 2e-4)
 
 
 def test_subtraction_degree1_with_eps_exponent():
@@ -409,5 +420,6 @@ def test_subtraction_degree1_with_eps_exponent():
             f = (lambda t, i=i, j=k - i: (b * math.log(t)) ** i / math.factorial(i) * bracket(t, j) / t ** 2)
             tot += quad(f, 0, 1, epsabs=1e-15, epsrel=1e-13, limit=400)[0]
         exact[k - lo] += tot
-    mean, var = rqmc_integral(I, [], next_prime(20000), 8, lo, no)
+    mean, var = rqmc_integral(I, [], next_prime(40000), 8, lo, no, transform=1)
     assert_within(mean, var, exact, rel=1e-9)
+    assert_sharp(var, exact, 2e-4)
