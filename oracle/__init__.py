@@ -98,8 +98,8 @@ class SectorView:
                 box *= -int(x)
         if box > 1 and s.deform and lam is not None:
             raise ValueError("Taylor subtraction beyond degree 0 (a_j <= -2) needs an undeformed sector")
-        if box > 64:
-            raise ValueError("the subtraction's Taylor box prod_j (-a_j) exceeds 64 coefficients")
+        if box > 128:
+            raise ValueError("the subtraction's Taylor box prod_j (-a_j) exceeds 128 coefficients")
         self.d = s.d
         self.Ue, self.Uc = integral.coefficients_at(sector, "U", inv)
         self.Fe, self.Fc = integral.coefficients_at(sector, "F", inv)

@@ -196,6 +196,13 @@ static cplx s_coef(const series *a, int order) {
     if (k < 0 || k >= a->n) return 0.0;
     return a->c[k];
 }
+/* |Re| + |Im| of every coefficient: products of such series bound the
+ * magnitudes of everything a product of the original series sums */
+static series s_mass(const series *a) {
+    series r = *a;
+    for (int i = 0; i < r.n; ++i) r.c[i] = fabs(creal(a->c[i])) + fabs(cimag(a->c[i]));
+    return r;
+}
 
 /* ---------------- polynomials ---------------- */
 static cplx cipow(cplx x, int e) {
@@ -307,7 +314,11 @@ static series G_series(const orc_sector *S, const double *tp, const double *omtp
         if (a == 0.0 && b == 0.0) continue;
         cplx lg = clog(base);
         series f = s_exp_eps(b * lg, hi);
-        f = s_scale(&f, cexp(a * lg));
+        /* base^a: the monomial factor itself; for a real positive base the
+         * library power (within an ulp), since exp(a ln base) would carry the
+         * rounding of ln base times |a ln base| */
+        cplx pa = (cimag(base) == 0.0 && creal(base) > 0.0) ? pow(creal(base), a) : cexp(a * lg);
+        f = s_scale(&f, pa);
         G = s_mul(&G, &f, hi);
     }
     {
@@ -328,7 +339,7 @@ static series G_series(const orc_sector *S, const double *tp, const double *omtp
 /* ---------------- Taylor coefficients of G in the zeroed variables ---------------- */
 /* Truncated multivariate power series ("jets") in the variables t_{V[0..nv-1]}
  * over the box 0 <= k_q < rad[q]; flat index sum_q k_q prod_{r<q} rad[r]. */
-#define ORC_JMAX 64
+#define ORC_JMAX 128
 typedef struct {
     int nv;
     int rad[ORC_SMAX];
@@ -375,7 +386,7 @@ static void jet_mul(const jbox *B, const cplx *a, const cplx *b, cplx *c) {
  * P0^{alpha - k} = P0^{e0 - k} exp(e1 eps ln P0). delta^k vanishes in the box
  * beyond k = sum_q (rad_q - 1). */
 static void jet_power(const orc_sector *S, int isF, const double *t, const int *V, const jbox *B,
-                      int hi, series *out) {
+                      int hi, series *out, series *mass) {
     int d = S->d;
     int nP = isF ? S->nF : S->nU;
     const int *ex = isF ? S->Fe : S->Ue;
@@ -383,8 +394,8 @@ static void jet_power(const orc_sector *S, int isF, const double *t, const int *
     double e0 = isF ? S->f0 : S->u0, e1 = isF ? S->f1 : S->u1;
     int inV[ORC_DMAX] = {0};
     for (int q = 0; q < B->nv; ++q) inV[V[q]] = 1;
-    cplx delta[ORC_JMAX];
-    for (int k = 0; k < B->size; ++k) delta[k] = 0.0;
+    cplx delta[ORC_JMAX], dabs[ORC_JMAX];
+    for (int k = 0; k < B->size; ++k) delta[k] = dabs[k] = 0.0;
     for (int m = 0; m < nP; ++m) {
         int idx = 0, stride = 1, inside = 1;
         for (int q = 0; q < B->nv; ++q) {
@@ -398,26 +409,31 @@ static void jet_power(const orc_sector *S, int isF, const double *t, const int *
         for (int j = 0; j < d; ++j)
             if (!inV[j]) v *= cipow(t[j], ex[m * d + j]);
         delta[idx] += v;
+        dabs[idx] += cabs(v);
     }
     cplx P0 = delta[0];
     if (cimag(P0) == 0.0) P0 = CMPLX(creal(P0), isF ? -0.0 : 0.0);   /* F - i0 */
     delta[0] = 0.0;
+    dabs[0] = 0.0;
     cplx lg = clog(P0);
     series pe = s_exp_eps(e1 * lg, hi);                /* P0^{e1 eps} */
+    series pem = s_mass(&pe);
     int K = 0;
     for (int q = 0; q < B->nv; ++q) K += B->rad[q] - 1;
     for (int i = 0; i < B->size; ++i) {
         memset(&out[i], 0, sizeof(series));
         out[i].lo = 0;
         out[i].n = hi + 1;
+        if (mass) mass[i] = out[i];
     }
-    cplx dk[ORC_JMAX];                                  /* delta^k */
-    for (int i = 0; i < B->size; ++i) dk[i] = 0.0;
-    dk[0] = 1.0;
+    cplx dk[ORC_JMAX], dkabs[ORC_JMAX];                 /* delta^k, |delta|^k */
+    for (int i = 0; i < B->size; ++i) dk[i] = dkabs[i] = 0.0;
+    dk[0] = dkabs[0] = 1.0;
     series binom = s_const(1.0);
     for (int k = 0; k <= K; ++k) {
         if (k > 0) {
             jet_mul(B, dk, delta, dk);
+            jet_mul(B, dkabs, dabs, dkabs);
             series lin;                                  /* (e0 - (k - 1) + e1 eps) / k */
             memset(&lin, 0, sizeof lin);
             lin.lo = 0; lin.n = 2;
@@ -427,10 +443,17 @@ static void jet_power(const orc_sector *S, int isF, const double *t, const int *
         }
         series c = s_mul(&binom, &pe, hi);
         c = s_scale(&c, cexp((e0 - k) * lg));
+        series bm = s_mass(&binom);
+        series cm = s_mul(&bm, &pem, hi);
+        cm = s_scale(&cm, cabs(cexp((e0 - k) * lg)));
         for (int i = 0; i < B->size; ++i)
-            if (dk[i] != 0.0) {
+            if (dk[i] != 0.0 || dkabs[i] != 0.0) {
                 series term = s_scale(&c, dk[i]);
                 out[i] = s_add(&out[i], &term, hi);
+                if (mass) {
+                    series tm = s_scale(&cm, dkabs[i]);
+                    mass[i] = s_add(&mass[i], &tm, hi);
+                }
             }
     }
 }
@@ -441,7 +464,7 @@ static void jet_power(const orc_sector *S, int isF, const double *t, const int *
  * only U and F depend on t_V: the coefficient is the regular factor times
  * sum_{k' <= kap} [U^.]_{k'} [F^.]_{kap - k'}. */
 static series taylor_G(const orc_sector *S, const double *t, int nv, const int *V, const int *kap,
-                       int hi) {
+                       int hi, series *massout) {
     jbox B;
     B.nv = nv;
     B.size = 1;
@@ -450,12 +473,13 @@ static series taylor_G(const orc_sector *S, const double *t, int nv, const int *
         B.size *= B.rad[q];
     }
     if (B.size > ORC_JMAX) abort();
-    series PU[ORC_JMAX], PF[ORC_JMAX];
-    jet_power(S, 0, t, V, &B, hi, PU);
-    jet_power(S, 1, t, V, &B, hi, PF);
-    series prod;
+    series PU[ORC_JMAX], PF[ORC_JMAX], MU[ORC_JMAX], MF[ORC_JMAX];
+    jet_power(S, 0, t, V, &B, hi, PU, MU);
+    jet_power(S, 1, t, V, &B, hi, PF, MF);
+    series prod, mass;
     memset(&prod, 0, sizeof prod);
     prod.lo = 0; prod.n = hi + 1;
+    mass = prod;
     for (int i = 0; i < B.size; ++i) {
         int di[ORC_SMAX], j = 0, stride = 1;
         jbox_digits(&B, i, di);
@@ -465,14 +489,19 @@ static series taylor_G(const orc_sector *S, const double *t, int nv, const int *
         }
         series term = s_mul(&PU[i], &PF[j], hi);
         prod = s_add(&prod, &term, hi);
+        series tm = s_mul(&MU[i], &MF[j], hi);
+        mass = s_add(&mass, &tm, hi);
     }
     for (int j = 0; j < S->d; ++j) {
         if (is_singular(S, j) || (S->a[j] == 0 && S->b[j] == 0.0)) continue;
         cplx lg = clog((cplx)t[j]);
         series f = s_exp_eps(S->b[j] * lg, hi);
-        f = s_scale(&f, cexp((double)S->a[j] * lg));
+        f = s_scale(&f, pow(t[j], (double)S->a[j]));
         prod = s_mul(&prod, &f, hi);
+        series fm = s_mass(&f);
+        mass = s_mul(&mass, &fm, hi);
     }
+    if (massout) *massout = mass;
     return prod;
 }
 
@@ -528,7 +557,8 @@ static void integrand_series(const orc_sector *S, const double *t, const double 
         /* every Taylor order 0: G itself at t_V = 0; else the Taylor coefficient
          * (undeformed sectors; the loader rejects the rest) */
         if (taylor && S->deform) abort();
-        series term = taylor ? taylor_G(S, t, nv, V, kap, H) : G_series(S, tp, omtp, H, signfail);
+        series gmass;
+        series term = taylor ? taylor_G(S, t, nv, V, kap, H, &gmass) : G_series(S, tp, omtp, H, signfail);
         for (int q = 0; q < ns; ++q) {
             int j = sing[q];
             int p = -S->a[j];
@@ -554,11 +584,17 @@ static void integrand_series(const orc_sector *S, const double *t, const double 
                 fac = tpow;
             }
             term = s_mul(&term, &fac, H);
+            if (taylor) {
+                series fm = s_mass(&fac);
+                gmass = s_mul(&gmass, &fm, H);
+            }
         }
         total = s_add(&total, &term, hi);
+        /* the mass of what cancels: |term| per order; for a Taylor state the
+         * magnitudes of the binomial-series terms inside its coefficient too */
         if (cond)
             for (int o = lo; o <= hi; ++o) {
-                cplx c = s_coef(&term, o);
+                cplx c = s_coef(taylor ? &gmass : &term, o);
                 cond[o - lo] += fabs(creal(c)) + fabs(cimag(c));
             }
     }
