@@ -79,6 +79,14 @@ def _workloads():
             nord=3, n=10007, m=32, deform=True,
             desc="box1L_massless deformed, 1024 (s,t) s~U[5,20] t~U[-8,-1] seed 3, 12 sectors d=3, "
                  "eps^-2..eps^0, n={n} CBC, m={m} shifts"),
+        # one-loop massless box in D = 2 - 2 eps: every sector has one or two
+        # exponents a_j = -2 (Taylor subtraction of degree 1); the baker transform,
+        # under which the subtracted remainder keeps its accuracy near the border
+        "box1L_massless_d2": dict(
+            make=lambda: w.box_massless_d2(), kin=[[-3.0, -2.0]], lo=-2, nord=3, n=100003, m=32, deform=False,
+            transform=1,
+            desc="box1L_massless in D=2-2eps s=-3 t=-2, 12 sectors d=3 with a_j=-2 (Taylor subtraction), "
+                 "eps^-2..eps^0, n={n} CBC, m={m} shifts, baker transform"),
         # the default: two-loop planar massless double box, Euclidean point
         "box2L_planar_massless": dict(
             make=lambda method="iterative": w.double_box_massless(method=method), kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
@@ -157,7 +165,7 @@ def clock_sampler_stop(proc, fh, path, device_index):
             "samples": len(sm)}
 
 
-def oracle_sample(I, inv, n, m, seed, ks, lo, nord, lam=None):
+def oracle_sample(I, inv, n, m, seed, ks, lo, nord, lam=None, transform=0):
     """Oracle per-shift sums of every sector at one kinematic point over lattice
     indices [0, ks): returns (evaluations, seconds, threads)."""
     import oracle
@@ -169,7 +177,7 @@ def oracle_sample(I, inv, n, m, seed, ks, lo, nord, lam=None):
         sec = I.sectors[s]
         _, z = lattice_for(n, sec.d)
         dl = oracle.shifts(seed, s, m, sec.d)
-        view = oracle.SectorView(I, s, inv, lam=None if lam is None else lam[s])
+        view = oracle.SectorView(I, s, inv, lam=None if lam is None else lam[s], transform=transform)
         oracle.shift_sums(view, n, z, dl, lo, nord, k0=0, k1=ks)
         evals += m * ks
     return evals, time.perf_counter() - t0, oracle.max_threads()
@@ -194,11 +202,12 @@ def run_reference(args):
     ks = oracle_ks(W, nsec)
     inv = W["kin"][0]
     lam = [1.0] * nsec if W["deform"] else None
+    tr = W.get("transform", 0)
     for _ in range(args.warmup):
-        oracle_sample(I, inv, n, m, 1, ks, W["lo"], W["nord"], lam)
+        oracle_sample(I, inv, n, m, 1, ks, W["lo"], W["nord"], lam, tr)
     tot_e, tot_t, thr = 0, 0.0, 1
     for _ in range(args.steps):
-        e, t, thr = oracle_sample(I, inv, n, m, 1, ks, W["lo"], W["nord"], lam)
+        e, t, thr = oracle_sample(I, inv, n, m, 1, ks, W["lo"], W["nord"], lam, tr)
         tot_e += e
         tot_t += t
     val = tot_e / tot_t
@@ -414,6 +423,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box1L_massless_physical",
+                             "box1L_massless_d2",
                              "box2L_planar_massless"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--decomposition", default="iterative", choices=["iterative", "geometric"],
@@ -460,6 +470,8 @@ def main():
         opts["ppt"] = args.ppt
     if args.precision == "mixed":
         opts["precision"] = qmc.QMC_PRECISION_MIXED
+    if W.get("transform", 0):
+        opts["transform"] = W["transform"]
     ctx = qmc.qmc_create(local, **opts)
     qmc.load_lattice_table(ctx)
     iid = qmc.qmc_load_sectors_mem(ctx, I.to_text())
@@ -589,7 +601,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ks = oracle_ks(dict(W, m=args.shifts, d=max(sec.d for sec in I.sectors)), nsec)
-        e, t, thr = oracle_sample(I, W["kin"][0], args.n, args.shifts, 1, ks, LO, NORD, lam0)
+        e, t, thr = oracle_sample(I, W["kin"][0], args.n, args.shifts, 1, ks, LO, NORD, lam0, W.get("transform", 0))
         cpu = {"value": e / t, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"all {nsec} sectors x {args.shifts} shifts x lattice indices [0,{ks}) of n={args.n}"
                          " at the first kinematic point"}

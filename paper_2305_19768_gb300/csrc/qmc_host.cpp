@@ -165,25 +165,32 @@ uint32_t pack_exps(const int *e, int d) {
 
 int classify(qmc_ctx *ctx, HostSector &S, int si) {
     S.ns = 0;
-    int n2 = 0;
+    int box = 1;   // Taylor coefficients of the full subtraction box, prod_q p_q
     for (int j = 0; j < S.d; ++j) {
-        if (S.a[j] < -2)
-            return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d < -2 needs subtraction beyond degree 1", si, j, S.a[j]);
+        if (S.a[j] < -QMC_PMAX)
+            return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d needs Taylor subtraction beyond degree %d", si, j,
+                        S.a[j], QMC_PMAX - 1);
         if (S.a[j] <= -1) {
             if (S.b[j] == 0.0) return fail(ctx, QMC_E_INVAL, "sector %d: unregulated 1/t_%d", si, j);
             ++S.ns;
-            if (S.a[j] == -2) ++n2;
+            box *= -S.a[j];
         } else if (S.a[j] > QMC_EMAX) {
             return fail(ctx, QMC_E_INVAL, "sector %d: a_%d=%d above %d", si, j, S.a[j], QMC_EMAX);
         }
     }
     if (S.ns > QMC_SMAX) return fail(ctx, QMC_E_INVAL, "sector %d: %d singular variables > %d", si, S.ns, QMC_SMAX);
-    if (n2) {
-        if (n2 > 1 || S.deform || S.d > 3 || S.ns > 2)
-            return fail(ctx, QMC_E_INVAL,
-                        "sector %d: a_j = -2 is supported for one variable of an undeformed sector with d <= 3 "
-                        "and at most 2 singular variables", si);
-        S.cls = QMC_CLASS_REAL3H;
+    if (box > 1) {
+        // some a_j <= -2: Taylor subtraction (undeformed sectors)
+        if (S.deform)
+            return fail(ctx, QMC_E_INVAL, "sector %d: a_j <= -2 (Taylor subtraction) needs an undeformed sector", si);
+        if (S.d <= 3 && S.ns <= 2 && box <= QMC_JMAX3) {
+            S.cls = QMC_CLASS_REAL3H;
+        } else if (box <= QMC_JMAX6) {
+            S.cls = QMC_CLASS_REAL6H;
+        } else {
+            return fail(ctx, QMC_E_INVAL, "sector %d: subtraction box of %d Taylor coefficients > %d", si, box,
+                        QMC_JMAX6);
+        }
         return QMC_OK;
     }
     if (S.deform) {
@@ -226,12 +233,10 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
         H.f1i = (int32_t)S.f1;
     }
     int q = 0;
-    H.p2slot = -1;
     for (int j = 0; j < S.d; ++j) {
         H.a[j] = S.a[j];
         H.b[j] = S.b[j];
         if (bint) H.bi[j] = (int32_t)S.b[j];
-        if (S.a[j] == -2) H.p2slot = q;
         if (S.a[j] <= -1) H.sing[q++] = j;
         else if (S.a[j] != 0 || S.b[j] != 0.0) H.regular_mask |= 1 << j;
     }
@@ -292,24 +297,6 @@ int pack_sector(qmc_ctx *ctx, const HostSector &S, int si, int ninv, std::vector
         }
         return out;
     };
-    if (H.p2slot >= 0) {
-        // dU/dt_q and dF/dt_q of the a = -2 variable (subtraction of degree 1)
-        const int j2 = H.sing[H.p2slot];
-        const int base = (int)local.size();
-        std::vector<Term> du = deriv(S.U, j2), df = deriv(S.F, j2);
-        H.dqUoff = (int)local.size() - base;
-        H.dqUn = (int)du.size();
-        for (const Term &T : du) {
-            int rc = push(T);
-            if (rc) return rc;
-        }
-        H.dqFoff = (int)local.size() - base;
-        H.dqFn = (int)df.size();
-        for (const Term &T : df) {
-            int rc = push(T);
-            if (rc) return rc;
-        }
-    }
     if (S.deform) {
         // dF/dt_j and d2F/dt_j dt_k (j <= k) as monomial tables, merged by exponent
         int base = (int)local.size();

@@ -10,6 +10,9 @@
 #define QMC_EMAX 4          // largest exponent of one variable in one monomial
 #define QMC_MAXMONO 160     // monomials per sector (U, F and, if deformed, dF, d2F)
 #define QMC_NGROUP (1 << QMC_SMAX)
+#define QMC_PMAX 4          // largest p of an endpoint singularity t^{-p + b eps} (Taylor degree p - 1)
+#define QMC_JMAX3 16        // Taylor coefficients per subtraction box, d <= 3 class (prod_q p_q)
+#define QMC_JMAX6 72        // the same, d <= 6 class (4 x 3 x 3 x 2)
 #define QMC_NHESS (QMC_DMAX * (QMC_DMAX + 1) / 2)
 
 // One monomial c(inv) * prod_j t_j^{e_j}; exponents packed 4 bits per variable.
@@ -34,8 +37,6 @@ struct QmcSectorDev {
                                             // corner); bit 1: every b_j too (one complex log per corner)
     int32_t bi[QMC_DMAX];                   // b_j, u1, f1 as integers where bit 1 / bit 0 of pad1 is set
     int32_t u1i, f1i;
-    int32_t p2slot;                         // singular slot with a = -2 (subtraction of degree 1), or -1
-    int32_t dqUoff, dqUn, dqFoff, dqFn;     // dU/dt, dF/dt of that variable (relative to monoF + nF)
     int32_t gU[QMC_NGROUP + 1];
     int32_t gF[QMC_NGROUP + 1];
     int32_t dFoff[QMC_DMAX], dFn[QMC_DMAX];   // relative to monoF + nF
@@ -95,15 +96,16 @@ enum QmcClass {
     QMC_CLASS_REAL6S = 5,  // former split of REAL6 (<= 2 singular variables); now the REAL6 kernel
     QMC_CLASS_REAL6SM = 6, // its mixed-precision variant (the REAL6M kernel)
     QMC_CLASS_CPLX3M = 7,  // CPLX3 with FP32 monomial products (derivatives of F, U and F at z)
-    QMC_CLASS_REAL3H = 8,  // real, d <= 3, <= 2 singular variables, one with a = -2 (degree-1 subtraction)
+    QMC_CLASS_REAL3H = 8,  // real, d <= 3, <= 2 singular variables, some with a <= -2 (Taylor subtraction)
     QMC_CLASS_REAL6T = 9,  // former split of REAL6 (3 singular variables); now the REAL6 kernel
     QMC_CLASS_REAL6TM = 10,// its mixed-precision variant (the REAL6M kernel)
-    QMC_NCLASS = 11
+    QMC_CLASS_REAL6H = 11, // real, d <= 6, <= 4 singular variables, some with a <= -2 (Taylor subtraction)
+    QMC_NCLASS = 12
 };
 
 static inline bool qmc_class_big(int cls) {
     return cls == QMC_CLASS_REAL6 || cls == QMC_CLASS_REAL6M || cls == QMC_CLASS_REAL6S || cls == QMC_CLASS_REAL6SM ||
-           cls == QMC_CLASS_REAL6T || cls == QMC_CLASS_REAL6TM;
+           cls == QMC_CLASS_REAL6T || cls == QMC_CLASS_REAL6TM || cls == QMC_CLASS_REAL6H;
 }
 // Series length (orders) each class supports: K + ns + 1 <= class_lmax.
 static inline int qmc_class_lmax(int cls) { return qmc_class_big(cls) ? 6 : 4; }

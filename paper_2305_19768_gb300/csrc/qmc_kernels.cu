@@ -1135,137 +1135,316 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
     assemble_fixed<NS, HI, double>(BV, LV, tb, lt, bq, A_empty, S.invb_full, resN);
 }
 
-// ---------------------------------------------------------------- degree-1 subtraction
-// One singular variable q with a_q = -2 (the others a = -1): its endpoint
-// singularity is removed with the Taylor polynomial of degree 1,
-//   int t^{-2+b eps} g = g(0)/(-1 + b eps) + g'(0)/(b eps)
-//                        + int t^{-2+b eps} (g - g(0) - t g'(0)),
-// and the a = -1 variables as in eval_real. Per singular variable the states
-// are 0 (t kept, factor t^{-p+b eps}) and k + 1 for k < p (t = 0, the k-th
-// t-derivative of G, factor 1/(k - p + 1 + b eps) - t^{k-p+b eps}); the
-// integrand sums over all state choices. G = C U^{u0+u1 eps} F^{f0+f1 eps}
-// (times the regular factors) depends on t_q only through U and F, so
-// dG/dt_q = G ((u0 + u1 eps) U_q / U + (f0 + f1 eps) F_q / F). Series run
-// over the orders -2..5 in fixed arrays; plain, not tuned: sectors with
-// a = -2 are rare.
-template <int LMAX>
-__device__ void eval_real_h(const TileSmem<LMAX> &S, const double (&t)[3], int lo, int hi, int nord,
-                            double (&res)[LMAX]) {
-    constexpr int NT = 8, OFF = 2;   // index i holds the order i - OFF
+// ---------------------------------------------------------------- Taylor subtraction
+// Sectors where some singular variables have a_q = -p_q, p_q >= 2 (undeformed).
+// Per singular variable the integrand takes
+//   t^{-p+b eps} g(t) + sum_{k<p} g_k [1/(k - p + 1 + b eps) - t^{k-p+b eps}],
+// g_k the k-th Taylor coefficient of g at t_q = 0, so that its integral over
+// [0,1] is that of t^{-p+b eps} g (the boundary terms g_k / (k - p + 1 + b eps)
+// plus the integral of the remainder). Grouped by the set V of variables at
+// t = 0, the terms of one V need the mixed Taylor coefficients G_kappa,
+// kappa_q < p_q, of G = C U^{u0+u1 eps} F^{f0+f1 eps} at t_V = 0 (only U and F
+// depend on t_V). Over the box of exponents, with U = U0 (1 + u) (u without
+// constant term) and L_U = ln(1 + u) as truncated power series ("jets"),
+//   U^{u0 + u1 eps} = U0^{u0} e^{eps u1 ln U0} exp(u0 L_U) exp(eps u1 L_U),
+// and the same for F; with A = u0 L_U + f0 L_F and B = u1 L_U + f1 L_F,
+//   G_kappa(eps) = C U0^{u0} F0^{f0} e^{eps Lam0} sum_i eps^i [exp(A) B^i / i!]_kappa,
+// where B^i vanishes beyond the box's total degree. Then
+//   f = sum_V base_V(eps) prod_{q not in V} t_q^{-p_q+b_q eps}
+//         sum_kappa G_kappa(eps) prod_{q in V} phi_q(kappa_q; eps),
+//   phi_q(k; eps) = 1/(k - p_q + 1 + b_q eps) - t_q^{k-p_q+b_q eps}.
+// Plain run-time loops over series and jets in local memory: such sectors are
+// few, and the code stays small.
+namespace taylor {
+// 1/k for k = 1..32 (k = 0 unused): series and jet recursions multiply by it
+__device__ __constant__ double inv_k[33] = {
+    0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,
+    1.0 / 9,    1.0 / 10,   1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17,
+    1.0 / 18,   1.0 / 19,   1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26,
+    1.0 / 27,   1.0 / 28,   1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32};
+
+// Series: index i holds the order i - OFF. out = a b truncated above order hmax.
+template <int NT, int OFF>
+__device__ __forceinline__ void ser_mul(const double *a, const double *b, double *out, int hmax) {
+#pragma unroll 1
+    for (int i = 0; i < NT; ++i) {
+        double v = 0.0;
+        if (i - OFF <= hmax) {
+#pragma unroll 1
+            for (int k = 0; k < NT; ++k) {
+                const int j = i + OFF - k;
+                if (j >= 0 && j < NT) v = fma(a[k], b[j], v);
+            }
+        }
+        out[i] = v;
+    }
+}
+
+// c = a b over the box: index i has packed digits dig[i] (4 bits per jet
+// dimension); a digit sum overflows its radix iff its nibble of
+// dig[i] + dig[j] + off reaches 8 (off holds 8 - radix per nibble), and
+// without overflow the flat index of the product term is i + j.
+__device__ __forceinline__ void jet_mul(const double *a, const double *b, double *c, int J, const uint16_t *dig,
+                                        uint32_t off) {
+#pragma unroll 1
+    for (int k = 0; k < J; ++k) c[k] = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < J; ++i) {
+        const double ai = a[i];
+#pragma unroll 1
+        for (int j = 0; i + j < J; ++j)
+            if ((((uint32_t)dig[i] + dig[j] + off) & 0x8888u) == 0u) c[i + j] = fma(ai, b[j], c[i + j]);
+    }
+}
+}  // namespace taylor
+
+template <int DMAX, int SMAX, int LMAX, int JMAX>
+__device__ __noinline__ void eval_real_taylor(const TileSmem<LMAX> &S, const double (&t)[DMAX], int lo, int hi,
+                                              int nord, double (&res)[LMAX]) {
+    constexpr int OFF = SMAX;            // series index i holds the order i - OFF
+    constexpr int NT = SMAX + LMAX;
+    constexpr int PMAX = QMC_PMAX;
     const QmcSectorDev &sec = S.sec;
     const int d = sec.d, ns = sec.ns;
     const uint64_t *tab = S.logtab;
-    const int Hm = hi + ns;          // orders every factor must carry
+    const int Hm = hi + ns;              // orders every factor must carry
+    // regular factors C = prod t_j^{a_j} and Lc = sum b_j ln t_j; slot of each variable
     double Cc = 1.0, Lc = 0.0;
+    int slot[DMAX];
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
+    for (int j = 0; j < DMAX; ++j) {
+        slot[j] = -1;
         if (j < d && ((sec.regular_mask >> j) & 1)) {
             if (sec.a[j] > 0) Cc *= ipow_signed<double>(t[j], 1.0, sec.a[j]);
             if (sec.b[j] != 0.0) Lc = fma(sec.b[j], qlog(t[j], tab), Lc);
         }
-    double ts[2] = {1.0, 1.0}, lts[2] = {0.0, 0.0}, bs[2] = {0.0, 0.0};
-    int ps[2] = {1, 1}, js[2] = {0, 0};
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-        if (q < ns) {
-            const int j = sec.sing[q];
-            js[q] = j;
-            ts[q] = j == 0 ? t[0] : (j == 1 ? t[1] : t[2]);
-            lts[q] = qlog(ts[q], tab);
-            bs[q] = sec.b[j];
-            ps[q] = -sec.a[j];
+    }
+    // per singular slot: psi_q = t^{-p+b eps} (kept) and phi_q(k) (at t = 0)
+    double psi[SMAX][NT];
+    double phi[SMAX][PMAX][NT];
+    int p[SMAX];
+#pragma unroll 1
+    for (int q = 0; q < ns; ++q) {
+        const int j = sec.sing[q];
+        slot[j] = q;
+        p[q] = -sec.a[j];
+        const double tq = t[j], tinv = qrcp(tq), bq = sec.b[j];
+        const double bl = bq * qlog(tq, tab);
+        const double rb = qrcp(bq);
+        double E[NT];                    // e^{eps b ln t}: orders 0..Hm
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) E[i] = 0.0;
+        double e = 1.0;
+#pragma unroll 1
+        for (int i = 0; i <= Hm; ++i) {
+            E[OFF + i] = e;
+            e = e * bl * taylor::inv_k[i + 1];
         }
+        const double tp = ipow_signed<double>(tq, tinv, -p[q]);
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) psi[q][i] = tp * E[i];
+#pragma unroll 1
+        for (int k = 0; k < p[q]; ++k) {
+            const double c = ipow_signed<double>(tq, tinv, k - p[q]);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) phi[q][k][i] = -c * E[i];
+            const int m = k - p[q] + 1;  // 1/(m + b eps), m <= 0
+            if (m == 0) {
+                phi[q][k][OFF - 1] += rb;
+            } else {
+                double v = -taylor::inv_k[-m];
+                const double r = -bq * v;
+#pragma unroll 1
+                for (int i = 0; i <= Hm; ++i) {
+                    phi[q][k][OFF + i] += v;
+                    v *= r;
+                }
+            }
+        }
+    }
+    double tpw[DMAX][QMC_EMAX];
+    powers<DMAX, double>(t, d, sec.pad0, tpw);
     double acc[NT];
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < NT; ++i) acc[i] = 0.0;
-    const int r0 = ns > 0 ? ps[0] + 1 : 1, r1 = ns > 1 ? ps[1] + 1 : 1;
-    for (int s0 = 0; s0 < r0; ++s0)
-        for (int s1 = 0; s1 < r1; ++s1) {
-            const int st[2] = {s0, s1};
-            double tc[3] = {t[0], t[1], t[2]};
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (q < ns && st[q] > 0) {
-                    if (js[q] == 0) tc[0] = 0.0;
-                    if (js[q] == 1) tc[1] = 0.0;
-                    if (js[q] == 2) tc[2] = 0.0;
-                }
-            double tp[3][QMC_EMAX];
-            powers<3, double>(tc, d, sec.pad0, tp);
-            const double U = poly_sum<3, double>(S.exps, S.cval, 0, sec.nU, tp);
-            const double F = poly_sum<3, double>(S.exps, S.cval, sec.nU, sec.nU + sec.nF, tp);
-            double B = Cc;
-            B *= sec.u0_int ? ipow_signed<double>(U, qrcp(U), (int)sec.u0) : exp(sec.u0 * qlog(U, tab));
-            B *= sec.f0_int ? ipow_signed<double>(F, qrcp(F), (int)sec.f0) : exp(sec.f0 * qlog(F, tab));
-            const double Lam = Lc + sec.u1 * qlog(U, tab) + sec.f1 * qlog(F, tab);
-            double g[NT];
-#pragma unroll
-            for (int i = 0; i < NT; ++i) g[i] = 0.0;
-            double term = B;
-#pragma unroll
-            for (int i = 0; i + OFF < NT; ++i) {
-                if (i <= Hm) g[OFF + i] = term;
-                term = term * Lam * (1.0 / (i + 1));
+
+    double ju[JMAX], jf[JMAX], ja[JMAX], jb[JMAX], jx[JMAX], jy[JMAX];
+    double ei[LMAX][JMAX];
+    uint16_t dig[JMAX];
+#pragma unroll 1
+    for (int V = 0; V < (1 << ns); ++V) {
+        // jet dimensions: the slots in V with p >= 2
+        int rad[SMAX], stride[SMAX];
+        int J = 1, K = 0, nd = 0;
+        uint32_t off = 0;
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            rad[q] = 1;
+            stride[q] = 0;
+            if (((V >> q) & 1) && p[q] > 1) {
+                rad[q] = p[q];
+                stride[q] = J;
+                J *= p[q];
+                K += p[q] - 1;
+                off |= (uint32_t)(8 - p[q]) << (4 * nd);
+                ++nd;
             }
-            const int p2 = sec.p2slot;
-            if (p2 >= 0 && st[p2] == 2) {
-                const int db = sec.nU + sec.nF;
-                const double Uq = poly_sum<3, double>(S.exps, S.cval, db + sec.dqUoff, db + sec.dqUoff + sec.dqUn, tp);
-                const double Fq = poly_sum<3, double>(S.exps, S.cval, db + sec.dqFoff, db + sec.dqFoff + sec.dqFn, tp);
-                const double rU = Uq / U, rF = Fq / F;
-                const double al = fma(sec.u0, rU, sec.f0 * rF), be = fma(sec.u1, rU, sec.f1 * rF);
-#pragma unroll
-                for (int i = NT - 1; i >= 0; --i) g[i] = al * g[i] + (i > 0 ? be * g[i - 1] : 0.0);
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q >= ns) continue;
-                const int p = ps[q], sq = st[q];
-                const int c = sq == 0 ? -p : (sq - 1) - p;       // power of t in the factor
-                double fac[NT];
-                double e = ipow_signed<double>(ts[q], qrcp(ts[q]), c);
-                const double bl = bs[q] * lts[q];
-#pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    fac[i] = 0.0;
-                    if (i >= OFF && i - OFF <= Hm) {
-                        fac[i] = sq == 0 ? e : -e;
-                        e = e * bl * (1.0 / (i - OFF + 1));
-                    }
-                }
-                if (sq > 0) {
-                    const int m = sq - p;                          // 1/(m + b eps)
-                    if (m == 0) {
-                        fac[OFF - 1] += 1.0 / bs[q];
-                    } else {
-                        double v = 1.0 / m;
-#pragma unroll
-                        for (int i = OFF; i < NT; ++i) {
-                            if (i - OFF <= Hm) fac[i] += v;
-                            v *= -bs[q] / m;
-                        }
-                    }
-                }
-                double pr[NT];
-#pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    pr[i] = 0.0;
-#pragma unroll
-                    for (int k = 0; k < NT; ++k) {
-                        const int j = i + OFF - k;   // order(i) = order(k) + order(j)
-                        if (j >= 0 && j < NT) pr[i] = fma(g[k], fac[j], pr[i]);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < NT; ++i) g[i] = pr[i];
-            }
-#pragma unroll
-            for (int i = 0; i < NT; ++i) acc[i] += g[i];
         }
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) {
+            uint32_t w = 0;
+            int n4 = 0;
+#pragma unroll 1
+            for (int q = 0; q < ns; ++q)
+                if (rad[q] > 1) {
+                    w |= (uint32_t)((i / stride[q]) % rad[q]) << (4 * n4);
+                    ++n4;
+                }
+            dig[i] = (uint16_t)w;
+            ju[i] = 0.0;
+            jf[i] = 0.0;
+        }
+        // U and F over the box: monomials whose exponent in a zeroed variable
+        // is beyond the box (or > 0 where p = 1) drop out
+#pragma unroll 1
+        for (int m = 0; m < sec.nU + sec.nF; ++m) {
+            const uint32_t ex = S.exps[m];
+            double v = S.cval[m];
+            int idx = 0;
+            bool keep = true;
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j) {
+                const uint32_t ej = (ex >> (4 * j)) & 15u;
+                if (j >= d || ej == 0u) continue;
+                const int q = slot[j];
+                if (q >= 0 && ((V >> q) & 1)) {
+                    if ((int)ej >= rad[q]) keep = false;
+                    else idx += (int)ej * stride[q];
+                } else {
+                    v *= pow_sel<double>(tpw[j], ej);
+                }
+            }
+            if (!keep) continue;
+            if (m < sec.nU) ju[idx] += v;
+            else jf[idx] += v;
+        }
+        const double U0 = ju[0], F0 = jf[0];
+        const double rU = qrcp(U0), rF = qrcp(F0);
+        ju[0] = 0.0;
+        jf[0] = 0.0;
+#pragma unroll 1
+        for (int i = 1; i < J; ++i) {
+            ju[i] *= rU;
+            jf[i] *= rF;
+        }
+        // L = ln(1 + x) = x h, h = sum_{k<K} (-1)^k x^k / (k + 1) by Horner
+#pragma unroll 1
+        for (int w = 0; w < 2; ++w) {
+            double *x = w == 0 ? ju : jf;
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) jy[i] = 0.0;
+            jy[0] = ((K - 1) & 1 ? -1.0 : 1.0) * taylor::inv_k[K > 0 ? K : 1];
+#pragma unroll 1
+            for (int k = K - 2; k >= 0; --k) {
+                taylor::jet_mul(x, jy, jx, J, dig, off);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) jy[i] = jx[i];
+                jy[0] += (k & 1 ? -1.0 : 1.0) * taylor::inv_k[k + 1];
+            }
+            taylor::jet_mul(x, jy, jx, J, dig, off);
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) x[i] = K > 0 ? jx[i] : 0.0;
+        }
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) {
+            ja[i] = fma(sec.u0, ju[i], sec.f0 * jf[i]);
+            jb[i] = fma(sec.u1, ju[i], sec.f1 * jf[i]);
+        }
+        // exp(A) = 1 + A (1 + A/2 (1 + A/3 (...))) by Horner
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) jy[i] = 0.0;
+        jy[0] = 1.0;
+#pragma unroll 1
+        for (int k = K; k >= 1; --k) {
+            taylor::jet_mul(ja, jy, jx, J, dig, off);
+            const double r = taylor::inv_k[k];
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) jy[i] = jx[i] * r;
+            jy[0] += 1.0;
+        }
+        // E_i = exp(A) B^i / i!, i <= min(K, Hm)
+        const int Imax = K < Hm ? K : Hm;
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) ei[0][i] = jy[i];
+#pragma unroll 1
+        for (int n = 1; n <= Imax; ++n) {
+            taylor::jet_mul(ei[n - 1], jb, ei[n], J, dig, off);
+            const double r = taylor::inv_k[n];
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) ei[n][i] *= r;
+        }
+        // T = sum_kappa (sum_i eps^i E_i[kappa]) prod_{q in V} phi_q(kappa_q)
+        double T[NT];
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) T[i] = 0.0;
+#pragma unroll 1
+        for (int kap = 0; kap < J; ++kap) {
+            double P[NT], Q[NT];
+            bool first = true;
+#pragma unroll 1
+            for (int q = 0; q < ns; ++q) {
+                if (!((V >> q) & 1)) continue;
+                const int k = rad[q] > 1 ? (kap / stride[q]) % rad[q] : 0;
+                if (first) {
+#pragma unroll 1
+                    for (int i = 0; i < NT; ++i) P[i] = phi[q][k][i];
+                    first = false;
+                } else {
+                    taylor::ser_mul<NT, OFF>(P, phi[q][k], Q, Hm);
+#pragma unroll 1
+                    for (int i = 0; i < NT; ++i) P[i] = Q[i];
+                }
+            }
+            if (first) {                 // V empty: the factor 1
+#pragma unroll 1
+                for (int i = 0; i < NT; ++i) P[i] = i == OFF ? 1.0 : 0.0;
+            }
+            double g[NT];
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) g[i] = (i >= OFF && i - OFF <= Imax) ? ei[i - OFF][kap] : 0.0;
+            taylor::ser_mul<NT, OFF>(g, P, Q, Hm);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) T[i] += Q[i];
+        }
+        // base: C U0^{u0} F0^{f0} e^{eps Lam0} prod_{q not in V} psi_q
+        double Bv = Cc;
+        Bv *= sec.u0_int ? ipow_signed<double>(U0, rU, (int)sec.u0) : exp(sec.u0 * qlog(U0, tab));
+        Bv *= sec.f0_int ? ipow_signed<double>(F0, rF, (int)sec.f0) : exp(sec.f0 * qlog(F0, tab));
+        const double Lam = Lc + sec.u1 * qlog(U0, tab) + sec.f1 * qlog(F0, tab);
+        double base[NT], Q[NT];
+        double e = Bv;
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) base[i] = 0.0;
+#pragma unroll 1
+        for (int i = 0; i <= Hm; ++i) {
+            base[OFF + i] = e;
+            e = e * Lam * taylor::inv_k[i + 1];
+        }
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            if ((V >> q) & 1) continue;
+            taylor::ser_mul<NT, OFF>(base, psi[q], Q, Hm);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) base[i] = Q[i];
+        }
+        taylor::ser_mul<NT, OFF>(base, T, Q, Hm);
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) acc[i] += Q[i];
+    }
 #pragma unroll
     for (int o = 0; o < LMAX; ++o) {
         res[o] = 0.0;
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < NT; ++i)
             if (o < nord && i == lo + o + OFF) res[o] = acc[i];
     }
@@ -1678,7 +1857,7 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
                 eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
             } else {
                 if constexpr (HS) {
-                    eval_real_h<LMAX>(S, t, lo, hi, nord, res);
+                    eval_real_taylor<DMAX, SMAX, LMAX, (DMAX <= 3 ? QMC_JMAX3 : QMC_JMAX6)>(S, t, lo, hi, nord, res);
                 } else if constexpr (DMAX <= 3) {
                     // one instantiation per number of singular variables (uniform per tile)
                     if (S.sec.ns == 2) eval_real<DMAX, SMAX, LMAX, MIXED, 2>(S, t, lo, hi, nord, res);
@@ -2028,7 +2207,7 @@ int occupancy_cls(int block) {
 // instantiates (-2 / 0 for the others). The evaluator classes are compiled in
 // four translation units in parallel: part 0 the real d <= 3 classes (and
 // everything that is not an evaluator), part 1 the deformed classes, part 2
-// the d <= 6 classes, part 3 the degree-1 subtraction class.
+// the d <= 6 classes, part 3 the Taylor-subtraction classes.
 #define QMC_PART_FN2(name, part) name##_part##part
 #define QMC_PART_FN(name, part) QMC_PART_FN2(name, part)
 
@@ -2053,6 +2232,7 @@ extern "C" int QMC_PART_FN(qmc_k_launch_eval, QMC_PART)(int cls, const QmcLaunch
         case QMC_CLASS_REAL6TM: return launch_cls<6, 4, 6, false, true>(L, block, ppt, grid, st);
 #elif QMC_PART == 3
         case QMC_CLASS_REAL3H: return launch_cls<3, 2, 4, false, false, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_REAL6H: return launch_cls<6, 4, 6, false, false, true>(L, block, ppt, grid, st);
 #endif
         default: return -2;
     }
@@ -2075,6 +2255,7 @@ extern "C" int QMC_PART_FN(qmc_k_occupancy, QMC_PART)(int cls, int block) {
         case QMC_CLASS_REAL6TM: return occupancy_cls<6, 4, 6, false, true>(block);
 #elif QMC_PART == 3
         case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block);
+        case QMC_CLASS_REAL6H: return occupancy_cls<6, 4, 6, false, false, true>(block);
 #endif
         default: return 0;
     }

@@ -326,9 +326,107 @@ def deformed_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> 
     return w
 
 
+def _ser_mul_pairs(NT: int, OFF: int, hmax: int) -> int:
+    """FMAs of one truncated series product of the Taylor path (index i holds
+    the order i - OFF; output orders above hmax skipped)."""
+    return sum(1 for i in range(NT) if i - OFF <= hmax for k in range(NT) if 0 <= i + OFF - k < NT)
+
+
+def taylor_sector_work(sector, lo: int, norders: int) -> Work:
+    """Work of one evaluation of a sector with exponents a_j <= -2 (the
+    Taylor-subtraction classes), counted along the kernel's loops: run-time
+    series of NT = SMAX + LMAX orders, jets over the box prod_q p_q of each
+    zeroed set V (products of two jets: prod_q p_q (p_q + 1) / 2 FMAs)."""
+    d, sing, ns, _ = _sector_shape(sector)
+    hi = lo + norders - 1
+    p = [-int(sector.a[j]) for j in sing]
+    box = 1
+    for x in p:
+        box *= x
+    small = d <= 3 and ns <= 2 and box <= 16
+    SMAX, LMAX = (2, 4) if small else (4, 6)
+    NT, OFF = SMAX + LMAX, SMAX
+    Hm = hi + ns
+    smul = 2 * _ser_mul_pairs(NT, OFF, Hm)
+    w = Work()
+    w.fp64 += d - 1 + 2                        # korobov3 weight product, W = Ws^3
+    for j in range(d):                         # regular factors
+        if j in sing:
+            continue
+        a, b = int(sector.a[j]), float(sector.b[j])
+        if a > 0:
+            w.fp64 += a                        # t^a (a - 1) and Cc *= (1)
+        if b != 0.0:
+            w.log += 1
+            w.fp64 += 2
+    for pq in p:                               # per singular slot
+        w.recip(2)                             # 1/t, 1/b
+        w.log += 1
+        w.fp64 += 1                            # b ln t
+        w.fp64 += 2 * (Hm + 1)                 # e^{eps b ln t}
+        w.fp64 += (pq - 1) + NT                # t^-p, psi
+        for k in range(pq):
+            w.fp64 += max(pq - k - 1, 0) + NT  # t^{k-p}, phi
+            if k == pq - 1:
+                w.fp64 += 1                    # pole 1/b
+            else:
+                w.fp64 += 1 + 2 * (Hm + 1)     # 1/(m + b eps)
+    emax = max(sector.U.max_var_exponent(), sector.F.max_var_exponent(), 1)
+    w.fp64 += _powers(d, emax)
+    monos = list(sector.U.terms) + list(sector.F.terms)
+    u0, f0 = float(sector.u0), float(sector.f0)
+    for V in range(1 << ns):
+        rad = [p[q] if (V >> q) & 1 and p[q] > 1 else 1 for q in range(ns)]
+        J = 1
+        pairs = 1
+        for r in rad:
+            J *= r
+            pairs *= r * (r + 1) // 2
+        K = sum(r - 1 for r in rad)
+        jm = 2 * pairs                         # one jet product
+        for e in monos:                        # U and F over the box
+            keep = True
+            for j in range(d):
+                if e[j] == 0:
+                    continue
+                if j in sing and (V >> sing.index(j)) & 1:
+                    q = sing.index(j)
+                    if e[j] >= rad[q]:
+                        keep = False
+                else:
+                    w.fp64 += 1
+            if keep:
+                w.fp64 += 1
+        w.recip(2)                             # 1/U0, 1/F0
+        w.fp64 += 2 * (J - 1)
+        for _ in range(2):                     # ln(1 + x) by Horner
+            w.fp64 += 1 + max(K - 1, 0) * (jm + 2) + jm
+        w.fp64 += 6 * J                        # A, B
+        w.fp64 += K * (jm + J + 1)             # exp(A) by Horner
+        imax = min(K, Hm)
+        w.fp64 += imax * (jm + J)              # E_i = E_{i-1} B / i
+        inV = sum(1 for q in range(ns) if (V >> q) & 1)
+        w.fp64 += J * (max(inV - 1, 0) * smul + smul + NT)   # sum_kappa g_kappa prod phi
+        for e0 in (u0, f0):                    # base C U0^u0 F0^f0 e^{eps Lam0}
+            if _is_small_int(e0):
+                w.fp64 += max(abs(int(e0)) - 1, 0) + 1
+            else:
+                w.log += 1
+                w.exp += 1
+                w.fp64 += 2
+        w.log += 2
+        w.fp64 += 4                            # Lam0
+        w.fp64 += 2 * (Hm + 1)
+        w.fp64 += (ns - inV) * smul + smul + NT   # psi products, base x T, acc
+    w.fp64 += 2 * norders                      # acc += res W
+    return w
+
+
 def sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
     if getattr(sector, "deform", False):
         return deformed_sector_work(sector, lo, norders, mixed)
+    if any(int(a) <= -2 for a in sector.a):
+        return taylor_sector_work(sector, lo, norders)
     return real_sector_work(sector, lo, norders, mixed)
 
 

@@ -99,6 +99,16 @@ def box_massive(msq=1, deform: bool = True) -> Integral:
     return _integral_from_graph(g, 4, deform=deform)
 
 
+def double_box_massless_d2(method: str = "iterative") -> Integral:
+    """The two-loop planar massless double box in D = 2 - 2 eps: 282 sectors
+    with exponents down to a_j = -4 (Taylor subtraction up to degree 3 in up
+    to four variables)."""
+    g = Graph(edges=[(0, 1), (1, 2), (2, 5), (5, 4), (4, 3), (3, 0), (1, 4)],
+              masses_sq=[Fraction(0)] * 7, legs=[3, 0, 2, 5], kin=kin_massless_4pt(),
+              name="box2L_planar_massless_d2")
+    return _integral_from_graph(g, 2, deform=False, method=method)
+
+
 def double_box_massless(method: str = "iterative") -> Integral:
     # vertices: 0-1-2 top row, 3-4-5 bottom row; rung 1-4
     # legs: p0 at 3 (bottom left), p1 at 0 (top left), p2 at 2 (top right), p3 at 5

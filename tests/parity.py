@@ -19,6 +19,18 @@ before they cancel (the oracle reports both).
   reachable there by any FP64 evaluation of this formula, the oracle's
   included. Measured over every parity case: |gpu - oracle| <= 0.3 u C on
   those orders; CTOL = 3e-16 (2.7 u) leaves a margin of about 10.
+* CTOL_TAYLOR is CTOL for sectors with exponents a_j <= -2 (Taylor
+  subtraction). There C also holds, per Taylor state, the magnitudes of the
+  binomial-series terms that the oracle sums into each Taylor coefficient.
+  The kernel forms the same coefficients through ln(1 + x) and exp of
+  truncated power series by Horner's rule (2K + 4 rounded steps for a box of
+  total degree K <= 7), and U0^{u0} F0^{f0} through exp(e ln P) where the
+  exponent is not a small integer (relative error about |e ln P| u: 5 ln F
+  with f0 = -5 in the two-loop D = 2 - 2 eps sectors). Worst case about
+  40 u C. Measured on every GPU parity case of these sectors: up to 18 u C
+  under korobov3 (the two-loop sectors, where both sums are rounding noise
+  near the border), 5.4 u C under baker. CTOL_TAYLOR = 1e-14 (45 u), the
+  worst case.
 """
 import json
 import os
@@ -31,6 +43,7 @@ from paper_2305_19768_gb300.inputs.lattice import lattice_for
 
 RTOL = 1e-12
 CTOL = 3e-16
+CTOL_TAYLOR = 1e-14
 
 
 class Gpu:

@@ -369,7 +369,7 @@ def test_invalid_inputs_rejected(gpu):
     with pytest.raises(qmc.QmcError) as e:
         qmc.qmc_load_sectors_mem(gpu.ctx, "qmc-sectors 1 name broken")
     assert e.value.code == -2
-    bad = I.to_text().replace("a -1 -1 0", "a -3 -1 0", 1)   # below a = -2: not subtracted
+    bad = I.to_text().replace("a -1 -1 0", "a -5 -1 0", 1)   # below a = -4: no Taylor subtraction
     with pytest.raises(qmc.QmcError) as e:
         qmc.qmc_load_sectors_mem(gpu.ctx, bad)
     assert e.value.code == -1
@@ -379,9 +379,10 @@ def test_invalid_inputs_rejected(gpu):
 
 
 def test_degree1_subtraction_sectors(gpu):
-    # sectors with one a_j = -2 variable (class REAL3H) against the oracle: the
-    # pinned 1-D and 2-D polynomial cases and a 3-D sector with eps-dependent
-    # exponents of U and F and a second (a = -1) singular variable
+    # sectors with one a_j = -2 variable (the d <= 3 Taylor-subtraction class)
+    # against the oracle: the pinned 1-D and 2-D polynomial cases and a 3-D
+    # sector with eps-dependent exponents of U and F and a second (a = -1)
+    # singular variable
     from test_oracle_pins import _toy_integral
 
     I1 = _toy_integral(1, [-2], [1.25], {(0,): 1.0, (1,): 2.0, (2,): 3.0, (3,): -1.0})

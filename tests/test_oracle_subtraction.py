@@ -34,6 +34,7 @@ import pytest
 import oracle
 from oracle import combine
 from paper_2305_19768_gb300.inputs.lattice import cbc_fast, next_prime
+from subtraction_cases import CASES
 from test_oracle_pins import _series_of_inverse_linear, _toy_integral
 
 sp = pytest.importorskip("sympy")
@@ -92,24 +93,6 @@ def _oracle_integrand(d, a, b, Uterms, u0, u1, Fterms, f0, f1, tpoint, lo, norde
     v = oracle.SectorView(I, 0, [])
     val = oracle.integrand_at(v, np.array([float(Fraction(x)) for x in tpoint]), lo, norders)
     return val[:, 0] + 1j * val[:, 1]
-
-
-U1 = {(0,): 1, (1,): 2, (2,): 3, (3,): -1}
-CASES = [
-    # d, a, b, U, u0, u1, F, f0, f1, lo, norders, points
-    (1, [-2], ["5/4"], U1, 1, 0, {(0,): 1}, 0, 0, -1, 4, [["3/10"], ["4/5"]]),
-    (1, [-3], ["-3/2"], U1, 1, "-3/2", {(0,): 2, (1,): 1}, -2, 1, -1, 4, [["3/10"], ["7/10"]]),
-    (1, [-4], ["1/2"], U1, "1/2", 1, {(0,): 1, (2,): 1}, "-3/2", -1, -1, 4, [["2/5"]]),
-    (2, [-2, -2], ["5/4", "-1/2"], {(0, 0): 1, (1, 0): 1, (1, 1): 2, (0, 2): 1}, 1, 2,
-     {(0, 0): 2, (1, 0): 1, (0, 1): 1}, -1, -1, -2, 4, [["3/10", "7/10"], ["11/20", "1/5"]]),
-    (2, [-3, -1], ["-3/2", "3/4"], {(0, 0): 1, (1, 0): 2, (1, 1): 3, (0, 2): "1/2"}, 1, 2,
-     {(0, 0): 2, (1, 0): 1, (0, 1): 1}, "-3/2", -1, -2, 4, [["3/10", "7/10"]]),
-    (3, [-2, 1, -3], ["1", "1/2", "-2"], {(0, 0, 0): 1, (1, 0, 0): 1, (0, 1, 0): 2, (1, 1, 1): "1/2"}, -1, 2,
-     {(0, 0, 0): 2, (1, 0, 1): 1, (0, 2, 0): "1/2"}, -2, -1, -2, 3, [["3/10", "1/2", "7/10"]]),
-    (4, [-2, 0, -2, -1], ["3/2", "0", "-1", "1/2"],
-     {(0, 0, 0, 0): 1, (1, 0, 0, 0): 1, (1, 1, 1, 0): 2, (0, 0, 1, 1): 1, (0, 1, 0, 0): "1/2"}, 2, 3,
-     {(0, 0, 0, 0): 3, (1, 0, 1, 0): 1, (0, 1, 0, 1): 2}, -3, -1, -3, 3, [["2/5", "3/5", "3/10", "7/10"]]),
-]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
