@@ -28,6 +28,7 @@ struct QmcHostSector {
     int ns = 0;
     int cls = 0;
     int global_index = 0;  // index in the device sector table
+    int prow = 4;          // largest exponent of one variable (monomials and t^{a_j}): power-table rows
     double weight = 1.0;   // constant factor of the sector (geometric decomposition: |det N|)
 };
 

@@ -23,7 +23,7 @@ extern "C" int qmc_k_log(const double *x_dev, uint64_t n, double *out_dev, void 
 extern "C" int qmc_k_rcp(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_korobov(const double *x_dev, uint64_t n, double *out_dev, void *stream);
 extern "C" int qmc_k_atan2(const double *yx_dev, uint64_t n, double *out_dev, void *stream);
-extern "C" int qmc_k_occupancy(int cls, int block);
+extern "C" int qmc_k_occupancy(int cls, int block, int prow);
 
 namespace {
 
@@ -345,6 +345,7 @@ int upload_tables(qmc_ctx *ctx) {
             int rc = pack_sector(ctx, S, (int)si, (int)I.invariants.size(), monos, H);
             if (rc) return rc;
             S.global_index = (int)secs.size();
+            S.prow = std::min(std::max(H.pad0, 1), QMC_EMAX);
             secs.push_back(H);
         }
     }
@@ -689,7 +690,14 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         PLAN_TRY(cudaMemset(c.d_queue, 0, sizeof(unsigned long long)));
         PLAN_TRY(cudaMalloc(&c.d_jobfail, v.size() * sizeof(unsigned int)));
         PLAN_TRY(cudaMemset(c.d_jobfail, 0, v.size() * sizeof(unsigned int)));
-        int occ = qmc_k_occupancy(cls, c.block);
+        // power-table rows: the largest exponent among the launch's sectors
+        // (fewer rows, less shared memory per block, more resident blocks)
+        int prow = 1;
+        for (int u : c.orig) {
+            const qmc_job &J = jobs[u];
+            prow = std::max(prow, ctx->integrals[J.integral_id].sectors[J.sector].prow);
+        }
+        int occ = qmc_k_occupancy(cls, c.block, prow);
         if (occ < 1) occ = 1;
         c.grid = (int)std::min<uint64_t>(tiles, (uint64_t)ctx->sm_count * occ);
         if (c.grid < 1) c.grid = 1;
@@ -705,6 +713,7 @@ int qmc_plan_create(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int no
         L.ntiles = tiles;
         L.tile_k = (uint32_t)tile_k;
         L.transform = ctx->opt.transform;
+        L.prow = prow;
         L.partials = c.d_partials;
         L.queue = c.d_queue;
         L.status = p->d_status;
@@ -1167,6 +1176,7 @@ extern "C" int qmc_eval_jobs_noalloc(qmc_ctx *ctx, const qmc_job *jobs, int njob
     L.ntiles = tiles;
     L.tile_k = (uint32_t)tile_k;
     L.transform = ctx->opt.transform;
+    L.prow = QMC_EMAX;   // the fixed launch shape: a table for every exponent
     L.out = out_dev;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     unsigned long long status[2] = {0, 0};

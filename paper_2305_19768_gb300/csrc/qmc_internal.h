@@ -75,6 +75,7 @@ struct QmcLaunch {
     uint64_t ntiles;
     uint32_t tile_k;       // points per tile = block * ppt
     int32_t transform;     // 0 korobov3, 1 baker, 2 none
+    int32_t prow;          // power-table rows per variable (x^1..x^prow): the launch's largest exponent, 1..4
     double *partials;      // [ntiles][norders][2]
     unsigned long long *queue;   // tile counter (reset by the finish kernel)
     unsigned long long *status;  // [0]: sign-check failures, [1]: non-finite partials
@@ -132,7 +133,7 @@ int qmc_k_lattice_points(uint64_t n, const uint32_t *z_dev, int d, const double 
 int qmc_k_fp64_probe(double *out_dev, int iters, int grid, int block, void *stream);
 int qmc_k_fp32_probe(float *out_dev, int iters, int grid, int block, void *stream);
 int qmc_k_sm_count(int device);
-int qmc_k_occupancy(int cls, int block);
+int qmc_k_occupancy(int cls, int block, int prow);
 size_t qmc_k_noalloc_partial_capacity(void);
 int qmc_k_noalloc_setup(int device, void **ptr);
 int qmc_k_noalloc_eval(int device, int cls, const QmcJobDev *jobs_host, int njobs, const QmcLaunch *tmpl,

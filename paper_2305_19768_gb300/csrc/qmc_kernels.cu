@@ -535,19 +535,20 @@ __device__ __forceinline__ T poly_sum_tab(const uint64_t *desc, const CT *cval, 
     return s;
 }
 
-// The thread's power table x_j^e (e = 1 .. emax) into rows 4 j + e - 1
+// The thread's power table x_j^e (e = 1 .. emax <= prow) into rows prow j + e - 1
 template <int DMAX, class T>
-__device__ __forceinline__ void powers_tab(const T (&x)[DMAX], int d, int emax, T *pt, int stride) {
+__device__ __forceinline__ void powers_tab(const T (&x)[DMAX], int d, int emax, int prow, T *pt, int stride) {
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d) {
             const T x1 = x[j];
-            pt[(4 * j) * stride] = x1;
+            T *r = pt + prow * j * stride;
+            r[0] = x1;
             if (emax >= 2) {
                 const T x2 = x1 * x1;
-                pt[(4 * j + 1) * stride] = x2;
-                if (emax >= 3) pt[(4 * j + 2) * stride] = x2 * x1;
-                if (emax >= 4) pt[(4 * j + 3) * stride] = x2 * x2;
+                r[stride] = x2;
+                if (emax >= 3) r[2 * stride] = x2 * x1;
+                if (emax >= 4) r[3 * stride] = x2 * x2;
             }
         }
     }
@@ -969,10 +970,12 @@ __device__ __forceinline__ double qlog_fx(double x, const uint64_t *tab) {
 }
 
 // ptd / ptf: this thread's column of the power table in shared memory (FP64
-// and, for the mixed classes, FP32 view of the same storage), row stride `ps`
+// and, for the mixed classes, FP32 view of the same storage), row stride
+// `ps`, prow rows per variable
 template <int DMAX, int NS, int HI, bool MIXED, int LMAX>
 __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const double (&t)[DMAX],
-                                             double (&resN)[NS + HI + 1], double *ptd, float *ptf, int ps) {
+                                             double (&resN)[NS + HI + 1], double *ptd, float *ptf, int ps,
+                                             int prow) {
     constexpr int NG = 1 << NS;
     constexpr int NSA = SlotArr<NS>::N;
     const QmcSectorDev &sec = S.sec;
@@ -985,14 +988,14 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
         float tf[DMAX];
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) tf[j] = __double2float_rn(t[j]);
-        powers_tab<DMAX, float>(tf, d, sec.pad0, ptf, ps);
+        powers_tab<DMAX, float>(tf, d, sec.pad0, prow, ptf, ps);
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             hU[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.gU[g], sec.gU[g + 1], ptf, ps);
             hF[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptf, ps);
         }
     } else {
-        powers_tab<DMAX, double>(t, d, sec.pad0, ptd, ps);
+        powers_tab<DMAX, double>(t, d, sec.pad0, prow, ptd, ps);
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             hU[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.gU[g], sec.gU[g + 1], ptd, ps);
@@ -1017,7 +1020,7 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
             const int a = sec.a[j];
             if (a > 0) {
                 // t_j^a: the FP64 power table, or (mixed classes, whose table is FP32) products
-                const double p = MIXED ? ipow_signed<double>(t[j], 1.0, a) : ptd[(4 * j + a - 1) * ps];
+                const double p = MIXED ? ipow_signed<double>(t[j], 1.0, a) : ptd[(prow * j + a - 1) * ps];
                 Cc = hasCc ? Cc * p : p;
                 hasCc = true;
             }
@@ -1715,7 +1718,7 @@ __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
             for (int j = 0; j < QMC_DMAX; ++j) {
                 const uint32_t ej = (M.exps >> (4 * j)) & 15u;
                 if (ej) {
-                    dsc |= (uint64_t)(4 * j + ej - 1) << (3 + 5 * k);
+                    dsc |= (uint64_t)(Lc.prow * j + ej - 1) << (3 + 5 * k);
                     ++k;
                 }
             }
@@ -1848,7 +1851,8 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
         if constexpr (FIXED) {
             double resN[NO];
             eval_real_fx<DMAX, NSC, HIC, MIXED, LMAX>(S, t, resN, reinterpret_cast<double *>(ptab) + threadIdx.x,
-                                                      reinterpret_cast<float *>(ptab) + threadIdx.x, (int)blockDim.x);
+                                                      reinterpret_cast<float *>(ptab) + threadIdx.x, (int)blockDim.x,
+                                                      Lc.prow);
 #pragma unroll
             for (int i = 0; i < NO; ++i) accN[i] = fma(resN[i], W, accN[i]);
         } else {
@@ -2138,19 +2142,27 @@ __global__ void qmc_fp32_probe_kernel(float *out, int iters) {
 // run near the register limit, where a second warp set per block buys nothing
 // (and their instantiations dominate the build).
 // Dynamic shared memory of an evaluator kernel: the power tables of the
-// fixed-order real kernels
+// fixed-order real kernels, prow rows of x^1..x^prow per variable
 template <int DMAX, bool CPLX, bool HS, bool FIX>
-constexpr int eval_dyn_smem(int block) {
-    return (!CPLX && !HS && FIX) ? 4 * DMAX * block * (int)sizeof(double) : 0;
+constexpr int eval_dyn_smem(int block, int prow) {
+    return (!CPLX && !HS && FIX) ? prow * DMAX * block * (int)sizeof(double) : 0;
+}
+
+// The attribute allows the largest table (QMC_EMAX rows); each launch asks for its own
+template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS, bool FIX>
+bool allow_dyn_smem() {
+    constexpr int dmax = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK, QMC_EMAX);
+    static const bool ok =
+        dmax == 0 || cudaFuncSetAttribute(qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, dmax) == cudaSuccess;
+    return ok;
 }
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS, bool FIX>
 int launch_block(const QmcLaunch *L, int ppt, int grid, cudaStream_t st) {
-    constexpr int dyn = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK);
-    static const bool attr_ok =
-        dyn == 0 || cudaFuncSetAttribute(qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
-    if (!attr_ok) return -1;
+    if (L->prow < 1 || L->prow > QMC_EMAX) return -1;
+    if (!allow_dyn_smem<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>()) return -1;
+    const int dyn = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK, L->prow);
     qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX><<<grid, BLOCK, dyn, st>>>(*L, ppt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -2172,11 +2184,9 @@ int launch_cls(const QmcLaunch *L, int block, int ppt, int grid, cudaStream_t st
 }
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, int BLOCK, bool HS, bool FIX>
-int occupancy_block() {
-    constexpr int dyn = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK);
-    if (dyn && cudaFuncSetAttribute(qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
-        return 0;
+int occupancy_block(int prow) {
+    if (!allow_dyn_smem<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>()) return 0;
+    const int dyn = eval_dyn_smem<DMAX, CPLX, HS, FIX>(BLOCK, prow);
     int v = 0;
     const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &v, qmc_eval_kernel<DMAX, SMAX, LMAX, CPLX, MIXED, BLOCK, HS, FIX>, BLOCK, dyn);
@@ -2184,20 +2194,20 @@ int occupancy_block() {
 }
 
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS, bool FIX>
-int occupancy_shape(int block) {
+int occupancy_shape(int block, int prow) {
     if constexpr (DMAX <= 3) {
-        if (block == 256) return occupancy_block<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX>();
+        if (block == 256) return occupancy_block<DMAX, SMAX, LMAX, CPLX, MIXED, 256, HS, FIX>(prow);
     }
-    return occupancy_block<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>();
+    return occupancy_block<DMAX, SMAX, LMAX, CPLX, MIXED, 128, HS, FIX>(prow);
 }
 
 // Resident blocks per SM of the class's kernels (the larger of the fixed-order
 // and the general kernel: a persistent grid sized for it only over-subscribes
 // the other, whose surplus blocks find the tile queue empty)
 template <int DMAX, int SMAX, int LMAX, bool CPLX, bool MIXED, bool HS = false>
-int occupancy_cls(int block) {
-    int v = occupancy_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, false>(block);
-    if constexpr (!CPLX && !HS) v = std::max(v, occupancy_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, true>(block));
+int occupancy_cls(int block, int prow) {
+    int v = occupancy_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, false>(block, prow);
+    if constexpr (!CPLX && !HS) v = std::max(v, occupancy_shape<DMAX, SMAX, LMAX, CPLX, MIXED, HS, true>(block, prow));
     return v;
 }
 
@@ -2238,24 +2248,24 @@ extern "C" int QMC_PART_FN(qmc_k_launch_eval, QMC_PART)(int cls, const QmcLaunch
     }
 }
 
-extern "C" int QMC_PART_FN(qmc_k_occupancy, QMC_PART)(int cls, int block) {
+extern "C" int QMC_PART_FN(qmc_k_occupancy, QMC_PART)(int cls, int block, int prow) {
     switch (cls) {
 #if QMC_PART == 0
-        case QMC_CLASS_REAL3: return occupancy_cls<3, 2, 4, false, false>(block);
-        case QMC_CLASS_REAL3M: return occupancy_cls<3, 2, 4, false, true>(block);
+        case QMC_CLASS_REAL3: return occupancy_cls<3, 2, 4, false, false>(block, prow);
+        case QMC_CLASS_REAL3M: return occupancy_cls<3, 2, 4, false, true>(block, prow);
 #elif QMC_PART == 1
-        case QMC_CLASS_CPLX3: return occupancy_cls<3, 2, 4, true, false>(block);
-        case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block);
+        case QMC_CLASS_CPLX3: return occupancy_cls<3, 2, 4, true, false>(block, prow);
+        case QMC_CLASS_CPLX3M: return occupancy_cls<3, 2, 4, true, true>(block, prow);
 #elif QMC_PART == 2
         case QMC_CLASS_REAL6:
         case QMC_CLASS_REAL6S:
-        case QMC_CLASS_REAL6T: return occupancy_cls<6, 4, 6, false, false>(block);
+        case QMC_CLASS_REAL6T: return occupancy_cls<6, 4, 6, false, false>(block, prow);
         case QMC_CLASS_REAL6M:
         case QMC_CLASS_REAL6SM:
-        case QMC_CLASS_REAL6TM: return occupancy_cls<6, 4, 6, false, true>(block);
+        case QMC_CLASS_REAL6TM: return occupancy_cls<6, 4, 6, false, true>(block, prow);
 #elif QMC_PART == 3
-        case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block);
-        case QMC_CLASS_REAL6H: return occupancy_cls<6, 4, 6, false, false, true>(block);
+        case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block, prow);
+        case QMC_CLASS_REAL6H: return occupancy_cls<6, 4, 6, false, false, true>(block, prow);
 #endif
         default: return 0;
     }
@@ -2265,9 +2275,9 @@ extern "C" int QMC_PART_FN(qmc_k_occupancy, QMC_PART)(int cls, int block) {
 extern "C" int qmc_k_launch_eval_part1(int, const QmcLaunch *, int, int, int, void *);
 extern "C" int qmc_k_launch_eval_part2(int, const QmcLaunch *, int, int, int, void *);
 extern "C" int qmc_k_launch_eval_part3(int, const QmcLaunch *, int, int, int, void *);
-extern "C" int qmc_k_occupancy_part1(int, int);
-extern "C" int qmc_k_occupancy_part2(int, int);
-extern "C" int qmc_k_occupancy_part3(int, int);
+extern "C" int qmc_k_occupancy_part1(int, int, int);
+extern "C" int qmc_k_occupancy_part2(int, int, int);
+extern "C" int qmc_k_occupancy_part3(int, int, int);
 
 extern "C" int qmc_k_launch_eval(int cls, const QmcLaunch *L, int block, int ppt, int grid, void *stream) {
     int (*const parts[4])(int, const QmcLaunch *, int, int, int, void *) = {
@@ -2343,11 +2353,11 @@ extern "C" int qmc_k_sm_count(int device) {
     return v;
 }
 
-extern "C" int qmc_k_occupancy(int cls, int block) {
-    int (*const parts[4])(int, int) = {qmc_k_occupancy_part0, qmc_k_occupancy_part1, qmc_k_occupancy_part2,
-                                       qmc_k_occupancy_part3};
+extern "C" int qmc_k_occupancy(int cls, int block, int prow) {
+    int (*const parts[4])(int, int, int) = {qmc_k_occupancy_part0, qmc_k_occupancy_part1, qmc_k_occupancy_part2,
+                                            qmc_k_occupancy_part3};
     for (auto f : parts) {
-        const int v = f(cls, block);
+        const int v = f(cls, block, prow);
         if (v) return v;
     }
     return 0;
@@ -2407,7 +2417,7 @@ extern "C" int qmc_k_noalloc_eval(int device, int cls, const QmcJobDev *jobs_hos
     if (cudaMemcpyAsync(b + kNoallocJobOff, jobs_host, (size_t)njobs * sizeof(QmcJobDev),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
         return -1;
-    int occ = qmc_k_occupancy(cls, block);
+    int occ = qmc_k_occupancy(cls, block, L.prow);
     if (occ < 1) occ = 1;
     uint64_t g = (uint64_t)sm_count * occ;
     if (L.ntiles < g) g = L.ntiles;
