@@ -102,8 +102,11 @@ PROFILED = {
     # double box, n = 1000003, m = 32 (the default line): traffic from a 1-pass
     # capture of one full launch; FP64 instructions and pipe activity from the
     # full capture of the same kernel at n = 20011 (per evaluation, the same code)
-    ("197a52c5a2d3eb5a059dfcfe56610a40eeea51c2", "box2L_planar_massless", "fp64", "iterative", 1000003): {
-        "traffic": 2435328 + 5240269568, "fp64_executed_flops_per_eval": 457.2, "fp64_pipe_busy": 0.677},
+    ("1ddf6e40e67e8e417936ce06d963bba0ebbb6e47", "box2L_planar_massless", "fp64", "iterative", 1000003): {
+        "traffic": 1605120 + 3574509056, "fp64_executed_flops_per_eval": 457.2, "fp64_pipe_busy": 0.693},
+    # one-loop box in D = 2 - 2 eps (Taylor subtraction), n = 10007: full capture
+    ("1ddf6e40e67e8e417936ce06d963bba0ebbb6e47", "box1L_massless_d2", "fp64", "iterative", 10007): {
+        "traffic": 801792 + 330914048, "fp64_executed_flops_per_eval": 1239.6, "fp64_pipe_busy": 0.532},
 }
 
 def kernel_sha1():
