@@ -590,7 +590,7 @@ def main():
         from paper_2305_19768_gb300 import scan
 
         modes = ("plain", "unsized", "learned", "learned_variance")
-        sc = scan.compare(10000, 1e-4, ",".join(modes), 2000, plain_sample=50, steps=SCAN_TRAIN_STEPS)
+        sc = scan.compare(10000, 1e-4, ",".join(modes), 2000, plain_sample=10, steps=SCAN_TRAIN_STEPS)
         keep = ("seconds", "evaluations", "presample_evaluations", "max_rel_error", "rc", "iterations",
                 "sampled_points", "accepted", "train_seconds", "model_seconds", "sized_seconds",
                 "sized_evaluations", "fit_rel_error", "logn_fit_median_abs", "logw_fit_median_abs",

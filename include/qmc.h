@@ -288,7 +288,7 @@ int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int nor
  * mixed-precision variant, 11: real d <= 6 with exponents a_j <= -2; class 2
  * then holds the d <= 6 sectors with 4): on up to 32 of the
  * given jobs per class (at most 8 shifts each) every block size in
- * {128, 256} and points per thread in {4, 8, 16, 32} is timed with CUDA
+ * {128, 256} and points per thread in {1, 2, 4, 8, 16, 32} is timed with CUDA
  * events; the fastest is kept in the context and used by later plans whose
  * options leave block/ppt at 0. best_block/best_ppt (may be NULL) receive
  * QMC_NUM_CLASSES entries (0 = class absent). */

@@ -1049,7 +1049,7 @@ extern "C" int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo
         }
     }
     const int blocks[2] = {128, 256};
-    const int ppts[4] = {4, 8, 16, 32};
+    const int ppts[6] = {1, 2, 4, 8, 16, 32};
     const qmc_options saved = ctx->opt;
     for (int cls = 0; cls < QMC_NCLASS; ++cls) {
         if (per[cls].empty()) continue;
