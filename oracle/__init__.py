@@ -96,8 +96,6 @@ class SectorView:
         for x in s.a:
             if int(x) <= -1:
                 box *= -int(x)
-        if box > 1 and s.deform and lam is not None:
-            raise ValueError("Taylor subtraction beyond degree 0 (a_j <= -2) needs an undeformed sector")
         if box > 128:
             raise ValueError("the subtraction's Taylor box prod_j (-a_j) exceeds 128 coefficients")
         self.d = s.d

@@ -16,7 +16,8 @@
  *    determinant (the paper only names the presampling that tunes lambda);
  *  - the eps-expanded sector integrand with subtraction of the endpoint
  *    singularities t_j^{-p + b_j eps}: plus distributions for p = 1, the
- *    Taylor polynomial of degree p - 1 for p >= 2 (undeformed sectors).
+ *    Taylor polynomial of degree p - 1 for p >= 2 (in deformed sectors with
+ *    every quantity of the deformation formed on truncated power series).
  * The paper is silent on the lattice-point rounding, the transform formula,
  * the deformation formula and the subtraction; the readings used here are:
  *  x = (double)r / (double)n + Delta; if (x >= 1) x -= 1, with r = k z mod n
@@ -376,43 +377,25 @@ static void jet_mul(const jbox *B, const cplx *a, const cplx *b, cplx *c) {
     for (int k = 0; k < B->size; ++k) c[k] = r[k];
 }
 
-/* Taylor coefficients of P^{e0 + e1 eps} (P = U or F) in the variables V at
- * t_V = 0, the other variables at t: out[k] = coefficient of prod t_V^{k},
- * as eps-series up to eps^hi, for every k in the box. P = P0 + delta with
- * P0 = P(t_V = 0) and delta (no constant term) read off the monomial table;
- * the generalized binomial theorem gives
+/* P^{e0 + e1 eps} over the box for a jet P with P[0] != 0 (Pabs: magnitudes
+ * of P's entries), as eps-series up to eps^hi per box entry, by the
+ * generalized binomial theorem: with P = P0 + delta (delta without constant
+ * term),
  *   P^alpha = sum_k binom(alpha, k) P0^{alpha - k} delta^k,
  * binom(alpha, k) = prod_{i<k} (alpha - i) / k! a polynomial in eps, and
- * P0^{alpha - k} = P0^{e0 - k} exp(e1 eps ln P0). delta^k vanishes in the box
- * beyond k = sum_q (rad_q - 1). */
-static void jet_power(const orc_sector *S, int isF, const double *t, const int *V, const jbox *B,
-                      int hi, series *out, series *mass) {
-    int d = S->d;
-    int nP = isF ? S->nF : S->nU;
-    const int *ex = isF ? S->Fe : S->Ue;
-    const double *co = isF ? S->Fc : S->Uc;
-    double e0 = isF ? S->f0 : S->u0, e1 = isF ? S->f1 : S->u1;
-    int inV[ORC_DMAX] = {0};
-    for (int q = 0; q < B->nv; ++q) inV[V[q]] = 1;
+ * P0^{alpha - k} = P0^{e0 - k} exp(e1 eps ln P0) (principal log; m0: on the
+ * real axis the argument is taken from below, the F - i0 prescription).
+ * delta^k vanishes in the box beyond k = sum_q (rad_q - 1). mass (may be
+ * NULL) receives the same sums of the terms' magnitudes. */
+static void sjet_pow(const jbox *B, const cplx *P, const cplx *Pabs, double e0, double e1, int m0, int hi,
+                     series *out, series *mass) {
     cplx delta[ORC_JMAX], dabs[ORC_JMAX];
-    for (int k = 0; k < B->size; ++k) delta[k] = dabs[k] = 0.0;
-    for (int m = 0; m < nP; ++m) {
-        int idx = 0, stride = 1, inside = 1;
-        for (int q = 0; q < B->nv; ++q) {
-            int e = ex[m * d + V[q]];
-            if (e >= B->rad[q]) { inside = 0; break; }
-            idx += e * stride;
-            stride *= B->rad[q];
-        }
-        if (!inside) continue;
-        cplx v = co[m];
-        for (int j = 0; j < d; ++j)
-            if (!inV[j]) v *= cipow(t[j], ex[m * d + j]);
-        delta[idx] += v;
-        dabs[idx] += cabs(v);
+    for (int k = 0; k < B->size; ++k) {
+        delta[k] = P[k];
+        dabs[k] = Pabs[k];
     }
     cplx P0 = delta[0];
-    if (cimag(P0) == 0.0) P0 = CMPLX(creal(P0), isF ? -0.0 : 0.0);   /* F - i0 */
+    if (cimag(P0) == 0.0) P0 = CMPLX(creal(P0), m0 ? -0.0 : 0.0);
     delta[0] = 0.0;
     dabs[0] = 0.0;
     cplx lg = clog(P0);
@@ -456,6 +439,39 @@ static void jet_power(const orc_sector *S, int isF, const double *t, const int *
                 }
             }
     }
+}
+
+/* Taylor coefficients of P^{e0 + e1 eps} (P = U or F) in the variables V at
+ * t_V = 0, the other variables at t (undeformed sector): P's box entries are
+ * read off the monomial table (t_V^e lands at entry e, the other variables
+ * multiply in), then sjet_pow. */
+static void jet_power(const orc_sector *S, int isF, const double *t, const int *V, const jbox *B,
+                      int hi, series *out, series *mass) {
+    int d = S->d;
+    int nP = isF ? S->nF : S->nU;
+    const int *ex = isF ? S->Fe : S->Ue;
+    const double *co = isF ? S->Fc : S->Uc;
+    double e0 = isF ? S->f0 : S->u0, e1 = isF ? S->f1 : S->u1;
+    int inV[ORC_DMAX] = {0};
+    for (int q = 0; q < B->nv; ++q) inV[V[q]] = 1;
+    cplx P[ORC_JMAX], Pabs[ORC_JMAX];
+    for (int k = 0; k < B->size; ++k) P[k] = Pabs[k] = 0.0;
+    for (int m = 0; m < nP; ++m) {
+        int idx = 0, stride = 1, inside = 1;
+        for (int q = 0; q < B->nv; ++q) {
+            int e = ex[m * d + V[q]];
+            if (e >= B->rad[q]) { inside = 0; break; }
+            idx += e * stride;
+            stride *= B->rad[q];
+        }
+        if (!inside) continue;
+        cplx v = co[m];
+        for (int j = 0; j < d; ++j)
+            if (!inV[j]) v *= cipow(t[j], ex[m * d + j]);
+        P[idx] += v;
+        Pabs[idx] += cabs(v);
+    }
+    sjet_pow(B, P, Pabs, e0, e1, isF, hi, out, mass);
 }
 
 /* Taylor coefficient of G (undeformed sector) of prod_{q} t_{V[q]}^{kap[q]}
@@ -503,6 +519,199 @@ static series taylor_G(const orc_sector *S, const double *t, int nv, const int *
     }
     if (massout) *massout = mass;
     return prod;
+}
+
+/* ---------------- Taylor coefficients of G in deformed sectors ---------------- */
+/* Jets of eps-series: c = a b over the box (every series starts at eps^0). */
+static void sjet_mul(const jbox *B, const series *a, const series *b, int hi, series *c) {
+    for (int k = 0; k < B->size; ++k) {
+        memset(&c[k], 0, sizeof(series));
+        c[k].lo = 0;
+        c[k].n = hi + 1;
+    }
+    for (int i = 0; i < B->size; ++i) {
+        int di[ORC_SMAX];
+        jbox_digits(B, i, di);
+        for (int j = 0; j < B->size; ++j) {
+            int dj[ORC_SMAX];
+            jbox_digits(B, j, dj);
+            int k = 0, stride = 1, inside = 1;
+            for (int q = 0; q < B->nv; ++q) {
+                int e = di[q] + dj[q];
+                if (e >= B->rad[q]) { inside = 0; break; }
+                k += e * stride;
+                stride *= B->rad[q];
+            }
+            if (!inside) continue;
+            series term = s_mul(&a[i], &b[j], hi);
+            c[k] = s_add(&c[k], &term, hi);
+        }
+    }
+}
+
+/* A polynomial's mixed partial derivative d^|D| P / prod dt^D (D may be NULL)
+ * at jet arguments x_j: sum_m c_m prod_j e(e-1)..(e-D_j+1) x_j^(e - D_j), the
+ * powers by repeated jet products. outabs: the sum of the terms' magnitudes. */
+static void jet_poly(const jbox *B, int nterms, int d, const int *ex, const double *co, cplx x[][ORC_JMAX],
+                     const int *D, cplx *out, cplx *outabs) {
+    for (int k = 0; k < B->size; ++k) out[k] = outabs[k] = 0.0;
+    for (int m = 0; m < nterms; ++m) {
+        cplx term[ORC_JMAX];
+        for (int k = 0; k < B->size; ++k) term[k] = 0.0;
+        term[0] = co[m];
+        int zero = 0;
+        for (int j = 0; j < d && !zero; ++j) {
+            int e = ex[m * d + j], dj = D ? D[j] : 0;
+            if (e < dj) { zero = 1; break; }
+            for (int q = 0; q < dj; ++q) term[0] *= (double)(e - q);
+            for (int r = 0; r < e - dj; ++r) jet_mul(B, term, x[j], term);
+        }
+        if (zero) continue;
+        for (int k = 0; k < B->size; ++k) {
+            out[k] += term[k];
+            outabs[k] += cabs(term[k]);
+        }
+    }
+}
+
+/* Taylor coefficient of G of prod_q t_{V[q]}^{kap[q]} at t_V = 0 in a deformed
+ * sector, the other variables at t (omt = 1 - t). Every quantity of G_series
+ * is formed on jets in t_V: t_j, 1 - t_j, dF/dt_j and d2F/dt_j dt_l, then
+ *   z_j = t_j - i lambda_j t_j (1 - t_j) dF_j,  rho_j = 1 - i lambda_j (1 - t_j) dF_j,
+ *   J_jl = delta_jl - i lambda_j (t_j (1 - t_j) d2F_jl + delta_jl (1 - 2 t_j) dF_j),
+ * det J by the Leibniz formula, U(z) and F(z); each power factor (rho_j or
+ * z_j, U, F) by sjet_pow, and G = det J times their product. massout: the
+ * coefficient's mass (magnitudes of the binomial terms and of the products). */
+static series taylor_G_deformed(const orc_sector *S, const double *t, const double *omt, int nv, const int *V,
+                                const int *kap, int hi, series *massout) {
+    int d = S->d;
+    jbox B;
+    B.nv = nv;
+    B.size = 1;
+    int stride[ORC_SMAX], pos[ORC_DMAX];
+    for (int j = 0; j < d; ++j) pos[j] = -1;
+    for (int q = 0; q < nv; ++q) {
+        B.rad[q] = kap[q] + 1;
+        stride[q] = B.size;
+        B.size *= B.rad[q];
+        pos[V[q]] = q;
+    }
+    if (B.size > ORC_JMAX) abort();
+    static __thread cplx tj[ORC_DMAX][ORC_JMAX], oj[ORC_DMAX][ORC_JMAX], Fj[ORC_DMAX][ORC_JMAX],
+        zj[ORC_DMAX][ORC_JMAX], rj[ORC_DMAX][ORC_JMAX], Jm[ORC_DMAX * ORC_DMAX][ORC_JMAX];
+    cplx tmp[ORC_JMAX], tabs[ORC_JMAX];
+    for (int j = 0; j < d; ++j) {
+        for (int k = 0; k < B.size; ++k) tj[j][k] = oj[j][k] = 0.0;
+        int q = pos[j];
+        if (q >= 0) {                                 /* t_j = 0 + the jet variable */
+            oj[j][0] = 1.0;
+            if (B.rad[q] > 1) {
+                tj[j][stride[q]] = 1.0;
+                oj[j][stride[q]] = -1.0;
+            }
+        } else {
+            tj[j][0] = t[j];
+            oj[j][0] = omt[j];
+        }
+    }
+    int D[ORC_DMAX];
+    for (int j = 0; j < d; ++j) {
+        memset(D, 0, sizeof D);
+        D[j] = 1;
+        jet_poly(&B, S->nF, d, S->Fe, S->Fc, tj, D, Fj[j], tabs);
+    }
+    for (int j = 0; j < d; ++j) {
+        cplx g[ORC_JMAX];                             /* lambda_j (1 - t_j) dF_j */
+        jet_mul(&B, oj[j], Fj[j], g);
+        for (int k = 0; k < B.size; ++k) {
+            g[k] *= S->lambda[j];
+            rj[j][k] = (k == 0 ? 1.0 : 0.0) - I * g[k];
+        }
+        jet_mul(&B, tj[j], rj[j], zj[j]);             /* z_j = t_j rho_j */
+        for (int l = 0; l < d; ++l) {
+            memset(D, 0, sizeof D);
+            D[j] += 1;
+            D[l] += 1;
+            cplx h[ORC_JMAX], w[ORC_JMAX];
+            jet_poly(&B, S->nF, d, S->Fe, S->Fc, tj, D, h, tabs);
+            jet_mul(&B, tj[j], oj[j], w);             /* t_j (1 - t_j) d2F_jl */
+            jet_mul(&B, w, h, w);
+            if (j == l) {                             /* + (1 - 2 t_j) dF_j */
+                cplx u[ORC_JMAX];
+                for (int k = 0; k < B.size; ++k) u[k] = oj[j][k] - tj[j][k];
+                jet_mul(&B, u, Fj[j], u);
+                for (int k = 0; k < B.size; ++k) w[k] += u[k];
+            }
+            for (int k = 0; k < B.size; ++k)
+                Jm[j * d + l][k] = (j == l && k == 0 ? 1.0 : 0.0) - I * S->lambda[j] * w[k];
+        }
+    }
+    /* det J = sum over permutations of sign prod_i J[i][perm i] */
+    cplx detJ[ORC_JMAX], dabsJ[ORC_JMAX];
+    for (int k = 0; k < B.size; ++k) detJ[k] = dabsJ[k] = 0.0;
+    {
+        int perm[ORC_DMAX];
+        for (int i = 0; i < d; ++i) perm[i] = i;
+        for (;;) {
+            int inv = 0;
+            for (int i = 0; i < d; ++i)
+                for (int j = i + 1; j < d; ++j)
+                    if (perm[i] > perm[j]) ++inv;
+            for (int k = 0; k < B.size; ++k) tmp[k] = (k == 0) ? ((inv % 2) ? -1.0 : 1.0) : 0.0;
+            for (int i = 0; i < d; ++i) jet_mul(&B, tmp, Jm[i * d + perm[i]], tmp);
+            for (int k = 0; k < B.size; ++k) {
+                detJ[k] += tmp[k];
+                dabsJ[k] += cabs(tmp[k]);
+            }
+            int i = d - 2;
+            while (i >= 0 && perm[i] > perm[i + 1]) --i;
+            if (i < 0) break;
+            int j = d - 1;
+            while (perm[j] < perm[i]) --j;
+            int tt = perm[i]; perm[i] = perm[j]; perm[j] = tt;
+            for (int l = i + 1, r = d - 1; l < r; ++l, --r) {
+                tt = perm[l]; perm[l] = perm[r]; perm[r] = tt;
+            }
+        }
+    }
+    /* the product of the power factors, starting from det J (no eps exponent) */
+    static __thread series prod[ORC_JMAX], mass[ORC_JMAX], fs[ORC_JMAX], fm[ORC_JMAX], nx[ORC_JMAX];
+    for (int k = 0; k < B.size; ++k) {
+        prod[k] = s_const(detJ[k]);
+        prod[k].n = hi + 1;
+        mass[k] = s_const(dabsJ[k]);
+        mass[k].n = hi + 1;
+    }
+    for (int f = 0; f < d + 2; ++f) {
+        const cplx *P;
+        cplx Pabs[ORC_JMAX], pv[ORC_JMAX];
+        double e0, e1;
+        int m0 = 0;
+        if (f < d) {
+            if (is_singular(S, f)) P = rj[f];
+            else if (S->a[f] != 0 || S->b[f] != 0.0) P = zj[f];
+            else continue;
+            e0 = S->a[f];
+            e1 = S->b[f];
+            for (int k = 0; k < B.size; ++k) Pabs[k] = cabs(P[k]);
+        } else {
+            int isF = f == d + 1;
+            jet_poly(&B, isF ? S->nF : S->nU, d, isF ? S->Fe : S->Ue, isF ? S->Fc : S->Uc, zj, NULL, pv, Pabs);
+            P = pv;
+            e0 = isF ? S->f0 : S->u0;
+            e1 = isF ? S->f1 : S->u1;
+            m0 = isF;
+        }
+        if (e0 == 0.0 && e1 == 0.0) continue;
+        sjet_pow(&B, P, Pabs, e0, e1, m0, hi, fs, fm);
+        sjet_mul(&B, prod, fs, hi, nx);
+        for (int k = 0; k < B.size; ++k) prod[k] = nx[k];
+        for (int k = 0; k < B.size; ++k) fm[k] = s_mass(&fm[k]);
+        sjet_mul(&B, mass, fm, hi, nx);
+        for (int k = 0; k < B.size; ++k) mass[k] = nx[k];
+    }
+    if (massout) *massout = mass[B.size - 1];
+    return prod[B.size - 1];
 }
 
 /* The eps-expanded integrand at the transformed point t (omt = 1 - t):
@@ -554,11 +763,11 @@ static void integrand_series(const orc_sector *S, const double *t, const double 
                 if (state[q] > 1) taylor = 1;
             }
         }
-        /* every Taylor order 0: G itself at t_V = 0; else the Taylor coefficient
-         * (undeformed sectors; the loader rejects the rest) */
-        if (taylor && S->deform) abort();
+        /* every Taylor order 0: G itself at t_V = 0; else the Taylor coefficient */
         series gmass;
-        series term = taylor ? taylor_G(S, t, nv, V, kap, H, &gmass) : G_series(S, tp, omtp, H, signfail);
+        series term = !taylor ? G_series(S, tp, omtp, H, signfail)
+                      : S->deform ? taylor_G_deformed(S, t, omt, nv, V, kap, H, &gmass)
+                                  : taylor_G(S, t, nv, V, kap, H, &gmass);
         for (int q = 0; q < ns; ++q) {
             int j = sing[q];
             int p = -S->a[j];

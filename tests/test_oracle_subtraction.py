@@ -34,7 +34,7 @@ import pytest
 import oracle
 from oracle import combine
 from paper_2305_19768_gb300.inputs.lattice import cbc_fast, next_prime
-from subtraction_cases import CASES
+from subtraction_cases import CASES, DEFORMED_CASES
 from test_oracle_pins import _series_of_inverse_linear, _toy_integral
 
 sp = pytest.importorskip("sympy")
@@ -42,23 +42,37 @@ mpmath = pytest.importorskip("mpmath")
 
 
 # ---------------------------------------------------------------- exact integrand
-def _exact_integrand(d, a, b, Uterms, u0, u1, Fterms, f0, f1, tpoint, lo, norders):
+def _exact_integrand(d, a, b, Uterms, u0, u1, Fterms, f0, f1, tpoint, lo, norders, lam=None):
     """Laurent coefficients eps^lo.. of the subtracted sector integrand at tpoint
-    (rationals), by symbolic differentiation and a numerical eps expansion."""
+    (rationals), by symbolic differentiation and a numerical eps expansion.
+    With lam (rationals, one per variable) the sector is contour-deformed:
+    z_j = t_j - i lam_j t_j (1 - t_j) dF/dt_j, rho_j = z_j / t_j, J = dz/dt, and
+    G = det J prod_{singular} rho_j^{a_j + b_j eps} prod_{regular} z_j^{a_j + b_j eps}
+        U(z)^{u0 + u1 eps} F(z)^{f0 + f1 eps} (principal branches)."""
     ts = sp.symbols(f"t0:{d}")
     e = sp.Symbol("eps")
     R = sp.Rational
 
-    def poly(terms):
-        return sum(R(c) * sp.Mul(*[ts[j] ** k for j, k in enumerate(ex)]) for ex, c in terms.items())
+    def poly(terms, x):
+        return sum(R(c) * sp.Mul(*[x[j] ** k for j, k in enumerate(ex)]) for ex, c in terms.items())
 
-    G = poly(Uterms) ** (R(u0) + R(u1) * e) * poly(Fterms) ** (R(f0) + R(f1) * e)
+    if lam is None:
+        x, G = ts, sp.Integer(1)
+        fac = [ts[j] for j in range(d)]
+    else:
+        Ft = poly(Fterms, ts)
+        x = [ts[j] - sp.I * R(lam[j]) * ts[j] * (1 - ts[j]) * sp.diff(Ft, ts[j]) for j in range(d)]
+        G = sp.Matrix(d, d, lambda j, l: sp.diff(x[j], ts[l])).det()
+        fac = [1 - sp.I * R(lam[j]) * (1 - ts[j]) * sp.diff(Ft, ts[j]) for j in range(d)]
+    G = G * poly(Uterms, x) ** (R(u0) + R(u1) * e) * poly(Fterms, x) ** (R(f0) + R(f1) * e)
     sing = []
     for j in range(d):
         if a[j] <= -1:
             sing.append(j)
+            if lam is not None:
+                G = G * fac[j] ** (a[j] + R(b[j]) * e)
         elif a[j] != 0 or R(b[j]) != 0:
-            G = G * ts[j] ** (a[j] + R(b[j]) * e)
+            G = G * (x[j] if lam is not None else ts[j]) ** (a[j] + R(b[j]) * e)
     f = G
     for j in reversed(sing):
         p, bj, tv = -a[j], R(b[j]), ts[j]
@@ -88,9 +102,11 @@ def _exact_integrand(d, a, b, Uterms, u0, u1, Fterms, f0, f1, tpoint, lo, norder
         return np.array(out)
 
 
-def _oracle_integrand(d, a, b, Uterms, u0, u1, Fterms, f0, f1, tpoint, lo, norders):
+def _oracle_integrand(d, a, b, Uterms, u0, u1, Fterms, f0, f1, tpoint, lo, norders, lam=None):
     I = _toy_integral(d, a, b, Uterms, u0=u0, u1=u1, Fterms=Fterms, f0=f0, f1=f1)
-    v = oracle.SectorView(I, 0, [])
+    if lam is not None:
+        I.sectors[0].deform = True
+    v = oracle.SectorView(I, 0, [], None if lam is None else [float(Fraction(x)) for x in lam])
     val = oracle.integrand_at(v, np.array([float(Fraction(x)) for x in tpoint]), lo, norders)
     return val[:, 0] + 1j * val[:, 1]
 
@@ -101,6 +117,18 @@ def test_subtracted_integrand_matches_symbolic(case):
     for tp in points:
         got = _oracle_integrand(d, a, b, U, u0, u1, F, f0, f1, tp, lo, no)
         exact = _exact_integrand(d, a, b, U, u0, u1, F, f0, f1, tp, lo, no)
+        scale = np.max(np.abs(exact))
+        assert np.max(np.abs(got - exact)) <= 1e-12 * scale, (tp, got, exact)
+
+
+@pytest.mark.parametrize("case", range(len(DEFORMED_CASES)))
+def test_deformed_subtracted_integrand_matches_symbolic(case):
+    # contour-deformed sectors: the Taylor coefficients pass through z(t),
+    # rho(t), det J and U(z), F(z)
+    d, a, b, U, u0, u1, F, f0, f1, lo, no, points, lam = DEFORMED_CASES[case]
+    for tp in points:
+        got = _oracle_integrand(d, a, b, U, u0, u1, F, f0, f1, tp, lo, no, lam)
+        exact = _exact_integrand(d, a, b, U, u0, u1, F, f0, f1, tp, lo, no, lam)
         scale = np.max(np.abs(exact))
         assert np.max(np.abs(got - exact)) <= 1e-12 * scale, (tp, got, exact)
 
