@@ -87,6 +87,12 @@ def _workloads():
             transform=1,
             desc="box1L_massless in D=2-2eps s=-3 t=-2, 12 sectors d=3 with a_j=-2 (Taylor subtraction), "
                  "eps^-2..eps^0, n={n} CBC, m={m} shifts, baker transform"),
+        # the same box at 64 physical points: deformed sectors with a_j = -2
+        "box1L_massless_d2_physical": dict(
+            make=lambda: w.box_massless_d2(deform=True), kin=w.massive_box_points(64, seed=3).tolist(), lo=-2,
+            nord=3, n=10007, m=32, deform=True, transform=1,
+            desc="box1L_massless in D=2-2eps deformed, 64 (s,t) s~U[5,20] t~U[-8,-1] seed 3, 12 sectors d=3 "
+                 "with a_j=-2 (Taylor subtraction), eps^-2..eps^0, n={n} CBC, m={m} shifts, baker transform"),
         # the default: two-loop planar massless double box, Euclidean point
         "box2L_planar_massless": dict(
             make=lambda method="iterative": w.double_box_massless(method=method), kin=[[-3.0, -1.0]], lo=-4, nord=5, n=1000003, m=32, deform=False,
@@ -426,7 +432,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["box1L_massless", "triangle_massive", "box1L_massive_batch", "box1L_massless_physical",
-                             "box1L_massless_d2",
+                             "box1L_massless_d2", "box1L_massless_d2_physical",
                              "box2L_planar_massless"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--decomposition", default="iterative", choices=["iterative", "geometric"],

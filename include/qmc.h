@@ -176,11 +176,12 @@ int qmc_set_lattices(qmc_ctx *ctx, const uint64_t *n, const uint32_t *z, int cou
  * F^{f0+f1 eps}) is the one written by the Python input generators. Sector
  * limits: d <= 6, at most 4 singular variables (a_j <= -1), a_j >= -4,
  * exponents <= 4 per variable, <= 3 invariants; deformed sectors d <= 3 with
- * at most 2 singular variables, all with a_j = -1. A variable with
+ * at most 2 singular variables. A variable with
  * a_j = -p, p >= 2, takes the Taylor subtraction of degree p - 1 (the
  * integrand gains the boundary terms g_k / (k - p + 1 + b_j eps), k < p, of
  * int_0^1 t^{-p + b_j eps} g(t) dt); prod_j p_j over the singular variables
- * must stay <= 16 (d <= 3, <= 2 singular variables) or <= 72 (otherwise).
+ * must stay <= 16 (d <= 3, <= 2 singular variables, and every deformed
+ * sector) or <= 72 (otherwise).
  * Sectors with d <= 3 and <= 2 singular variables run in the compact
  * evaluators (series of <= 4 eps orders, i.e. highest requested order +
  * singular variables + 1 <= 4), the others in the d <= 6 evaluators (<= 6).
@@ -285,14 +286,15 @@ int qmc_presample_lambda(qmc_ctx *ctx, qmc_job *jobs, int njobs, int lo, int nor
  * singular variables, 6: its mixed-precision variant, 7: the mixed-precision
  * variant of 1, 8: real d <= 3 with exponents a_j <= -2 (Taylor
  * subtraction), 9: real d <= 6 with 3 singular variables, 10: its
- * mixed-precision variant, 11: real d <= 6 with exponents a_j <= -2; class 2
- * then holds the d <= 6 sectors with 4): on up to 32 of the
+ * mixed-precision variant, 11: real d <= 6 with exponents a_j <= -2, 12:
+ * deformed d <= 3 with exponents a_j <= -2; class 2 then holds the d <= 6
+ * sectors with 4): on up to 32 of the
  * given jobs per class (at most 8 shifts each) every block size in
  * {128, 256} and points per thread in {1, 2, 4, 8, 16, 32} is timed with CUDA
  * events; the fastest is kept in the context and used by later plans whose
  * options leave block/ppt at 0. best_block/best_ppt (may be NULL) receive
  * QMC_NUM_CLASSES entries (0 = class absent). */
-#define QMC_NUM_CLASSES 12
+#define QMC_NUM_CLASSES 13
 int qmc_autotune(qmc_ctx *ctx, const qmc_job *jobs, int njobs, int lo, int norders, int *best_block,
                  int *best_ppt);
 

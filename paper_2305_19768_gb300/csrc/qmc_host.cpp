@@ -180,9 +180,15 @@ int classify(qmc_ctx *ctx, HostSector &S, int si) {
     }
     if (S.ns > QMC_SMAX) return fail(ctx, QMC_E_INVAL, "sector %d: %d singular variables > %d", si, S.ns, QMC_SMAX);
     if (box > 1) {
-        // some a_j <= -2: Taylor subtraction (undeformed sectors)
-        if (S.deform)
-            return fail(ctx, QMC_E_INVAL, "sector %d: a_j <= -2 (Taylor subtraction) needs an undeformed sector", si);
+        // some a_j <= -2: Taylor subtraction
+        if (S.deform) {
+            if (S.d > 3 || S.ns > 2 || box > QMC_JMAX3)
+                return fail(ctx, QMC_E_INVAL,
+                            "sector %d: a deformed sector with a_j <= -2 needs d <= 3, <= 2 singular variables "
+                            "and a Taylor box of <= %d coefficients", si, QMC_JMAX3);
+            S.cls = QMC_CLASS_CPLX3H;
+            return QMC_OK;
+        }
         if (S.d <= 3 && S.ns <= 2 && box <= QMC_JMAX3) {
             S.cls = QMC_CLASS_REAL3H;
         } else if (box <= QMC_JMAX6) {

@@ -101,7 +101,8 @@ enum QmcClass {
     QMC_CLASS_REAL6T = 9,  // former split of REAL6 (3 singular variables); now the REAL6 kernel
     QMC_CLASS_REAL6TM = 10,// its mixed-precision variant (the REAL6M kernel)
     QMC_CLASS_REAL6H = 11, // real, d <= 6, <= 4 singular variables, some with a <= -2 (Taylor subtraction)
-    QMC_NCLASS = 12
+    QMC_CLASS_CPLX3H = 12, // contour-deformed, d <= 3, <= 2 singular variables, some with a <= -2
+    QMC_NCLASS = 13
 };
 
 static inline bool qmc_class_big(int cls) {

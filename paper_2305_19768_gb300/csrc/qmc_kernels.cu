@@ -1691,6 +1691,452 @@ __device__ __forceinline__ void eval_deformed(const TileSmem<LMAX> &S, const dou
     assemble<SMAX, LMAX, dc>(ns, lo, hi, nord, BV, LV, it, lt, bq, ib, A_empty, S.invb_full, res);
 }
 
+// ---------------------------------------------------------------- Taylor subtraction, deformed
+// Deformed sectors (d <= 3, <= 2 singular variables) with some a_q <= -2.
+// The subtraction is that of eval_real_taylor; the Taylor coefficients of
+//   G = det J prod_{singular} rho_j^{a_j+b_j eps} prod_{regular} z_j^{a_j+b_j eps}
+//       U(z)^{u0+u1 eps} F(z)^{f0+f1 eps}
+// in the zeroed variables come from every quantity of the deformation formed
+// on jets: dF/dt_j and d2F/dt_j dt_l from their monomial tables (t_V^e lands
+// at entry e), g_j = lambda_j (1 - t_j) dF_j, rho_j = 1 - i g_j, z_j = t_j rho_j,
+// det J = (1 - E2(V)) + i (det V - tr V) with V_jl = lambda_j (t_j (1 - t_j)
+// d2F_jl + delta_jl (1 - 2 t_j) dF_j), U(z) and F(z) from complex jet powers of
+// z. Each power factor P^{e0 + e1 eps} enters through L_P = ln P0 + ln(1 + x):
+// with A = sum e0 L_P and B = sum e1 L_P, G = det J exp(A) exp(eps B), and
+//   G(eps) = sum_i eps^i det J exp(A) B^i / i!.
+// Complex jets in local memory, plain loops: such sectors are few.
+namespace taylor {
+// c = a b over the box for complex jets (see jet_mul)
+__device__ __forceinline__ void cjet_mul(const dc *a, const dc *b, dc *c, int J, const uint16_t *dig, uint32_t off) {
+#pragma unroll 1
+    for (int k = 0; k < J; ++k) c[k] = dc{0.0, 0.0};
+#pragma unroll 1
+    for (int i = 0; i < J; ++i) {
+        const dc ai = a[i];
+#pragma unroll 1
+        for (int j = 0; i + j < J; ++j)
+            if ((((uint32_t)dig[i] + dig[j] + off) & 0x8888u) == 0u) {
+                const dc bj = b[j];
+                dc &r = c[i + j];
+                r.re = fma(ai.re, bj.re, fma(-ai.im, bj.im, r.re));
+                r.im = fma(ai.re, bj.im, fma(ai.im, bj.re, r.im));
+            }
+    }
+}
+// principal log; on the real axis the argument from below (m0: F - i0) or above
+__device__ __forceinline__ dc clog_br(dc a, bool m0, const uint64_t *tab, const double *atab) {
+    double arg = (a.im == 0.0) ? (a.re < 0.0 ? (m0 ? -CUDART_PI : CUDART_PI) : 0.0) : qatan2(a.im, a.re, atab);
+    return dc{0.5 * qlog(fma(a.re, a.re, a.im * a.im), tab), arg};
+}
+}  // namespace taylor
+
+template <int LMAX, int JMAX>
+__device__ __noinline__ void eval_deformed_taylor(const TileSmem<LMAX> &S, const double (&t)[3], const double (&omt)[3],
+                                                  int lo, int hi, int nord, dc (&res)[LMAX], int &signfail) {
+    constexpr int SMAX = 2, DM = 3;
+    constexpr int OFF = SMAX;
+    constexpr int NT = SMAX + LMAX;
+    constexpr int PMAX = QMC_PMAX;
+    const QmcSectorDev &sec = S.sec;
+    const int d = sec.d, ns = sec.ns;
+    const int dbase = sec.nU + sec.nF;
+    const uint64_t *tab = S.logtab;
+    const double *atab = S.atantab;
+    const int Hm = hi + ns;
+    int slot[DM];
+#pragma unroll
+    for (int j = 0; j < DM; ++j) slot[j] = -1;
+    // per singular slot: psi_q = t^{-p+b eps} (kept) and phi_q(k) (at t = 0)
+    double psi[SMAX][NT];
+    double phi[SMAX][PMAX][NT];
+    int p[SMAX];
+#pragma unroll 1
+    for (int q = 0; q < ns; ++q) {
+        const int j = sec.sing[q];
+        slot[j] = q;
+        p[q] = -sec.a[j];
+        const double tq = t[j], tinv = qrcp(tq), bq = sec.b[j];
+        const double bl = bq * qlog(tq, tab);
+        const double rb = qrcp(bq);
+        double E[NT];
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) E[i] = 0.0;
+        double e = 1.0;
+#pragma unroll 1
+        for (int i = 0; i <= Hm; ++i) {
+            E[OFF + i] = e;
+            e = e * bl * taylor::inv_k[i + 1];
+        }
+        const double tp = ipow_signed<double>(tq, tinv, -p[q]);
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) psi[q][i] = tp * E[i];
+#pragma unroll 1
+        for (int k = 0; k < p[q]; ++k) {
+            const double c = ipow_signed<double>(tq, tinv, k - p[q]);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) phi[q][k][i] = -c * E[i];
+            const int m = k - p[q] + 1;
+            if (m == 0) {
+                phi[q][k][OFF - 1] += rb;
+            } else {
+                double v = -taylor::inv_k[-m];
+                const double r = -bq * v;
+#pragma unroll 1
+                for (int i = 0; i <= Hm; ++i) {
+                    phi[q][k][OFF + i] += v;
+                    v *= r;
+                }
+            }
+        }
+    }
+    double tpw[DM][QMC_EMAX];
+    powers<DM, double>(t, d, sec.pad0, tpw);
+    double acc_re[NT], acc_im[NT];
+#pragma unroll 1
+    for (int i = 0; i < NT; ++i) acc_re[i] = acc_im[i] = 0.0;
+
+    double tj[DM][JMAX], oj[DM][JMAX], Fj[DM][JMAX], Hs[DM][DM][JMAX], gj[DM][JMAX], wk[JMAX], wk2[JMAX];
+    dc zj[DM][JMAX], rj[DM][JMAX], zp[DM][QMC_EMAX][JMAX], cu[JMAX], cf[JMAX], cx[JMAX], cy[JMAX], cA[JMAX],
+        cB[JMAX], dJ[JMAX];
+    dc gi[LMAX][JMAX];
+    uint16_t dig[JMAX];
+#pragma unroll 1
+    for (int V = 0; V < (1 << ns); ++V) {
+        int rad[SMAX], stride[SMAX];
+        int J = 1, K = 0, nd = 0;
+        uint32_t off = 0;
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            rad[q] = 1;
+            stride[q] = 0;
+            if (((V >> q) & 1) && p[q] > 1) {
+                rad[q] = p[q];
+                stride[q] = J;
+                J *= p[q];
+                K += p[q] - 1;
+                off |= (uint32_t)(8 - p[q]) << (4 * nd);
+                ++nd;
+            }
+        }
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) {
+            uint32_t w = 0;
+            int n4 = 0;
+#pragma unroll 1
+            for (int q = 0; q < ns; ++q)
+                if (rad[q] > 1) {
+                    w |= (uint32_t)((i / stride[q]) % rad[q]) << (4 * n4);
+                    ++n4;
+                }
+            dig[i] = (uint16_t)w;
+        }
+        // t_j and 1 - t_j as jets
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) tj[j][i] = oj[j][i] = 0.0;
+            const int q = slot[j];
+            if (q >= 0 && ((V >> q) & 1)) {
+                oj[j][0] = 1.0;
+                if (rad[q] > 1) {
+                    tj[j][stride[q]] = 1.0;
+                    oj[j][stride[q]] = -1.0;
+                }
+            } else {
+                tj[j][0] = t[j];
+                oj[j][0] = omt[j];
+            }
+        }
+        // a polynomial's monomials [m0, m1) of the staged table as a jet
+        auto poly_jet = [&](int m0, int m1, double *out) {
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) out[i] = 0.0;
+#pragma unroll 1
+            for (int m = m0; m < m1; ++m) {
+                const uint32_t ex = S.exps[m];
+                double v = S.cval[m];
+                int idx = 0;
+                bool keep = true;
+#pragma unroll
+                for (int j = 0; j < DM; ++j) {
+                    const uint32_t ej = (ex >> (4 * j)) & 15u;
+                    if (j >= d || ej == 0u) continue;
+                    const int q = slot[j];
+                    if (q >= 0 && ((V >> q) & 1)) {
+                        if ((int)ej >= rad[q]) keep = false;
+                        else idx += (int)ej * stride[q];
+                    } else {
+                        v *= pow_sel<double>(tpw[j], ej);
+                    }
+                }
+                if (keep) out[idx] += v;
+            }
+        };
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) poly_jet(dbase + sec.dFoff[j], dbase + sec.dFoff[j] + sec.dFn[j], Fj[j]);
+#pragma unroll 1
+        for (int j = 0; j < d; ++j)
+#pragma unroll 1
+            for (int l = j; l < d; ++l) {
+                const int h = j * QMC_DMAX - j * (j - 1) / 2 + (l - j);   // host packing order
+                poly_jet(dbase + sec.Hoff[h], dbase + sec.Hoff[h] + sec.Hn[h], Hs[j][l]);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) Hs[l][j][i] = Hs[j][l][i];
+            }
+        // g_j, rho_j = 1 - i g_j, z_j = t_j rho_j, and V_jl into Hs
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            const double lam = S.job.lambda[j];
+            taylor::jet_mul(oj[j], Fj[j], gj[j], J, dig, off);
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) {
+                gj[j][i] *= lam;
+                rj[j][i] = dc{i == 0 ? 1.0 : 0.0, -gj[j][i]};
+            }
+            taylor::jet_mul(tj[j], gj[j], wk, J, dig, off);
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) zj[j][i] = dc{tj[j][i], -wk[i]};
+        }
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            const double lam = S.job.lambda[j];
+            taylor::jet_mul(tj[j], oj[j], wk, J, dig, off);       // t_j (1 - t_j)
+#pragma unroll 1
+            for (int l = 0; l < d; ++l) {
+                taylor::jet_mul(wk, Hs[j][l], wk2, J, dig, off);
+                if (l == j) {
+                    double u[JMAX];
+#pragma unroll 1
+                    for (int i = 0; i < J; ++i) u[i] = oj[j][i] - tj[j][i];
+                    double u2[JMAX];
+                    taylor::jet_mul(u, Fj[j], u2, J, dig, off);
+#pragma unroll 1
+                    for (int i = 0; i < J; ++i) wk2[i] += u2[i];
+                }
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) gi[0][i].re = lam * wk2[i];   // scratch row
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) Hs[j][l][i] = gi[0][i].re;    // Hs now holds V_jl
+            }
+        }
+        // det J = (1 - E2) + i (det V - tr V) (d = 3); (1 - det V) - i tr V (d = 2); 1 - i V00 (d = 1)
+        {
+            double e2[JMAX], dv[JMAX], tr[JMAX];
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) e2[i] = dv[i] = tr[i] = 0.0;
+#pragma unroll 1
+            for (int j = 0; j < d; ++j)
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) tr[i] += Hs[j][j][i];
+            auto minor2 = [&](int a, int b, int c, int e, double *out) {   // V_ab V_ce - V_ae V_cb
+                taylor::jet_mul(Hs[a][b], Hs[c][e], out, J, dig, off);
+                taylor::jet_mul(Hs[a][e], Hs[c][b], wk, J, dig, off);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) out[i] -= wk[i];
+            };
+            if (d == 2) {
+                minor2(0, 0, 1, 1, dv);
+            } else if (d == 3) {
+                double m[JMAX];
+                minor2(0, 0, 1, 1, m);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) e2[i] += m[i];
+                minor2(0, 0, 2, 2, m);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) e2[i] += m[i];
+                minor2(1, 1, 2, 2, m);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) e2[i] += m[i];
+                // det V by the first row: V00 c00 - V01 c01 + V02 c02
+                minor2(1, 1, 2, 2, m);
+                taylor::jet_mul(Hs[0][0], m, dv, J, dig, off);
+                minor2(1, 0, 2, 2, m);
+                taylor::jet_mul(Hs[0][1], m, wk2, J, dig, off);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) dv[i] -= wk2[i];
+                minor2(1, 0, 2, 1, m);
+                taylor::jet_mul(Hs[0][2], m, wk2, J, dig, off);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) dv[i] += wk2[i];
+            }
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) {
+                const double one = i == 0 ? 1.0 : 0.0;
+                if (d == 3) dJ[i] = dc{one - e2[i], dv[i] - tr[i]};
+                else if (d == 2) dJ[i] = dc{one - dv[i], -tr[i]};
+                else dJ[i] = dc{one, -tr[i]};
+            }
+        }
+        // powers of z_j, then U(z) and F(z)
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) zp[j][0][i] = zj[j][i];
+#pragma unroll 1
+            for (int e = 1; e < sec.pad0 && e < QMC_EMAX; ++e) taylor::cjet_mul(zp[j][e - 1], zj[j], zp[j][e], J, dig, off);
+        }
+#pragma unroll 1
+        for (int w = 0; w < 2; ++w) {
+            dc *P = w == 0 ? cu : cf;
+            const int m0 = w == 0 ? 0 : sec.nU, m1 = w == 0 ? sec.nU : sec.nU + sec.nF;
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) P[i] = dc{0.0, 0.0};
+#pragma unroll 1
+            for (int m = m0; m < m1; ++m) {
+                const uint32_t ex = S.exps[m];
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) cx[i] = dc{i == 0 ? S.cval[m] : 0.0, 0.0};
+#pragma unroll 1
+                for (int j = 0; j < d; ++j) {
+                    const uint32_t ej = (ex >> (4 * j)) & 15u;
+                    if (ej == 0u) continue;
+                    taylor::cjet_mul(cx, zp[j][ej - 1], cy, J, dig, off);
+#pragma unroll 1
+                    for (int i = 0; i < J; ++i) cx[i] = cy[i];
+                }
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) P[i] = P[i] + cx[i];
+            }
+        }
+        if (cf[0].im > 0.0) ++signfail;   // F on the wrong side of the cut at this corner
+        // A = sum e0 L_P, B = sum e1 L_P over the power factors
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) cA[i] = cB[i] = dc{0.0, 0.0};
+#pragma unroll 1
+        for (int f = 0; f < d + 2; ++f) {
+            const dc *P;
+            double e0, e1;
+            bool m0 = false;
+            if (f < d) {
+                if (slot[f] >= 0) P = rj[f];
+                else if (sec.a[f] != 0 || sec.b[f] != 0.0) P = zj[f];
+                else continue;
+                e0 = sec.a[f];
+                e1 = sec.b[f];
+            } else if (f == d) {
+                P = cu;
+                e0 = sec.u0;
+                e1 = sec.u1;
+            } else {
+                P = cf;
+                e0 = sec.f0;
+                e1 = sec.f1;
+                m0 = true;
+            }
+            if (e0 == 0.0 && e1 == 0.0) continue;
+            // L = ln P0 + ln(1 + x), x = (P - P0) / P0, ln(1 + x) = x h by Horner
+            const dc r0 = cinv(P[0]);
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) cx[i] = i == 0 ? dc{0.0, 0.0} : P[i] * r0;
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) cy[i] = dc{0.0, 0.0};
+            cy[0] = dc{((K - 1) & 1 ? -1.0 : 1.0) * taylor::inv_k[K > 0 ? K : 1], 0.0};
+#pragma unroll 1
+            for (int k = K - 2; k >= 0; --k) {
+                taylor::cjet_mul(cx, cy, gi[0], J, dig, off);
+#pragma unroll 1
+                for (int i = 0; i < J; ++i) cy[i] = gi[0][i];
+                cy[0].re += (k & 1 ? -1.0 : 1.0) * taylor::inv_k[k + 1];
+            }
+            taylor::cjet_mul(cx, cy, gi[0], J, dig, off);
+            const dc l0 = taylor::clog_br(P[0], m0, tab, atab);
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) {
+                const dc L = i == 0 ? l0 : (K > 0 ? gi[0][i] : dc{0.0, 0.0});
+                cA[i] = cA[i] + L * e0;
+                cB[i] = cB[i] + L * e1;
+            }
+        }
+        // exp(A) = exp(A0) (1 + A~ (1 + A~/2 (1 + ...))), A~ = A - A0
+        const dc ea = cexp_(cA[0]);
+        cA[0] = dc{0.0, 0.0};
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) cy[i] = dc{i == 0 ? 1.0 : 0.0, 0.0};
+#pragma unroll 1
+        for (int k = K; k >= 1; --k) {
+            taylor::cjet_mul(cA, cy, cx, J, dig, off);
+            const double r = taylor::inv_k[k];
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) cy[i] = cx[i] * r;
+            cy[0].re += 1.0;
+        }
+#pragma unroll 1
+        for (int i = 0; i < J; ++i) cx[i] = cy[i] * ea;
+        taylor::cjet_mul(dJ, cx, gi[0], J, dig, off);    // det J exp(A)
+        // G_i = det J exp(A) B^i / i!
+#pragma unroll 1
+        for (int n = 1; n <= Hm; ++n) {
+            taylor::cjet_mul(gi[n - 1], cB, gi[n], J, dig, off);
+            const double r = taylor::inv_k[n];
+#pragma unroll 1
+            for (int i = 0; i < J; ++i) gi[n][i] = gi[n][i] * r;
+        }
+        // T = sum_kappa (sum_i eps^i G_i[kappa]) prod_{q in V} phi_q(kappa_q)
+        double Tr[NT], Ti[NT];
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) Tr[i] = Ti[i] = 0.0;
+#pragma unroll 1
+        for (int kap = 0; kap < J; ++kap) {
+            double P[NT], Q[NT], gr[NT], gim[NT];
+            bool first = true;
+#pragma unroll 1
+            for (int q = 0; q < ns; ++q) {
+                if (!((V >> q) & 1)) continue;
+                const int k = rad[q] > 1 ? (kap / stride[q]) % rad[q] : 0;
+                if (first) {
+#pragma unroll 1
+                    for (int i = 0; i < NT; ++i) P[i] = phi[q][k][i];
+                    first = false;
+                } else {
+                    taylor::ser_mul<NT, OFF>(P, phi[q][k], Q, Hm);
+#pragma unroll 1
+                    for (int i = 0; i < NT; ++i) P[i] = Q[i];
+                }
+            }
+            if (first) {
+#pragma unroll 1
+                for (int i = 0; i < NT; ++i) P[i] = i == OFF ? 1.0 : 0.0;
+            }
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) {
+                const bool in = i >= OFF && i - OFF <= Hm;
+                gr[i] = in ? gi[i - OFF][kap].re : 0.0;
+                gim[i] = in ? gi[i - OFF][kap].im : 0.0;
+            }
+            taylor::ser_mul<NT, OFF>(gr, P, Q, Hm);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) Tr[i] += Q[i];
+            taylor::ser_mul<NT, OFF>(gim, P, Q, Hm);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) Ti[i] += Q[i];
+        }
+        // prod_{q not in V} psi_q
+        double base[NT], Q[NT];
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) base[i] = i == OFF ? 1.0 : 0.0;
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            if ((V >> q) & 1) continue;
+            taylor::ser_mul<NT, OFF>(base, psi[q], Q, Hm);
+#pragma unroll 1
+            for (int i = 0; i < NT; ++i) base[i] = Q[i];
+        }
+        taylor::ser_mul<NT, OFF>(base, Tr, Q, Hm);
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) acc_re[i] += Q[i];
+        taylor::ser_mul<NT, OFF>(base, Ti, Q, Hm);
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i) acc_im[i] += Q[i];
+    }
+#pragma unroll
+    for (int o = 0; o < LMAX; ++o) {
+        res[o] = dc{0.0, 0.0};
+#pragma unroll 1
+        for (int i = 0; i < NT; ++i)
+            if (o < nord && i == lo + o + OFF) res[o] = dc{acc_re[i], acc_im[i]};
+    }
+}
+
 // ---------------------------------------------------------------- tile staging
 template <int LMAX>
 __device__ void stage_tile(TileSmem<LMAX> &S, const QmcLaunch &Lc, int jidx) {
@@ -1857,7 +2303,9 @@ __device__ __forceinline__ void thread_points(const TileSmem<LMAX> &S, const Qmc
             for (int i = 0; i < NO; ++i) accN[i] = fma(resN[i], W, accN[i]);
         } else {
             T res[LMAX];
-            if constexpr (CPLX) {
+            if constexpr (CPLX && HS) {
+                eval_deformed_taylor<LMAX, QMC_JMAX3>(S, t, omt, lo, hi, nord, res, signfail_tile);
+            } else if constexpr (CPLX) {
                 eval_deformed<DMAX, SMAX, LMAX, MIXED>(S, t, omt, lo, hi, nord, res, signfail_tile);
             } else {
                 if constexpr (HS) {
@@ -2243,6 +2691,7 @@ extern "C" int QMC_PART_FN(qmc_k_launch_eval, QMC_PART)(int cls, const QmcLaunch
 #elif QMC_PART == 3
         case QMC_CLASS_REAL3H: return launch_cls<3, 2, 4, false, false, true>(L, block, ppt, grid, st);
         case QMC_CLASS_REAL6H: return launch_cls<6, 4, 6, false, false, true>(L, block, ppt, grid, st);
+        case QMC_CLASS_CPLX3H: return launch_cls<3, 2, 4, true, false, true>(L, block, ppt, grid, st);
 #endif
         default: return -2;
     }
@@ -2266,6 +2715,7 @@ extern "C" int QMC_PART_FN(qmc_k_occupancy, QMC_PART)(int cls, int block, int pr
 #elif QMC_PART == 3
         case QMC_CLASS_REAL3H: return occupancy_cls<3, 2, 4, false, false, true>(block, prow);
         case QMC_CLASS_REAL6H: return occupancy_cls<6, 4, 6, false, false, true>(block, prow);
+        case QMC_CLASS_CPLX3H: return occupancy_cls<3, 2, 4, true, false, true>(block, prow);
 #endif
         default: return 0;
     }

@@ -422,8 +422,121 @@ def taylor_sector_work(sector, lo: int, norders: int) -> Work:
     return w
 
 
+def _deriv_terms(terms, j):
+    """Exponent tuples of dP/dt_j, merged by exponent (the host's table)."""
+    out = []
+    for e in terms:
+        if e[j] == 0:
+            continue
+        f = list(e)
+        f[j] -= 1
+        f = tuple(f)
+        if f not in out:
+            out.append(f)
+    return out
+
+
+def deformed_taylor_sector_work(sector, lo: int, norders: int) -> Work:
+    """Work of one evaluation of a deformed sector with exponents a_j <= -2
+    (the deformed Taylor class), counted along the kernel's loops: real jet
+    products of 2 flops per (i, j) pair, complex ones of 8, series products
+    over NT = 6 orders."""
+    d, sing, ns, _ = _sector_shape(sector)
+    hi = lo + norders - 1
+    p = [-int(sector.a[j]) for j in sing]
+    SMAX, LMAX = 2, 4
+    NT, OFF = SMAX + LMAX, SMAX
+    Hm = hi + ns
+    smul = 2 * _ser_mul_pairs(NT, OFF, Hm)
+    emax = max(sector.U.max_var_exponent(), sector.F.max_var_exponent(), 1)
+    for j in range(d):
+        if sector.a[j] > 0:
+            emax = max(emax, int(sector.a[j]))
+    Fterms = list(sector.F.terms)
+    dF = [_deriv_terms(Fterms, j) for j in range(d)]
+    emax = max([emax] + [max(e) for tl in dF for e in tl if e])
+    Hterms = {}
+    for j in range(d):
+        for l in range(j, d):
+            Hterms[(j, l)] = _deriv_terms(dF[j], l)
+    w = Work()
+    w.fp64 += d - 1 + 2                        # korobov3 weight product, W = Ws^3
+    for pq in p:                               # per singular slot (as the real class)
+        w.recip(2)
+        w.log += 1
+        w.fp64 += 1 + 2 * (Hm + 1) + (pq - 1) + NT
+        for k in range(pq):
+            w.fp64 += max(pq - k - 1, 0) + NT
+            w.fp64 += 1 if k == pq - 1 else 1 + 2 * (Hm + 1)
+    w.fp64 += _powers(d, emax)
+    u0, f0, u1, f1 = (float(x) for x in (sector.u0, sector.f0, sector.u1, sector.f1))
+    nfac = sum(1 for j in range(d) if j in sing or int(sector.a[j]) != 0 or float(sector.b[j]) != 0.0)
+    nfac += (u0 != 0 or u1 != 0) + (f0 != 0 or f1 != 0)
+    for V in range(1 << ns):
+        rad = [p[q] if (V >> q) & 1 and p[q] > 1 else 1 for q in range(ns)]
+        J = 1
+        pairs = 1
+        for r in rad:
+            J *= r
+            pairs *= r * (r + 1) // 2
+        K = sum(r - 1 for r in rad)
+        jm, cjm = 2 * pairs, 8 * pairs
+        zeroed = [sing[q] for q in range(ns) if (V >> q) & 1]
+
+        def poly_jet(terms):
+            f = 0
+            for e in terms:
+                keep = True
+                for j in range(d):
+                    if e[j] == 0:
+                        continue
+                    if j in zeroed:
+                        q = sing.index(j)
+                        if e[j] >= rad[q]:
+                            keep = False
+                    else:
+                        f += 1
+                f += 1 if keep else 0
+            return f
+
+        for j in range(d):
+            w.fp64 += poly_jet(dF[j])
+        for key in Hterms:
+            w.fp64 += poly_jet(Hterms[key])
+        w.fp64 += d * (2 * jm + J)             # g_j, z_j
+        w.fp64 += d * jm + d * d * (jm + J) + d * (2 * J + jm)   # V_jl
+        minor2 = 2 * jm + J
+        w.fp64 += d * J                        # tr V
+        if d == 3:
+            w.fp64 += 6 * minor2 + 3 * jm + 5 * J + 2 * J
+        elif d == 2:
+            w.fp64 += minor2 + 2 * J
+        else:
+            w.fp64 += J
+        w.fp64 += d * max(emax - 1, 0) * cjm   # powers of z
+        for P in (sector.U.terms, sector.F.terms):
+            for e in P:
+                w.fp64 += sum(1 for j in range(d) if e[j] > 0) * cjm + 2 * J
+        for _ in range(nfac):                  # ln P0 + ln(1 + x), into A and B
+            w.recip()
+            w.fp64 += 5 + 6 * (J - 1) + 1 + max(K - 1, 0) * (cjm + 2) + cjm + 3 + 8 * J
+            w.log += 1
+            w.atan2 += 1
+        w.exp += 1
+        w.sincos += 1
+        w.fp64 += 2 + K * (cjm + 2 * J + 1) + 6 * J + cjm   # exp(A), det J exp(A)
+        w.fp64 += max(Hm, 0) * (cjm + 2 * J)   # G_i
+        inV = len(zeroed)
+        w.fp64 += J * (max(inV - 1, 0) * smul + 2 * smul + 2 * NT)
+        w.fp64 += (ns - inV) * smul + 2 * smul + 2 * NT
+    w.fp64 += 4 * norders                      # acc += res W (complex)
+    return w
+
+
 def sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
     if getattr(sector, "deform", False):
+        if any(int(a) <= -2 for a in sector.a):
+            return deformed_taylor_sector_work(sector, lo, norders)
         return deformed_sector_work(sector, lo, norders, mixed)
     if any(int(a) <= -2 for a in sector.a):
         return taylor_sector_work(sector, lo, norders)

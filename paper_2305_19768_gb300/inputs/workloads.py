@@ -84,13 +84,14 @@ def box_massless(deform: bool = False, method: str = "iterative") -> Integral:
     return _integral_from_graph(g, 4, deform=deform, method=method)
 
 
-def box_massless_d2(method: str = "iterative") -> Integral:
+def box_massless_d2(deform: bool = False, method: str = "iterative") -> Integral:
     """The one-loop massless box in D = 2 - 2 eps: U^{2 + 2 eps} F^{-3 - eps};
     12 sectors, each with one or two exponents a_j = -2 (Taylor subtraction of
-    degree 1 in one or two variables)."""
+    degree 1 in one or two variables); deform: contour deformation for
+    physical (s, t)."""
     g = Graph(edges=[(0, 1), (1, 2), (2, 3), (3, 0)], masses_sq=[Fraction(0)] * 4,
               legs=[0, 1, 2, 3], kin=kin_massless_4pt(), name="box1L_massless_d2")
-    return _integral_from_graph(g, 2, deform=False, method=method)
+    return _integral_from_graph(g, 2, deform=deform, method=method)
 
 
 def box_massive(msq=1, deform: bool = True) -> Integral:

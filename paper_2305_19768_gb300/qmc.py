@@ -32,7 +32,7 @@ ERRORS = {-1: "QMC_E_INVAL", -2: "QMC_E_PARSE", -3: "QMC_E_CUDA", -4: "QMC_E_TIM
           -5: "QMC_E_NOT_CONVERGED", -6: "QMC_E_SIGN_CHECK", -7: "QMC_E_NONFINITE", -8: "QMC_E_NOMEM"}
 
 
-QMC_NUM_CLASSES = 12  # evaluator classes (include/qmc.h)
+QMC_NUM_CLASSES = 13  # evaluator classes (include/qmc.h)
 
 
 class QmcError(RuntimeError):

@@ -21,7 +21,7 @@ from paper_2305_19768_gb300.inputs import workloads as w
 from paper_2305_19768_gb300.inputs.lattice import lattice_for
 
 from parity import CTOL_TAYLOR, Gpu, assert_close
-from subtraction_cases import CASES
+from subtraction_cases import CASES, DEFORMED_CASES
 from test_oracle_pins import _toy_integral
 
 pytestmark = pytest.mark.gpu
@@ -41,20 +41,20 @@ def _toy(case):
                          Fterms=fr(F), f0=Fraction(str(f0)), f1=Fraction(str(f1))), lo, no
 
 
-def _compare(g, tr, I, inv, n, m, lo, no, sectors=None, seed=3):
+def _compare(g, tr, I, inv, n, m, lo, no, sectors=None, seed=3, lam=None):
     iid = g.load(I)
     inv_arr = np.array([inv], dtype=np.float64) if inv else np.zeros((0, 0))
     qmc.qmc_set_kinematics(g.ctx, inv_arr)
     sectors = list(range(len(I.sectors))) if sectors is None else sectors
-    specs = [dict(integral_id=iid, sector=s, point=0, shifts=m, n=n, seed=seed, stream=s, **{"lambda": 0.0})
-             for s in sectors]
+    specs = [dict(integral_id=iid, sector=s, point=0, shifts=m, n=n, seed=seed, stream=s,
+                  **{"lambda": 0.0 if lam is None else lam}) for s in sectors]
     out, fails, rc = g.eval(iid, specs, lo, no)
     assert rc == 0, qmc.qmc_last_error(g.ctx)
     out = out.reshape(len(specs), m, no, 2)
     for i, sp in enumerate(specs):
         s = I.sectors[sp["sector"]]
         _, z = lattice_for(n, s.d)
-        view = oracle.SectorView(I, sp["sector"], list(inv), transform=tr)
+        view = oracle.SectorView(I, sp["sector"], list(inv), lam, transform=tr)
         o, a, f, c = oracle.shift_sums(view, n, z, oracle.shifts(seed, sp["stream"], m, s.d), lo, no,
                                        with_cond=True)
         assert_close(out[i], o, a, c, lo=lo, ctol=CTOL_TAYLOR,
@@ -95,3 +95,30 @@ def test_double_box_d2_sectors_of_every_box(gpu_tr):
             seen.add(key)
             sel.append(i)
     _compare(g, tr, I, [-3.0, -1.0], 1009, 2, -4, 5, sectors=sel)
+
+
+def _deformed_toy(case):
+    d, a, b, U, u0, u1, F, f0, f1, lo, no, _, lam = DEFORMED_CASES[case]
+    fr = lambda v: {e: Fraction(str(c)) for e, c in v.items()}
+    I = _toy_integral(d, a, [Fraction(x) for x in b], fr(U), u0=Fraction(str(u0)), u1=Fraction(str(u1)),
+                      Fterms=fr(F), f0=Fraction(str(f0)), f1=Fraction(str(f1)))
+    I.sectors[0].deform = True
+    return I, lo, no, float(Fraction(lam[0]))
+
+
+@pytest.mark.parametrize("case", range(len(DEFORMED_CASES)))
+def test_deformed_toy_sectors(gpu_tr, case):
+    # contour-deformed sectors with a_j <= -2 (the deformed Taylor class); one
+    # lambda for every variable of a job
+    g, tr = gpu_tr
+    I, lo, no, lam = _deformed_toy(case)
+    _compare(g, tr, I, [], 4001, 4, lo, no, lam=lam)
+    if case == 0:
+        _compare(g, tr, I, [], 100003, 2, lo, no, lam=lam)
+
+
+def test_deformed_massless_box_d2_physical(gpu_tr):
+    # D = 2 - 2 eps at a physical point (s = 9, t = -2): all 12 sectors deformed
+    g, tr = gpu_tr
+    I = w.box_massless_d2(deform=True)
+    _compare(g, tr, I, [9.0, -2.0], 4001, 4, -2, 3, lam=0.3)

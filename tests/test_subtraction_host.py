@@ -31,8 +31,12 @@ def test_loader_accepts_every_degree_and_rejects_the_rest():
                    toy([-4, -4, -4, -2], [1, 1, 1, 1]),   # box 128 > 72
                    toy([-2, -1], [0, 1])]                 # unregulated
         deformed = toy([-2, -1], [1, 1])
-        deformed.sectors[0].deform = True                 # a = -2 in a deformed sector
-        rejects.append(deformed)
+        deformed.sectors[0].deform = True                 # a = -2 in a deformed d = 2 sector: accepted
+        qmc.qmc_load_sectors_mem(ctx, deformed.to_text())
+        qmc.qmc_load_sectors_mem(ctx, w.box_massless_d2(deform=True).to_text())
+        wide = toy([-2, -2, 0, -1], [1, -1, 0, 2])
+        wide.sectors[0].deform = True                     # deformed with d = 4: rejected
+        rejects.append(wide)
         for I in rejects:
             with pytest.raises(qmc.QmcError) as e:
                 qmc.qmc_load_sectors_mem(ctx, I.to_text())
