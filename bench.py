@@ -103,16 +103,16 @@ def _workloads():
 # SHA-1 and this workload (any other source or workload reports null):
 # traffic = dram__bytes_read.sum + dram__bytes_write.sum per launch;
 # fp64_executed_flops_per_eval = (2 DFMA + DMUL + DADD thread instructions)
-# per evaluation; fp64_pipe_busy = sm__pipe_fp64_cycles_active of peak.
+# per evaluation; fp64_pipe_busy = sm__pipe_fp64_cycles_active of peak;
+# warp_inst_per_eval = smsp__inst_executed.sum per evaluation (the issue
+# roofline's numerator); issue_busy = smsp__issue_active of peak.
 PROFILED = {
     # double box, n = 1000003, m = 32 (the default line): traffic from a 1-pass
-    # capture of one full launch; FP64 instructions and pipe activity from the
+    # capture of one full launch; instruction counts and pipe activity from the
     # full capture of the same kernel at n = 20011 (per evaluation, the same code)
-    ("1ddf6e40e67e8e417936ce06d963bba0ebbb6e47", "box2L_planar_massless", "fp64", "iterative", 1000003): {
-        "traffic": 1605120 + 3574509056, "fp64_executed_flops_per_eval": 457.2, "fp64_pipe_busy": 0.693},
-    # one-loop box in D = 2 - 2 eps (Taylor subtraction), n = 10007: full capture
-    ("1ddf6e40e67e8e417936ce06d963bba0ebbb6e47", "box1L_massless_d2", "fp64", "iterative", 10007): {
-        "traffic": 801792 + 330914048, "fp64_executed_flops_per_eval": 1239.6, "fp64_pipe_busy": 0.532},
+    ("76aa350fe61515433bc16a2675f5d037ffad47af", "box2L_planar_massless", "fp64", "iterative", 1000003): {
+        "traffic": 1628160 + 3601233152, "fp64_executed_flops_per_eval": 290.7, "fp64_pipe_busy": 0.419,
+        "warp_inst_per_eval": 445.4, "issue_busy": 0.364},
 }
 
 def kernel_sha1():
@@ -564,17 +564,33 @@ def main():
     # against the FFMA peak; transcendentals per evaluation beside them
     work = flopmod.workload_work(I, LO, NORD, mixed=args.precision == "mixed")
     avg_eval_ms = float(np.mean(eval_ms))
-    achieved = work.fp64 * evals_per_step / (avg_eval_ms * 1e-3) / 1e9
+    rate = evals_per_step / (avg_eval_ms * 1e-3)
+    achieved = work.fp64 * rate / 1e9
     sha = kernel_sha1()
     prof = PROFILED.get((sha, args.workload, args.precision, args.decomposition, args.n), {})
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s (fp64)",
             "frac": achieved / peak_gflops, "traffic": prof.get("traffic"),
             "flops_per_eval": work.fp64, "peak_source": "DFMA probe in this run (of measured)",
-            "transcendentals_per_eval": {k: getattr(work, k) for k in ("log", "atan2", "rcp", "exp")},
+            "transcendentals_per_eval": {k: getattr(work, k) for k in ("log", "atan2", "rcp", "exp", "rcp_int")},
             "fp64_executed_flops_per_eval": prof.get("fp64_executed_flops_per_eval"),
             "fp64_pipe_busy": prof.get("fp64_pipe_busy"),
             "evals_per_launch": evals_per_step, "eval_ms_per_step": avg_eval_ms,
             "kernel_sha1": sha}
+    # the same formulation counted as if all of it ran in FP64 (the corner stage
+    # that the d <= 6 kernel runs on the integer pipe included): algorithmic,
+    # not FP64-pipe work
+    eq = flopmod.workload_work(I, LO, NORD, mixed=args.precision == "mixed", fp64_corners=True).fp64
+    if eq != work.fp64:
+        roof["algorithmic_fp64_equivalent"] = {"flops_per_eval": eq, "achieved": eq * rate / 1e9,
+                                               "frac": eq * rate / 1e9 / peak_gflops}
+    # the issue roofline: warp instructions per evaluation (ncu, this source)
+    # at the measured rate, against 4 warp instructions per SM per clock
+    if prof.get("warp_inst_per_eval") and clocks and clocks.get("sm_mhz"):
+        ipeak = 4.0 * torch.cuda.get_device_properties(local).multi_processor_count * clocks["sm_mhz"] * 1e6
+        roof["issue"] = {"warp_inst_per_eval": prof["warp_inst_per_eval"],
+                         "achieved": prof["warp_inst_per_eval"] * rate, "peak": ipeak,
+                         "frac": prof["warp_inst_per_eval"] * rate / ipeak, "unit": "warp instructions/s",
+                         "ncu_issue_busy": prof.get("issue_busy")}
     if work.fp32 > 0:
         peak32 = qmc.qmc_fp32_peak(ctx)
         a32 = work.fp32 * evals_per_step / (avg_eval_ms * 1e-3) / 1e9

@@ -74,27 +74,16 @@ QMC_HD int64_t qmc_smulhi(int64_t a, int64_t b) {
 #endif
 }
 
-// tab: 3 words per row j = 0..1024: RN(2^63/F_j), RN(2^116 ln F_j) low, high.
-QMC_HD double qmc_ilog(double x, const uint64_t *tab) {
-    const uint64_t bits = qmc_bits_of(x);
-    if (bits - 1ULL >= 0x7FEFFFFFFFFFFFFFULL) {      // zero, inf, NaN or negative
-        if ((bits << 1) == 0) return qmc_double_of(0xFFF0000000000000ULL);   // -inf
-        if (bits == 0x7FF0000000000000ULL) return x;                          // +inf
-        return qmc_double_of(0x7FF8000000000000ULL);                          // NaN
-    }
-    int e = (int)(bits >> 52) - 1023;
-    int64_t mb = (int64_t)(bits & 0xFFFFFFFFFFFFFULL);
-    if (e == -1023) {                                 // subnormal: normalise the mantissa
-        const int p = 63 - qmc_clz64(bits);
-        e = p - 1074;
-        mb = (int64_t)((bits << (52 - p)) & 0xFFFFFFFFFFFFFULL);
-    }
-    const int j = (int)((mb + (1LL << 41)) >> 42);   // 0..1024
-    const int64_t ri = mb - ((int64_t)j << 42);       // (m - F) 2^52, in [-2^41, 2^41)
+// ln(2^e (1 + frac63 2^-63)), frac63 in [0, 2^63), |e| <= 1074: the
+// reduction and the Q116 sum, rounded once. tab: 3 words per row
+// j = 0..1024: RN(2^63/F_j), RN(2^116 ln F_j) low, high.
+QMC_HD double qmc_ilog_core(int e, uint64_t frac63, const uint64_t *tab) {
+    const int j = (int)((frac63 + (1ULL << 52)) >> 53);   // 0..1024
+    const int64_t ri = (int64_t)frac63 - ((int64_t)j << 53);   // (m - F) 2^63, in [-2^52, 2^52)
     const bool fneg = ri < 0;
     const uint64_t ra = fneg ? (uint64_t)(-ri) : (uint64_t)ri;
-    // |f| 2^74 = |m - F| 2^52 RN(2^63/F) 2^-41 (truncated; exact for F = 1, 2)
-    const uint64_t fm = (uint64_t)(((qmc_u128)ra * tab[3 * j]) >> 41);
+    // |f| 2^74 = |m - F| 2^63 RN(2^63/F) 2^-52 (truncated; exact for F = 1, 2)
+    const uint64_t fm = (uint64_t)(((qmc_u128)ra * tab[3 * j]) >> 52);
     const int64_t fq = fneg ? -(int64_t)fm : (int64_t)fm;
     // c(f) in Q63: each step c <- C_k - f c, with f c = (f 2^74)(c 2^63) 2^-74
     int64_t c = QMC_ILOG_C6;
@@ -123,4 +112,21 @@ QMC_HD double qmc_ilog(double x, const uint64_t *tab) {
     // value 2^(11 - lz) (mant 2^-52); a carry out of mant moves into the exponent
     const uint64_t out = ((uint64_t)(1023 + 11 - lz - 1) << 52) + mant;
     return qmc_double_of(out | ((uint64_t)neg << 63));
+}
+
+QMC_HD double qmc_ilog(double x, const uint64_t *tab) {
+    const uint64_t bits = qmc_bits_of(x);
+    if (bits - 1ULL >= 0x7FEFFFFFFFFFFFFFULL) {      // zero, inf, NaN or negative
+        if ((bits << 1) == 0) return qmc_double_of(0xFFF0000000000000ULL);   // -inf
+        if (bits == 0x7FF0000000000000ULL) return x;                          // +inf
+        return qmc_double_of(0x7FF8000000000000ULL);                          // NaN
+    }
+    int e = (int)(bits >> 52) - 1023;
+    uint64_t mb = bits & 0xFFFFFFFFFFFFFULL;
+    if (e == -1023) {                                 // subnormal: normalise the mantissa
+        const int p = 63 - qmc_clz64(bits);
+        e = p - 1074;
+        mb = (bits << (52 - p)) & 0xFFFFFFFFFFFFFULL;
+    }
+    return qmc_ilog_core(e, mb << 11, tab);
 }

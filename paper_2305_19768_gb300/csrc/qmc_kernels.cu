@@ -27,6 +27,7 @@
 #include "qmc_ilog.h"
 #include "qmc_internal.h"
 #include "qmc_log_table.h"
+#include "qmc_xf.h"
 
 #ifndef QMC_PART
 #define QMC_PART 0
@@ -878,25 +879,48 @@ template <int NS> struct SlotArr {
     static constexpr int N = NS > 0 ? NS : 1;
 };
 
-template <int NS, int HI, class T>
-__device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (&LV)[1 << NS],
-                                               const double (&tb)[SlotArr<NS>::N],
-                                               const double (&lt)[SlotArr<NS>::N],
-                                               const double (&bq)[SlotArr<NS>::N], double A_empty,
-                                               double A_full, T (&resN)[NS + HI + 1]) {
+// The real fixed-order kernels' corner stage on the integer pipe (qmc_xf.h)
+// or in FP64: bit 0 for the d <= 6 kernel, bit 1 for the d <= 3 kernel.
+// Measured (evaluations/s): the double box 9.40e8 -> 1.01e9 at n = 1000003
+// with the integer corners; the box 4.28e9 with FP64 corners, 3.86e9 with
+// integer ones (its corners are few, and the conversions cost more than the
+// FP64 work they replace).
+#ifndef QMC_XF_CORNERS
+#define QMC_XF_CORNERS 1
+#endif
+// the pole sets' exponential series by Horner's rule (1) or by its powers (0)
+#ifndef QMC_HORNER
+#define QMC_HORNER 1
+#endif
+// the d <= 6 kernel's corner as one out-of-line function (1) or inlined with
+// an out-of-line logarithm (0): inlined, its sixteen copies per tile path
+// overflowed the instruction cache (8.3e8 evaluations/s on the double box)
+#ifndef QMC_CORNER_CALL
+#define QMC_CORNER_CALL 1
+#endif
+
+// Corner series B_V Lambda_V^i / i! in FP64, i < HI + |V| + 1
+template <int NS, int HI>
+__device__ __forceinline__ void series_fp64(const double (&BV)[1 << NS], const double (&LV)[1 << NS],
+                                            double (&g)[1 << NS][HI + NS + 1]) {
     constexpr int NG = 1 << NS;
     constexpr int LM = HI + NS + 1;   // series length of the full corner
-    T g[NG][LM];
-    // corner series B_V Lambda_V^i / i!, i < HI + |V| + 1
 #pragma unroll
     for (int V = 0; V < NG; ++V) {
         const int nV = HI + __popc(V) + 1;
         g[V][0] = BV[V];
 #pragma unroll
         for (int i = 1; i < LM; ++i)
-            if (i < nV) g[V][i] = i == 1 ? g[V][0] * LV[V] : mulsc(g[V][i - 1] * LV[V], 1.0 / i);
+            if (i < nV) g[V][i] = i == 1 ? g[V][0] * LV[V] : (g[V][i - 1] * LV[V]) * (1.0 / i);
     }
-    // superset Moebius transform: D_P = sum_{V >= P} (-1)^|V\P| G_V
+}
+
+// Superset Moebius transform of the corner series, in place:
+// g[P][i] <- D_P coefficient i, D_P = sum_{V >= P} (-1)^|V\P| B_V exp(eps Lambda_V)
+template <int NS, int HI>
+__device__ __forceinline__ void moebius_fp64(double (&g)[1 << NS][HI + NS + 1]) {
+    constexpr int NG = 1 << NS;
+    constexpr int LM = HI + NS + 1;
 #pragma unroll
     for (int q = 0; q < NS; ++q)
 #pragma unroll
@@ -907,6 +931,20 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
             for (int i = 0; i < LM; ++i)
                 if (i < nP) g[P][i] = g[P][i] - g[P | (1 << q)][i];
         }
+}
+
+// Assemble the Laurent coefficients from the Moebius-transformed corner
+// series g[P][i] (above):
+//   f = sum_P eps^{-|P|} A_P D_P(eps) exp(eps E_P),
+//   A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q,  E_P = sum_{q not in P} b_q ln t_q.
+template <int NS, int HI>
+__device__ __forceinline__ void pole_sets_fixed(const double (&g)[1 << NS][HI + NS + 1],
+                                                const double (&tb)[SlotArr<NS>::N],
+                                                const double (&lt)[SlotArr<NS>::N],
+                                                const double (&bq)[SlotArr<NS>::N], double A_empty,
+                                                double A_full, double (&resN)[NS + HI + 1]) {
+    constexpr int NG = 1 << NS;
+    constexpr int LM = HI + NS + 1;   // series length of the full corner
     // A_P = prod_{q in P} 1/b_q prod_{q not in P} 1/t_q by the subset
     // recursion A_P = A_{P - q} t_q / b_q (q the lowest slot of P), and
     // E_P = sum_{q not in P} b_q ln t_q by E_P = E_{P + q} + b_q ln t_q (q the
@@ -926,21 +964,39 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
         if (nP > 1) EP[P] = (P | (1 << q)) == NG - 1 ? bl[q] : EP[P | (1 << q)] + bl[q];
     }
 #pragma unroll
-    for (int i = 0; i < LM; ++i) resN[i] = zero<T>();
+    for (int i = 0; i < LM; ++i) resN[i] = 0.0;
 #pragma unroll
     for (int P = 0; P < NG; ++P) {
         const int np = __popc(P);
         const int nP = HI + np + 1;
         const double A = AP[P];
-        T PE[LM];
+        double PE[LM];
         if (P == NG - 1) {
             // every singular variable in the pole set: no exp(eps E_P) factor
 #pragma unroll
             for (int k = 0; k < LM; ++k)
                 if (k < nP) PE[k] = g[P][k];
         } else {
-            // the exponential series of E_P
             const double E = EP[P];
+#if QMC_HORNER
+            // PE_k = sum_{i <= k} g_i E^{k-i} / (k-i)! by Horner's rule:
+            // PE_k = g_k + E (g_{k-1} + E/2 (g_{k-2} + E/3 (...)))
+            double Ej[LM + 1];
+            Ej[1] = E;
+#pragma unroll
+            for (int j = 2; j < LM; ++j)
+                if (j < nP) Ej[j] = E * (1.0 / j);
+#pragma unroll
+            for (int k = 0; k < LM; ++k) {
+                if (k >= nP) continue;
+                double h = g[P][0];
+#pragma unroll
+                for (int i = 1; i < LM; ++i)
+                    if (i <= k) h = fma(Ej[k - i + 1], h, g[P][i]);
+                PE[k] = h;
+            }
+#else
+            // the exponential series of E_P
             double e[LM];
             e[0] = 1.0;
 #pragma unroll
@@ -952,13 +1008,14 @@ __device__ __forceinline__ void assemble_fixed(const T (&BV)[1 << NS], const T (
                 PE[k] = g[P][k];
 #pragma unroll
                 for (int i = 0; i < LM; ++i)
-                    if (i < k) PE[k] = PE[k] + mulsc(g[P][i], e[k - i]);
+                    if (i < k) PE[k] = fma(g[P][i], e[k - i], PE[k]);
             }
+#endif
         }
         // term k of pole set P is the order k - |P|
 #pragma unroll
         for (int k = 0; k < LM; ++k)
-            if (k < nP) resN[k - np + NS] = resN[k - np + NS] + mulsc(PE[k], A);
+            if (k < nP) resN[k - np + NS] = fma(PE[k], A, resN[k - np + NS]);
     }
 }
 
@@ -969,39 +1026,17 @@ __device__ __forceinline__ double qlog_fx(double x, const uint64_t *tab) {
     else return qmc_ilog(x, tab);
 }
 
-// ptd / ptf: this thread's column of the power table in shared memory (FP64
-// and, for the mixed classes, FP32 view of the same storage), row stride
-// `ps`, prow rows per variable
-template <int DMAX, int NS, int HI, bool MIXED, int LMAX>
-__device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const double (&t)[DMAX],
-                                             double (&resN)[NS + HI + 1], double *ptd, float *ptf, int ps,
-                                             int prow) {
+// The corner stage in FP64 for sectors whose exponents are not all small
+// integers (none of the built-in workloads): subset sums, 1/F in pairs of
+// corners, B_V and Lambda_V per corner, the corner series and their Moebius
+// transform.
+template <int DMAX, int NS, int HI>
+__device__ __forceinline__ void corners_fp64(const QmcSectorDev &sec, double (&hU)[1 << NS], double (&hF)[1 << NS],
+                                          double Cc, bool hasCc, double Lc, bool hasLc, const uint64_t *tab,
+                                          double (&gm)[1 << NS][HI + NS + 1]) {
     constexpr int NG = 1 << NS;
-    constexpr int NSA = SlotArr<NS>::N;
-    const QmcSectorDev &sec = S.sec;
-    const int d = sec.d;
-    const uint64_t *tab = S.logtab;
-    // group sums by singular mask, then subset sums h[X] = sum_{M subset X} g[M];
-    // the polynomial at corner V (t_V = 0) is h[(NG-1) ^ V]
-    double hU[NG], hF[NG];
-    if constexpr (MIXED) {
-        float tf[DMAX];
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j) tf[j] = __double2float_rn(t[j]);
-        powers_tab<DMAX, float>(tf, d, sec.pad0, prow, ptf, ps);
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            hU[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.gU[g], sec.gU[g + 1], ptf, ps);
-            hF[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptf, ps);
-        }
-    } else {
-        powers_tab<DMAX, double>(t, d, sec.pad0, prow, ptd, ps);
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            hU[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.gU[g], sec.gU[g + 1], ptd, ps);
-            hF[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptd, ps);
-        }
-    }
+    // subset sums h[X] = sum_{M subset X} g[M]; the polynomial at corner V
+    // (t_V = 0) is h[(NG-1) ^ V]
 #pragma unroll
     for (int q = 0; q < NS; ++q)
 #pragma unroll
@@ -1010,68 +1045,6 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
                 hU[g] += hU[g ^ (1 << q)];
                 hF[g] += hF[g ^ (1 << q)];
             }
-    constexpr bool need_lam = HI + NS >= 1;   // some corner needs its eps exponent
-    // factors of the regular variables: prod t^{a_j} and sum b_j ln t_j
-    double Cc = 1.0, Lc = 0.0;
-    bool hasCc = false, hasLc = false;
-#pragma unroll
-    for (int j = 0; j < DMAX; ++j) {
-        if (j < d && ((sec.regular_mask >> j) & 1)) {
-            const int a = sec.a[j];
-            if (a > 0) {
-                // t_j^a: the FP64 power table, or (mixed classes, whose table is FP32) products
-                const double p = MIXED ? ipow_signed<double>(t[j], 1.0, a) : ptd[(prow * j + a - 1) * ps];
-                Cc = hasCc ? Cc * p : p;
-                hasCc = true;
-            }
-            if (need_lam && sec.b[j] != 0.0) {
-                const double l = qlog_fx<DMAX>(t[j], tab);
-                Lc = hasLc ? fma(sec.b[j], l, Lc) : sec.b[j] * l;
-                hasLc = true;
-            }
-        }
-    }
-    // singular slots: t, ln t (needed when a pole set without q has a term of
-    // order >= 1 below HI), b
-    constexpr bool need_lt = HI + NS - 1 >= 1;
-    double it[NSA], lt[NSA], bq[NSA];
-#pragma unroll
-    for (int q = 0; q < NSA; ++q) {
-        it[q] = 1.0;
-        lt[q] = 0.0;
-        bq[q] = 0.0;
-        if (q < NS) {
-            double tq = 1.0, bb = 0.0;
-#pragma unroll
-            for (int j = 0; j < DMAX; ++j)
-                if (j == sec.sing[q]) {
-                    tq = t[j];
-                    bb = sec.b[j];
-                }
-            it[q] = tq;
-            bq[q] = bb;
-            if (need_lt) lt[q] = qlog_fx<DMAX>(tq, tab);
-        }
-    }
-    // t_q / b_q (the factors of the pole-set prefactors A_P), then 1/t_q in
-    // pairs: 1/a = b / (a b) with one reciprocal per pair, whose value is also
-    // the pair's share of A of the empty pole set prod 1/t_q
-    double tb[NSA];
-#pragma unroll
-    for (int q = 0; q < NSA; ++q) tb[q] = q < NS ? it[q] * S.invb[q] : 0.0;
-    double A_empty = 1.0;
-#pragma unroll
-    for (int q = 0; q + 1 < NS; q += 2) {
-        const double r = qrcp(it[q] * it[q + 1]);
-        const double t0 = it[q];
-        it[q] = it[q + 1] * r;
-        it[q + 1] = t0 * r;
-        A_empty = q == 0 ? r : A_empty * r;
-    }
-    if constexpr (NS & 1) {
-        it[NS - 1] = qrcp(it[NS - 1]);
-        A_empty = NS == 1 ? it[0] : A_empty * it[NS - 1];
-    }
     // corners: B_V = Cc U^u0 F^f0, Lambda_V = Lc + ln(U^u1 F^f1) (one log when
     // u1, f1 are small integers, else u1 ln U + f1 ln F)
     const int u0 = (int)sec.u0, f0 = (int)sec.f0, u1 = (int)sec.u1, f1 = (int)sec.f1;
@@ -1135,7 +1108,216 @@ __device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const doub
             LV[V] = hasLc ? Lc + l : l;
         }
     }
-    assemble_fixed<NS, HI, double>(BV, LV, tb, lt, bq, A_empty, S.invb_full, resN);
+    series_fp64<NS, HI>(BV, LV, gm);
+    moebius_fp64<NS, HI>(gm);
+}
+
+// One corner on the integer pipe: U, F at the corner (exact in 64-bit
+// mantissas), their reciprocals where a negative exponent needs them,
+// B = Cc U^u0 F^f0 and, where the corner needs its eps exponent,
+// Lambda = Lc + ln(U^u1 F^f1); B rounded once to FP64 (the corner series and
+// their Moebius transform stay in FP64 registers: in 64-bit-mantissa form
+// they took twice the registers and spilled, -15 % on the double box).
+// bad: a reciprocal of zero was needed.
+struct XfCorner {
+    double B;
+    double L;
+    int bad;
+};
+// the logarithm of a 64-bit mantissa: out of line in the d <= 6 kernel (its
+// instruction cache; see qlog_call)
+__device__ __noinline__ double qlog_xf_call(qmc_xf x, const uint64_t *tab) { return qmc_ilog_xf(x, tab); }
+template <int DMAX>
+__device__ __forceinline__ XfCorner corner_xf(double Ud, double Fd, double Cc, int u0, int f0, int u1, int f1,
+                                              bool lam, bool hasLc, double Lc, const uint64_t *tab) {
+    const qmc_xf U = qmc_xf_of(Ud), F = qmc_xf_of(Fd), Ccx = qmc_xf_of(Cc);
+    const bool needU = u0 < 0 || (lam && u1 < 0);
+    const bool needF = f0 < 0 || (lam && f1 < 0);
+    XfCorner r;
+    r.bad = (needU && U.m == 0) || (needF && F.m == 0);
+    const qmc_xf rU = needU ? qmc_xf_rcp(U) : U;
+    const qmc_xf rF = needF ? qmc_xf_rcp(F) : F;
+    r.B = qmc_xf_to_double(qmc_xf_mul(Ccx, qmc_xf_mul(qmc_xf_ipow(U, rU, u0), qmc_xf_ipow(F, rF, f0))));
+    r.L = 0.0;
+    if (lam) {
+        const qmc_xf X = qmc_xf_mul(qmc_xf_ipow(U, rU, u1), qmc_xf_ipow(F, rF, f1));
+        double l;
+        if constexpr (DMAX > 3 && QMC_CORNER_CALL == 0) l = qlog_xf_call(X, tab);
+        else l = qmc_ilog_xf(X, tab);
+        r.L = hasLc ? Lc + l : l;
+    }
+    return r;
+}
+// the whole corner out of line (one copy of its code, the logarithm inlined)
+__device__ __noinline__ XfCorner corner_xf_call(double Ud, double Fd, double Cc, int u0, int f0, int u1, int f1,
+                                                bool lam, bool hasLc, double Lc, const uint64_t *tab) {
+    return corner_xf<6>(Ud, Fd, Cc, u0, f0, u1, f1, lam, hasLc, Lc, tab);
+}
+
+// Subset sums h[X] = sum_{M subset X} g[M] of one polynomial's group sums on
+// the integer pipe (64-bit mantissas, each sum within 2^-62 of its larger
+// operand), rounded once to FP64 in place: the polynomial at corner V
+// (t_V = 0) is h[(NG-1) ^ V]
+template <int NS>
+__device__ __forceinline__ void subset_sums_xf(double (&h)[1 << NS]) {
+    constexpr int NG = 1 << NS;
+    qmc_xf x[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) x[g] = qmc_xf_of(h[g]);
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+            if (g & (1 << q)) x[g] = qmc_xf_add(x[g], x[g ^ (1 << q)]);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) h[g] = qmc_xf_to_double(x[g]);
+}
+
+// The corner stage on the integer pipe (qmc_xf.h): the subset sums of U and
+// F, each corner's B_V and Lambda_V, then the corner series and their Moebius
+// transform into gm. Returns true if some corner needed the reciprocal of a
+// zero polynomial value.
+template <int DMAX, int NS, int HI>
+__device__ __forceinline__ bool corners_xf(double (&hU)[1 << NS], double (&hF)[1 << NS], double Cc, bool hasCc,
+                                           double Lc, bool hasLc, int u0, int f0, int u1, int f1,
+                                           const uint64_t *tab, double (&gm)[1 << NS][HI + NS + 1]) {
+    constexpr int NG = 1 << NS;
+    subset_sums_xf<NS>(hU);
+    subset_sums_xf<NS>(hF);
+    const double Cc1 = hasCc ? Cc : 1.0;
+    double BV[NG], LV[NG];
+    int bad = 0;
+#pragma unroll
+    for (int V = 0; V < NG; ++V) {
+        XfCorner c;
+        if constexpr (DMAX > 3 && QMC_CORNER_CALL)
+            c = corner_xf_call(hU[(NG - 1) ^ V], hF[(NG - 1) ^ V], Cc1, u0, f0, u1, f1, HI + __popc(V) >= 1, hasLc,
+                               Lc, tab);
+        else
+            c = corner_xf<DMAX>(hU[(NG - 1) ^ V], hF[(NG - 1) ^ V], Cc1, u0, f0, u1, f1, HI + __popc(V) >= 1,
+                                hasLc, Lc, tab);
+        BV[V] = c.B;
+        LV[V] = c.L;
+        bad |= c.bad;
+    }
+    series_fp64<NS, HI>(BV, LV, gm);
+    moebius_fp64<NS, HI>(gm);
+    return bad != 0;
+}
+
+// ptd / ptf: this thread's column of the power table in shared memory (FP64
+// and, for the mixed classes, FP32 view of the same storage), row stride
+// `ps`, prow rows per variable
+template <int DMAX, int NS, int HI, bool MIXED, int LMAX>
+__device__ __forceinline__ void eval_real_fx(const TileSmem<LMAX> &S, const double (&t)[DMAX],
+                                             double (&resN)[NS + HI + 1], double *ptd, float *ptf, int ps,
+                                             int prow) {
+    constexpr int NG = 1 << NS;
+    constexpr int NSA = SlotArr<NS>::N;
+    const QmcSectorDev &sec = S.sec;
+    const int d = sec.d;
+    const uint64_t *tab = S.logtab;
+    // group sums by singular mask, then subset sums h[X] = sum_{M subset X} g[M];
+    // the polynomial at corner V (t_V = 0) is h[(NG-1) ^ V]
+    double hU[NG], hF[NG];
+    if constexpr (MIXED) {
+        float tf[DMAX];
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) tf[j] = __double2float_rn(t[j]);
+        powers_tab<DMAX, float>(tf, d, sec.pad0, prow, ptf, ps);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            hU[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.gU[g], sec.gU[g + 1], ptf, ps);
+            hF[g] = (double)poly_sum_tab<float>(S.mdesc, S.cvalf, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptf, ps);
+        }
+    } else {
+        powers_tab<DMAX, double>(t, d, sec.pad0, prow, ptd, ps);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            hU[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.gU[g], sec.gU[g + 1], ptd, ps);
+            hF[g] = poly_sum_tab<double>(S.mdesc, S.cval, sec.nU + sec.gF[g], sec.nU + sec.gF[g + 1], ptd, ps);
+        }
+    }
+    constexpr bool need_lam = HI + NS >= 1;   // some corner needs its eps exponent
+    // factors of the regular variables: prod t^{a_j} and sum b_j ln t_j
+    double Cc = 1.0, Lc = 0.0;
+    bool hasCc = false, hasLc = false;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d && ((sec.regular_mask >> j) & 1)) {
+            const int a = sec.a[j];
+            if (a > 0) {
+                // t_j^a: the FP64 power table, or (mixed classes, whose table is FP32) products
+                const double p = MIXED ? ipow_signed<double>(t[j], 1.0, a) : ptd[(prow * j + a - 1) * ps];
+                Cc = hasCc ? Cc * p : p;
+                hasCc = true;
+            }
+            if (need_lam && sec.b[j] != 0.0) {
+                const double l = qlog_fx<DMAX>(t[j], tab);
+                Lc = hasLc ? fma(sec.b[j], l, Lc) : sec.b[j] * l;
+                hasLc = true;
+            }
+        }
+    }
+    // singular slots: t, ln t (needed when a pole set without q has a term of
+    // order >= 1 below HI), b
+    constexpr bool need_lt = HI + NS - 1 >= 1;
+    double it[NSA], lt[NSA], bq[NSA];
+#pragma unroll
+    for (int q = 0; q < NSA; ++q) {
+        it[q] = 1.0;
+        lt[q] = 0.0;
+        bq[q] = 0.0;
+        if (q < NS) {
+            double tq = 1.0, bb = 0.0;
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j)
+                if (j == sec.sing[q]) {
+                    tq = t[j];
+                    bb = sec.b[j];
+                }
+            it[q] = tq;
+            bq[q] = bb;
+            if (need_lt) lt[q] = qlog_fx<DMAX>(tq, tab);
+        }
+    }
+    // t_q / b_q (the factors of the pole-set prefactors A_P), then 1/t_q in
+    // pairs: 1/a = b / (a b) with one reciprocal per pair, whose value is also
+    // the pair's share of A of the empty pole set prod 1/t_q
+    double tb[NSA];
+#pragma unroll
+    for (int q = 0; q < NSA; ++q) tb[q] = q < NS ? it[q] * S.invb[q] : 0.0;
+    double A_empty = 1.0;
+#pragma unroll
+    for (int q = 0; q + 1 < NS; q += 2) {
+        const double r = qrcp(it[q] * it[q + 1]);
+        const double t0 = it[q];
+        it[q] = it[q + 1] * r;
+        it[q + 1] = t0 * r;
+        A_empty = q == 0 ? r : A_empty * r;
+    }
+    if constexpr (NS & 1) {
+        it[NS - 1] = qrcp(it[NS - 1]);
+        A_empty = NS == 1 ? it[0] : A_empty * it[NS - 1];
+    }
+    // corners: B_V = Cc U^u0 F^f0 and Lambda_V = Lc + ln(U^u1 F^f1) on the
+    // integer pipe where every exponent is a small integer (the corner values
+    // of U and F as 64-bit-mantissa subset sums), else in FP64; then the
+    // corner series and their Moebius transform, and the pole sets
+    double gm[NG][HI + NS + 1];
+    constexpr bool xf_corners = (QMC_XF_CORNERS & (DMAX > 3 ? 1 : 2)) != 0;
+    if (xf_corners && sec.u0_int && sec.f0_int && (sec.pad1 & 1)) {
+        const bool bad = corners_xf<DMAX, NS, HI>(hU, hF, Cc, hasCc, Lc, hasLc, (int)sec.u0, (int)sec.f0, sec.u1i,
+                                                  sec.f1i, tab, gm);
+        pole_sets_fixed<NS, HI>(gm, tb, lt, bq, A_empty, S.invb_full, resN);
+        if (bad) {
+#pragma unroll
+            for (int i = 0; i < NS + HI + 1; ++i) resN[i] = __longlong_as_double(0x7FF8000000000000LL);
+        }
+    } else {
+        corners_fp64<DMAX, NS, HI>(sec, hU, hF, Cc, hasCc, Lc, hasLc, tab, gm);
+        pole_sets_fixed<NS, HI>(gm, tb, lt, bq, A_empty, S.invb_full, resN);
+    }
 }
 
 // ---------------------------------------------------------------- Taylor subtraction

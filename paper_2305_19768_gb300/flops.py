@@ -6,8 +6,11 @@ formulation of the method, operation by operation:
 
 * FP64 flops: add, subtract and multiply count 1, a fused multiply-add 2.
   Steps that the evaluator computes on the integer pipe count 0 FP64 flops:
-  the lattice coordinate (exact fixed-point walk), the korobov3 transform
-  and every logarithm (fixed-point table reduction).
+  the lattice coordinate (exact fixed-point walk), the korobov3 transform,
+  every logarithm (fixed-point table reduction) and, in the d <= 6
+  fixed-order kernel for sectors whose exponents are small integers, the
+  corner stage (subset sums of U and F, their reciprocals and powers at the
+  corners, in 64-bit-mantissa arithmetic).
   Multiplications by the constant 1 that the compiler folds away (first
   factors of products started at 1, the 1/1 of series recursions) are not
   counted.
@@ -17,7 +20,8 @@ formulation of the method, operation by operation:
   (integer pipe), arctangents (table plus a series on the FP64 pipe; its
   FP64 operations are in the flop count), hardware reciprocal seeds
   (rcp.approx, followed by two Newton steps = 4 FMA counted as flops),
-  exponentials and sine/cosine pairs (library).
+  exponentials and sine/cosine pairs (library); the integer-pipe
+  reciprocals of the corner stage apart again (rcp_int).
 * Only terms the requested orders need are counted: corner V carries its eps
   exponent only if hi + |V| >= 1, the ln t of a singular variable only if
   hi + ns - 1 >= 1, pole set P forms its series terms below hi + |P| + 1.
@@ -40,6 +44,7 @@ class Work:
     rcp: float = 0.0
     exp: float = 0.0
     sincos: float = 0.0
+    rcp_int: float = 0.0
 
     def add(self, other: "Work", scale: float = 1.0) -> "Work":
         for k in self.__dataclass_fields__:
@@ -100,9 +105,9 @@ def _powers(d, emax):
 def _assemble_fixed(ns, hi) -> float:
     """The real classes' assembly with the singular-variable count and the
     highest order fixed at compile time: corner series, superset Moebius
-    transform, A_P and E_P by subset recursions, the exponential series of
-    E_P, the convolution, and every order from the leading pole eps^-ns up to
-    eps^hi into the accumulator."""
+    transform, A_P and E_P by subset recursions, the pole sets' exponential
+    series by Horner's rule (E/l, l >= 2, then one FMA per term), and every
+    order from the leading pole eps^-ns up to eps^hi into the accumulator."""
     f = 0.0
     full = (1 << ns) - 1
     for V in range(full + 1):
@@ -123,8 +128,8 @@ def _assemble_fixed(ns, hi) -> float:
         np_ = _popc(P)
         nP = hi + np_ + 1
         if P != full:
-            f += 2 * max(nP - 2, 0)              # e_l = e_{l-1} (E / l), l >= 2
-            f += sum(2 * k for k in range(nP))   # PE_k = g_k + sum_{i<k} g_i e_{k-i}
+            f += max(nP - 2, 0)                  # E / l, l >= 2
+            f += sum(2 * k for k in range(nP))   # PE_k by Horner: k FMAs
         f += 2 * nP                              # res[k - |P|] += A_P PE_k
     f += 2 * (ns + hi + 1)                       # acc += res W, every order -ns .. hi
     return f
@@ -166,42 +171,9 @@ def _assemble(ns, lo, hi, nord, cplx: bool) -> float:
     return f
 
 
-def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
-    """Work of one evaluation in the real (undeformed) evaluator classes."""
-    d, sing, ns, emax = _sector_shape(sector)
-    hi = lo + norders - 1
-    w = Work()
-    # transform on the integer pipe: only the product of the per-coordinate
-    # weights u(1-u) is FP64
-    w.fp64 += d - 1
-    w.fp64 += 2                          # W = Ws^3
-    # power tables and grouped monomial sums (FP32 in the mixed classes)
-    pw = _powers(d, emax)
-    polys = _grouped_poly(sector.U, sing, ns) + _grouped_poly(sector.F, sing, ns)
-    if mixed:
-        w.fp32 += pw + polys
-        # the regular prefactor's powers t^a as FP64 products (the table is FP32)
-        w.fp64 += sum(max(int(sector.a[j]) - 1, 0) for j in range(d) if sector.a[j] > 0)
-    else:
-        w.fp64 += pw + polys
-    w.fp64 += 2 * ns * (1 << max(ns - 1, 0))   # subset sums of U and F
-    need_lam = hi + ns >= 1
-    nb_reg = sum(1 for j in range(d) if sector.a[j] > -1 and float(sector.b[j]) != 0.0)
-    na_reg = sum(1 for j in range(d) if sector.a[j] > 0)
-    if need_lam:
-        w.log += nb_reg
-        w.fp64 += 2 * nb_reg             # Lc += b_j ln t_j
-    w.fp64 += max(na_reg - 1, 0)         # Cc = prod t^a
-    if hi + ns - 1 >= 1:
-        w.log += ns                      # ln t of the singular variables
-    # A of the empty pole set, prod 1/t_q: one reciprocal per pair of singular
-    # variables (of the pair's product) and one for an odd one left
-    pairs, odd = ns // 2, ns % 2
-    w.fp64 += pairs + max(pairs + odd - 1, 0)
-    w.recip(pairs + odd)
-    u0, f0, u1, f1 = (float(x) for x in (sector.u0, sector.f0, sector.u1, sector.f1))
-    u0i, f0i = _is_small_int(u0), _is_small_int(f0)
-    comb = _is_small_int(u1) and _is_small_int(f1)
+def _corners_fp64(w, ns, hi, u0, f0, u1, f1, u0i, f0i, comb, na_reg):
+    """The corner stage in FP64: 1/F in pairs of corners, then per corner
+    B = Cc U^u0 F^f0 and Lambda = Lc + ln(U^u1 F^f1)."""
     full = (1 << ns) - 1
     # 1/F at the corners that need it, in pairs
     needF = [V <= full and ((f0i and f0 < 0) or (hi + _popc(V) >= 1 and comb and f1 < 0))
@@ -237,6 +209,62 @@ def real_sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work
                 w.log += 2
                 w.fp64 += 3
             w.fp64 += 1                  # Lambda_V = Lc + log
+
+
+def real_sector_work(sector, lo: int, norders: int, mixed: bool = False, fp64_corners: bool = False) -> Work:
+    """Work of one evaluation in the real (undeformed) evaluator classes.
+    fp64_corners: count the corner stage as FP64 work even where the kernel
+    runs it on the integer pipe (the FP64-equivalent arithmetic of the
+    formulation)."""
+    d, sing, ns, emax = _sector_shape(sector)
+    hi = lo + norders - 1
+    w = Work()
+    # transform on the integer pipe: only the product of the per-coordinate
+    # weights u(1-u) is FP64
+    w.fp64 += d - 1
+    w.fp64 += 2                          # W = Ws^3
+    # power tables and grouped monomial sums (FP32 in the mixed classes)
+    pw = _powers(d, emax)
+    polys = _grouped_poly(sector.U, sing, ns) + _grouped_poly(sector.F, sing, ns)
+    if mixed:
+        w.fp32 += pw + polys
+        # the regular prefactor's powers t^a as FP64 products (the table is FP32)
+        w.fp64 += sum(max(int(sector.a[j]) - 1, 0) for j in range(d) if sector.a[j] > 0)
+    else:
+        w.fp64 += pw + polys
+    u0, f0, u1, f1 = (float(x) for x in (sector.u0, sector.f0, sector.u1, sector.f1))
+    u0i, f0i = _is_small_int(u0), _is_small_int(f0)
+    comb = _is_small_int(u1) and _is_small_int(f1)
+    # the d <= 6 fixed-order kernel's integer-pipe corner stage (subset sums,
+    # the reciprocals and powers of U and F at the corners); the d <= 3 kernel
+    # keeps the FP64 corners
+    xf = hi == 0 and u0i and f0i and comb and (d > 3 or ns > 2) and not fp64_corners
+    if not xf:
+        w.fp64 += 2 * ns * (1 << max(ns - 1, 0))   # subset sums of U and F
+    need_lam = hi + ns >= 1
+    nb_reg = sum(1 for j in range(d) if sector.a[j] > -1 and float(sector.b[j]) != 0.0)
+    na_reg = sum(1 for j in range(d) if sector.a[j] > 0)
+    if need_lam:
+        w.log += nb_reg
+        w.fp64 += 2 * nb_reg             # Lc += b_j ln t_j
+    w.fp64 += max(na_reg - 1, 0)         # Cc = prod t^a
+    if hi + ns - 1 >= 1:
+        w.log += ns                      # ln t of the singular variables
+    # A of the empty pole set, prod 1/t_q: one reciprocal per pair of singular
+    # variables (of the pair's product) and one for an odd one left
+    pairs, odd = ns // 2, ns % 2
+    w.fp64 += pairs + max(pairs + odd - 1, 0)
+    w.recip(pairs + odd)
+    full = (1 << ns) - 1
+    if xf:
+        for V in range(full + 1):
+            lam_here = hi + _popc(V) >= 1
+            w.rcp_int += int(u0 < 0 or (lam_here and u1 < 0)) + int(f0 < 0 or (lam_here and f1 < 0))
+            if lam_here:
+                w.log += 1
+                w.fp64 += 1 if nb_reg else 0     # Lambda_V = Lc + log
+    else:
+        _corners_fp64(w, ns, hi, u0, f0, u1, f1, u0i, f0i, comb, na_reg)
     if hi == 0:
         w.fp64 += _assemble_fixed(ns, hi)
     else:
@@ -533,21 +561,21 @@ def deformed_taylor_sector_work(sector, lo: int, norders: int) -> Work:
     return w
 
 
-def sector_work(sector, lo: int, norders: int, mixed: bool = False) -> Work:
+def sector_work(sector, lo: int, norders: int, mixed: bool = False, fp64_corners: bool = False) -> Work:
     if getattr(sector, "deform", False):
         if any(int(a) <= -2 for a in sector.a):
             return deformed_taylor_sector_work(sector, lo, norders)
         return deformed_sector_work(sector, lo, norders, mixed)
     if any(int(a) <= -2 for a in sector.a):
         return taylor_sector_work(sector, lo, norders)
-    return real_sector_work(sector, lo, norders, mixed)
+    return real_sector_work(sector, lo, norders, mixed, fp64_corners)
 
 
-def workload_work(integral, lo: int, norders: int, mixed: bool = False) -> Work:
+def workload_work(integral, lo: int, norders: int, mixed: bool = False, fp64_corners: bool = False) -> Work:
     """Mean work per evaluation over the integral's sectors (equal lattices)."""
     tot = Work()
     for s in integral.sectors:
-        tot.add(sector_work(s, lo, norders, mixed))
+        tot.add(sector_work(s, lo, norders, mixed, fp64_corners))
     n = max(1, len(integral.sectors))
     return Work(**{k: v / n for k, v in tot.as_dict().items()})
 
